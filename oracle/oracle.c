@@ -1,0 +1,503 @@
+/*
+ * Oracle for nested multilevel Monte Carlo with low-precision approximate
+ * random variables (Giles & Sheridan-Methven, "Rounding error using low
+ * precision approximate random variables").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, obviously correct CPU
+ * restatement of the method in FP64.  Only the test-suite, the smoke check and
+ * the CPU-baseline leg of the benchmark may build, load or call it.  It shares
+ * no code with the CUDA library and includes none of its headers.
+ *
+ * Contents, each following the paper (or, where the paper is silent, the
+ * reading stated beside it):
+ *   - Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,
+ *     SC'11; the paper names no generator).
+ *   - 24-bit uniform map u = (2*(w>>9)+1) * 2^-24 (reading: the paper only
+ *     says U_n is uniform, Sec. 3).
+ *   - Exact inverse Gaussian CDF in FP64 (Sec. 2.1, inverse transform
+ *     sampling; Sec. 3 Z_n = Phi^-1(U_n)).
+ *   - Piecewise-linear approximate inverse CDF on 16 dyadic intervals,
+ *     mirrored (Sec. 2.1, Fig. 1).  The coefficients are an input (built by
+ *     oracle/table.py).
+ *   - Rounding of every operation to binary16 / binary32 / p-bit mantissa
+ *     with round-to-nearest-even (Sec. 2.2 assumes RNE; Sec. 2.2 Fig. 2
+ *     varies the mantissa width).
+ *   - Euler-Maruyama with the finite-precision operation order
+ *     X <- X (+) (A (+) B), A = a (x) delta, B = (b (x) sqrt(delta)) (x) Z
+ *     (Sec. 2.2), optionally with Kahan compensated summation (Sec. 2.3,
+ *     Algorithm 1).
+ *   - Fine/coarse coupling: delta_f = 2^-l T, coarse increments are the
+ *     pairwise sums of the fine ones; exact and approximate normals share
+ *     the same U_n (Sec. 3).
+ *   - Two-way P_l - P_{l-1} and four-way P^_l - P^_{l-1} - P-_l + P-_{l-1}
+ *     differences and their sums (Sec. 3, estimators theta^ and theta-).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al. 2011): 10 rounds of two 32x32->64      */
+/* multiplications with a Weyl-sequence key schedule.                  */
+/* ------------------------------------------------------------------ */
+static void philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {           /* key schedule: add the Weyl constants */
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t prod_a = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t prod_b = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(prod_b >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)prod_b;
+        uint32_t y2 = (uint32_t)(prod_a >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)prod_a;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i)
+        philox(ctr + 4 * i, key + 2 * i, out + 4 * i);
+}
+
+/* u = (2*(w >> 9) + 1) * 2^-24: 2^23 equiprobable values, symmetric about
+ * 1/2, never 0 or 1, exact in binary32 and binary64. */
+static double uniform_of(uint32_t w)
+{
+    return ldexp(2.0 * (double)(w >> 9) + 1.0, -24);
+}
+
+void orc_u32_to_uniform(const uint32_t *w, double *u, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) u[i] = uniform_of(w[i]);
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact inverse Gaussian CDF in FP64.                                 */
+/* Initial guess: Abramowitz & Stegun 26.2.23 (|error| < 4.5e-4), then */
+/* Halley iterations on F(x) = Phi(x) - p.  Near the centre the        */
+/* residual is formed with erf (accurate for small x), in the tail     */
+/* with erfc.                                                          */
+/* ------------------------------------------------------------------ */
+static double ndtri_lower(double p)     /* p in (0, 1/2] */
+{
+    if (p == 0.5) return 0.0;
+    double t = sqrt(-2.0 * log(p));
+    double x = -(t - (2.515517 + 0.802853 * t + 0.010328 * t * t) /
+                     (1.0 + 1.432788 * t + 0.189269 * t * t + 0.001308 * t * t * t));
+    const double inv_sqrt2 = 0.70710678118654752440;
+    const double inv_sqrt2pi = 0.39894228040143267794;
+    for (int it = 0; it < 10; ++it) {
+        double r;                       /* r = Phi(x) - p */
+        if (p >= 0.25) r = 0.5 * erf(x * inv_sqrt2) - (p - 0.5);
+        else r = 0.5 * erfc(-x * inv_sqrt2) - p;
+        double dens = inv_sqrt2pi * exp(-0.5 * x * x);
+        double e = r / dens;
+        double dx = e / (1.0 + 0.5 * x * e);
+        x -= dx;
+        if (fabs(dx) <= 1e-17 * fabs(x)) break;
+    }
+    return x;
+}
+
+double orc_ndtri1(double p)
+{
+    if (!(p > 0.0 && p < 1.0)) {
+        if (p == 0.0) return -INFINITY;
+        if (p == 1.0) return INFINITY;
+        return NAN;
+    }
+    if (p > 0.5) return -ndtri_lower(1.0 - p);
+    return ndtri_lower(p);
+}
+
+void orc_ndtri(const double *p, double *x, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) x[i] = orc_ndtri1(p[i]);
+}
+
+/* ------------------------------------------------------------------ */
+/* Rounding to a p-bit significand with minimum normal exponent emin   */
+/* (gradual underflow) and overflow to infinity above maxv, round to   */
+/* nearest even.  binary16: p=11, emin=-14, maxv=65504.  binary32:      */
+/* p=24, emin=-126.  Applied to the exact-or-FP64 result of each +,-,x. */
+/* For these operations FP64 has 53 >= 2p+2 bits, so computing in FP64 */
+/* and then rounding equals a single correct rounding.                 */
+/* ------------------------------------------------------------------ */
+typedef struct { int p; int emin; double maxv; int active; } rmode;
+
+static double round_p(double x, const rmode *m)
+{
+    if (!m->active || x == 0.0 || !isfinite(x)) return x;
+    int e;
+    frexp(x, &e);                       /* |x| in [2^(e-1), 2^e) */
+    int q = e - m->p;                   /* exponent of one unit in the last place */
+    if (e - 1 < m->emin) q = m->emin - m->p + 1;
+    double r = ldexp(nearbyint(ldexp(x, -q)), q);
+    if (fabs(r) > m->maxv) r = copysign(INFINITY, x);
+    return r;
+}
+
+void orc_round_bits(const double *x, double *y, int64_t n, int p, int emin, double maxv)
+{
+    rmode m = {p, emin, maxv, 1};
+    for (int64_t i = 0; i < n; ++i) y[i] = round_p(x[i], &m);
+}
+
+/* precision codes shared with oracle/__init__.py */
+enum { ORC_F64 = 0, ORC_F32 = 1, ORC_F16 = 2, ORC_BF16 = 3, ORC_PBITS = 4 };
+
+static rmode mode_of(int prec, int pbits)
+{
+    rmode m = {53, -1022, 1.0e308, 0};
+    switch (prec) {
+    case ORC_F32: m.p = 24; m.emin = -126; m.maxv = 3.4028234663852886e38; m.active = 1; break;
+    case ORC_F16: m.p = 11; m.emin = -14; m.maxv = 65504.0; m.active = 1; break;
+    case ORC_BF16: m.p = 8; m.emin = -126; m.maxv = 3.3895313892515355e38; m.active = 1; break;
+    case ORC_PBITS: m.p = pbits; m.emin = -1022; m.maxv = 1.0e308; m.active = 1; break;
+    default: break;
+    }
+    return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* Approximate inverse CDF.                                            */
+/* Piecewise linear (Sec. 2.1): on v = min(u, 1-u) in (0, 1/2], interval */
+/* k = 1..15 is [2^-(k+1), 2^-k), interval 16 is (0, 2^-16); g(v) =     */
+/* c0 + c1 v on each; Phi~^-1(u) = g(v) for u <= 1/2 and -g(v) above.   */
+/* table[2i], table[2i+1] = c0, c1 of interval i+1.  Evaluation in      */
+/* working precision: z = R(R(c0) + R(R(c1) * R(v))).                   */
+/* ------------------------------------------------------------------ */
+static int interval_of(double v)
+{
+    int e;
+    frexp(v, &e);                       /* v in [2^(e-1), 2^e) */
+    int k = -e;                         /* v in [2^-(k+1), 2^-k) */
+    if (k > 16) k = 16;
+    if (k < 1) k = 1;                   /* v = 1/2 joins the first interval */
+    return k - 1;
+}
+
+static double table_icdf(double u, const double *table, const rmode *m)
+{
+    int upper = u > 0.5;
+    double v = upper ? 1.0 - u : u;
+    int i = interval_of(v);
+    double c0 = round_p(table[2 * i], m);
+    double c1 = round_p(table[2 * i + 1], m);
+    double z = round_p(c0 + round_p(c1 * round_p(v, m), m), m);
+    return upper ? -z : z;
+}
+
+/* MLP surrogate: t = sqrt(-2 ln v), y = W3 tanh(W2 tanh(W1 t + b1) + b2)
+ * + b3 approximates |Phi^-1(v)|; Phi~^-1(u) = -y for u <= 1/2, +y above.
+ * Weight layout (1153 values): W1[32], b1[32], W2[32][32] (row = output
+ * unit), b2[32], W3[32], b3. */
+#define MLP_H 32
+static double mlp_forward(double t, const double *w)
+{
+    const double *W1 = w, *b1 = w + 32, *W2 = w + 64, *b2 = w + 64 + 1024;
+    const double *W3 = w + 64 + 1024 + 32, *b3 = w + 64 + 1024 + 64;
+    double h1[MLP_H], y = b3[0];
+    for (int j = 0; j < MLP_H; ++j) h1[j] = tanh(W1[j] * t + b1[j]);
+    for (int o = 0; o < MLP_H; ++o) {
+        double a = b2[o];
+        for (int j = 0; j < MLP_H; ++j) a += W2[o * MLP_H + j] * h1[j];
+        y += W3[o] * tanh(a);
+    }
+    return y;
+}
+
+static double mlp_icdf(double u, const double *w)
+{
+    int upper = u > 0.5;
+    double v = upper ? 1.0 - u : u;
+    double y = mlp_forward(sqrt(-2.0 * log(v)), w);
+    return upper ? y : -y;
+}
+
+enum { ORC_RV_EXACT = 0, ORC_RV_TABLE = 1, ORC_RV_MLP = 2 };
+
+static double rv_of(double u, int rv, const double *table, const double *mlp, const rmode *m)
+{
+    switch (rv) {
+    case ORC_RV_TABLE: return table_icdf(u, table, m);
+    case ORC_RV_MLP: return round_p(mlp_icdf(u, mlp), m);
+    default: return round_p(orc_ndtri1(u), m);
+    }
+}
+
+void orc_approx_icdf(const double *u, double *z, int64_t n, int rv, int prec, int pbits,
+                     const double *table, const double *mlp)
+{
+    rmode m = mode_of(prec, pbits);
+    for (int64_t i = 0; i < n; ++i) z[i] = rv_of(u[i], rv, table, mlp, &m);
+}
+
+/* ------------------------------------------------------------------ */
+/* SDEs and Euler-Maruyama in working precision.                       */
+/* ------------------------------------------------------------------ */
+enum { ORC_GBM = 0, ORC_OU = 1 };
+enum { ORC_PAYOFF_X = 0, ORC_PAYOFF_CALL = 1 };
+
+typedef struct {
+    int sde, payoff;
+    double p0, p1, p2;      /* GBM: mu, sigma, -;  OU: theta, m, s */
+    double x0, T, K, disc;  /* call payoff: disc * max(X_T - K, 0) */
+} orc_sde;
+
+/* Per-level constants of one path, each rounded once to the working
+ * precision.  GBM: a(X) delta = (mu delta) X, b(X) sqrt(delta) = (sigma
+ * sqrt(delta)) X.  OU: a(X) delta = (theta delta)(m - X), b sqrt(delta) =
+ * s sqrt(delta). */
+typedef struct {
+    rmode m;
+    int kahan, sde;
+    double drift, diff, mean;   /* drift: mu*delta or theta*delta; diff: sigma*sqrt(delta_f) or s*sqrt(delta_f) */
+    double X, c;                /* state and Kahan compensation */
+} path_state;
+
+static void path_init(path_state *s, const orc_sde *p, int prec, int pbits, int kahan, double delta, double sqrt_delta_f)
+{
+    s->m = mode_of(prec, pbits);
+    s->kahan = kahan;
+    s->sde = p->sde;
+    s->drift = round_p(p->p0 * delta, &s->m);
+    s->diff = round_p(p->p1 * sqrt_delta_f, &s->m);
+    s->mean = 0.0;
+    if (p->sde == ORC_OU) {
+        s->diff = round_p(p->p2 * sqrt_delta_f, &s->m);
+        s->mean = round_p(p->p1, &s->m);
+    }
+    s->X = round_p(p->x0, &s->m);
+    s->c = 0.0;
+}
+
+/* One step X <- X (+) (A (+) B) (Sec. 2.2), with Kahan (Algorithm 1) if on.
+ * dW is the normal increment multiplier: Z for a fine step, Z1 (+) Z2 for
+ * a coarse step (the coarse Wiener increment is the pairwise sum of the
+ * two fine ones, Sec. 3). */
+static void path_step(path_state *s, double z)
+{
+    const rmode *m = &s->m;
+    double A, B;
+    if (s->sde == ORC_GBM) {
+        A = round_p(s->drift * s->X, m);
+        B = round_p(round_p(s->diff * s->X, m) * z, m);
+    } else {
+        A = round_p(s->drift * round_p(s->mean - s->X, m), m);
+        B = round_p(s->diff * z, m);
+    }
+    double inc = round_p(A + B, m);
+    if (s->kahan) {
+        double y = round_p(inc - s->c, m);
+        double t = round_p(s->X + y, m);
+        s->c = round_p(round_p(t - s->X, m) - y, m);
+        s->X = t;
+    } else {
+        s->X = round_p(s->X + inc, m);
+    }
+}
+
+/* Payoff in FP64 for an FP64 path, in binary32 otherwise. */
+static double payoff_of(double X, const orc_sde *p, int prec)
+{
+    if (p->payoff == ORC_PAYOFF_X) return X;
+    if (prec == ORC_F64) {
+        double t = X - p->K;
+        return p->disc * (t > 0.0 ? t : 0.0);
+    }
+    rmode f = mode_of(ORC_F32, 0);
+    double t = round_p(X - round_p(p->K, &f), &f);
+    if (!(t > 0.0)) t = 0.0;
+    return round_p(round_p(p->disc, &f) * t, &f);
+}
+
+/* Random-number counter layout.  ctr = (path lo32, path hi32, j, tag),
+ * key = (seed lo32, seed hi32); fine step n of a path uses word n mod 4 of
+ * call j = n / 4.  tag = kind | level << 8 | set << 16 with kind 0: standard
+ * two-way with exact normals, 1: two-way with approximate normals, 2:
+ * four-way.  (Reading: the paper is silent on the generator.) */
+static void draw4(uint64_t path, uint32_t j, uint32_t tag, uint64_t seed, double u[4])
+{
+    uint32_t ctr[4] = {(uint32_t)path, (uint32_t)(path >> 32), j, tag};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    philox(ctr, key, w);
+    for (int i = 0; i < 4; ++i) u[i] = uniform_of(w[i]);
+}
+
+typedef struct { int prec, pbits, kahan, rv; } orc_variant;
+
+/* Two-way sample of level l: out = (P_fine, P_coarse, D); P_coarse = 0 at l = 0. */
+static void twoway_one(int l, uint64_t path, const orc_variant *v, const orc_sde *p, uint64_t seed,
+                       uint32_t tag, const double *table, const double *mlp, double out[3])
+{
+    int64_t nf = (int64_t)1 << l;
+    double delta_f = ldexp(p->T, -l);
+    double sq = sqrt(delta_f);
+    path_state fine, coarse;
+    path_init(&fine, p, v->prec, v->pbits, v->kahan, delta_f, sq);
+    path_init(&coarse, p, v->prec, v->pbits, v->kahan, 2.0 * delta_f, sq);
+    double zprev = 0.0, u[4];
+    for (int64_t n = 0; n < nf; ++n) {
+        if ((n & 3) == 0) draw4(path, (uint32_t)(n >> 2), tag, seed, u);
+        double z = rv_of(u[n & 3], v->rv, table, mlp, &fine.m);
+        path_step(&fine, z);
+        if (l > 0 && (n & 1)) path_step(&coarse, round_p(zprev + z, &coarse.m));
+        zprev = z;
+    }
+    double pf = payoff_of(fine.X, p, v->prec);
+    double pc = l > 0 ? payoff_of(coarse.X, p, v->prec) : 0.0;
+    double d;
+    if (l == 0) d = pf;
+    else if (v->prec == ORC_F64) d = pf - pc;
+    else { rmode f = mode_of(ORC_F32, 0); d = round_p(pf - pc, &f); }
+    out[0] = pf; out[1] = pc; out[2] = d;
+}
+
+/* Four-way sample: out = (P^_f, P^_c, P-_f, P-_c, D) with
+ * D = (P^_f - P^_c) - (P-_f - P-_c); all four paths share U_n (Sec. 3). */
+static void fourway_one(int l, uint64_t path, const orc_variant *hat, const orc_variant *bar, const orc_sde *p,
+                        uint64_t seed, uint32_t tag, const double *table, const double *mlp, double out[5])
+{
+    int64_t nf = (int64_t)1 << l;
+    double delta_f = ldexp(p->T, -l);
+    double sq = sqrt(delta_f);
+    path_state hf, hc, bf, bc;
+    path_init(&hf, p, hat->prec, hat->pbits, hat->kahan, delta_f, sq);
+    path_init(&hc, p, hat->prec, hat->pbits, hat->kahan, 2.0 * delta_f, sq);
+    path_init(&bf, p, bar->prec, bar->pbits, bar->kahan, delta_f, sq);
+    path_init(&bc, p, bar->prec, bar->pbits, bar->kahan, 2.0 * delta_f, sq);
+    double zh_prev = 0.0, zb_prev = 0.0, u[4];
+    for (int64_t n = 0; n < nf; ++n) {
+        if ((n & 3) == 0) draw4(path, (uint32_t)(n >> 2), tag, seed, u);
+        double zh = rv_of(u[n & 3], hat->rv, table, mlp, &hf.m);
+        double zb = rv_of(u[n & 3], bar->rv, table, mlp, &bf.m);
+        path_step(&hf, zh);
+        path_step(&bf, zb);
+        if (l > 0 && (n & 1)) {
+            path_step(&hc, round_p(zh_prev + zh, &hc.m));
+            path_step(&bc, round_p(zb_prev + zb, &bc.m));
+        }
+        zh_prev = zh; zb_prev = zb;
+    }
+    double phf = payoff_of(hf.X, p, hat->prec);
+    double phc = l > 0 ? payoff_of(hc.X, p, hat->prec) : 0.0;
+    double pbf = payoff_of(bf.X, p, bar->prec);
+    double pbc = l > 0 ? payoff_of(bc.X, p, bar->prec) : 0.0;
+    double d;
+    if (hat->prec == ORC_F64 || bar->prec == ORC_F64) {
+        d = (phf - phc) - (pbf - pbc);
+    } else {
+        rmode f = mode_of(ORC_F32, 0);
+        d = round_p(round_p(phf - phc, &f) - round_p(pbf - pbc, &f), &f);
+    }
+    out[0] = phf; out[1] = phc; out[2] = pbf; out[3] = pbc; out[4] = d;
+}
+
+static orc_variant variant_of(const int *v) { orc_variant r = {v[0], v[1], v[2], v[3]}; return r; }
+
+/* Per-path outputs for an explicit list of path indices (sampled parity). */
+void orc_twoway_paths(int l, const uint64_t *idx, int64_t n, const int *var, const orc_sde *p, uint64_t seed,
+                      uint32_t tag, const double *table, const double *mlp, double *out)
+{
+    orc_variant v = variant_of(var);
+    for (int64_t i = 0; i < n; ++i) twoway_one(l, idx[i], &v, p, seed, tag, table, mlp, out + 3 * i);
+}
+
+void orc_fourway_paths(int l, const uint64_t *idx, int64_t n, const int *hat, const int *bar, const orc_sde *p,
+                       uint64_t seed, uint32_t tag, const double *table, const double *mlp, double *out)
+{
+    orc_variant h = variant_of(hat), b = variant_of(bar);
+    for (int64_t i = 0; i < n; ++i) fourway_one(l, idx[i], &h, &b, p, seed, tag, table, mlp, out + 5 * i);
+}
+
+/* Level sums over paths path_offset .. path_offset + N - 1:
+ * sums = (sum D, sum D^2).  four = 0: two-way with variant var; four = 1:
+ * four-way with hat var and bar var2.  nthreads > 1 splits the paths
+ * across OpenMP threads. */
+void orc_level_sums(int l, uint64_t N, uint64_t path_offset, int four, const int *var, const int *var2,
+                    const orc_sde *p, uint64_t seed, uint32_t tag, const double *table, const double *mlp,
+                    int nthreads, double *sums)
+{
+    orc_variant v = variant_of(var), v2 = variant_of(four ? var2 : var);
+    double s1 = 0.0, s2 = 0.0;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for reduction(+ : s1, s2) num_threads(nthreads) schedule(static)
+#endif
+    for (int64_t i = 0; i < (int64_t)N; ++i) {
+        double out[5];
+        double d;
+        if (four) { fourway_one(l, path_offset + (uint64_t)i, &v, &v2, p, seed, tag, table, mlp, out); d = out[4]; }
+        else { twoway_one(l, path_offset + (uint64_t)i, &v, p, seed, tag, table, mlp, out); d = out[2]; }
+        s1 += d;
+        s2 += d * d;
+    }
+    sums[0] = s1;
+    sums[1] = s2;
+    (void)nthreads;
+}
+
+/* Terminal values of the exact (FP64, exact normals) and low-precision
+ * paths driven by the same normals Z~ (the same approximate variable in
+ * both), for the rounding-error experiments of Sec. 2.2-2.3 (Fig. 2):
+ * out[2i] = X in FP64, out[2i+1] = X in the working precision. */
+void orc_rounding_pairs(int l, uint64_t N, uint64_t path_offset, const int *var, const orc_sde *p, uint64_t seed,
+                        uint32_t tag, const double *table, const double *mlp, double *out)
+{
+    orc_variant v = variant_of(var);
+    int64_t nf = (int64_t)1 << l;
+    double delta_f = ldexp(p->T, -l);
+    double sq = sqrt(delta_f);
+    for (int64_t i = 0; i < (int64_t)N; ++i) {
+        path_state hi, lo;
+        path_init(&hi, p, ORC_F64, 53, 0, delta_f, sq);
+        path_init(&lo, p, v.prec, v.pbits, v.kahan, delta_f, sq);
+        double u[4];
+        rmode exact = mode_of(ORC_F64, 0);
+        for (int64_t n = 0; n < nf; ++n) {
+            if ((n & 3) == 0) draw4(path_offset + (uint64_t)i, (uint32_t)(n >> 2), tag, seed, u);
+            double z64 = rv_of(u[n & 3], v.rv, table, mlp, &exact);
+            path_step(&hi, z64);
+            path_step(&lo, round_p(z64, &lo.m));
+        }
+        out[2 * i] = hi.X;
+        out[2 * i + 1] = lo.X;
+    }
+}
+
+/* Kahan compensated summation of a sequence in working precision
+ * (Algorithm 1).  Returns the accumulator a. */
+double orc_kahan_sum(const double *x, int64_t n, int prec, int pbits)
+{
+    rmode m = mode_of(prec, pbits);
+    double a = 0.0, c = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double y = round_p(round_p(x[i], &m) - c, &m);
+        double t = round_p(a + y, &m);
+        c = round_p(round_p(t - a, &m) - y, &m);
+        a = t;
+    }
+    return a;
+}
+
+int orc_openmp_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
