@@ -1,0 +1,352 @@
+"""Benchmark: nested MLMC level estimation with FP16 + Kahan approximate
+random variables (piecewise-linear table) on GB300.
+
+Workload (one step): GBM dX = 0.05 X dt + 0.2 X dW, X0 = 1, T = 1, discounted
+European call K = 1; levels l = 0..12, N = 2^20 samples per level and
+estimator; for every level the two-way approximate difference (FP16 + Kahan,
+table) and the four-way nested difference (exact FP32 + Kahan vs FP16 + Kahan
+table).  One step = 2 x 2^20 x (2^13 - 1) = 1.718e10 fine Euler path-steps.
+Beside it, the plain FP32 exact-normal two-way MLMC over the same levels.
+
+value: fine path-steps per second of the FP16 + Kahan nested step, timed on
+the device with CUDA events; e2e: the same through the synchronous C-ABI
+calls that return the sums to host memory.  `--impl reference` times the CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LEVELS = list(range(13))
+N_PER_LEVEL = 1 << 20
+SEED = 1234
+WORKLOAD = "GBM call, levels 0..12, N=2^20 per level, two-way + four-way, FP16+Kahan table vs FP32"
+
+# Algorithmic lane-instructions per fine path-step (one sample of one
+# estimator), counted from the method's operations; derivation in the design doc.
+OPS_FOURWAY_F16K_TABLE = 74.5
+OPS_TWOWAY_F16K_TABLE = 32.25
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_step_items(M):
+    """(four, level, prec, kahan, icdf) of every launch in one FP16+Kahan nested step."""
+    items = []
+    for l in LEVELS:
+        items.append((0, l, M.MLMC_F16, True, M.MLMC_ICDF_TABLE))
+        items.append((1, l, M.MLMC_F16, True, M.MLMC_ICDF_TABLE))
+    return items
+
+
+def path_steps(levels, n):
+    return sum(n * (1 << l) for l in levels)
+
+
+def run_gpu(args):
+    import torch
+    import paper_2012_09739_gb300 as M
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    stream = torch.cuda.current_stream()
+    items = gpu_step_items(M)
+    sums = torch.zeros(len(items) * 2, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # 256 MiB > 129 MB L2
+    # each rank simulates its own disjoint path range (weak scaling)
+    offset = rank * N_PER_LEVEL
+
+    def step(ev_pairs=None):
+        for i, (four, l, prec, kahan, icdf) in enumerate(items):
+            if ev_pairs is not None:
+                ev_pairs[i][0].record(stream)
+            M.mlmc_level_async(four, l, N_PER_LEVEL, prec, kahan, icdf, params, SEED, offset, sums[2 * i:],
+                               stream.cuda_stream)
+            if ev_pairs is not None:
+                ev_pairs[i][1].record(stream)
+
+    def fp32_step():
+        for l in LEVELS:
+            M.mlmc_level_async(0, l, N_PER_LEVEL, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, params, SEED, offset,
+                               sums[2 * l:], stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+        if not args.no_fp32:
+            fp32_step()
+    torch.cuda.synchronize()
+
+    # --- device-timed FP16+Kahan nested step
+    step_ms, per_item = [], [[0.0, 0] for _ in items]
+    with ClockSampler(local) as clocks:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.fill_(1)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in items]
+            step(evs)
+            torch.cuda.synchronize()
+            tot = 0.0
+            for i, (a, b) in enumerate(evs):
+                ms = a.elapsed_time(b)
+                per_item[i][0] += ms
+                per_item[i][1] += 1
+                tot += ms
+            step_ms.append(tot)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    ms_total = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ps_step = 2 * path_steps(LEVELS, N_PER_LEVEL)
+    value = ps_step * args.steps * world / (ms_total / 1e3)
+
+    # --- plain FP32 exact-normal MLMC over the same levels (comparison)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fp32_ms = 0.0
+    for _ in range(0 if args.no_fp32 else args.steps):
+        flush.fill_(1)
+        e0.record(stream)
+        fp32_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp32_ms += e0.elapsed_time(e1)
+    fp32_value = path_steps(LEVELS, N_PER_LEVEL) * args.steps * world / (fp32_ms / 1e3) if fp32_ms else None
+
+    # --- end to end through the synchronous C-ABI calls (sums to host memory)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(0 if args.no_e2e else args.steps):
+        for four, l, prec, kahan, icdf in items:
+            fn = M.mlmc_nested_level if four else M.mlmc_level
+            fn(l, N_PER_LEVEL, prec, kahan, icdf, params, SEED, offset, stream.cuda_stream)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ps_step * args.steps * world / e2e_s if not args.no_e2e else None
+
+    # --- roofline of the dominant kernel (four-way FP16+Kahan table)
+    clk = clocks.summary()
+    four_ms = sum(per_item[i][0] for i, it in enumerate(items) if it[0] == 1)
+    four_launches = sum(per_item[i][1] for i, it in enumerate(items) if it[0] == 1)
+    four_ps = path_steps(LEVELS, N_PER_LEVEL) * args.steps
+    achieved = OPS_FOURWAY_F16K_TABLE * four_ps / (four_ms / 1e3) / 1e9     # Gop/s (lane-instructions)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = clk["sm_mhz"] or 1477.0
+    peak = sm_count * 128 * clk_mhz * 1e6 / 1e9                              # Gop/s issue peak
+    two_ms = sum(per_item[i][0] for i, it in enumerate(items) if it[0] == 0)
+
+    line = {
+        "metric": "EM path-steps/s and time-to-RMSE 1e-3: FP16+Kahan vs plain FP32, one GB300",
+        "value": value,
+        "unit": "path-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_total / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f16",
+        "data": "synthetic (Philox4x32-10 seed 1234; counter-based, generated in-kernel)",
+        "config": {"workload": WORKLOAD, "levels": [min(LEVELS), max(LEVELS)], "N_per_level": N_PER_LEVEL,
+                   "path_steps_per_step": ps_step, "estimators": "two-way FP16+Kahan table + four-way nested",
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "fp32_plain": {"value": fp32_value, "unit": "path-steps/s", "ms_per_step": fp32_ms / args.steps,
+                       "ratio": (value / fp32_value) if fp32_value else None,
+                       "path_steps_per_step": path_steps(LEVELS, N_PER_LEVEL)},
+        "kernel_ms_per_step": {"fourway_f16_kahan_table": four_ms / args.steps,
+                               "twoway_f16_kahan_table": two_ms / args.steps},
+        "roofline": {"bound": "alu", "kernel": "level_kernel<FOUR,F16,kahan,TABLE,GBM>",
+                     "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "ops_per_path_step": OPS_FOURWAY_F16K_TABLE,
+                     "peak_basis": f"{sm_count} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock sampled)",
+                     "launches": four_launches},
+        "e2e": {"value": e2e_value, "unit": "path-steps/s", "h2d_bytes_per_step": len(items) * 64,
+                "d2h_bytes_per_step": len(items) * 16},
+        "gpu_launches": 2 * len(items) * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def _cpu_sample(target_s: float, nthreads: int):
+    """Times the oracle on a bounded sample of the same workload: every level,
+    the two-way (FP16+Kahan emulated) and four-way (FP64 exact vs FP16+Kahan
+    emulated) estimators, with n samples per level scaled to ~target_s."""
+    import oracle as O
+    from oracle import table
+    tab = table.build_table()
+    sde = O.gbm(payoff=O.PAYOFF_CALL)
+    bar = O.variant(prec=O.F16, kahan=True, rv=O.RV_TABLE)
+    hat = O.variant()
+
+    def run(n):
+        t0 = time.perf_counter()
+        for l in LEVELS:
+            O.level_sums(l, n, 0, bar, sde, SEED, O.make_tag(O.KIND_APPROX, l), table=tab, nthreads=nthreads)
+            O.level_sums(l, n, 0, hat, sde, SEED, O.make_tag(O.KIND_FOUR, l), table=tab, four=True, var2=bar,
+                         nthreads=nthreads)
+        return time.perf_counter() - t0
+
+    n = 16 * nthreads
+    dt = run(n)
+    n2 = max(n, int(n * target_s / max(dt, 1e-3)))
+    dt = run(n2)
+    ps = 2 * path_steps(LEVELS, n2)
+    return ps / dt, n2, dt
+
+
+def cpu_baseline(target_s: float):
+    import oracle as O
+    threads = os.cpu_count() or 1
+    O.build()
+    rate, n, dt = _cpu_sample(target_s, threads)
+    return {"value": rate, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"levels 0..12, {n} samples per level and estimator (two-way + four-way), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    threads = os.cpu_count() or 1
+    rates = []
+    for _ in range(args.warmup):
+        _cpu_sample(args.cpu_seconds / 4, threads)
+    t_total, ps_total = 0.0, 0
+    for _ in range(args.steps):
+        rate, n, dt = _cpu_sample(args.cpu_seconds / 2, threads)
+        rates.append(rate)
+        t_total += dt
+        ps_total += 2 * path_steps(LEVELS, n)
+    value = ps_total / t_total
+    line = {
+        "impl": "reference",
+        "metric": "EM path-steps/s and time-to-RMSE 1e-3: FP16+Kahan vs plain FP32, one GB300",
+        "value": value, "unit": "path-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16 (emulated in FP64)", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (bounded sample per step)"},
+        "cpu_baseline": {"value": value, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
+                         "sample": f"per step: levels 0..12, a few thousand samples per level, ~{args.cpu_seconds / 2:.0f} s"},
+        "e2e": {"value": value, "unit": "path-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison leg (profiling runs)")
+    ap.add_argument("--levels", type=str, default=None, help="comma-separated levels (profiling runs)")
+    ap.add_argument("--n", type=int, default=None, help="samples per level (profiling runs)")
+    args = ap.parse_args()
+    global LEVELS, N_PER_LEVEL
+    if args.levels:
+        LEVELS = [int(x) for x in args.levels.split(",")]
+    if args.n:
+        N_PER_LEVEL = args.n
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * mlmc.h -- C ABI of the GB300 (sm_103a) library for nested multilevel Monte
+ * Carlo with low-precision approximate random variables, after Giles &
+ * Sheridan-Methven, "Rounding error using low precision approximate random
+ * variables" (arXiv 2012.09739).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *_dev are CUDA device pointers on the current device;
+ *     pointers named *_host are ordinary host memory.  All memory passed in
+ *     belongs to the caller; the library never frees it.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that return results in host memory synchronise with `stream` before
+ *     returning; calls with device outputs only enqueue work.
+ *   - Every call returns an mlmc_status and never aborts.  Invalid arguments
+ *     give MLMC_EINVAL before anything is launched.  A CUDA error gives
+ *     MLMC_ECUDA; mlmc_last_error() describes it.
+ *   - Results are a deterministic function of (seed, path_offset, N, level,
+ *     estimator kind, variant, set id) and of the launch configuration.
+ *
+ * Random numbers.  Philox4x32-10 (Salmon et al., SC'11; the paper names no
+ * generator).  Counter (path lo32, path hi32, j, tag), key (seed lo32, seed
+ * hi32); fine step n of a path uses word n mod 4 of call j = n / 4;
+ * tag = kind | level << 8 | set << 16 with kind 0 = standard two-way with
+ * exact normals, 1 = two-way with approximate normals, 2 = four-way.  A word
+ * w becomes the uniform u = (2 (w >> 9) + 1) 2^-24 (Sec. 3: Z_n = Phi^-1(U_n)
+ * and Z~_n = Phi~^-1(U_n) share U_n).
+ */
+#ifndef MLMC_H
+#define MLMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MLMC_OK = 0,
+    MLMC_EINVAL = 1,      /* invalid argument; nothing launched */
+    MLMC_ECUDA = 2,       /* CUDA runtime error (see mlmc_last_error) */
+    MLMC_ETIMEOUT = 3,    /* wait exceeded the library's wall-clock limit */
+    MLMC_ENOMEM = 4,      /* device or host allocation failed */
+    MLMC_ENOTCONV = 5,    /* mlmc_run reached max_level without meeting eps */
+    MLMC_ENOTREADY = 6    /* MLP weights requested but never set or trained */
+} mlmc_status;
+
+typedef enum { MLMC_GBM = 0, MLMC_OU = 1 } mlmc_sde_kind;
+typedef enum { MLMC_PAYOFF_X = 0, MLMC_PAYOFF_CALL = 1 } mlmc_payoff;
+/* working precision of the approximate ("bar") paths and of Z~ */
+typedef enum { MLMC_F32 = 0, MLMC_F16 = 1 } mlmc_prec;
+typedef enum { MLMC_ICDF_EXACT = 0, MLMC_ICDF_TABLE = 1, MLMC_ICDF_MLP = 2 } mlmc_icdf;
+
+/* SDE dX = a(X) dt + b(X) dW on [0, T], X_0 = x0.
+ *   GBM: a = p0 X, b = p1 X            (mu = p0, sigma = p1)
+ *   OU:  a = p0 (p1 - X), b = p2       (theta = p0, m = p1, s = p2)
+ * Payoff P = X_T, or disc * max(X_T - K, 0) for the call. */
+typedef struct {
+    int32_t sde;      /* mlmc_sde_kind */
+    int32_t payoff;   /* mlmc_payoff */
+    double p0, p1, p2;
+    double x0, T, K, disc;
+} mlmc_sde_params;
+
+/* Sums of one level estimator: s1 = sum D, s2 = sum D^2 over n samples
+ * (accumulated in FP32 per thread and warp, in FP64 across warps and
+ * blocks); cost_ns = device time of the level kernel in nanoseconds. */
+typedef struct {
+    double s1, s2;
+    uint64_t n;
+    double cost_ns;
+} mlmc_sums;
+
+/* Two-way level difference D = P_l - P_{l-1} (P_{-1} = 0) over N samples,
+ * paths path_offset .. path_offset + N - 1 (Sec. 3, estimator theta^ with
+ * icdf = EXACT, first sum of theta- otherwise).
+ *   fine: 2^l Euler steps of delta = T 2^-l; coarse: 2^(l-1) steps of 2 delta
+ *   driven by the pairwise sums of the fine normals (Sec. 3).
+ *   Each Euler step is X <- X (+) (A (+) B), A = (a delta) X-term,
+ *   B = ((b sqrt(delta)) X-term) (x) Z in working precision `prec`, every
+ *   operation rounded to nearest even and never fused (Sec. 2.2); with
+ *   kahan != 0 the addition is Kahan-compensated (Sec. 2.3, Algorithm 1).
+ *   The normals are Phi^-1 (icdf EXACT, computed in FP32) or the
+ *   approximate inverse CDF (TABLE: 16-interval piecewise linear, Sec. 2.1;
+ *   MLP: the network set by mlmc_mlp_set_weights / mlmc_mlp_train).
+ * 0 <= l <= 18, N >= 1, T > 0; GBM sigma > 0; OU s > 0.
+ * out_host receives the sums; the call synchronises with `stream`. */
+mlmc_status mlmc_level(int l, uint64_t N, int prec, int kahan, int icdf, const mlmc_sde_params *params,
+                       uint64_t seed, uint64_t path_offset, mlmc_sums *out_host, void *stream);
+
+/* Four-way nested difference D = P^_l - P^_{l-1} - P-_l + P-_{l-1} (Sec. 3,
+ * second sum of theta-).  The "hat" pair uses exact normals Phi^-1(U_n) in
+ * FP32 with Kahan compensation; the "bar" pair uses the approximate normals
+ * Phi~^-1(U_n) of kind `icdf` (TABLE or MLP) in precision `prec`, with Kahan
+ * if kahan != 0.  All four paths share U_n.  Same arguments and errors as
+ * mlmc_level; icdf = EXACT is invalid. */
+mlmc_status mlmc_nested_level(int l, uint64_t N, int prec, int kahan, int icdf, const mlmc_sde_params *params,
+                              uint64_t seed, uint64_t path_offset, mlmc_sums *out_host, void *stream);
+
+/* As mlmc_level / mlmc_nested_level (four = 0 / 1) but asynchronous: writes
+ * {s1, s2} as two doubles to sums_dev and nothing to the host.  Launches
+ * two kernels (level, finalize) on `stream`. */
+mlmc_status mlmc_level_async(int four, int l, uint64_t N, int prec, int kahan, int icdf,
+                             const mlmc_sde_params *params, uint64_t seed, uint64_t path_offset,
+                             double *sums_dev, void *stream);
+
+/* Per-path diagnostics of the same computation: writes, for sample i,
+ * out_dev[i*3 + {0,1,2}] = (P_fine, P_coarse, D) for the two-way difference
+ * (four = 0) or out_dev[i*5 + {0..4}] = (P^_f, P^_c, P-_f, P-_c, D) for the
+ * four-way difference (four = 1), as float.  Enqueued on `stream`. */
+mlmc_status mlmc_level_paths(int four, int l, uint64_t N, int prec, int kahan, int icdf,
+                             const mlmc_sde_params *params, uint64_t seed, uint64_t path_offset,
+                             float *out_dev, void *stream);
+
+/* Bulk approximate inverse CDF (Sec. 2.1): z_dev[i] = Phi~^-1(u_dev[i]) for
+ * 0 < u < 1 (values outside give unspecified finite results).  z_dev is
+ * float for prec = F32 and IEEE binary16 (uint16_t storage) for F16.
+ * icdf = EXACT evaluates Phi^-1 in FP32. */
+mlmc_status approx_icdf(const float *u_dev, void *z_dev, size_t n, int icdf, int prec, void *stream);
+
+/* Philox4x32-10 of n counters: ctr_dev (n x 4 uint32), key_dev (n x 2),
+ * out_dev (n x 4).  And the uniform map u = (2 (w >> 9) + 1) 2^-24. */
+mlmc_status mlmc_philox4x32_10(const uint32_t *ctr_dev, const uint32_t *key_dev, uint32_t *out_dev, size_t n,
+                               void *stream);
+mlmc_status mlmc_uniforms(const uint32_t *w_dev, float *u_dev, size_t n, void *stream);
+
+/* The piecewise-linear table as built on the device (FP64 closed-form L2
+ * fit of Phi^-1 on the 16 dyadic intervals of v = min(u, 1-u), Sec. 2.1):
+ * c_host[2i], c_host[2i+1] = (c0, c1) of interval i+1.  Any pointer may be
+ * NULL.  c32_host / c16_host receive the binary32 / binary16 roundings. */
+mlmc_status mlmc_icdf_table(double *c_host, float *c32_host, uint16_t *c16_host);
+
+/* ---- MLP surrogate inverse CDF: 1 -> 32 -> 32 -> 1 tanh network on
+ * t = sqrt(-2 ln v), v = min(u, 1-u); Z~ = -y for u <= 1/2, +y above.
+ * 1153 parameters, layout W1[32], b1[32], W2[32][32] (row = output unit),
+ * b2[32], W3[32], b3.  The library keeps one FP32 master copy per device. */
+#define MLMC_MLP_PARAMS 1153
+mlmc_status mlmc_mlp_set_weights(const float *w_host, size_t n);
+mlmc_status mlmc_mlp_get_weights(float *w_host, size_t n);
+
+typedef struct {
+    uint64_t steps;       /* Adam steps */
+    uint32_t batch;       /* samples per step (multiple of 128) */
+    float lr0, lr_min;    /* cosine schedule from lr0 to lr_min */
+    float beta1, beta2, eps;
+    uint64_t seed;        /* minibatch sampling */
+} mlmc_train_opts;
+
+/* Loss and gradient of the mean squared error over n pairs (t = features of
+ * u_dev, target z_dev = |Phi^-1(v)|) with the current weights: grad_dev
+ * receives 1153 floats, *loss_host the loss.  FP16 tensor-core forward and
+ * backward with FP32 accumulation. */
+mlmc_status mlmc_mlp_grad(const float *u_dev, const float *z_dev, size_t n, float *grad_dev, float *loss_host,
+                          void *stream);
+/* Adam training on n (u, |Phi^-1(min(u,1-u))|) pairs.  If z_dev is NULL the
+ * targets are computed on the device with FP64 Phi^-1.  The final loss
+ * (over the last minibatch) goes to *loss_host if non-NULL. */
+mlmc_status mlmc_mlp_train(const float *u_dev, const float *z_dev, size_t n, const mlmc_train_opts *opts,
+                           float *loss_host, void *stream);
+
+/* ---- Batched levels: many (parameter set, level, estimator) items in one
+ * persistent launch.  kind: 0 two-way, 1 four-way. */
+typedef struct {
+    mlmc_sde_params params;
+    int32_t l, kind, prec, kahan, icdf, set_id;
+    uint64_t N, path_offset;
+} mlmc_work;
+
+/* Runs all items, longest first, in one persistent kernel captured in a
+ * CUDA graph (re-used while the item list's shape is unchanged), followed by
+ * one finalize kernel.  out_host[i] receives the sums of items[i]. */
+mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t seed, mlmc_sums *out_host, void *stream);
+
+/* ---- Adaptive MLMC to a target RMSE (Sec. 3 cost model). */
+typedef struct {
+    int32_t estimator;    /* 0: standard theta^ (FP32, exact normals, plain Euler);
+                             1: nested theta- (two-way approximate + four-way) */
+    int32_t prec, kahan, icdf;   /* variant of the approximate paths (estimator 1) */
+    int32_t max_level;    /* <= 18 */
+    int32_t min_levels;   /* levels 0 .. min_levels-1 always present (>= 3) */
+    uint64_t n0;          /* warm-up samples per level and estimator */
+    uint64_t seed;
+    double alpha;         /* weak order used in the bias test (Euler: 1) */
+    double timeout_s;     /* wall-clock limit; MLMC_ETIMEOUT beyond it */
+} mlmc_run_opts;
+
+#define MLMC_MAX_LEVELS 19
+typedef struct {
+    double estimate;              /* sum over levels and estimators of the means */
+    double variance;              /* sum of V_l / N_l (estimated MSE minus bias^2) */
+    int32_t levels;               /* L + 1 */
+    int32_t rounds;
+    double wall_s;                /* wall-clock time of mlmc_run */
+    double path_steps;            /* fine path-steps simulated */
+    uint64_t n[2][MLMC_MAX_LEVELS];       /* samples per estimator (0: two-way, 1: four-way) and level */
+    double mean[2][MLMC_MAX_LEVELS];
+    double var[2][MLMC_MAX_LEVELS];
+    double cost[2][MLMC_MAX_LEVELS];      /* device ns per sample */
+} mlmc_run_result;
+
+mlmc_status mlmc_run(double eps, const mlmc_sde_params *params, const mlmc_run_opts *opts, mlmc_run_result *out);
+
+/* Optimal sample counts (Sec. 3): N_i = ceil(2 eps^-2 sqrt(V_i / C_i)
+ * sum_j sqrt(V_j C_j)) over n estimator terms.  Host-only; no GPU needed. */
+mlmc_status mlmc_optimal_samples(const double *V, const double *C, int n, double eps, uint64_t *N_out);
+
+/* ---- Measurement: peak issue-rate probes of the non-tensor pipes.
+ * kind 0: FP32 FFMA, 1: FP16x2 HFMA2, 2: 32-bit IMAD, 3: LOP3.  Writes
+ * the measured thread-operations per second (one FMA = one operation, one
+ * HFMA2 = two). */
+mlmc_status mlmc_peak_probe(int kind, double *ops_per_s, void *stream);
+
+/* Library info and lifetime. */
+const char *mlmc_strerror(mlmc_status s);
+const char *mlmc_last_error(void);
+const char *mlmc_version(void);
+/* Frees the library's per-device state (tables, weights, graphs). */
+mlmc_status mlmc_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLMC_H */

@@ -1,0 +1,274 @@
+"""Python binding of libmlmc (include/mlmc.h): nested multilevel Monte Carlo
+with low-precision approximate random variables on GB300 (sm_103a).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch tensors on the current CUDA device; the
+stream is torch's current stream unless one is given.  If the compiled
+library is missing, every call raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmlmc.so")
+
+# enums (include/mlmc.h)
+MLMC_OK, MLMC_EINVAL, MLMC_ECUDA, MLMC_ETIMEOUT, MLMC_ENOMEM, MLMC_ENOTCONV, MLMC_ENOTREADY = range(7)
+MLMC_GBM, MLMC_OU = 0, 1
+MLMC_PAYOFF_X, MLMC_PAYOFF_CALL = 0, 1
+MLMC_F32, MLMC_F16 = 0, 1
+MLMC_ICDF_EXACT, MLMC_ICDF_TABLE, MLMC_ICDF_MLP = 0, 1, 2
+MLMC_MLP_PARAMS = 1153
+MLMC_MAX_LEVELS = 19
+
+
+class MlmcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"mlmc status {status}: {message}")
+        self.status = status
+
+
+class mlmc_sde_params(ctypes.Structure):
+    _fields_ = [("sde", ctypes.c_int32), ("payoff", ctypes.c_int32),
+                ("p0", ctypes.c_double), ("p1", ctypes.c_double), ("p2", ctypes.c_double),
+                ("x0", ctypes.c_double), ("T", ctypes.c_double), ("K", ctypes.c_double), ("disc", ctypes.c_double)]
+
+
+class mlmc_sums(ctypes.Structure):
+    _fields_ = [("s1", ctypes.c_double), ("s2", ctypes.c_double), ("n", ctypes.c_uint64),
+                ("cost_ns", ctypes.c_double)]
+
+    def mean(self) -> float:
+        return self.s1 / self.n
+
+    def var(self) -> float:
+        n = self.n
+        return (self.s2 - self.s1 * self.s1 / n) / (n - 1) if n > 1 else 0.0
+
+
+class mlmc_train_opts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("batch", ctypes.c_uint32), ("lr0", ctypes.c_float),
+                ("lr_min", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class mlmc_work(ctypes.Structure):
+    _fields_ = [("params", mlmc_sde_params), ("l", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("kahan", ctypes.c_int32), ("icdf", ctypes.c_int32),
+                ("set_id", ctypes.c_int32), ("N", ctypes.c_uint64), ("path_offset", ctypes.c_uint64)]
+
+
+class mlmc_run_opts(ctypes.Structure):
+    _fields_ = [("estimator", ctypes.c_int32), ("prec", ctypes.c_int32), ("kahan", ctypes.c_int32),
+                ("icdf", ctypes.c_int32), ("max_level", ctypes.c_int32), ("min_levels", ctypes.c_int32),
+                ("n0", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("alpha", ctypes.c_double),
+                ("timeout_s", ctypes.c_double)]
+
+
+class mlmc_run_result(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("variance", ctypes.c_double), ("levels", ctypes.c_int32),
+                ("rounds", ctypes.c_int32), ("wall_s", ctypes.c_double), ("path_steps", ctypes.c_double),
+                ("n", (ctypes.c_uint64 * MLMC_MAX_LEVELS) * 2), ("mean", (ctypes.c_double * MLMC_MAX_LEVELS) * 2),
+                ("var", (ctypes.c_double * MLMC_MAX_LEVELS) * 2), ("cost", (ctypes.c_double * MLMC_MAX_LEVELS) * 2)]
+
+
+# exported symbols and their signatures
+_P = ctypes.POINTER
+_vp, _u64, _i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+_SIGS = {
+    "mlmc_level": [_i32, _u64, _i32, _i32, _i32, _P(mlmc_sde_params), _u64, _u64, _P(mlmc_sums), _vp],
+    "mlmc_nested_level": [_i32, _u64, _i32, _i32, _i32, _P(mlmc_sde_params), _u64, _u64, _P(mlmc_sums), _vp],
+    "mlmc_level_async": [_i32, _i32, _u64, _i32, _i32, _i32, _P(mlmc_sde_params), _u64, _u64, _vp, _vp],
+    "mlmc_level_paths": [_i32, _i32, _u64, _i32, _i32, _i32, _P(mlmc_sde_params), _u64, _u64, _vp, _vp],
+    "approx_icdf": [_vp, _vp, ctypes.c_size_t, _i32, _i32, _vp],
+    "mlmc_philox4x32_10": [_vp, _vp, _vp, ctypes.c_size_t, _vp],
+    "mlmc_uniforms": [_vp, _vp, ctypes.c_size_t, _vp],
+    "mlmc_icdf_table": [_vp, _vp, _vp],
+    "mlmc_mlp_set_weights": [_vp, ctypes.c_size_t],
+    "mlmc_mlp_get_weights": [_vp, ctypes.c_size_t],
+    "mlmc_mlp_grad": [_vp, _vp, ctypes.c_size_t, _vp, _vp, _vp],
+    "mlmc_mlp_train": [_vp, _vp, ctypes.c_size_t, _P(mlmc_train_opts), _vp, _vp],
+    "mlmc_batch": [_P(mlmc_work), _i32, _u64, _P(mlmc_sums), _vp],
+    "mlmc_run": [ctypes.c_double, _P(mlmc_sde_params), _P(mlmc_run_opts), _P(mlmc_run_result)],
+    "mlmc_optimal_samples": [_vp, _vp, _i32, ctypes.c_double, _vp],
+    "mlmc_peak_probe": [_i32, _vp, _vp],
+    "mlmc_strerror": [_i32],
+    "mlmc_last_error": [],
+    "mlmc_version": [],
+    "mlmc_shutdown": [],
+}
+_CHAR_RET = {"mlmc_strerror", "mlmc_last_error", "mlmc_version"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmlmc.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"libmlmc.so not built ({path}); run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            for name, args in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_char_p if name in _CHAR_RET else ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != MLMC_OK:
+        raise MlmcError(status, load().mlmc_last_error().decode())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def sde_params(sde=MLMC_GBM, payoff=MLMC_PAYOFF_X, p0=0.05, p1=0.2, p2=0.0, x0=1.0, T=1.0, K=1.0,
+               disc=None) -> mlmc_sde_params:
+    """GBM: (p0, p1) = (mu, sigma); OU: (p0, p1, p2) = (theta, m, s).  The call
+    is discounted by disc (default e^{-p0 T} for GBM, 1 for OU)."""
+    import math
+    if disc is None:
+        disc = math.exp(-p0 * T) if sde == MLMC_GBM else 1.0
+    return mlmc_sde_params(sde, payoff, p0, p1, p2, x0, T, K, disc)
+
+
+def mlmc_level(l, N, prec, kahan, icdf, params, seed, path_offset=0, stream=None) -> mlmc_sums:
+    out = mlmc_sums()
+    _check(load().mlmc_level(l, N, prec, int(kahan), icdf, ctypes.byref(params), seed, path_offset,
+                             ctypes.byref(out), _stream(stream)))
+    return out
+
+
+def mlmc_nested_level(l, N, prec, kahan, icdf, params, seed, path_offset=0, stream=None) -> mlmc_sums:
+    out = mlmc_sums()
+    _check(load().mlmc_nested_level(l, N, prec, int(kahan), icdf, ctypes.byref(params), seed, path_offset,
+                                    ctypes.byref(out), _stream(stream)))
+    return out
+
+
+def mlmc_level_async(four, l, N, prec, kahan, icdf, params, seed, path_offset, sums_dev, stream=None):
+    """sums_dev: float64 CUDA tensor with >= 2 elements (receives sum D, sum D^2)."""
+    _check(load().mlmc_level_async(int(four), l, N, prec, int(kahan), icdf, ctypes.byref(params), seed,
+                                   path_offset, _dptr(sums_dev), _stream(stream)))
+
+
+def mlmc_level_paths(four, l, N, prec, kahan, icdf, params, seed, path_offset, out_dev, stream=None):
+    """out_dev: float32 CUDA tensor of N*3 (two-way) or N*5 (four-way) elements."""
+    need = N * (5 if four else 3)
+    if out_dev.numel() < need:
+        raise ValueError(f"out_dev needs {need} elements")
+    _check(load().mlmc_level_paths(int(four), l, N, prec, int(kahan), icdf, ctypes.byref(params), seed,
+                                   path_offset, _dptr(out_dev), _stream(stream)))
+
+
+def approx_icdf(u_dev, z_dev, icdf, prec, stream=None):
+    """u_dev float32; z_dev float32 (F32) or float16 (F16), same length."""
+    if z_dev.numel() < u_dev.numel():
+        raise ValueError("z_dev too small")
+    _check(load().approx_icdf(_dptr(u_dev), _dptr(z_dev), u_dev.numel(), icdf, prec, _stream(stream)))
+
+
+def mlmc_philox4x32_10(ctr_dev, key_dev, out_dev, stream=None):
+    """ctr_dev (n, 4), key_dev (n, 2), out_dev (n, 4): int32 CUDA tensors holding uint32 bits."""
+    n = ctr_dev.shape[0]
+    _check(load().mlmc_philox4x32_10(_dptr(ctr_dev), _dptr(key_dev), _dptr(out_dev), n, _stream(stream)))
+
+
+def mlmc_uniforms(w_dev, u_dev, stream=None):
+    _check(load().mlmc_uniforms(_dptr(w_dev), _dptr(u_dev), w_dev.numel(), _stream(stream)))
+
+
+def mlmc_icdf_table():
+    """(c64 (16, 2) float64, c32 (16, 2) float32, c16 (16, 2) uint16 bits) as built on the device."""
+    import numpy as np
+    c64 = np.zeros(32, np.float64)
+    c32 = np.zeros(32, np.float32)
+    c16 = np.zeros(32, np.uint16)
+    _check(load().mlmc_icdf_table(c64.ctypes.data_as(_vp), c32.ctypes.data_as(_vp), c16.ctypes.data_as(_vp)))
+    return c64.reshape(16, 2), c32.reshape(16, 2), c16.reshape(16, 2)
+
+
+def mlmc_mlp_set_weights(w):
+    import numpy as np
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    _check(load().mlmc_mlp_set_weights(w.ctypes.data_as(_vp), w.size))
+
+
+def mlmc_mlp_get_weights():
+    import numpy as np
+    w = np.zeros(MLMC_MLP_PARAMS, np.float32)
+    _check(load().mlmc_mlp_get_weights(w.ctypes.data_as(_vp), w.size))
+    return w
+
+
+def mlmc_mlp_grad(u_dev, z_dev, grad_dev, stream=None) -> float:
+    loss = ctypes.c_float(0.0)
+    _check(load().mlmc_mlp_grad(_dptr(u_dev), _dptr(z_dev), u_dev.numel(), _dptr(grad_dev), ctypes.byref(loss),
+                                _stream(stream)))
+    return float(loss.value)
+
+
+def mlmc_mlp_train(u_dev, z_dev, opts: mlmc_train_opts, stream=None) -> float:
+    loss = ctypes.c_float(0.0)
+    zp = _dptr(z_dev) if z_dev is not None else ctypes.c_void_p(0)
+    _check(load().mlmc_mlp_train(_dptr(u_dev), zp, u_dev.numel(), ctypes.byref(opts), ctypes.byref(loss),
+                                 _stream(stream)))
+    return float(loss.value)
+
+
+def mlmc_batch(items, seed, stream=None):
+    arr = (mlmc_work * len(items))(*items)
+    out = (mlmc_sums * len(items))()
+    _check(load().mlmc_batch(arr, len(items), seed, out, _stream(stream)))
+    return list(out)
+
+
+def mlmc_run(eps, params, opts: mlmc_run_opts) -> mlmc_run_result:
+    out = mlmc_run_result()
+    _check(load().mlmc_run(eps, ctypes.byref(params), ctypes.byref(opts), ctypes.byref(out)))
+    return out
+
+
+def mlmc_optimal_samples(V, C, eps):
+    import numpy as np
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    N = np.zeros(V.size, np.uint64)
+    _check(load().mlmc_optimal_samples(V.ctypes.data_as(_vp), C.ctypes.data_as(_vp), V.size, eps,
+                                       N.ctypes.data_as(_vp)))
+    return N
+
+
+def mlmc_peak_probe(kind, stream=None) -> float:
+    v = ctypes.c_double(0.0)
+    _check(load().mlmc_peak_probe(kind, ctypes.byref(v), _stream(stream)))
+    return float(v.value)
+
+
+def mlmc_version() -> str:
+    return load().mlmc_version().decode()
+
+
+def mlmc_shutdown():
+    _check(load().mlmc_shutdown())
+
+
+def exported_symbols():
+    return list(_SIGS)

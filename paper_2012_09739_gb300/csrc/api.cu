@@ -1,0 +1,408 @@
+// C ABI of the library (include/mlmc.h): argument checking, per-device
+// state, launch configuration, and the host side of every entry point.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "api_internal.h"
+#include "level_kernels.cuh"
+
+namespace mlmc {
+
+// ---------------------------------------------------------------- errors
+static thread_local char g_last_error[512] = "";
+
+mlmc_status fail(mlmc_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+mlmc_status cuda_fail(cudaError_t e, const char *where) {
+    return fail(e == cudaErrorMemoryAllocation ? MLMC_ENOMEM : MLMC_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------- device state
+static std::mutex g_mu;
+static DeviceState g_dev[MAX_DEVICES];
+
+mlmc_status device_state(DeviceState **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(MLMC_EINVAL, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_mu);
+    DeviceState &d = g_dev[dev];
+    if (!d.ready) {
+        if ((e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_fail(e, "cudaDeviceGetAttribute");
+        if ((e = cudaMalloc(&d.tab64, 32 * sizeof(double))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(table)");
+        if ((e = cudaMalloc(&d.tab32, TAB_ENTRIES * sizeof(float2))) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(table)");
+        if ((e = cudaMalloc(&d.tab16, TAB_ENTRIES * sizeof(__half2))) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(table)");
+        if ((e = cudaMalloc(&d.mlp, sizeof(MlpWeights))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(mlp)");
+        if ((e = cudaMemset(d.mlp, 0, sizeof(MlpWeights))) != cudaSuccess) return cuda_fail(e, "cudaMemset(mlp)");
+        if ((e = launch_build_table(d.tab64, d.tab32, d.tab16, 0)) != cudaSuccess)
+            return cuda_fail(e, "build_table");
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "build_table");
+        d.device = dev;
+        d.ready = true;
+    }
+    *out = &d;
+    return MLMC_OK;
+}
+
+// ---------------------------------------------------------------- waiting
+double wait_limit_s() {
+    static double limit = [] {
+        const char *s = getenv("MLMC_TIMEOUT_S");
+        double v = s ? atof(s) : 0.0;
+        return v > 0.0 ? v : 600.0;
+    }();
+    return limit;
+}
+
+mlmc_status wait_event(cudaEvent_t ev, double limit_s) {
+    const auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return MLMC_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "wait");
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > limit_s) return fail(MLMC_ETIMEOUT, "wait exceeded %.1f s", limit_s);
+        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+// ---------------------------------------------------------------- validation
+mlmc_status check_params(const mlmc_sde_params *p) {
+    if (!p) return fail(MLMC_EINVAL, "params is NULL");
+    if (p->sde != MLMC_GBM && p->sde != MLMC_OU) return fail(MLMC_EINVAL, "unknown sde %d", p->sde);
+    if (p->payoff != MLMC_PAYOFF_X && p->payoff != MLMC_PAYOFF_CALL) return fail(MLMC_EINVAL, "unknown payoff");
+    const double v[] = {p->p0, p->p1, p->p2, p->x0, p->T, p->K, p->disc};
+    for (double x : v)
+        if (!isfinite(x)) return fail(MLMC_EINVAL, "non-finite SDE parameter");
+    if (!(p->T > 0.0)) return fail(MLMC_EINVAL, "T must be > 0");
+    if (p->sde == MLMC_GBM && !(p->p1 > 0.0)) return fail(MLMC_EINVAL, "GBM sigma must be > 0");
+    if (p->sde == MLMC_OU && !(p->p2 > 0.0)) return fail(MLMC_EINVAL, "OU s must be > 0");
+    return MLMC_OK;
+}
+
+mlmc_status check_level(int four, int l, uint64_t N, int prec, int icdf, const mlmc_sde_params *p) {
+    if (l < 0 || l > 18) return fail(MLMC_EINVAL, "level %d outside 0..18", l);
+    if (N == 0) return fail(MLMC_EINVAL, "N must be >= 1");
+    if (N > (1ull << 40)) return fail(MLMC_EINVAL, "N too large");
+    if (prec != MLMC_F32 && prec != MLMC_F16) return fail(MLMC_EINVAL, "unknown precision %d", prec);
+    if (icdf < 0 || icdf > 2) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
+    if (four && icdf == MLMC_ICDF_EXACT) return fail(MLMC_EINVAL, "four-way difference needs approximate normals");
+    return check_params(p);
+}
+
+// ---------------------------------------------------------------- launches
+LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int icdf, const mlmc_sde_params *p,
+                          uint64_t seed, uint64_t path_offset, uint32_t set_id) {
+    (void)icdf;
+    LevelArgs a;
+    memset(&a, 0, sizeof a);
+    const double delta_f = ldexp(p->T, -l);
+    const double sq = sqrt(delta_f);
+    a.l = l;
+    a.payoff = p->payoff;
+    a.N = N;
+    a.npairs = (N + 1) / 2;
+    a.path_offset = path_offset;
+    const uint32_t kind = four ? 2u : (icdf == MLMC_ICDF_EXACT ? 0u : 1u);
+    a.tag = kind | ((uint32_t)l << 8) | (set_id << 16);
+    a.k0 = (uint32_t)seed;
+    a.k1 = (uint32_t)(seed >> 32);
+    a.drift_f = p->p0 * delta_f;
+    a.drift_c = p->p0 * (2.0 * delta_f);
+    if (p->sde == MLMC_GBM) {
+        a.diff = p->p1 * sq;
+        a.mean = 0.0;
+    } else {
+        a.diff = p->p2 * sq;
+        a.mean = p->p1;
+    }
+    a.x0 = p->x0;
+    a.K = p->K;
+    a.disc = p->disc;
+    a.tab32 = d.tab32;
+    a.tab16 = d.tab16;
+    a.mlp = d.mlp;
+    return a;
+}
+
+LevelKernelFn pick_level_kernel(int four, int prec, int kahan, int icdf, int sde) {
+    return prec == MLMC_F32 ? level_kernel_f32(four, kahan, icdf, sde) : level_kernel_f16(four, kahan, icdf, sde);
+}
+
+static int env_int(const char *name, int dflt) {
+    const char *s = getenv(name);
+    return s ? atoi(s) : dflt;
+}
+
+// Grid for npairs pairs: whole rounds of resident threads, the grid a
+// multiple of the SM count where possible so every SM gets the same number
+// of blocks and every thread the same number of pairs (+-1).
+LaunchCfg level_launch_cfg(const DeviceState &d, LevelKernelFn fn, uint64_t npairs) {
+    LaunchCfg c;
+    c.block = env_int("MLMC_BLOCK", 256);
+    if (c.block < 32 || c.block > 256 || c.block % 32) c.block = 256;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, c.block, 0) != cudaSuccess || bps < 1) bps = 1;
+    const int cap = env_int("MLMC_BLOCKS_PER_SM", 0);
+    if (cap > 0 && cap < bps) bps = cap;
+    const uint64_t max_blocks = (uint64_t)bps * d.sm_count;
+    const uint64_t need = (npairs + c.block - 1) / c.block;
+    uint64_t grid;
+    if (need <= max_blocks) {
+        grid = need;
+    } else {
+        const uint64_t rounds = (need + max_blocks - 1) / max_blocks;
+        grid = (need + rounds - 1) / rounds;
+        const uint64_t sm = (uint64_t)d.sm_count;
+        const uint64_t up = (grid + sm - 1) / sm * sm;
+        if (up <= max_blocks) grid = up;
+    }
+    c.grid = (int)(grid > 0 ? grid : 1);
+    return c;
+}
+
+mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int prec, int kahan, int icdf,
+                          const mlmc_sde_params *p, uint64_t seed, uint64_t path_offset, uint32_t set_id,
+                          double *sums_dev, float *paths_dev, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+    LevelKernelFn fn = pick_level_kernel(four, prec, kahan, icdf, p->sde);
+    if (!fn) return fail(MLMC_EINVAL, "no kernel for this variant");
+    LevelArgs a = make_level_args(d, four, l, N, icdf, p, seed, path_offset, set_id);
+    const LaunchCfg cfg = level_launch_cfg(d, fn, a.npairs);
+    double2 *partials = nullptr;
+    cudaError_t e = cudaMallocAsync(&partials, (size_t)cfg.grid * sizeof(double2), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(partials)");
+    a.partials = partials;
+    a.paths_out = paths_dev;
+    if (ev0) cudaEventRecord(ev0, s);
+    fn<<<cfg.grid, cfg.block, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (ev1) cudaEventRecord(ev1, s);
+    if (e == cudaSuccess && sums_dev) e = launch_finalize(partials, cfg.grid, sums_dev, s);
+    cudaError_t e2 = cudaFreeAsync(partials, s);
+    if (e != cudaSuccess) return cuda_fail(e, "level kernel launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return MLMC_OK;
+}
+
+// Per-thread pinned staging for small device->host results.
+double *host_staging() {
+    static thread_local double *buf = nullptr;
+    if (!buf && cudaMallocHost(&buf, 64 * sizeof(double)) != cudaSuccess) buf = nullptr;
+    return buf;
+}
+
+mlmc_status level_sync(int four, int l, uint64_t N, int prec, int kahan, int icdf, const mlmc_sde_params *p,
+                       uint64_t seed, uint64_t path_offset, mlmc_sums *out, void *stream) {
+    mlmc_status st = check_level(four, l, N, prec, icdf, p);
+    if (st) return st;
+    if (!out) return fail(MLMC_EINVAL, "out_host is NULL");
+    DeviceState *d;
+    if ((st = device_state(&d))) return st;
+    if (icdf == MLMC_ICDF_MLP && !d->mlp_ready) return fail(MLMC_ENOTREADY, "MLP weights not set");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *host = host_staging();
+    if (!host) return fail(MLMC_ENOMEM, "cudaMallocHost");
+    double *sums_dev = nullptr;
+    cudaError_t e = cudaMallocAsync(&sums_dev, 2 * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    st = enqueue_level(*d, four, l, N, prec, kahan, icdf, p, seed, path_offset, 0, sums_dev, nullptr, s, ev0, ev1);
+    if (st == MLMC_OK) {
+        e = cudaMemcpyAsync(host, sums_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync");
+    }
+    cudaFreeAsync(sums_dev, s);
+    cudaEvent_t done;
+    cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    cudaEventRecord(done, s);
+    if (st == MLMC_OK) st = wait_event(done, wait_limit_s());
+    if (st == MLMC_OK) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        out->s1 = host[0];
+        out->s2 = host[1];
+        out->n = N;
+        out->cost_ns = (double)ms * 1e6;
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaEventDestroy(done);
+    return st;
+}
+
+}  // namespace mlmc
+
+using namespace mlmc;
+
+extern "C" {
+
+mlmc_status mlmc_level(int l, uint64_t N, int prec, int kahan, int icdf, const mlmc_sde_params *params, uint64_t seed,
+                       uint64_t path_offset, mlmc_sums *out_host, void *stream) {
+    return level_sync(0, l, N, prec, kahan, icdf, params, seed, path_offset, out_host, stream);
+}
+
+mlmc_status mlmc_nested_level(int l, uint64_t N, int prec, int kahan, int icdf, const mlmc_sde_params *params,
+                              uint64_t seed, uint64_t path_offset, mlmc_sums *out_host, void *stream) {
+    return level_sync(1, l, N, prec, kahan, icdf, params, seed, path_offset, out_host, stream);
+}
+
+mlmc_status mlmc_level_async(int four, int l, uint64_t N, int prec, int kahan, int icdf,
+                             const mlmc_sde_params *params, uint64_t seed, uint64_t path_offset, double *sums_dev,
+                             void *stream) {
+    mlmc_status st = check_level(four, l, N, prec, icdf, params);
+    if (st) return st;
+    if (!sums_dev) return fail(MLMC_EINVAL, "sums_dev is NULL");
+    DeviceState *d;
+    if ((st = device_state(&d))) return st;
+    if (icdf == MLMC_ICDF_MLP && !d->mlp_ready) return fail(MLMC_ENOTREADY, "MLP weights not set");
+    return enqueue_level(*d, four ? 1 : 0, l, N, prec, kahan, icdf, params, seed, path_offset, 0, sums_dev, nullptr,
+                         (cudaStream_t)stream, nullptr, nullptr);
+}
+
+mlmc_status mlmc_level_paths(int four, int l, uint64_t N, int prec, int kahan, int icdf,
+                             const mlmc_sde_params *params, uint64_t seed, uint64_t path_offset, float *out_dev,
+                             void *stream) {
+    mlmc_status st = check_level(four, l, N, prec, icdf, params);
+    if (st) return st;
+    if (!out_dev) return fail(MLMC_EINVAL, "out_dev is NULL");
+    DeviceState *d;
+    if ((st = device_state(&d))) return st;
+    if (icdf == MLMC_ICDF_MLP && !d->mlp_ready) return fail(MLMC_ENOTREADY, "MLP weights not set");
+    return enqueue_level(*d, four ? 1 : 0, l, N, prec, kahan, icdf, params, seed, path_offset, 0, nullptr, out_dev,
+                         (cudaStream_t)stream, nullptr, nullptr);
+}
+
+mlmc_status approx_icdf(const float *u_dev, void *z_dev, size_t n, int icdf, int prec, void *stream) {
+    if (icdf < 0 || icdf > 2) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
+    if (prec != MLMC_F32 && prec != MLMC_F16) return fail(MLMC_EINVAL, "unknown precision %d", prec);
+    if (n == 0) return MLMC_OK;
+    if (!u_dev || !z_dev) return fail(MLMC_EINVAL, "NULL buffer");
+    DeviceState *d;
+    mlmc_status st = device_state(&d);
+    if (st) return st;
+    if (icdf == MLMC_ICDF_MLP && !d->mlp_ready) return fail(MLMC_ENOTREADY, "MLP weights not set");
+    cudaError_t e = launch_icdf_bulk(u_dev, z_dev, n, icdf, prec, d->tab32, d->tab16, d->mlp, (cudaStream_t)stream);
+    return e == cudaSuccess ? MLMC_OK : cuda_fail(e, "approx_icdf");
+}
+
+mlmc_status mlmc_philox4x32_10(const uint32_t *ctr_dev, const uint32_t *key_dev, uint32_t *out_dev, size_t n,
+                               void *stream) {
+    if (n == 0) return MLMC_OK;
+    if (!ctr_dev || !key_dev || !out_dev) return fail(MLMC_EINVAL, "NULL buffer");
+    if (((uintptr_t)ctr_dev | (uintptr_t)out_dev) & 15) return fail(MLMC_EINVAL, "ctr/out must be 16-byte aligned");
+    if ((uintptr_t)key_dev & 7) return fail(MLMC_EINVAL, "key must be 8-byte aligned");
+    cudaError_t e = launch_philox_bulk(ctr_dev, key_dev, out_dev, n, (cudaStream_t)stream);
+    return e == cudaSuccess ? MLMC_OK : cuda_fail(e, "philox");
+}
+
+mlmc_status mlmc_uniforms(const uint32_t *w_dev, float *u_dev, size_t n, void *stream) {
+    if (n == 0) return MLMC_OK;
+    if (!w_dev || !u_dev) return fail(MLMC_EINVAL, "NULL buffer");
+    cudaError_t e = launch_uniform_bulk(w_dev, u_dev, n, (cudaStream_t)stream);
+    return e == cudaSuccess ? MLMC_OK : cuda_fail(e, "uniforms");
+}
+
+mlmc_status mlmc_icdf_table(double *c_host, float *c32_host, uint16_t *c16_host) {
+    DeviceState *d;
+    mlmc_status st = device_state(&d);
+    if (st) return st;
+    double t64[32];
+    float2 t32[TAB_ENTRIES];
+    __half2 t16[TAB_ENTRIES];
+    cudaError_t e = cudaMemcpy(t64, d->tab64, sizeof t64, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(t32, d->tab32, sizeof t32, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(t16, d->tab16, sizeof t16, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "mlmc_icdf_table");
+    for (int i = 0; i < 16; ++i) {
+        // interval i+1 sits in entry E - 103 with E = 125 - i (i < 15), E = 103 for the last
+        const int entry = i < 15 ? 22 - i : 0;
+        if (c_host) {
+            c_host[2 * i] = t64[2 * i];
+            c_host[2 * i + 1] = t64[2 * i + 1];
+        }
+        if (c32_host) {
+            c32_host[2 * i] = t32[entry].x;
+            c32_host[2 * i + 1] = t32[entry].y;
+        }
+        if (c16_host) {
+            __half2_raw r = *reinterpret_cast<__half2_raw *>(&t16[entry]);
+            c16_host[2 * i] = r.x;
+            c16_host[2 * i + 1] = r.y;
+        }
+    }
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_optimal_samples(const double *V, const double *C, int n, double eps, uint64_t *N_out) {
+    if (!V || !C || !N_out || n <= 0) return fail(MLMC_EINVAL, "bad arguments");
+    if (!(eps > 0.0) || !isfinite(eps)) return fail(MLMC_EINVAL, "eps must be > 0");
+    double total = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!(V[i] >= 0.0) || !(C[i] > 0.0) || !isfinite(V[i]) || !isfinite(C[i]))
+            return fail(MLMC_EINVAL, "V must be >= 0 and C > 0");
+        total += sqrt(V[i] * C[i]);
+    }
+    for (int i = 0; i < n; ++i) {
+        const double Ni = ceil(2.0 / (eps * eps) * sqrt(V[i] / C[i]) * total);
+        N_out[i] = Ni < 1.0 ? 1 : (Ni > 1.8e19 ? (uint64_t)1.8e19 : (uint64_t)Ni);
+    }
+    return MLMC_OK;
+}
+
+const char *mlmc_strerror(mlmc_status s) {
+    switch (s) {
+    case MLMC_OK: return "ok";
+    case MLMC_EINVAL: return "invalid argument";
+    case MLMC_ECUDA: return "CUDA error";
+    case MLMC_ETIMEOUT: return "timeout";
+    case MLMC_ENOMEM: return "out of memory";
+    case MLMC_ENOTCONV: return "not converged";
+    case MLMC_ENOTREADY: return "MLP weights not set";
+    }
+    return "unknown status";
+}
+
+const char *mlmc_last_error(void) { return g_last_error; }
+
+const char *mlmc_version(void) { return "mlmc-gb300 0.1 (sm_103a)"; }
+
+mlmc_status mlmc_shutdown(void) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int i = 0; i < MAX_DEVICES; ++i) {
+        DeviceState &d = g_dev[i];
+        if (!d.ready) continue;
+        cudaSetDevice(i);
+        release_device_extras(d);
+        cudaFree(d.tab64);
+        cudaFree(d.tab32);
+        cudaFree(d.tab16);
+        cudaFree(d.mlp);
+        d = DeviceState();
+    }
+    cudaSetDevice(cur);
+    return MLMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// Host-side state and helpers shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "level_kernels.cuh"
+
+namespace mlmc {
+
+constexpr int MAX_DEVICES = 16;
+
+struct BatchCache;   // batch.cu: captured graph of the last batch shape
+
+// Per-device library state: the piecewise-linear table (FP64 and its
+// binary32/binary16 roundings), the MLP weights, cached graphs.
+struct DeviceState {
+    bool ready = false;
+    int device = -1;
+    int sm_count = 0;
+    double *tab64 = nullptr;
+    float2 *tab32 = nullptr;
+    __half2 *tab16 = nullptr;
+    MlpWeights *mlp = nullptr;
+    bool mlp_ready = false;
+    BatchCache *batch = nullptr;
+};
+
+struct LaunchCfg {
+    int grid = 1, block = 256;
+};
+
+mlmc_status fail(mlmc_status s, const char *fmt, ...);
+mlmc_status cuda_fail(cudaError_t e, const char *where);
+mlmc_status device_state(DeviceState **out);
+mlmc_status wait_event(cudaEvent_t ev, double limit_s);
+double wait_limit_s();
+double *host_staging();
+mlmc_status check_params(const mlmc_sde_params *p);
+mlmc_status check_level(int four, int l, uint64_t N, int prec, int icdf, const mlmc_sde_params *p);
+LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int icdf, const mlmc_sde_params *p,
+                          uint64_t seed, uint64_t path_offset, uint32_t set_id);
+LevelKernelFn pick_level_kernel(int four, int prec, int kahan, int icdf, int sde);
+LaunchCfg level_launch_cfg(const DeviceState &d, LevelKernelFn fn, uint64_t npairs);
+mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int prec, int kahan, int icdf,
+                          const mlmc_sde_params *p, uint64_t seed, uint64_t path_offset, uint32_t set_id,
+                          double *sums_dev, float *paths_dev, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+mlmc_status level_sync(int four, int l, uint64_t N, int prec, int kahan, int icdf, const mlmc_sde_params *p,
+                       uint64_t seed, uint64_t path_offset, mlmc_sums *out, void *stream);
+void release_device_extras(DeviceState &d);
+
+}  // namespace mlmc

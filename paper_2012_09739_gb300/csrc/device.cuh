@@ -1,0 +1,152 @@
+// Device building blocks of the level kernels (sm_103a).
+//
+// Philox4x32-10, the 24-bit uniform map, rounding-exact arithmetic on path
+// pairs (binary32 pairs and packed binary16x2), and the inverse CDFs:
+// exact Phi^-1 in FP32 and the 16-interval piecewise-linear approximation
+// (Sec. 2.1) staged in shared memory.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace mlmc {
+
+// ---------------------------------------------------------------- RNG
+// Philox4x32-10 (Salmon et al. 2011): ten rounds of two 32x32->64 products
+// with a Weyl key schedule.  The key is the same for every thread (the
+// seed), so the schedule stays in uniform registers.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t word(const uint4 &w, int q) {
+    return q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
+}
+
+// u = (2 (w >> 9) + 1) 2^-24, exact in binary32.
+__device__ __forceinline__ float uniform_of(uint32_t w) {
+    return __fsub_rn(__uint_as_float((w >> 9) | 0x3F800000u), 0x1.fffffep-1f);
+}
+
+// v = min(u, 1 - u) for the same u, exact: flipping all bits of a word with
+// the top bit set maps u to 1 - u on the 2^23-point grid.
+__device__ __forceinline__ float mirrored_v(uint32_t w) {
+    const uint32_t m = (w ^ (uint32_t)((int32_t)w >> 31)) >> 9;   // < 2^22
+    return __fsub_rn(__uint_as_float(m | 0x3F800000u), 0x1.fffffep-1f);
+}
+
+// ---------------------------------------------------------------- arithmetic
+// Every operation is a single IEEE operation rounded to nearest even; none
+// is ever fused into an FMA (Sec. 2.2 models exactly this operation order).
+__device__ __forceinline__ __half2 h2add(__half2 a, __half2 b) {
+    __half2 r;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(*reinterpret_cast<uint32_t *>(&r))
+        : "r"(*reinterpret_cast<uint32_t *>(&a)), "r"(*reinterpret_cast<uint32_t *>(&b)));
+    return r;
+}
+__device__ __forceinline__ __half2 h2sub(__half2 a, __half2 b) {
+    __half2 r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(*reinterpret_cast<uint32_t *>(&r))
+        : "r"(*reinterpret_cast<uint32_t *>(&a)), "r"(*reinterpret_cast<uint32_t *>(&b)));
+    return r;
+}
+__device__ __forceinline__ __half2 h2mul(__half2 a, __half2 b) {
+    __half2 r;
+    asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(*reinterpret_cast<uint32_t *>(&r))
+        : "r"(*reinterpret_cast<uint32_t *>(&a)), "r"(*reinterpret_cast<uint32_t *>(&b)));
+    return r;
+}
+
+// binary64 -> binary16 with a single rounding to nearest even.
+__device__ __forceinline__ __half f64_to_f16(double v) {
+    unsigned short r;
+    asm("cvt.rn.f16.f64 %0, %1;" : "=h"(r) : "d"(v));
+    return __ushort_as_half(r);
+}
+
+// A pair of paths in working precision P: two binary32 values or one
+// packed binary16x2 register.
+enum { P_F32 = 0, P_F16 = 1 };
+
+template <int P> struct Pair;
+
+template <> struct Pair<P_F32> {
+    float x, y;
+    static __device__ __forceinline__ Pair of(double v) { float f = __double2float_rn(v); return {f, f}; }
+    static __device__ __forceinline__ Pair of2(float a, float b) { return {a, b}; }
+    __device__ __forceinline__ float2 f32() const { return make_float2(x, y); }
+};
+template <> struct Pair<P_F16> {
+    __half2 h;
+    static __device__ __forceinline__ Pair of(double v) { __half t = f64_to_f16(v); return {__halves2half2(t, t)}; }
+    static __device__ __forceinline__ Pair of2(float a, float b) { return {__floats2half2_rn(a, b)}; }
+    __device__ __forceinline__ float2 f32() const { return __half22float2(h); }
+};
+
+__device__ __forceinline__ Pair<P_F32> add(Pair<P_F32> a, Pair<P_F32> b) { return {__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)}; }
+__device__ __forceinline__ Pair<P_F32> sub(Pair<P_F32> a, Pair<P_F32> b) { return {__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)}; }
+__device__ __forceinline__ Pair<P_F32> mul(Pair<P_F32> a, Pair<P_F32> b) { return {__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)}; }
+__device__ __forceinline__ Pair<P_F16> add(Pair<P_F16> a, Pair<P_F16> b) { return {h2add(a.h, b.h)}; }
+__device__ __forceinline__ Pair<P_F16> sub(Pair<P_F16> a, Pair<P_F16> b) { return {h2sub(a.h, b.h)}; }
+__device__ __forceinline__ Pair<P_F16> mul(Pair<P_F16> a, Pair<P_F16> b) { return {h2mul(a.h, b.h)}; }
+
+// ---------------------------------------------------------------- inverse CDFs
+enum { ICDF_EXACT = 0, ICDF_TABLE = 1, ICDF_MLP = 2 };
+
+// Shared-memory copy of the piecewise-linear table, indexed by the biased
+// binary32 exponent E of v: v in [2^(E-127), 2^(E-126)) lies in interval
+// k = 126 - E (k = 1..15) or in interval 16 for E <= 110.  Entry E - 103
+// for E = 103..125 (v >= 2^-24 on the uniform grid).
+constexpr int TAB_ENTRIES = 23;
+struct SmemTable {
+    float2 c32[TAB_ENTRIES];     // (c0, c1) in binary32
+    __half2 c16[TAB_ENTRIES];    // (c0, c1) in binary16
+};
+
+// Entry index of v; CLAMP widens it to any v in (0, 1/2] (bulk API).
+template <bool CLAMP>
+__device__ __forceinline__ int tab_index(float v) {
+    int e = (int)(__float_as_uint(v) >> 23);
+    if (CLAMP) e = min(max(e, 103), 125);
+    return e - 103;
+}
+
+// Exact normal in FP32: Phi^-1(v) with the sign of the word's half.
+__device__ __forceinline__ float exact_z(uint32_t w) {
+    const float v = mirrored_v(w);
+    const float z = normcdfinvf(v);
+    return __uint_as_float(__float_as_uint(z) ^ (w & 0x80000000u));
+}
+
+// Piecewise-linear Z~ in binary32: z = R(c0 + R(c1 v)), negated for u > 1/2.
+template <bool CLAMP>
+__device__ __forceinline__ float table_z32(const SmemTable &s, uint32_t w, float v) {
+    const float2 c = s.c32[tab_index<CLAMP>(v)];
+    const float z = __fadd_rn(c.x, __fmul_rn(c.y, v));
+    return __uint_as_float(__float_as_uint(z) ^ (w & 0x80000000u));
+}
+
+// Piecewise-linear Z~ for two paths in binary16x2:
+// z = R16(R16(c0) + R16(R16(c1) R16(v))), negated for u > 1/2.
+template <bool CLAMP>
+__device__ __forceinline__ __half2 table_z16(const SmemTable &s, uint32_t w0, uint32_t w1, float v0, float v1) {
+    const __half2 t0 = s.c16[tab_index<CLAMP>(v0)];
+    const __half2 t1 = s.c16[tab_index<CLAMP>(v1)];
+    const __half2 c0 = __lows2half2(t0, t1);
+    const __half2 c1 = __highs2half2(t0, t1);
+    const __half2 v = __floats2half2_rn(v0, v1);
+    __half2 z = h2add(c0, h2mul(c1, v));
+    const uint32_t sgn = ((w0 >> 16) & 0x8000u) | (w1 & 0x80000000u);
+    uint32_t zb = *reinterpret_cast<uint32_t *>(&z) ^ sgn;
+    return *reinterpret_cast<__half2 *>(&zb);
+}
+
+}  // namespace mlmc

@@ -1,0 +1,233 @@
+// Level kernels: two-way and four-way MLMC differences (Sec. 3).
+//
+// One thread carries a pair of samples (paths 2g and 2g+1 of the level), so
+// that binary16 arithmetic runs packed as f16x2.  Path state lives in
+// registers for all 2^l fine steps; the piecewise-linear table sits in
+// shared memory; per-thread sums are reduced with warp shuffles in FP32,
+// across warps in FP64, and one FP64 (sum D, sum D^2) pair per block goes
+// to global memory for the finalize kernel.
+#pragma once
+
+#include "device.cuh"
+#include "mlp_device.cuh"
+
+namespace mlmc {
+
+enum { MODE_TWO = 0, MODE_FOUR = 1 };
+enum { SDE_GBM = 0, SDE_OU = 1 };
+enum { PAYOFF_X = 0, PAYOFF_CALL = 1 };
+
+struct LevelArgs {
+    int l;                    // level: 2^l fine steps
+    int payoff;
+    uint64_t npairs;          // ceil(N / 2)
+    uint64_t N;
+    uint64_t path_offset;
+    uint32_t tag, k0, k1;     // Philox counter tag and key (seed)
+    // per-level coefficients in FP64, rounded once to the working precision
+    // in the kernel: GBM drift = mu delta_f (fine) / mu 2 delta_f (coarse),
+    // diff = sigma sqrt(delta_f); OU drift = theta delta, diff = s sqrt(delta_f),
+    // mean = m.
+    double drift_f, drift_c, diff, mean, x0;
+    double K, disc;
+    const float2 *tab32;      // table in binary32, TAB_ENTRIES entries
+    const __half2 *tab16;     // table in binary16
+    const MlpWeights *mlp;    // network (ICDF_MLP only)
+    double2 *partials;        // one (sum D, sum D^2) per block
+    float *paths_out;         // optional per-sample output (3 or 5 floats per sample)
+};
+
+template <int P, bool KAHAN, int SDE>
+struct PathPair {
+    Pair<P> X, c, drift, diff, mean;
+
+    __device__ __forceinline__ void init(double drift_, double diff_, double mean_, double x0) {
+        drift = Pair<P>::of(drift_);
+        diff = Pair<P>::of(diff_);
+        mean = Pair<P>::of(mean_);
+        X = Pair<P>::of(x0);
+        c = Pair<P>::of(0.0);
+    }
+    // X <- X (+) (A (+) B): A = a delta, B = (b sqrt(delta)) (x) z  (Sec. 2.2);
+    // with Kahan compensation of the outer addition (Sec. 2.3, Algorithm 1).
+    __device__ __forceinline__ void step(Pair<P> z) {
+        Pair<P> A, B;
+        if (SDE == SDE_GBM) {
+            A = mul(drift, X);
+            B = mul(mul(diff, X), z);
+        } else {
+            A = mul(drift, sub(mean, X));
+            B = mul(diff, z);
+        }
+        const Pair<P> inc = add(A, B);
+        if (KAHAN) {
+            const Pair<P> y = sub(inc, c);
+            const Pair<P> t = add(X, y);
+            c = sub(sub(t, X), y);
+            X = t;
+        } else {
+            X = add(X, inc);
+        }
+    }
+};
+
+template <int P, int ICDF>
+__device__ __forceinline__ Pair<P> icdf_pair(const SmemTable &s, const MlpWeights *mlp, uint32_t w0, uint32_t w1) {
+    if (ICDF == ICDF_EXACT) {
+        if (P == P_F32) return Pair<P>::of2(exact_z(w0), exact_z(w1));
+        return Pair<P>::of2(exact_z(w0), exact_z(w1));
+    } else if (ICDF == ICDF_TABLE) {
+        const float v0 = mirrored_v(w0), v1 = mirrored_v(w1);
+        if constexpr (P == P_F32) {
+            return Pair<P>::of2(table_z32<false>(s, w0, v0), table_z32<false>(s, w1, v1));
+        } else {
+            return Pair<P>{table_z16<false>(s, w0, w1, v0, v1)};
+        }
+    } else {
+        const float2 z = mlp_z_pair(mlp, w0, w1);
+        return Pair<P>::of2(z.x, z.y);
+    }
+}
+
+// Payoff in binary32: X, or disc (x) max(X (-) K, 0).
+__device__ __forceinline__ float payoff_of(float X, int payoff, float K, float disc) {
+    if (payoff == PAYOFF_X) return X;
+    const float t = __fsub_rn(X, K);
+    return __fmul_rn(disc, t > 0.0f ? t : 0.0f);
+}
+
+template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
+__global__ void __launch_bounds__(256) level_kernel(const LevelArgs a) {
+    __shared__ SmemTable tab;
+    __shared__ double red[2][32];
+    if (ICDF == ICDF_TABLE) {
+        for (int i = threadIdx.x; i < TAB_ENTRIES; i += blockDim.x) {
+            tab.c32[i] = a.tab32[i];
+            tab.c16[i] = a.tab16[i];
+        }
+        __syncthreads();
+    }
+
+    const uint32_t nf = 1u << a.l;
+    const uint32_t ncalls = (nf + 3u) >> 2;
+    const float K = __double2float_rn(a.K), disc = __double2float_rn(a.disc);
+    float s1 = 0.0f, s2 = 0.0f;
+
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.npairs; g += stride) {
+        const uint64_t p0 = a.path_offset + 2 * g, p1 = p0 + 1;
+        PathPair<P, KAHAN, SDE> fine, coarse;
+        fine.init(a.drift_f, a.diff, a.mean, a.x0);
+        coarse.init(a.drift_c, a.diff, a.mean, a.x0);
+        PathPair<P_F32, true, SDE> hfine, hcoarse;       // exact-normal pair (four-way only)
+        if (MODE == MODE_FOUR) {
+            hfine.init(a.drift_f, a.diff, a.mean, a.x0);
+            hcoarse.init(a.drift_c, a.diff, a.mean, a.x0);
+        }
+        Pair<P> zprev;
+        Pair<P_F32> zhprev;
+
+        auto body = [&](uint32_t w0, uint32_t w1, int q) {
+            const Pair<P> z = icdf_pair<P, ICDF>(tab, a.mlp, w0, w1);
+            fine.step(z);
+            if (q & 1) coarse.step(add(zprev, z));
+            else zprev = z;
+            if (MODE == MODE_FOUR) {
+                const Pair<P_F32> zh = Pair<P_F32>::of2(exact_z(w0), exact_z(w1));
+                hfine.step(zh);
+                if (q & 1) hcoarse.step(add(zhprev, zh));
+                else zhprev = zh;
+            }
+        };
+
+        for (uint32_t j = 0; j < ncalls; ++j) {
+            const uint4 r0 = philox4x32_10(make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), j, a.tag), a.k0, a.k1);
+            const uint4 r1 = philox4x32_10(make_uint4((uint32_t)p1, (uint32_t)(p1 >> 32), j, a.tag), a.k0, a.k1);
+            if (nf >= 4) {
+                body(r0.x, r1.x, 0);
+                body(r0.y, r1.y, 1);
+                body(r0.z, r1.z, 2);
+                body(r0.w, r1.w, 3);
+            } else {
+                body(r0.x, r1.x, 0);
+                if (nf == 2) body(r0.y, r1.y, 1);
+            }
+        }
+
+        const float2 xf = fine.X.f32(), xc = coarse.X.f32();
+        float d0, d1;
+        float out0[5], out1[5];
+        if (MODE == MODE_TWO) {
+            const float pf0 = payoff_of(xf.x, a.payoff, K, disc), pf1 = payoff_of(xf.y, a.payoff, K, disc);
+            float pc0 = 0.0f, pc1 = 0.0f;
+            if (a.l > 0) {
+                pc0 = payoff_of(xc.x, a.payoff, K, disc);
+                pc1 = payoff_of(xc.y, a.payoff, K, disc);
+                d0 = __fsub_rn(pf0, pc0);
+                d1 = __fsub_rn(pf1, pc1);
+            } else {
+                d0 = pf0;
+                d1 = pf1;
+            }
+            out0[0] = pf0; out0[1] = pc0; out0[2] = d0;
+            out1[0] = pf1; out1[1] = pc1; out1[2] = d1;
+        } else {
+            const float2 hf = hfine.X.f32(), hc = hcoarse.X.f32();
+            const float phf0 = payoff_of(hf.x, a.payoff, K, disc), phf1 = payoff_of(hf.y, a.payoff, K, disc);
+            const float pbf0 = payoff_of(xf.x, a.payoff, K, disc), pbf1 = payoff_of(xf.y, a.payoff, K, disc);
+            float phc0 = 0.0f, phc1 = 0.0f, pbc0 = 0.0f, pbc1 = 0.0f;
+            if (a.l > 0) {
+                phc0 = payoff_of(hc.x, a.payoff, K, disc);
+                phc1 = payoff_of(hc.y, a.payoff, K, disc);
+                pbc0 = payoff_of(xc.x, a.payoff, K, disc);
+                pbc1 = payoff_of(xc.y, a.payoff, K, disc);
+            }
+            d0 = __fsub_rn(__fsub_rn(phf0, phc0), __fsub_rn(pbf0, pbc0));
+            d1 = __fsub_rn(__fsub_rn(phf1, phc1), __fsub_rn(pbf1, pbc1));
+            out0[0] = phf0; out0[1] = phc0; out0[2] = pbf0; out0[3] = pbc0; out0[4] = d0;
+            out1[0] = phf1; out1[1] = phc1; out1[2] = pbf1; out1[3] = pbc1; out1[4] = d1;
+        }
+        const bool valid1 = 2 * g + 1 < a.N;
+        s1 += d0;
+        s2 += d0 * d0;
+        if (valid1) {
+            s1 += d1;
+            s2 += d1 * d1;
+        }
+        if (a.paths_out != nullptr) {
+            constexpr int W = MODE == MODE_TWO ? 3 : 5;
+            float *o = a.paths_out + (2 * g) * W;
+#pragma unroll
+            for (int k = 0; k < W; ++k) o[k] = out0[k];
+            if (valid1) {
+#pragma unroll
+                for (int k = 0; k < W; ++k) o[W + k] = out1[k];
+            }
+        }
+    }
+
+    // warp reduction in FP32, then FP64 across warps
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][warp] = (double)s1;
+        red[1][warp] = (double)s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t1 += red[0][w];
+            t2 += red[1][w];
+        }
+        a.partials[blockIdx.x] = make_double2(t1, t2);
+    }
+}
+
+using LevelKernelFn = void (*)(LevelArgs);
+
+}  // namespace mlmc

@@ -1,0 +1,176 @@
+// Small kernels: table construction, finalize reduction, and the bulk RNG /
+// inverse-CDF entry points.
+#include <math.h>
+
+#include "internal.h"
+#include "level_kernels.cuh"
+
+namespace mlmc {
+
+// ---------------------------------------------------------------- table
+// L2 (uniform-measure) linear fit of Phi^-1 on each interval [a, b) of
+// v = min(u, 1-u): I_k = [2^-(k+1), 2^-k) for k = 1..15, I_16 = (0, 2^-16)
+// (Sec. 2.1; the construction is deferred by the paper to its cited work,
+// this is the least-squares reading).  The moments have closed forms in
+// z = Phi^-1(v):
+//   int_a^b Phi^-1(v) dv   = phi(z_a) - phi(z_b)
+//   int_a^b v Phi^-1(v) dv = [ -phi(z) Phi(z) + Phi(sqrt(2) z) / (2 sqrt(pi)) ]_{z_a}^{z_b}
+// and the normal equations are solved in centred form.
+__global__ void build_table_kernel(double *t64, float2 *t32, __half2 *t16) {
+    __shared__ double c[32];
+    const int i = threadIdx.x;
+    if (i < 16) {
+        const int k = i + 1;
+        const double b = ldexp(1.0, -k);
+        const double a = k < 16 ? ldexp(1.0, -(k + 1)) : 0.0;
+        const double inv_sqrt2pi = 0.39894228040143267794;
+        const double inv_2sqrtpi = 0.28209479177387814347;
+        const double zb = normcdfinv(b);
+        const double phib = inv_sqrt2pi * exp(-0.5 * zb * zb);
+        double F0 = -phib;
+        double F1 = -phib * b + inv_2sqrtpi * normcdf(1.41421356237309504880 * zb);
+        if (a > 0.0) {
+            const double za = normcdfinv(a);
+            const double phia = inv_sqrt2pi * exp(-0.5 * za * za);
+            F0 += phia;
+            F1 -= -phia * a + inv_2sqrtpi * normcdf(1.41421356237309504880 * za);
+        }
+        const double M0 = b - a;
+        const double vbar = 0.5 * (a + b);
+        const double Svv = M0 * M0 * M0 / 12.0;
+        const double c1 = (F1 - vbar * F0) / Svv;
+        const double c0 = F0 / M0 - c1 * vbar;
+        c[2 * i] = c0;
+        c[2 * i + 1] = c1;
+        t64[2 * i] = c0;
+        t64[2 * i + 1] = c1;
+    }
+    __syncthreads();
+    if (i < TAB_ENTRIES) {
+        const int E = 103 + i;                       // biased exponent of v
+        const int interval = min(126 - E, 16) - 1;   // 0-based
+        const double c0 = c[2 * interval], c1 = c[2 * interval + 1];
+        t32[i] = make_float2(__double2float_rn(c0), __double2float_rn(c1));
+        t16[i] = __halves2half2(f64_to_f16(c0), f64_to_f16(c1));
+    }
+}
+
+cudaError_t launch_build_table(double *t64, float2 *t32, __half2 *t16, cudaStream_t s) {
+    build_table_kernel<<<1, 32, 0, s>>>(t64, t32, t16);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- finalize
+// Deterministic FP64 sum of per-block partials: fixed strided split across
+// 256 threads, then a fixed tree.  out[0] = sum D, out[1] = sum D^2.
+__global__ void __launch_bounds__(256) finalize_kernel(const double2 *partials, int nblocks, double *out) {
+    __shared__ double r1[256], r2[256];
+    double t1 = 0.0, t2 = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += 256) {
+        t1 += partials[i].x;
+        t2 += partials[i].y;
+    }
+    r1[threadIdx.x] = t1;
+    r2[threadIdx.x] = t2;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            r1[threadIdx.x] += r1[threadIdx.x + h];
+            r2[threadIdx.x] += r2[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = r1[0];
+        out[1] = r2[0];
+    }
+}
+
+cudaError_t launch_finalize(const double2 *partials, int nblocks, double *out, cudaStream_t s) {
+    finalize_kernel<<<1, 256, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- bulk RNG
+__global__ void philox_bulk_kernel(const uint4 *ctr, const uint2 *key, uint4 *out, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = philox4x32_10(ctr[i], key[i].x, key[i].y);
+}
+
+__global__ void uniform_bulk_kernel(const uint32_t *w, float *u, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        u[i] = uniform_of(w[i]);
+}
+
+static int bulk_grid(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
+cudaError_t launch_philox_bulk(const uint32_t *ctr, const uint32_t *key, uint32_t *out, size_t n, cudaStream_t s) {
+    philox_bulk_kernel<<<bulk_grid(n), 256, 0, s>>>(reinterpret_cast<const uint4 *>(ctr),
+                                                     reinterpret_cast<const uint2 *>(key),
+                                                     reinterpret_cast<uint4 *>(out), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uniform_bulk(const uint32_t *w, float *u, size_t n, cudaStream_t s) {
+    uniform_bulk_kernel<<<bulk_grid(n), 256, 0, s>>>(w, u, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- bulk inverse CDF
+// Any u in (0, 1): v = min(u, 1-u) is exact in binary32 (1 - u is exact for
+// u >= 1/2), the sign comes from u > 1/2.
+template <int P, int ICDF>
+__global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const float2 *tab32, const __half2 *tab16,
+                                 const MlpWeights *mlp) {
+    __shared__ SmemTable tab;
+    for (int i = threadIdx.x; i < TAB_ENTRIES; i += blockDim.x) {
+        tab.c32[i] = tab32[i];
+        tab.c16[i] = tab16[i];
+    }
+    __syncthreads();
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float ui = u[i];
+        const bool upper = ui > 0.5f;
+        const float v = upper ? __fsub_rn(1.0f, ui) : ui;
+        const uint32_t sgn = upper ? 0x80000000u : 0u;
+        float r32;
+        if (ICDF == ICDF_EXACT) {
+            r32 = __uint_as_float(__float_as_uint(normcdfinvf(v)) ^ sgn);
+        } else if (ICDF == ICDF_TABLE) {
+            if (P == P_F16) {
+                const __half2 h = table_z16<true>(tab, sgn, sgn, v, v);
+                static_cast<__half *>(z)[i] = __low2half(h);
+                continue;
+            }
+            r32 = table_z32<true>(tab, sgn, v);
+        } else {
+            // the MLP reads the sign from the word's top bit and v from its
+            // remaining bits; pass the float path through the same evaluation
+            r32 = mlp_z_from_v(mlp, v, upper);
+        }
+        if (P == P_F32) static_cast<float *>(z)[i] = r32;
+        else static_cast<__half *>(z)[i] = __float2half_rn(r32);
+    }
+}
+
+cudaError_t launch_icdf_bulk(const float *u, void *z, size_t n, int icdf, int prec, const float2 *tab32,
+                             const __half2 *tab16, const MlpWeights *mlp, cudaStream_t s) {
+    const int g = bulk_grid(n);
+#define MLMC_ICDF_CASE(PP, II) icdf_bulk_kernel<PP, II><<<g, 256, 0, s>>>(u, z, n, tab32, tab16, mlp)
+    if (prec == P_F32) {
+        if (icdf == ICDF_EXACT) MLMC_ICDF_CASE(P_F32, ICDF_EXACT);
+        else if (icdf == ICDF_TABLE) MLMC_ICDF_CASE(P_F32, ICDF_TABLE);
+        else MLMC_ICDF_CASE(P_F32, ICDF_MLP);
+    } else {
+        if (icdf == ICDF_EXACT) MLMC_ICDF_CASE(P_F16, ICDF_EXACT);
+        else if (icdf == ICDF_TABLE) MLMC_ICDF_CASE(P_F16, ICDF_TABLE);
+        else MLMC_ICDF_CASE(P_F16, ICDF_MLP);
+    }
+#undef MLMC_ICDF_CASE
+    return cudaGetLastError();
+}
+
+}  // namespace mlmc

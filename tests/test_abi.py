@@ -1,0 +1,77 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point that
+include/mlmc.h declares, rejects invalid arguments before any launch, and
+its host-only sample allocation matches the oracle's (Sec. 3)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2012_09739_gb300 as M
+from paper_2012_09739_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return M.load()
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "mlmc.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^(?:mlmc_status|const char \*)\s*(\w+)\(", text, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["mlmc_level", "mlmc_nested_level", "approx_icdf", "mlmc_run", "mlmc_batch", "mlmc_mlp_train"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    # and the binding wraps each of them
+    assert sorted(M.exported_symbols()) == sorted(_declared())
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    p = M.sde_params()
+    out = M.mlmc_sums()
+    bad = [
+        (19, 10, 0, 0, 0, p),       # level above 18
+        (-1, 10, 0, 0, 0, p),
+        (3, 0, 0, 0, 0, p),         # N = 0
+        (3, 10, 7, 0, 0, p),        # precision
+        (3, 10, 0, 0, 5, p),        # icdf kind
+        (3, 10, 0, 0, 0, M.sde_params(p1=-0.2)),     # sigma <= 0
+        (3, 10, 0, 0, 0, M.sde_params(T=0.0)),
+        (3, 10, 0, 0, 0, M.sde_params(p0=float("nan"))),
+        (3, 10, 0, 0, 0, M.sde_params(sde=M.MLMC_OU, p2=0.0)),
+    ]
+    for l, N, prec, kahan, icdf, params in bad:
+        st = lib.mlmc_level(l, N, prec, kahan, icdf, ctypes.byref(params), 1, 0, ctypes.byref(out), None)
+        assert st == M.MLMC_EINVAL, (l, N, prec, icdf)
+        assert lib.mlmc_last_error()
+    st = lib.mlmc_nested_level(3, 10, 0, 0, M.MLMC_ICDF_EXACT, ctypes.byref(p), 1, 0, ctypes.byref(out), None)
+    assert st == M.MLMC_EINVAL
+    st = lib.mlmc_level(3, 10, 0, 0, 0, None, 1, 0, ctypes.byref(out), None)
+    assert st == M.MLMC_EINVAL
+    assert lib.mlmc_strerror(M.MLMC_ETIMEOUT) == b"timeout"
+
+
+def test_optimal_samples_match_oracle(lib):
+    from oracle import mlmc
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        n = int(rng.integers(1, 19))
+        V = rng.uniform(1e-8, 1e-1, n)
+        C = rng.uniform(1.0, 1e4, n)
+        eps = float(rng.uniform(1e-4, 1e-2))
+        assert np.array_equal(M.mlmc_optimal_samples(V, C, eps).astype(np.int64), mlmc.optimal_samples(V, C, eps))
+    with pytest.raises(M.MlmcError):
+        M.mlmc_optimal_samples([1.0], [0.0], 1e-3)

@@ -1,0 +1,282 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Bit-exact: Philox words, uniforms, the binary32/binary16 table coefficients,
+the approximate normals, and every per-path output of the low-precision
+("bar") paths against the oracle's per-operation rounding emulation.
+Within tolerance: exact-normal FP32 paths against FP64 (1e-5 relative), and
+FP16 + Kahan paths against FP64 (2e-3 relative), per path, with
+|error| <= tol * max(1, |P_fine|).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle as O  # noqa: E402
+import paper_2012_09739_gb300 as M  # noqa: E402
+
+SEED = 1234
+TOL32, TOL16K = 1e-5, 2e-3
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _orc_sde(p):
+    return O.SDE(p.sde, p.payoff, p.p0, p.p1, p.p2, p.x0, p.T, p.K, p.disc)
+
+
+def gpu_paths(four, l, N, prec, kahan, icdf, params, seed=SEED, offset=0):
+    w = 5 if four else 3
+    out = torch.empty(N * w, dtype=torch.float32, device=_dev())
+    M.mlmc_level_paths(four, l, N, prec, kahan, icdf, params, seed, offset, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64).reshape(N, w)
+
+
+def _bar_variant(prec, kahan, icdf=O.RV_TABLE):
+    return O.variant(prec=O.F16 if prec == M.MLMC_F16 else O.F32, kahan=kahan, rv=icdf)
+
+
+def _kind_tag(four, icdf, l):
+    kind = O.KIND_FOUR if four else (O.KIND_STD if icdf == M.MLMC_ICDF_EXACT else O.KIND_APPROX)
+    return O.make_tag(kind, l)
+
+
+# ------------------------------------------------------------------ RNG
+
+
+def test_philox_bitexact():
+    dev = _dev()
+    rng = np.random.default_rng(0)
+    n = 100003
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0], key[0] = 0, 0
+    ctr[1], key[1] = 0xFFFFFFFF, 0xFFFFFFFF
+    out = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    M.mlmc_philox4x32_10(torch.from_numpy(ctr.view(np.int32)).to(dev), torch.from_numpy(key.view(np.int32)).to(dev),
+                         out)
+    torch.cuda.synchronize()
+    assert np.array_equal(_u32(out), O.philox4x32_10(ctr, key))
+
+
+def test_uniforms_bitexact():
+    dev = _dev()
+    w = np.random.default_rng(1).integers(0, 2 ** 32, size=1 << 20, dtype=np.uint64).astype(np.uint32)
+    w[:4] = [0, 0xFFFFFFFF, 0x80000000, 0x7FFFFFFF]
+    u = torch.empty(w.size, dtype=torch.float32, device=dev)
+    M.mlmc_uniforms(torch.from_numpy(w.view(np.int32)).to(dev), u)
+    torch.cuda.synchronize()
+    assert np.array_equal(u.cpu().numpy().astype(np.float64), O.uniforms(w))
+
+
+# ------------------------------------------------------------------ table and inverse CDFs
+
+
+def test_table_matches_oracle(pl_table):
+    _dev()
+    c64, c32, c16 = M.mlmc_icdf_table()
+    assert np.allclose(c64, pl_table, rtol=1e-11, atol=0)
+    assert np.array_equal(c32.astype(np.float64), O.round_bits(pl_table, O.F32).reshape(16, 2))
+    assert np.array_equal(c16.view(np.float16).astype(np.float64), O.round_bits(pl_table, O.F16).reshape(16, 2))
+
+
+@pytest.mark.parametrize("prec", [M.MLMC_F32, M.MLMC_F16])
+def test_approx_icdf_table_bitexact(prec, pl_table):
+    dev = _dev()
+    rng = np.random.default_rng(2)
+    u = np.concatenate([(2 * rng.integers(0, 1 << 23, 200000) + 1) * 2.0 ** -24,
+                        [2.0 ** -24, 1 - 2.0 ** -24, 0.5 - 2.0 ** -24, 0.25, 0.75, 2.0 ** -16, 2.0 ** -17,
+                         3e-9, 0.5]]).astype(np.float32)
+    ut = torch.from_numpy(u).to(dev)
+    z = torch.empty(u.size, dtype=torch.float32 if prec == M.MLMC_F32 else torch.float16, device=dev)
+    M.approx_icdf(ut, z, M.MLMC_ICDF_TABLE, prec)
+    torch.cuda.synchronize()
+    oprec = O.F32 if prec == M.MLMC_F32 else O.F16
+    ref = O.approx_icdf(u.astype(np.float64), O.RV_TABLE, prec=oprec, table=pl_table)
+    assert np.array_equal(z.cpu().numpy().astype(np.float64), ref)
+
+
+def test_exact_icdf_fp32_accuracy():
+    dev = _dev()
+    lower = (2 * np.arange(0, 1 << 22, 7) + 1) * 2.0 ** -24          # grid points below 1/2
+    u = np.concatenate([lower, 1.0 - lower]).astype(np.float32)
+    z = torch.empty(u.size, dtype=torch.float32, device=dev)
+    M.approx_icdf(torch.from_numpy(u).to(dev), z, M.MLMC_ICDF_EXACT, M.MLMC_F32)
+    torch.cuda.synchronize()
+    zz = z.cpu().numpy()
+    ref = O.ndtri(u.astype(np.float64))
+    err = np.abs(zz - ref) / np.maximum(np.abs(ref), 1e-30)
+    assert err.max() < 4 * 2.0 ** -23          # a few binary32 ulp
+    assert np.all(zz[lower.size:] == -zz[:lower.size])
+
+
+# ------------------------------------------------------------------ per-path parity
+
+
+GBM_CALL = dict(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+GBM_X = dict(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_X, p0=0.05, p1=0.2)
+OU_X = dict(sde=M.MLMC_OU, payoff=M.MLMC_PAYOFF_X, p0=2.0, p1=0.3, p2=0.5, x0=1.0)
+
+
+@pytest.mark.parametrize("prec", [M.MLMC_F16, M.MLMC_F32])
+@pytest.mark.parametrize("kahan", [True, False])
+@pytest.mark.parametrize("l", [0, 1, 2, 5, 9])
+@pytest.mark.parametrize("sde", ["gbm_call", "ou_x"])
+def test_twoway_table_paths_bitexact(prec, kahan, l, sde, pl_table):
+    params = M.sde_params(**(GBM_CALL if sde == "gbm_call" else OU_X))
+    N = 1537                                  # several blocks' worth of pairs and an odd tail
+    got = gpu_paths(0, l, N, prec, kahan, M.MLMC_ICDF_TABLE, params, offset=77)
+    ref = O.twoway_paths(l, np.arange(77, 77 + N), _bar_variant(prec, kahan), _orc_sde(params), SEED,
+                         _kind_tag(0, M.MLMC_ICDF_TABLE, l), table=pl_table)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("prec", [M.MLMC_F16, M.MLMC_F32])
+@pytest.mark.parametrize("kahan", [True, False])
+@pytest.mark.parametrize("l", [0, 1, 3, 8])
+def test_fourway_table_paths(prec, kahan, l, pl_table):
+    params = M.sde_params(**GBM_CALL)
+    N = 1025
+    got = gpu_paths(1, l, N, prec, kahan, M.MLMC_ICDF_TABLE, params)
+    ref = O.fourway_paths(l, np.arange(N), O.variant(), _bar_variant(prec, kahan), _orc_sde(params), SEED,
+                          _kind_tag(1, M.MLMC_ICDF_TABLE, l), table=pl_table)
+    # bar pair: bit-exact against the emulation
+    assert np.array_equal(got[:, 2:4], ref[:, 2:4])
+    # hat pair: FP32 + Kahan with exact normals against FP64
+    scale = np.maximum(1.0, np.abs(ref[:, 0]))
+    assert np.all(np.abs(got[:, 0:2] - ref[:, 0:2]) <= TOL32 * scale[:, None])
+    assert np.all(np.abs(got[:, 4] - ref[:, 4]) <= 2 * TOL32 * scale)
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 4, 6])
+@pytest.mark.parametrize("kahan", [False, True])
+def test_twoway_exact_fp32_within_1e5(l, kahan):
+    params = M.sde_params(**GBM_X)
+    N = 2049
+    got = gpu_paths(0, l, N, M.MLMC_F32, kahan, M.MLMC_ICDF_EXACT, params)
+    ref = O.twoway_paths(l, np.arange(N), O.variant(), _orc_sde(params), SEED, _kind_tag(0, 0, l))
+    scale = np.maximum(1.0, np.abs(ref[:, 0]))
+    assert np.all(np.abs(got - ref) <= TOL32 * scale[:, None])
+
+
+@pytest.mark.parametrize("l", [2, 6, 10, 12])
+def test_fp16_kahan_against_fp64_within_2e3(l, pl_table):
+    params = M.sde_params(**GBM_CALL)
+    N = 1024 if l < 12 else 256
+    got = gpu_paths(0, l, N, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, params)
+    ref = O.twoway_paths(l, np.arange(N), O.variant(rv=O.RV_TABLE), _orc_sde(params), SEED,
+                         _kind_tag(0, M.MLMC_ICDF_TABLE, l), table=pl_table)
+    scale = np.maximum(1.0, np.abs(ref[:, 0]))
+    err = np.abs(got - ref) / scale[:, None]
+    assert err.max() <= TOL16K, err.max()
+
+
+# ------------------------------------------------------------------ sums and statistics
+
+
+@pytest.mark.parametrize("four", [0, 1])
+def test_sums_equal_per_path_sums(four):
+    params = M.sde_params(**GBM_CALL)
+    N, l = 100001, 4
+    paths = gpu_paths(four, l, N, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, params)
+    fn = M.mlmc_nested_level if four else M.mlmc_level
+    s = fn(l, N, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, params, SEED)
+    d = paths[:, -1]
+    assert s.n == N
+    assert abs(s.s1 - d.sum()) <= 1e-5 * np.abs(d).sum()
+    assert abs(s.s2 - (d * d).sum()) <= 1e-5 * (d * d).sum()
+
+
+def test_deterministic_repeat():
+    params = M.sde_params(**GBM_CALL)
+    a = M.mlmc_nested_level(6, 300000, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, params, SEED)
+    b = M.mlmc_nested_level(6, 300000, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, params, SEED)
+    assert (a.s1, a.s2) == (b.s1, b.s2)
+
+
+@pytest.mark.parametrize("l", [0, 1, 3, 6])
+def test_config1_level_means_closed_form(l):
+    """Plain MLMC, GBM, P = X, FP32 exact normals, N = 1e5: level mean and
+    variance within statistical error of the exact Euler moments."""
+    from oracle import mlmc
+    params = M.sde_params(**GBM_X)
+    N = 100000
+    s = M.mlmc_level(l, N, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, params, SEED)
+    em, ev = mlmc.euler_twoway_moments(l)
+    assert abs(s.mean() - em) < 4 * math.sqrt(ev / N)
+    assert abs(s.var() / ev - 1) < 0.05
+
+
+def test_level_sums_match_oracle_sums(pl_table):
+    params = M.sde_params(**GBM_CALL)
+    N, l = 20000, 5
+    s = M.mlmc_level(l, N, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, params, SEED)
+    o1, o2 = O.level_sums(l, N, 0, _bar_variant(M.MLMC_F16, True), _orc_sde(params), SEED,
+                          _kind_tag(0, 1, l), table=pl_table, nthreads=4)
+    assert abs(s.s1 - o1) <= 1e-6 * (abs(o1) + math.sqrt(o2))
+    assert abs(s.s2 - o2) <= 1e-6 * o2
+
+
+# ------------------------------------------------------------------ full size, sampled
+
+
+def test_full_size_level12_sampled_paths(pl_table):
+    """N = 2^20 at l = 12 in the bench's launch configuration: per-path outputs
+    of sampled samples against the oracle computing those samples alone."""
+    params = M.sde_params(**GBM_CALL)
+    N, l = 1 << 20, 12
+    got = gpu_paths(1, l, N, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, params)
+    idx = np.unique(np.concatenate([np.random.default_rng(3).integers(0, N, 48), [0, 1, N - 2, N - 1]]))
+    ref = O.fourway_paths(l, idx, O.variant(), _bar_variant(M.MLMC_F16, True), _orc_sde(params), SEED,
+                          _kind_tag(1, 1, l), table=pl_table)
+    assert np.array_equal(got[idx, 2:4], ref[:, 2:4])
+    scale = np.maximum(1.0, np.abs(ref[:, 0]))
+    assert np.all(np.abs(got[idx, 0:2] - ref[:, 0:2]) <= TOL32 * scale[:, None])
+    # every sample's D is the FP32 combination of its four payoffs
+    f = got.astype(np.float32)
+    d = (f[:, 0] - f[:, 1]) - (f[:, 2] - f[:, 3])
+    assert np.array_equal(d, f[:, 4])
+    # fine payoffs: Black-Scholes within statistical error plus the Euler weak
+    # bias at l = 12 (hat) and the binary16 rounding bias (bar)
+    from oracle import mlmc
+    bs = mlmc.bs_call()
+    for col, extra in ((0, 2e-4), (2, 2e-3)):
+        p = got[:, col]
+        assert abs(p.mean() - bs) < 5 * p.std() / math.sqrt(N) + extra
+
+
+def test_edge_cases(pl_table):
+    params = M.sde_params(**GBM_CALL)
+    # N = 1 (a single sample, half of a pair) and the deepest level with few samples
+    got = gpu_paths(0, 3, 1, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, params, offset=5)
+    ref = O.twoway_paths(3, [5], _bar_variant(M.MLMC_F16, True), _orc_sde(params), SEED, _kind_tag(0, 1, 3),
+                         table=pl_table)
+    assert np.array_equal(got, ref)
+    got = gpu_paths(0, 18, 3, M.MLMC_F32, True, M.MLMC_ICDF_TABLE, params, offset=2 ** 33 + 1)
+    ref = O.twoway_paths(18, 2 ** 33 + 1 + np.arange(3), _bar_variant(M.MLMC_F32, True), _orc_sde(params), SEED,
+                         _kind_tag(0, 1, 18), table=pl_table)
+    assert np.array_equal(got, ref)
+    s = M.mlmc_level(0, 1, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, params, SEED)
+    assert s.n == 1 and s.var() == 0.0
+
+
+def test_invalid_arguments_raise():
+    _dev()
+    params = M.sde_params(**GBM_CALL)
+    with pytest.raises(M.MlmcError) as e:
+        M.mlmc_level(19, 10, M.MLMC_F32, False, 0, params, SEED)
+    assert e.value.status == M.MLMC_EINVAL
+    with pytest.raises(M.MlmcError):
+        M.mlmc_nested_level(3, 10, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, params, SEED)
