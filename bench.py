@@ -35,8 +35,8 @@ WORKLOAD = "GBM call, levels 0..12, N=2^20 per level, two-way + four-way, FP16+K
 
 # Algorithmic lane-instructions per fine path-step (one sample of one
 # estimator), counted from the method's operations; derivation in the design doc.
-OPS_FOURWAY_F16K_TABLE = 74.5
-OPS_TWOWAY_F16K_TABLE = 32.25
+OPS_FOURWAY_F16K_TABLE = 53.75
+OPS_TWOWAY_F16K_TABLE = 24.25
 
 
 def _env_rank():
