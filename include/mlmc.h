@@ -104,6 +104,28 @@ mlmc_status mlmc_level_async(int four, int l, uint64_t N, int prec, int kahan, i
                              const mlmc_sde_params *params, uint64_t seed, uint64_t path_offset,
                              double *sums_dev, void *stream);
 
+/* Allocation-free variant of mlmc_level_async (no counterpart in the paper:
+ * it exists for callers that cannot allocate device memory when they ask for
+ * an estimate -- e.g. a service that hands all of HBM to its own allocator at
+ * start-up, or a latency-critical loop where an allocation could synchronise
+ * the device or fail).  It calls no cudaMalloc, cudaFree or other allocating
+ * routine: its scratch (one FP64 pair per block of 256 threads, one sample
+ * pair per thread) is a fixed 64 KiB file-scope device array, held by every
+ * GPU that loads the library until the process exits, and it uses a private
+ * copy of the table in the same way.
+ *   - N <= 2,097,152 (the scratch holds 4096 blocks); larger N, or
+ *     icdf = MLP, gives MLMC_EINVAL with a message.
+ *   - The first call on a device does the set-up (looks up the arrays'
+ *     device addresses, builds the private table on `stream` and waits for
+ *     it); make that first call before any stream capture.
+ *   - All calls share the one scratch array, which keeps the last call's
+ *     contents: calls that overlap on the GPU (e.g. on different streams
+ *     without ordering) race and give wrong sums.
+ * Writes {sum D, sum D^2} to sums_dev; same arguments as mlmc_level_async. */
+mlmc_status mlmc_level_noalloc(int four, int l, uint64_t N, int prec, int kahan, int icdf,
+                               const mlmc_sde_params *params, uint64_t seed, uint64_t path_offset,
+                               double *sums_dev, void *stream);
+
 /* Per-path diagnostics of the same computation: writes, for sample i,
  * out_dev[i*3 + {0,1,2}] = (P_fine, P_coarse, D) for the two-way difference
  * (four = 0) or out_dev[i*5 + {0..4}] = (P^_f, P^_c, P-_f, P-_c, D) for the

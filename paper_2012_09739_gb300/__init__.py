@@ -83,6 +83,7 @@ _SIGS = {
     "mlmc_level": [_i32, _u64, _i32, _i32, _i32, _P(mlmc_sde_params), _u64, _u64, _P(mlmc_sums), _vp],
     "mlmc_nested_level": [_i32, _u64, _i32, _i32, _i32, _P(mlmc_sde_params), _u64, _u64, _P(mlmc_sums), _vp],
     "mlmc_level_async": [_i32, _i32, _u64, _i32, _i32, _i32, _P(mlmc_sde_params), _u64, _u64, _vp, _vp],
+    "mlmc_level_noalloc": [_i32, _i32, _u64, _i32, _i32, _i32, _P(mlmc_sde_params), _u64, _u64, _vp, _vp],
     "mlmc_level_paths": [_i32, _i32, _u64, _i32, _i32, _i32, _P(mlmc_sde_params), _u64, _u64, _vp, _vp],
     "approx_icdf": [_vp, _vp, ctypes.c_size_t, _i32, _i32, _vp],
     "mlmc_philox4x32_10": [_vp, _vp, _vp, ctypes.c_size_t, _vp],
@@ -167,6 +168,12 @@ def mlmc_level_async(four, l, N, prec, kahan, icdf, params, seed, path_offset, s
     """sums_dev: float64 CUDA tensor with >= 2 elements (receives sum D, sum D^2)."""
     _check(load().mlmc_level_async(int(four), l, N, prec, int(kahan), icdf, ctypes.byref(params), seed,
                                    path_offset, _dptr(sums_dev), _stream(stream)))
+
+
+def mlmc_level_noalloc(four, l, N, prec, kahan, icdf, params, seed, path_offset, sums_dev, stream=None):
+    """Allocation-free variant of mlmc_level_async (fixed device scratch, N <= 2^21)."""
+    _check(load().mlmc_level_noalloc(int(four), l, N, prec, int(kahan), icdf, ctypes.byref(params), seed,
+                                     path_offset, _dptr(sums_dev), _stream(stream)))
 
 
 def mlmc_level_paths(four, l, N, prec, kahan, icdf, params, seed, path_offset, out_dev, stream=None):
