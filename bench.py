@@ -206,6 +206,12 @@ def run_gpu(args):
         e2e_s = float(t.item())
     e2e_value = ps_step * args.steps * world / e2e_s if not args.no_e2e else None
 
+    # --- batching workload: 128 sets x 17 levels x (two-way + four-way), one launch
+    batch = None if args.no_batch else batch_leg(M, torch, stream)
+
+    # --- time to RMSE eps through mlmc_run: nested FP16+Kahan vs plain FP32
+    tte = None if args.no_tte else time_to_eps(M, params, args.eps)
+
     # --- roofline of the dominant kernel (four-way FP16+Kahan table)
     clk = clocks.summary()
     four_ms = sum(per_item[i][0] for i, it in enumerate(items) if it[0] == 1)
@@ -246,6 +252,8 @@ def run_gpu(args):
                      "launches": four_launches},
         "e2e": {"value": e2e_value, "unit": "path-steps/s", "h2d_bytes_per_step": len(items) * 64,
                 "d2h_bytes_per_step": len(items) * 16},
+        "time_to_eps": tte,
+        "batching": batch,
         "gpu_launches": 2 * len(items) * args.steps,
         "clocks": clk,
     }
@@ -255,6 +263,72 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(line))
+
+
+def batch_leg(M, torch, stream, repeats=5):
+    """The batching workload (64 GBM + 64 OU sets, levels 0..16, uneven N_l,
+    FP16 + Kahan table, two-way + four-way) through mlmc_batch (one persistent
+    launch replayed from a captured graph), against the same items launched
+    one by one through mlmc_level_async."""
+    from workloads import batching_sets, batch_level_samples
+    sets = batching_sets()
+    Ns = batch_level_samples()
+    items = []
+    for k, s in enumerate(sets):
+        if s["kind"] == "gbm":
+            p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=s["mu"], p1=s["sigma"], K=s["K"])
+        else:
+            p = M.sde_params(sde=M.MLMC_OU, payoff=M.MLMC_PAYOFF_X, p0=s["theta"], p1=s["m"], p2=s["s"], disc=1.0)
+        for l in range(len(Ns)):
+            for kind in (0, 1):
+                items.append(M.mlmc_work(p, l, kind, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, k, Ns[l], 0))
+    ps = sum(it.N * (1 << it.l) for it in items)
+    M.mlmc_batch(items, SEED)            # tunes, captures the graph
+    M.mlmc_batch(items, SEED)
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        M.mlmc_batch(items, SEED)
+        times.append(time.perf_counter() - t0)
+    t_batch = statistics.median(times)
+    sums = torch.zeros(2 * len(items), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    seq = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        for i, it in enumerate(items):
+            M.mlmc_level_async(it.kind, it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED, 0, sums[2 * i:],
+                               stream.cuda_stream)
+        torch.cuda.synchronize()
+        seq.append(time.perf_counter() - t0)
+    t_seq = min(seq)
+    return {"items": len(items), "path_steps": ps, "seconds": t_batch, "path_steps_per_s": ps / t_batch,
+            "one_launch_per_item_seconds": t_seq, "speedup_vs_one_launch_per_item": t_seq / t_batch,
+            "timing": "wall clock around the synchronous mlmc_batch call (graph replay), median of 5"}
+
+
+def time_to_eps(M, params, eps, repeats=3):
+    """Wall time of mlmc_run to RMSE eps: nested estimator (FP16 + Kahan,
+    table) against the standard estimator (FP32, exact normals, plain Euler).
+    Median of `repeats` runs with different seeds, after one untimed run."""
+    out = {"eps": eps}
+    for name, est, prec, kahan in (("nested_f16_kahan_table", 1, M.MLMC_F16, 1),
+                                   ("plain_fp32_exact", 0, M.MLMC_F32, 0)):
+        times, res = [], None
+        for rep in range(repeats + 1):
+            o = M.mlmc_run_opts(estimator=est, prec=prec, kahan=kahan, icdf=M.MLMC_ICDF_TABLE, max_level=18,
+                                min_levels=3, n0=10000, seed=1000 + rep, alpha=1.0, timeout_s=600.0)
+            t0 = time.perf_counter()
+            r = M.mlmc_run(eps, params, o)
+            dt = time.perf_counter() - t0
+            if rep > 0:
+                times.append(dt)
+                res = r
+        out[name] = {"seconds": statistics.median(times), "estimate": res.estimate,
+                     "rmse_est": math.sqrt(res.variance), "levels": res.levels, "rounds": res.rounds,
+                     "path_steps": res.path_steps}
+    out["speedup"] = out["plain_fp32_exact"]["seconds"] / out["nested_f16_kahan_table"]["seconds"]
+    return out
 
 
 def _cpu_sample(target_s: float, nthreads: int):
@@ -334,6 +408,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison leg (profiling runs)")
+    ap.add_argument("--no-tte", action="store_true", help="skip the time-to-eps leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batching leg")
+    ap.add_argument("--eps", type=float, default=1e-3)
     ap.add_argument("--levels", type=str, default=None, help="comma-separated levels (profiling runs)")
     ap.add_argument("--n", type=int, default=None, help="samples per level (profiling runs)")
     args = ap.parse_args()

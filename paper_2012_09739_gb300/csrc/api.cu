@@ -118,6 +118,8 @@ LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int
     const double sq = sqrt(delta_f);
     a.l = l;
     a.payoff = p->payoff;
+    a.mode = four ? MODE_FOUR : MODE_TWO;
+    a.sde = p->sde == MLMC_OU ? SDE_OU : SDE_GBM;
     a.N = N;
     a.npairs = (N + 1) / 2;
     a.path_offset = path_offset;

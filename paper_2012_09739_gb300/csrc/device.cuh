@@ -98,6 +98,19 @@ __device__ __forceinline__ Pair<P_F16> add(Pair<P_F16> a, Pair<P_F16> b) { retur
 __device__ __forceinline__ Pair<P_F16> sub(Pair<P_F16> a, Pair<P_F16> b) { return {h2sub(a.h, b.h)}; }
 __device__ __forceinline__ Pair<P_F16> mul(Pair<P_F16> a, Pair<P_F16> b) { return {h2mul(a.h, b.h)}; }
 
+// Kahan-compensated FP32 accumulator (Algorithm 1) for the per-thread sums
+// of D and D^2; value() is the compensated sum s - c.
+struct KahanF32 {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return __fsub_rn(s, c); }
+};
+
 // ---------------------------------------------------------------- inverse CDFs
 enum { ICDF_EXACT = 0, ICDF_TABLE = 1, ICDF_MLP = 2 };
 

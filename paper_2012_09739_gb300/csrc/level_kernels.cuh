@@ -6,10 +6,14 @@
 // shared memory; per-thread sums are reduced with warp shuffles in FP32,
 // across warps in FP64, and one FP64 (sum D, sum D^2) pair per block goes
 // to global memory for the finalize kernel.
+//
+// Every warp runs the same number of pair iterations (lanes past the end
+// simulate a clamped pair and discard it), so warp-cooperative steps such as
+// the MLP's tensor-core evaluation see all 32 lanes.
 #pragma once
 
 #include "device.cuh"
-#include "mlp_device.cuh"
+#include "mlp_tc.cuh"
 
 namespace mlmc {
 
@@ -20,6 +24,7 @@ enum { PAYOFF_X = 0, PAYOFF_CALL = 1 };
 struct LevelArgs {
     int l;                    // level: 2^l fine steps
     int payoff;
+    int mode, sde;            // MODE_*, SDE_* (read by the batched kernel)
     uint64_t npairs;          // ceil(N / 2)
     uint64_t N;
     uint64_t path_offset;
@@ -72,11 +77,10 @@ struct PathPair {
 };
 
 template <int P, int ICDF>
-__device__ __forceinline__ Pair<P> icdf_pair(const SmemTable &s, const MlpWeights *mlp, uint32_t w0, uint32_t w1) {
-    if (ICDF == ICDF_EXACT) {
-        if (P == P_F32) return Pair<P>::of2(exact_z(w0), exact_z(w1));
+__device__ __forceinline__ Pair<P> icdf_pair(const SmemTable &s, const MlpFrags &mlp, uint32_t w0, uint32_t w1) {
+    if constexpr (ICDF == ICDF_EXACT) {
         return Pair<P>::of2(exact_z(w0), exact_z(w1));
-    } else if (ICDF == ICDF_TABLE) {
+    } else if constexpr (ICDF == ICDF_TABLE) {
         const float v0 = mirrored_v(w0), v1 = mirrored_v(w1);
         if constexpr (P == P_F32) {
             return Pair<P>::of2(table_z32<false>(s, w0, v0), table_z32<false>(s, w1, v1));
@@ -84,7 +88,7 @@ __device__ __forceinline__ Pair<P> icdf_pair(const SmemTable &s, const MlpWeight
             return Pair<P>{table_z16<false>(s, w0, w1, v0, v1)};
         }
     } else {
-        const float2 z = mlp_z_pair(mlp, w0, w1);
+        const float2 z = mlp_z_warp(mlp, w0, w1);      // all 32 lanes together
         return Pair<P>::of2(z.x, z.y);
     }
 }
@@ -96,103 +100,127 @@ __device__ __forceinline__ float payoff_of(float X, int payoff, float K, float d
     return __fmul_rn(disc, t > 0.0f ? t : 0.0f);
 }
 
+// Simulates samples 2g and 2g+1 of the level described by `a` and returns
+// their differences D (d0, d1); out0/out1 receive the per-sample outputs
+// (P_f, P_c, D) or (P^_f, P^_c, P-_f, P-_c, D).
+template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
+__device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTable &tab, const MlpFrags &mlp,
+                                              uint64_t g, float &d0, float &d1, float *out0, float *out1) {
+    const uint32_t nf = 1u << a.l;
+    const uint32_t ncalls = (nf + 3u) >> 2;
+    const float K = __double2float_rn(a.K), disc = __double2float_rn(a.disc);
+    const uint64_t p0 = a.path_offset + 2 * g, p1 = p0 + 1;
+    PathPair<P, KAHAN, SDE> fine, coarse;
+    fine.init(a.drift_f, a.diff, a.mean, a.x0);
+    coarse.init(a.drift_c, a.diff, a.mean, a.x0);
+    PathPair<P_F32, true, SDE> hfine, hcoarse;       // exact-normal pair (four-way only)
+    if (MODE == MODE_FOUR) {
+        hfine.init(a.drift_f, a.diff, a.mean, a.x0);
+        hcoarse.init(a.drift_c, a.diff, a.mean, a.x0);
+    }
+    Pair<P> zprev;
+    Pair<P_F32> zhprev;
+
+    auto body = [&](uint32_t w0, uint32_t w1, int q) {
+        const Pair<P> z = icdf_pair<P, ICDF>(tab, mlp, w0, w1);
+        fine.step(z);
+        if (q & 1) coarse.step(add(zprev, z));
+        else zprev = z;
+        if (MODE == MODE_FOUR) {
+            const Pair<P_F32> zh = Pair<P_F32>::of2(exact_z(w0), exact_z(w1));
+            hfine.step(zh);
+            if (q & 1) hcoarse.step(add(zhprev, zh));
+            else zhprev = zh;
+        }
+    };
+
+    for (uint32_t j = 0; j < ncalls; ++j) {
+        const uint4 r0 = philox4x32_10(make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), j, a.tag), a.k0, a.k1);
+        const uint4 r1 = philox4x32_10(make_uint4((uint32_t)p1, (uint32_t)(p1 >> 32), j, a.tag), a.k0, a.k1);
+        if (nf >= 4) {
+            body(r0.x, r1.x, 0);
+            body(r0.y, r1.y, 1);
+            body(r0.z, r1.z, 2);
+            body(r0.w, r1.w, 3);
+        } else {
+            body(r0.x, r1.x, 0);
+            if (nf == 2) body(r0.y, r1.y, 1);
+        }
+    }
+
+    const float2 xf = fine.X.f32(), xc = coarse.X.f32();
+    if (MODE == MODE_TWO) {
+        const float pf0 = payoff_of(xf.x, a.payoff, K, disc), pf1 = payoff_of(xf.y, a.payoff, K, disc);
+        float pc0 = 0.0f, pc1 = 0.0f;
+        if (a.l > 0) {
+            pc0 = payoff_of(xc.x, a.payoff, K, disc);
+            pc1 = payoff_of(xc.y, a.payoff, K, disc);
+            d0 = __fsub_rn(pf0, pc0);
+            d1 = __fsub_rn(pf1, pc1);
+        } else {
+            d0 = pf0;
+            d1 = pf1;
+        }
+        out0[0] = pf0; out0[1] = pc0; out0[2] = d0;
+        out1[0] = pf1; out1[1] = pc1; out1[2] = d1;
+    } else {
+        const float2 hf = hfine.X.f32(), hc = hcoarse.X.f32();
+        const float phf0 = payoff_of(hf.x, a.payoff, K, disc), phf1 = payoff_of(hf.y, a.payoff, K, disc);
+        const float pbf0 = payoff_of(xf.x, a.payoff, K, disc), pbf1 = payoff_of(xf.y, a.payoff, K, disc);
+        float phc0 = 0.0f, phc1 = 0.0f, pbc0 = 0.0f, pbc1 = 0.0f;
+        if (a.l > 0) {
+            phc0 = payoff_of(hc.x, a.payoff, K, disc);
+            phc1 = payoff_of(hc.y, a.payoff, K, disc);
+            pbc0 = payoff_of(xc.x, a.payoff, K, disc);
+            pbc1 = payoff_of(xc.y, a.payoff, K, disc);
+        }
+        d0 = __fsub_rn(__fsub_rn(phf0, phc0), __fsub_rn(pbf0, pbc0));
+        d1 = __fsub_rn(__fsub_rn(phf1, phc1), __fsub_rn(pbf1, pbc1));
+        out0[0] = phf0; out0[1] = phc0; out0[2] = pbf0; out0[3] = pbc0; out0[4] = d0;
+        out1[0] = phf1; out1[1] = phc1; out1[2] = pbf1; out1[3] = pbc1; out1[4] = d1;
+    }
+}
+
+__device__ __forceinline__ void stage_table(SmemTable &tab, const float2 *t32, const __half2 *t16) {
+    for (int i = threadIdx.x; i < TAB_ENTRIES; i += blockDim.x) {
+        tab.c32[i] = t32[i];
+        tab.c16[i] = t16[i];
+    }
+}
+
+// Warp sum in FP32.
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
 __global__ void __launch_bounds__(256) level_kernel(const LevelArgs a) {
     __shared__ SmemTable tab;
     __shared__ double red[2][32];
     if (ICDF == ICDF_TABLE) {
-        for (int i = threadIdx.x; i < TAB_ENTRIES; i += blockDim.x) {
-            tab.c32[i] = a.tab32[i];
-            tab.c16[i] = a.tab16[i];
-        }
+        stage_table(tab, a.tab32, a.tab16);
         __syncthreads();
     }
-
-    const uint32_t nf = 1u << a.l;
-    const uint32_t ncalls = (nf + 3u) >> 2;
-    const float K = __double2float_rn(a.K), disc = __double2float_rn(a.disc);
-    float s1 = 0.0f, s2 = 0.0f;
-
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.npairs; g += stride) {
-        const uint64_t p0 = a.path_offset + 2 * g, p1 = p0 + 1;
-        PathPair<P, KAHAN, SDE> fine, coarse;
-        fine.init(a.drift_f, a.diff, a.mean, a.x0);
-        coarse.init(a.drift_c, a.diff, a.mean, a.x0);
-        PathPair<P_F32, true, SDE> hfine, hcoarse;       // exact-normal pair (four-way only)
-        if (MODE == MODE_FOUR) {
-            hfine.init(a.drift_f, a.diff, a.mean, a.x0);
-            hcoarse.init(a.drift_c, a.diff, a.mean, a.x0);
-        }
-        Pair<P> zprev;
-        Pair<P_F32> zhprev;
-
-        auto body = [&](uint32_t w0, uint32_t w1, int q) {
-            const Pair<P> z = icdf_pair<P, ICDF>(tab, a.mlp, w0, w1);
-            fine.step(z);
-            if (q & 1) coarse.step(add(zprev, z));
-            else zprev = z;
-            if (MODE == MODE_FOUR) {
-                const Pair<P_F32> zh = Pair<P_F32>::of2(exact_z(w0), exact_z(w1));
-                hfine.step(zh);
-                if (q & 1) hcoarse.step(add(zhprev, zh));
-                else zhprev = zh;
-            }
-        };
-
-        for (uint32_t j = 0; j < ncalls; ++j) {
-            const uint4 r0 = philox4x32_10(make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), j, a.tag), a.k0, a.k1);
-            const uint4 r1 = philox4x32_10(make_uint4((uint32_t)p1, (uint32_t)(p1 >> 32), j, a.tag), a.k0, a.k1);
-            if (nf >= 4) {
-                body(r0.x, r1.x, 0);
-                body(r0.y, r1.y, 1);
-                body(r0.z, r1.z, 2);
-                body(r0.w, r1.w, 3);
-            } else {
-                body(r0.x, r1.x, 0);
-                if (nf == 2) body(r0.y, r1.y, 1);
-            }
-        }
-
-        const float2 xf = fine.X.f32(), xc = coarse.X.f32();
-        float d0, d1;
-        float out0[5], out1[5];
-        if (MODE == MODE_TWO) {
-            const float pf0 = payoff_of(xf.x, a.payoff, K, disc), pf1 = payoff_of(xf.y, a.payoff, K, disc);
-            float pc0 = 0.0f, pc1 = 0.0f;
-            if (a.l > 0) {
-                pc0 = payoff_of(xc.x, a.payoff, K, disc);
-                pc1 = payoff_of(xc.y, a.payoff, K, disc);
-                d0 = __fsub_rn(pf0, pc0);
-                d1 = __fsub_rn(pf1, pc1);
-            } else {
-                d0 = pf0;
-                d1 = pf1;
-            }
-            out0[0] = pf0; out0[1] = pc0; out0[2] = d0;
-            out1[0] = pf1; out1[1] = pc1; out1[2] = d1;
-        } else {
-            const float2 hf = hfine.X.f32(), hc = hcoarse.X.f32();
-            const float phf0 = payoff_of(hf.x, a.payoff, K, disc), phf1 = payoff_of(hf.y, a.payoff, K, disc);
-            const float pbf0 = payoff_of(xf.x, a.payoff, K, disc), pbf1 = payoff_of(xf.y, a.payoff, K, disc);
-            float phc0 = 0.0f, phc1 = 0.0f, pbc0 = 0.0f, pbc1 = 0.0f;
-            if (a.l > 0) {
-                phc0 = payoff_of(hc.x, a.payoff, K, disc);
-                phc1 = payoff_of(hc.y, a.payoff, K, disc);
-                pbc0 = payoff_of(xc.x, a.payoff, K, disc);
-                pbc1 = payoff_of(xc.y, a.payoff, K, disc);
-            }
-            d0 = __fsub_rn(__fsub_rn(phf0, phc0), __fsub_rn(pbf0, pbc0));
-            d1 = __fsub_rn(__fsub_rn(phf1, phc1), __fsub_rn(pbf1, pbc1));
-            out0[0] = phf0; out0[1] = phc0; out0[2] = pbf0; out0[3] = pbc0; out0[4] = d0;
-            out1[0] = phf1; out1[1] = phc1; out1[2] = pbf1; out1[3] = pbc1; out1[4] = d1;
-        }
+    MlpFrags mlp;
+    if (ICDF == ICDF_MLP) mlp.load(a.mlp);
+    KahanF32 k1, k2;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t warp_id = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (uint64_t base = warp_id * 32; base < a.npairs; base += warps * 32) {
+        const uint64_t g = base + lane;
+        const bool active = g < a.npairs;
+        float d0, d1, out0[5], out1[5];
+        simulate_pair<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, active ? g : a.npairs - 1, d0, d1, out0, out1);
+        if (!active) continue;
         const bool valid1 = 2 * g + 1 < a.N;
-        s1 += d0;
-        s2 += d0 * d0;
+        k1.add(d0);
+        k2.add(d0 * d0);
         if (valid1) {
-            s1 += d1;
-            s2 += d1 * d1;
+            k1.add(d1);
+            k2.add(d1 * d1);
         }
         if (a.paths_out != nullptr) {
             constexpr int W = MODE == MODE_TWO ? 3 : 5;
@@ -205,14 +233,10 @@ __global__ void __launch_bounds__(256) level_kernel(const LevelArgs a) {
             }
         }
     }
-
     // warp reduction in FP32, then FP64 across warps
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float s1 = warp_sum(k1.value());
+    const float s2 = warp_sum(k2.value());
+    const int warp = threadIdx.x >> 5;
     if (lane == 0) {
         red[0][warp] = (double)s1;
         red[1][warp] = (double)s2;

@@ -4,6 +4,7 @@
 
 #include "internal.h"
 #include "level_kernels.cuh"
+#include "mlp_tc.cuh"
 
 namespace mlmc {
 
@@ -121,38 +122,53 @@ cudaError_t launch_uniform_bulk(const uint32_t *w, float *u, size_t n, cudaStrea
 
 // ---------------------------------------------------------------- bulk inverse CDF
 // Any u in (0, 1): v = min(u, 1-u) is exact in binary32 (1 - u is exact for
-// u >= 1/2), the sign comes from u > 1/2.
+// u >= 1/2), the sign comes from u > 1/2.  Each warp takes 64 consecutive
+// values per round (two per lane), so the MLP's warp-cooperative evaluation
+// sees all 32 lanes.
 template <int P, int ICDF>
 __global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const float2 *tab32, const __half2 *tab16,
-                                 const MlpWeights *mlp) {
+                                 const MlpWeights *mlpw) {
     __shared__ SmemTable tab;
-    for (int i = threadIdx.x; i < TAB_ENTRIES; i += blockDim.x) {
-        tab.c32[i] = tab32[i];
-        tab.c16[i] = tab16[i];
-    }
+    stage_table(tab, tab32, tab16);
     __syncthreads();
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float ui = u[i];
-        const bool upper = ui > 0.5f;
-        const float v = upper ? __fsub_rn(1.0f, ui) : ui;
-        const uint32_t sgn = upper ? 0x80000000u : 0u;
-        float r32;
-        if (ICDF == ICDF_EXACT) {
-            r32 = __uint_as_float(__float_as_uint(normcdfinvf(v)) ^ sgn);
-        } else if (ICDF == ICDF_TABLE) {
-            if (P == P_F16) {
-                const __half2 h = table_z16<true>(tab, sgn, sgn, v, v);
-                static_cast<__half *>(z)[i] = __low2half(h);
-                continue;
-            }
-            r32 = table_z32<true>(tab, sgn, v);
-        } else {
-            // the MLP reads the sign from the word's top bit and v from its
-            // remaining bits; pass the float path through the same evaluation
-            r32 = mlp_z_from_v(mlp, v, upper);
+    MlpFrags mlp;
+    if (ICDF == ICDF_MLP) mlp.load(mlpw);
+    const size_t lane = threadIdx.x & 31;
+    const size_t warps = (size_t)gridDim.x * (blockDim.x >> 5);
+    for (size_t base = ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 64; base < n;
+         base += warps * 64) {
+        float r[2];
+        float v[2], tt[2];
+        uint32_t sg[2];
+        size_t idx[2];
+        for (int h = 0; h < 2; ++h) {
+            idx[h] = base + 2 * lane + h;
+            const float ui = u[idx[h] < n ? idx[h] : n - 1];
+            const bool upper = ui > 0.5f;
+            v[h] = upper ? __fsub_rn(1.0f, ui) : ui;
+            sg[h] = upper ? 0x80000000u : 0u;
+            tt[h] = mlp_feature(v[h]);
         }
-        if (P == P_F32) static_cast<float *>(z)[i] = r32;
-        else static_cast<__half *>(z)[i] = __float2half_rn(r32);
+        if (ICDF == ICDF_MLP) {
+            const float2 y = mlp_eval_warp(mlp, tt[0], tt[1]);
+            r[0] = sg[0] ? y.x : -y.x;
+            r[1] = sg[1] ? y.y : -y.y;
+        }
+        for (int h = 0; h < 2; ++h) {
+            if (idx[h] >= n) continue;
+            if (ICDF == ICDF_EXACT) {
+                r[h] = __uint_as_float(__float_as_uint(normcdfinvf(v[h])) ^ sg[h]);
+            } else if (ICDF == ICDF_TABLE) {
+                if (P == P_F16) {
+                    const __half2 hz = table_z16<true>(tab, sg[h], sg[h], v[h], v[h]);
+                    static_cast<__half *>(z)[idx[h]] = __low2half(hz);
+                    continue;
+                }
+                r[h] = table_z32<true>(tab, sg[h], v[h]);
+            }
+            if (P == P_F32) static_cast<float *>(z)[idx[h]] = r[h];
+            else static_cast<__half *>(z)[idx[h]] = __float2half_rn(r[h]);
+        }
     }
 }
 

@@ -1,0 +1,87 @@
+"""mlmc_batch: all (set, level, estimator) items in one persistent launch give
+the same sums as item-by-item launches of the level kernels (same samples,
+different summation grouping), for GBM and OU sets, two-way and four-way,
+including items of 1 sample and ragged tiles; repeated calls replay the
+captured graph with identical results."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2012_09739_gb300 as M  # noqa: E402
+from workloads import batching_sets, batch_level_samples  # noqa: E402
+
+SEED = 1234
+
+
+def _params(s):
+    if s["kind"] == "gbm":
+        return M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=s["mu"], p1=s["sigma"], K=s["K"])
+    return M.sde_params(sde=M.MLMC_OU, payoff=M.MLMC_PAYOFF_X, p0=s["theta"], p1=s["m"], p2=s["s"], disc=1.0)
+
+
+def make_items(sets, levels, log2_n0, prec=M.MLMC_F16, kahan=1, icdf=M.MLMC_ICDF_TABLE):
+    Ns = batch_level_samples(levels, log2_n0)
+    items = []
+    for k, s in enumerate(sets):
+        p = _params(s)
+        for l in range(levels):
+            for kind in (0, 1):
+                items.append(M.mlmc_work(p, l, kind, prec, kahan, icdf, k, Ns[l], 0))
+    return items
+
+
+def _close(a, b):
+    assert a.n == b.n
+    tol1 = 2e-6 * (abs(b.s1) + math.sqrt(max(b.s2, 0.0) * b.n)) + 1e-30
+    assert abs(a.s1 - b.s1) <= tol1, (a.s1, b.s1)
+    assert abs(a.s2 - b.s2) <= 2e-6 * b.s2 + 1e-30, (a.s2, b.s2)
+
+
+def test_batch_matches_level_kernels():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sets = batching_sets(4, 4)
+    items = make_items(sets, 10, 15.0)
+    for it in items:
+        it.set_id = 0          # the level entry points use set id 0 in the counter tag
+    got = M.mlmc_batch(items, SEED)
+    for it, g in zip(items, got):
+        fn = M.mlmc_nested_level if it.kind else M.mlmc_level
+        ref = fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED, it.path_offset)
+        _close(g, ref)
+    again = M.mlmc_batch(items, SEED)           # replays the captured graph
+    assert [(a.s1, a.s2) for a in again] == [(a.s1, a.s2) for a in got]
+
+
+def test_single_item_batch_equals_level_kernel():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    for kind, l, N in [(0, 0, 1), (1, 3, 77777), (0, 7, 4097), (1, 12, 33), (0, 16, 1)]:
+        it = M.mlmc_work(p, l, kind, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 0, N, 5)
+        g = M.mlmc_batch([it], SEED)[0]
+        fn = M.mlmc_nested_level if kind else M.mlmc_level
+        ref = fn(l, N, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, p, SEED, 5)
+        _close(g, ref)
+
+
+def test_batch_config3_full_size_statistics():
+    """The full batching workload (128 sets x 17 levels x 2 estimators) in one
+    launch; the GBM sets' level sums telescope to a price near Black-Scholes."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import mlmc
+    sets = batching_sets()
+    items = make_items(sets, 17, 22.0)
+    got = M.mlmc_batch(items, SEED)
+    per = 17 * 2
+    for k in range(3):      # first three GBM sets: nested estimator sums
+        s = sets[k]
+        est = sum(g.s1 / g.n for g in got[k * per:(k + 1) * per])
+        var = sum(max(g.s2 / g.n - (g.s1 / g.n) ** 2, 0.0) / g.n for g in got[k * per:(k + 1) * per])
+        bs = mlmc.bs_call(mu=s["mu"], sigma=s["sigma"], K=s["K"])
+        assert abs(est - bs) < 5 * math.sqrt(var) + 2e-3
