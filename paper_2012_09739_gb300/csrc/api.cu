@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <mutex>
 #include <thread>
@@ -154,32 +155,60 @@ static int env_int(const char *name, int dflt) {
     return s ? atoi(s) : dflt;
 }
 
-// Grid for npairs pairs: whole rounds of resident threads, the grid a
-// multiple of the SM count where possible so every SM gets the same number
-// of blocks and every thread the same number of pairs (+-1).
+LaunchCfg level_launch_search(const DeviceState &d, LevelKernelFn fn, uint64_t npairs, int force_bt, int force_k);
+
+// Launch shape for npairs pairs.  A warp takes one chunk of 32 pairs per
+// round and every chunk costs the same, so the time is set by the number of
+// rounds, ceil(chunks / resident warps), and by how busy each SM is.  Among
+// block sizes 128..256 and blocks per SM up to the occupancy limit (grids a
+// whole multiple of the SM count), pick the shape whose last round is
+// fullest, counting fewer than 24 resident warps per SM as proportionally
+// slower (measured on GB300: 24 warps at a 90 %-full last round beat 18 warps
+// at 99.8 %); ties go to more warps.  MLMC_BLOCK / MLMC_BLOCKS_PER_SM
+// restrict the search (ignored if no valid shape matches them).
 LaunchCfg level_launch_cfg(const DeviceState &d, LevelKernelFn fn, uint64_t npairs) {
-    LaunchCfg c;
-    c.block = env_int("MLMC_BLOCK", 256);
-    if (c.block < 32 || c.block > 256 || c.block % 32) c.block = 256;
-    int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, c.block, 0) != cudaSuccess || bps < 1) bps = 1;
-    const int cap = env_int("MLMC_BLOCKS_PER_SM", 0);
-    if (cap > 0 && cap < bps) bps = cap;
-    const uint64_t max_blocks = (uint64_t)bps * d.sm_count;
-    const uint64_t need = (npairs + c.block - 1) / c.block;
-    uint64_t grid;
-    if (need <= max_blocks) {
-        grid = need;
-    } else {
-        const uint64_t rounds = (need + max_blocks - 1) / max_blocks;
-        grid = (need + rounds - 1) / rounds;
-        const uint64_t sm = (uint64_t)d.sm_count;
-        const uint64_t up = (grid + sm - 1) / sm * sm;
-        if (up <= max_blocks) grid = up;
-    }
-    c.grid = (int)(grid > 0 ? grid : 1);
-    return c;
+    LaunchCfg best = level_launch_search(d, fn, npairs, env_int("MLMC_BLOCK", 0), env_int("MLMC_BLOCKS_PER_SM", 0));
+    if (best.grid == 0) best = level_launch_search(d, fn, npairs, 0, 0);
+    return best;
 }
+
+LaunchCfg level_launch_search(const DeviceState &d, LevelKernelFn fn, uint64_t npairs, int force_bt, int force_k) {
+    LaunchCfg best;
+    best.grid = 0;
+    const uint64_t chunks = (npairs + 31) / 32;
+    double best_score = -1.0;
+    uint64_t best_w = 0;
+    for (int bt = 256; bt >= 128; bt -= 32) {
+        if (force_bt && bt != force_bt) continue;
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, bt, 0) != cudaSuccess || occ < 1) occ = 1;
+        for (int k = 1; k <= occ; ++k) {
+            if (force_k && k != force_k) continue;
+            const uint64_t wps = (uint64_t)k * bt / 32, W = wps * d.sm_count;
+            uint64_t grid = (uint64_t)k * d.sm_count;
+            double score;
+            if (chunks <= W) {
+                // one round: only the blocks that have work
+                grid = (chunks * 32 + bt - 1) / bt;
+                score = 1.0 + (double)W * 1e-9;
+            } else {
+                const uint64_t rounds = (chunks + W - 1) / W;
+                const double eff = (double)chunks / (double)(rounds * W);
+                score = eff * std::min(1.0, (double)wps / 24.0);
+            }
+            if (score > best_score + 1e-9 || (fabs(score - best_score) <= 1e-9 && W > best_w)) {
+                best_score = score;
+                best_w = W;
+                best.block = bt;
+                best.grid = (int)std::max<uint64_t>(grid, 1);
+            }
+        }
+    }
+    return best;
+}
+
+// Chunks of 32 pairs up to which each chunk gets its own partial sum.
+constexpr uint64_t MAX_CHUNK_PARTIALS = 1ull << 22;
 
 mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int prec, int kahan, int icdf,
                           const mlmc_sde_params *p, uint64_t seed, uint64_t path_offset, uint32_t set_id,
@@ -188,8 +217,11 @@ mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int
     if (!fn) return fail(MLMC_EINVAL, "no kernel for this variant");
     LevelArgs a = make_level_args(d, four, l, N, icdf, p, seed, path_offset, set_id);
     const LaunchCfg cfg = level_launch_cfg(d, fn, a.npairs);
+    const uint64_t chunks = (a.npairs + 31) / 32;
+    a.chunk_partials = chunks <= MAX_CHUNK_PARTIALS ? 1 : 0;
+    const uint64_t slots = a.chunk_partials ? chunks : (uint64_t)cfg.grid;
     double2 *partials = nullptr;
-    cudaError_t e = cudaMallocAsync(&partials, (size_t)cfg.grid * sizeof(double2), s);
+    cudaError_t e = cudaMallocAsync(&partials, slots * sizeof(double2), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(partials)");
     a.partials = partials;
     a.paths_out = paths_dev;
@@ -197,7 +229,7 @@ mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int
     fn<<<cfg.grid, cfg.block, 0, s>>>(a);
     e = cudaGetLastError();
     if (ev1) cudaEventRecord(ev1, s);
-    if (e == cudaSuccess && sums_dev) e = launch_finalize(partials, cfg.grid, sums_dev, s);
+    if (e == cudaSuccess && sums_dev) e = launch_finalize(partials, slots, sums_dev, s);
     cudaError_t e2 = cudaFreeAsync(partials, s);
     if (e != cudaSuccess) return cuda_fail(e, "level kernel launch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");

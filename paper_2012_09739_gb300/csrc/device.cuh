@@ -36,11 +36,14 @@ __device__ __forceinline__ float uniform_of(uint32_t w) {
     return __fsub_rn(__uint_as_float((w >> 9) | 0x3F800000u), 0x1.fffffep-1f);
 }
 
-// v = min(u, 1 - u) for the same u, exact: flipping all bits of a word with
-// the top bit set maps u to 1 - u on the 2^23-point grid.
+// v = min(u, 1 - u) for the same u, exact: f = 1 + (w >> 9) 2^-23 (one
+// funnel shift), s = (f - 3/2) + 2^-24 = u - 1/2 and v = 1/2 - |s| are exact
+// binary32 operations on the grid (at most 23 significant bits), and keep
+// the work on the FP32 pipe rather than the integer ALU.
 __device__ __forceinline__ float mirrored_v(uint32_t w) {
-    const uint32_t m = (w ^ (uint32_t)((int32_t)w >> 31)) >> 9;   // < 2^22
-    return __fsub_rn(__uint_as_float(m | 0x3F800000u), 0x1.fffffep-1f);
+    const float f = __uint_as_float(__funnelshift_r(w, 0x7Fu, 9));
+    const float s = __fadd_rn(__fsub_rn(f, 1.5f), 0x1p-24f);
+    return __fsub_rn(0.5f, fabsf(s));
 }
 
 // ---------------------------------------------------------------- arithmetic
@@ -132,10 +135,10 @@ __device__ __forceinline__ int tab_index(float v) {
     return e - 103;
 }
 
-// Exact normal in FP32: Phi^-1(v) with the sign of the word's half.
+// Exact normal in FP32: Phi^-1(v) (CUDA's normcdfinvf) with the sign of the
+// word's half.
 __device__ __forceinline__ float exact_z(uint32_t w) {
-    const float v = mirrored_v(w);
-    const float z = normcdfinvf(v);
+    const float z = normcdfinvf(mirrored_v(w));
     return __uint_as_float(__float_as_uint(z) ^ (w & 0x80000000u));
 }
 
@@ -157,8 +160,9 @@ __device__ __forceinline__ __half2 table_z16(const SmemTable &s, uint32_t w0, ui
     const __half2 c1 = __highs2half2(t0, t1);
     const __half2 v = __floats2half2_rn(v0, v1);
     __half2 z = h2add(c0, h2mul(c1, v));
-    const uint32_t sgn = ((w0 >> 16) & 0x8000u) | (w1 & 0x80000000u);
-    uint32_t zb = *reinterpret_cast<uint32_t *>(&z) ^ sgn;
+    // sign bits of the two words into bits 15 and 31 (top bytes of w0, w1)
+    const uint32_t top = __byte_perm(w0, w1, 0x7030u);
+    uint32_t zb = *reinterpret_cast<uint32_t *>(&z) ^ (top & 0x80008000u);
     return *reinterpret_cast<__half2 *>(&zb);
 }
 

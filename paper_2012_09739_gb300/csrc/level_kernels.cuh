@@ -38,7 +38,8 @@ struct LevelArgs {
     const float2 *tab32;      // table in binary32, TAB_ENTRIES entries
     const __half2 *tab16;     // table in binary16
     const MlpWeights *mlp;    // network (ICDF_MLP only)
-    double2 *partials;        // one (sum D, sum D^2) per block
+    double2 *partials;        // (sum D, sum D^2) per warp chunk, or per block
+    int chunk_partials;       // 1: one partial per chunk of 32 pairs (result independent of the grid)
     float *paths_out;         // optional per-sample output (3 or 5 floats per sample)
 };
 
@@ -195,8 +196,12 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Warp w takes chunks w, w + W, ... of 32 consecutive pairs (one per lane).
+// With chunk_partials each chunk's FP32 warp sum goes, in FP64, to its own
+// slot, so the finalize kernel adds the same values in the same order
+// whatever the grid; otherwise one slot per block (warps summed in FP64).
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__global__ void __launch_bounds__(256) level_kernel(const LevelArgs a) {
+__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 1 : 3) level_kernel(const LevelArgs a) {
     __shared__ SmemTable tab;
     __shared__ double red[2][32];
     if (ICDF == ICDF_TABLE) {
@@ -214,15 +219,25 @@ __global__ void __launch_bounds__(256) level_kernel(const LevelArgs a) {
         const bool active = g < a.npairs;
         float d0, d1, out0[5], out1[5];
         simulate_pair<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, active ? g : a.npairs - 1, d0, d1, out0, out1);
-        if (!active) continue;
         const bool valid1 = 2 * g + 1 < a.N;
-        k1.add(d0);
-        k2.add(d0 * d0);
-        if (valid1) {
-            k1.add(d1);
-            k2.add(d1 * d1);
+        if (a.chunk_partials) {
+            float c1 = 0.0f, c2 = 0.0f;
+            if (active) {
+                c1 = valid1 ? __fadd_rn(d0, d1) : d0;
+                c2 = valid1 ? fmaf(d1, d1, d0 * d0) : d0 * d0;
+            }
+            c1 = warp_sum(c1);
+            c2 = warp_sum(c2);
+            if (lane == 0) a.partials[base >> 5] = make_double2((double)c1, (double)c2);
+        } else if (active) {
+            k1.add(d0);
+            k2.add(d0 * d0);
+            if (valid1) {
+                k1.add(d1);
+                k2.add(d1 * d1);
+            }
         }
-        if (a.paths_out != nullptr) {
+        if (active && a.paths_out != nullptr) {
             constexpr int W = MODE == MODE_TWO ? 3 : 5;
             float *o = a.paths_out + (2 * g) * W;
 #pragma unroll
@@ -233,6 +248,7 @@ __global__ void __launch_bounds__(256) level_kernel(const LevelArgs a) {
             }
         }
     }
+    if (a.chunk_partials) return;
     // warp reduction in FP32, then FP64 across warps
     const float s1 = warp_sum(k1.value());
     const float s2 = warp_sum(k2.value());

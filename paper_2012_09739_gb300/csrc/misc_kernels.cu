@@ -62,19 +62,19 @@ cudaError_t launch_build_table(double *t64, float2 *t32, __half2 *t16, cudaStrea
 }
 
 // ---------------------------------------------------------------- finalize
-// Deterministic FP64 sum of per-block partials: fixed strided split across
-// 256 threads, then a fixed tree.  out[0] = sum D, out[1] = sum D^2.
-__global__ void __launch_bounds__(256) finalize_kernel(const double2 *partials, int nblocks, double *out) {
-    __shared__ double r1[256], r2[256];
+// Deterministic FP64 sum of the partials: a fixed strided split across 1024
+// threads, then a fixed tree.  out[0] = sum D, out[1] = sum D^2.
+__global__ void __launch_bounds__(1024) finalize_kernel(const double2 *partials, uint64_t count, double *out) {
+    __shared__ double r1[1024], r2[1024];
     double t1 = 0.0, t2 = 0.0;
-    for (int i = threadIdx.x; i < nblocks; i += 256) {
+    for (uint64_t i = threadIdx.x; i < count; i += 1024) {
         t1 += partials[i].x;
         t2 += partials[i].y;
     }
     r1[threadIdx.x] = t1;
     r2[threadIdx.x] = t2;
     __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
+    for (int h = 512; h > 0; h >>= 1) {
         if (threadIdx.x < h) {
             r1[threadIdx.x] += r1[threadIdx.x + h];
             r2[threadIdx.x] += r2[threadIdx.x + h];
@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(const double2 *partials, 
     }
 }
 
-cudaError_t launch_finalize(const double2 *partials, int nblocks, double *out, cudaStream_t s) {
-    finalize_kernel<<<1, 256, 0, s>>>(partials, nblocks, out);
+cudaError_t launch_finalize(const double2 *partials, uint64_t count, double *out, cudaStream_t s) {
+    finalize_kernel<<<1, 1024, 0, s>>>(partials, count, out);
     return cudaGetLastError();
 }
 

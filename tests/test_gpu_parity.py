@@ -199,6 +199,19 @@ def test_sums_equal_per_path_sums(four):
     assert abs(s.s2 - (d * d).sum()) <= 1e-5 * (d * d).sum()
 
 
+def test_sums_independent_of_launch_shape(monkeypatch):
+    """Each warp chunk of 32 pairs has its own partial sum, so the level sums
+    are bit-identical whatever block size and grid the launch uses."""
+    params = M.sde_params(**GBM_CALL)
+    res = []
+    for bt, k in [("256", "3"), ("160", "2"), ("128", "1")]:
+        monkeypatch.setenv("MLMC_BLOCK", bt)
+        monkeypatch.setenv("MLMC_BLOCKS_PER_SM", k)
+        s = M.mlmc_nested_level(5, 700001, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, params, SEED)
+        res.append((s.s1, s.s2))
+    assert res[0] == res[1] == res[2]
+
+
 def test_deterministic_repeat():
     params = M.sde_params(**GBM_CALL)
     a = M.mlmc_nested_level(6, 300000, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, params, SEED)
