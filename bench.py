@@ -210,7 +210,8 @@ def run_gpu(args):
     batch = None if args.no_batch else batch_leg(M, torch, stream)
 
     # --- time to RMSE eps through mlmc_run: nested FP16+Kahan vs plain FP32
-    tte = None if args.no_tte else time_to_eps(M, params, args.eps)
+    tte = None if args.no_tte else time_to_eps(M, params, [args.eps, 1e-5])
+    mlp = None if args.no_mlp else mlp_leg(M, torch, params)
 
     # --- roofline of the dominant kernel (four-way FP16+Kahan table)
     clk = clocks.summary()
@@ -254,6 +255,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": len(items) * 16},
         "time_to_eps": tte,
         "batching": batch,
+        "mlp": mlp,
         "gpu_launches": 2 * len(items) * args.steps,
         "clocks": clk,
     }
@@ -291,6 +293,7 @@ def batch_leg(M, torch, stream, repeats=5):
         M.mlmc_batch(items, SEED)
         times.append(time.perf_counter() - t0)
     t_batch = statistics.median(times)
+    dev_s = sum(x.cost_ns for x in M.mlmc_batch(items, SEED)) * 1e-9
     sums = torch.zeros(2 * len(items), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     seq = []
@@ -303,32 +306,83 @@ def batch_leg(M, torch, stream, repeats=5):
         seq.append(time.perf_counter() - t0)
     t_seq = min(seq)
     return {"items": len(items), "path_steps": ps, "seconds": t_batch, "path_steps_per_s": ps / t_batch,
+            "device_seconds": dev_s,
             "one_launch_per_item_seconds": t_seq, "speedup_vs_one_launch_per_item": t_seq / t_batch,
-            "timing": "wall clock around the synchronous mlmc_batch call (graph replay), median of 5"}
+            "timing": "wall clock around the synchronous mlmc_batch call (graph replay), median of 5; "
+                      "device_seconds from CUDA events around the graph launch"}
 
 
-def time_to_eps(M, params, eps, repeats=3):
-    """Wall time of mlmc_run to RMSE eps: nested estimator (FP16 + Kahan,
-    table) against the standard estimator (FP32, exact normals, plain Euler).
-    Median of `repeats` runs with different seeds, after one untimed run."""
-    out = {"eps": eps}
-    for name, est, prec, kahan in (("nested_f16_kahan_table", 1, M.MLMC_F16, 1),
-                                   ("plain_fp32_exact", 0, M.MLMC_F32, 0)):
-        times, res = [], None
-        for rep in range(repeats + 1):
-            o = M.mlmc_run_opts(estimator=est, prec=prec, kahan=kahan, icdf=M.MLMC_ICDF_TABLE, max_level=18,
-                                min_levels=3, n0=10000, seed=1000 + rep, alpha=1.0, timeout_s=600.0)
-            t0 = time.perf_counter()
-            r = M.mlmc_run(eps, params, o)
-            dt = time.perf_counter() - t0
-            if rep > 0:
-                times.append(dt)
-                res = r
-        out[name] = {"seconds": statistics.median(times), "estimate": res.estimate,
-                     "rmse_est": math.sqrt(res.variance), "levels": res.levels, "rounds": res.rounds,
-                     "path_steps": res.path_steps}
-    out["speedup"] = out["plain_fp32_exact"]["seconds"] / out["nested_f16_kahan_table"]["seconds"]
+def time_to_eps(M, params, eps_list, repeats=3):
+    """Wall time of mlmc_run to RMSE eps (Sec. 3 adaptive MLMC): the standard
+    estimator (FP32, exact normals, plain Euler) against the nested estimator
+    with FP16 + Kahan table normals, FP32 table normals, and the per-level
+    automatic choice.  Median of `repeats` runs with different seeds, after
+    one untimed run."""
+    variants = (("plain_fp32_exact", 0, M.MLMC_F32, 0), ("nested_f16_kahan_table", 1, M.MLMC_F16, 1),
+                ("nested_f32_table", 1, M.MLMC_F32, 0), ("nested_auto_table", 1, -1, 0))
+    out = {}
+    for eps in eps_list:
+        row = {}
+        for name, est, prec, kahan in variants:
+            times, res = [], None
+            for rep in range(repeats + 1):
+                o = M.mlmc_run_opts(estimator=est, prec=prec, kahan=kahan, icdf=M.MLMC_ICDF_TABLE, max_level=18,
+                                    min_levels=3, n0=10000, seed=1000 + rep, alpha=1.0, timeout_s=600.0)
+                t0 = time.perf_counter()
+                r = M.mlmc_run(eps, params, o)
+                dt = time.perf_counter() - t0
+                if rep > 0:
+                    times.append(dt)
+                    res = r
+            row[name] = {"seconds": statistics.median(times), "estimate": res.estimate,
+                         "rmse_est": math.sqrt(res.variance), "levels": res.levels, "rounds": res.rounds,
+                         "path_steps": res.path_steps}
+            if est == 1 and prec == -1:
+                row[name]["prec_per_level"] = ["f16" if res.prec[l] == M.MLMC_F16 else "f32"
+                                               for l in range(res.levels)]
+                row[name]["kahan_per_level"] = [int(res.kahan[l]) for l in range(res.levels)]
+                row[name]["efficiency_per_level"] = [round(res.efficiency[l], 3) for l in range(res.levels)]
+        row["speedup_f16_kahan_vs_plain"] = row["plain_fp32_exact"]["seconds"] / row["nested_f16_kahan_table"]["seconds"]
+        out[f"{eps:g}"] = row
     return out
+
+
+def mlp_leg(M, torch, params):
+    """The learned part: train the FP16 tensor-core MLP surrogate on 2^20
+    (u, |Phi^-1|) pairs (targets computed on the device in FP64), then its
+    E|Z - Z~|^2 against the table's and the four-way throughput with it."""
+    from workloads import mlp_initial_weights, uniform_grid_sample
+    dev = torch.device("cuda")
+    M.mlmc_mlp_set_weights(mlp_initial_weights(1234))
+    u = torch.tensor(uniform_grid_sample(1 << 20, 31), dtype=torch.float32, device=dev)
+    opts = M.mlmc_train_opts(steps=20000, batch=8192, lr0=1e-2, lr_min=1e-5, beta1=0.9, beta2=0.999, eps=1e-8,
+                             seed=SEED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = M.mlmc_mlp_train(u, None, opts)
+    train_s = time.perf_counter() - t0
+    ue = torch.tensor(uniform_grid_sample(1 << 22, 41), dtype=torch.float64, device=dev)
+    ref = torch.special.ndtri(ue)
+    err = {}
+    for name, kind in (("mlp", M.MLMC_ICDF_MLP), ("table", M.MLMC_ICDF_TABLE)):
+        z = torch.empty(ue.numel(), dtype=torch.float32, device=dev)
+        M.approx_icdf(ue.float(), z, kind, M.MLMC_F32)
+        err[name] = float(((z.double() - ref) ** 2).mean())
+    sums = torch.zeros(2, dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream()
+    rates = {}
+    for name, kind in (("mlp", M.MLMC_ICDF_MLP), ("table", M.MLMC_ICDF_TABLE)):
+        M.mlmc_level_async(1, 10, 1 << 20, M.MLMC_F16, 1, kind, params, SEED, 0, sums, s.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(3):
+            M.mlmc_level_async(1, 10, 1 << 20, M.MLMC_F16, 1, kind, params, SEED, 0, sums, s.cuda_stream)
+        e1.record(s)
+        torch.cuda.synchronize()
+        rates[name] = 3 * (1 << 20) * (1 << 10) / (e0.elapsed_time(e1) / 1e3)
+    return {"train_seconds": train_s, "steps": 20000, "batch": 8192, "pairs": 1 << 20, "final_loss": loss,
+            "l2_error_mlp": err["mlp"], "l2_error_table": err["table"],
+            "fourway_l10_path_steps_per_s": {"mlp": rates["mlp"], "table": rates["table"]}}
 
 
 def _cpu_sample(target_s: float, nthreads: int):
@@ -410,6 +464,7 @@ def main():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison leg (profiling runs)")
     ap.add_argument("--no-tte", action="store_true", help="skip the time-to-eps leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batching leg")
+    ap.add_argument("--no-mlp", action="store_true", help="skip the MLP leg")
     ap.add_argument("--eps", type=float, default=1e-3)
     ap.add_argument("--levels", type=str, default=None, help="comma-separated levels (profiling runs)")
     ap.add_argument("--n", type=int, default=None, help="samples per level (profiling runs)")

@@ -197,7 +197,10 @@ mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t seed, mlmc_
 typedef struct {
     int32_t estimator;    /* 0: standard theta^ (FP32, exact normals, plain Euler);
                              1: nested theta- (two-way approximate + four-way) */
-    int32_t prec, kahan, icdf;   /* variant of the approximate paths (estimator 1) */
+    int32_t prec, kahan, icdf;   /* variant of the approximate paths (estimator 1); prec = -1:
+                                    choose per level among FP16 + Kahan, FP16 and FP32 (kahan
+                                    ignored) the variant with the smallest sqrt(v c) + sqrt(V C)
+                                    measured on n0 warm-up samples of each (Sec. 3) */
     int32_t max_level;    /* <= 18 */
     int32_t min_levels;   /* levels 0 .. min_levels-1 always present (>= 3) */
     uint64_t n0;          /* warm-up samples per level and estimator */
@@ -218,6 +221,13 @@ typedef struct {
     double mean[2][MLMC_MAX_LEVELS];
     double var[2][MLMC_MAX_LEVELS];
     double cost[2][MLMC_MAX_LEVELS];      /* device ns per sample */
+    int32_t prec[MLMC_MAX_LEVELS];        /* variant used per level (nested estimator) */
+    int32_t kahan[MLMC_MAX_LEVELS];
+    /* Sec. 3 per-level efficiency of the nested estimator against the standard
+     * one: (v c / v^ c^) (1 + sqrt(V C / (v c)))^2 with v^, c^ of the FP32
+     * exact-normal two-way difference measured on n0 samples (< 1: saving);
+     * 0 when not measured (estimator 0, or levels added without warm-up). */
+    double efficiency[MLMC_MAX_LEVELS];
 } mlmc_run_result;
 
 mlmc_status mlmc_run(double eps, const mlmc_sde_params *params, const mlmc_run_opts *opts, mlmc_run_result *out);

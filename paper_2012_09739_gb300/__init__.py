@@ -73,7 +73,9 @@ class mlmc_run_result(ctypes.Structure):
     _fields_ = [("estimate", ctypes.c_double), ("variance", ctypes.c_double), ("levels", ctypes.c_int32),
                 ("rounds", ctypes.c_int32), ("wall_s", ctypes.c_double), ("path_steps", ctypes.c_double),
                 ("n", (ctypes.c_uint64 * MLMC_MAX_LEVELS) * 2), ("mean", (ctypes.c_double * MLMC_MAX_LEVELS) * 2),
-                ("var", (ctypes.c_double * MLMC_MAX_LEVELS) * 2), ("cost", (ctypes.c_double * MLMC_MAX_LEVELS) * 2)]
+                ("var", (ctypes.c_double * MLMC_MAX_LEVELS) * 2), ("cost", (ctypes.c_double * MLMC_MAX_LEVELS) * 2),
+                ("prec", ctypes.c_int32 * MLMC_MAX_LEVELS), ("kahan", ctypes.c_int32 * MLMC_MAX_LEVELS),
+                ("efficiency", ctypes.c_double * MLMC_MAX_LEVELS)]
 
 
 # exported symbols and their signatures

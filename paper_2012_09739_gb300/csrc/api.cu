@@ -155,59 +155,26 @@ static int env_int(const char *name, int dflt) {
     return s ? atoi(s) : dflt;
 }
 
-LaunchCfg level_launch_search(const DeviceState &d, LevelKernelFn fn, uint64_t npairs, int force_bt, int force_k);
-
-// Launch shape for npairs pairs.  A warp takes one chunk of 32 pairs per
-// round and every chunk costs the same, so the time is set by the number of
-// rounds, ceil(chunks / resident warps), and by how busy each SM is.  Among
-// block sizes 128..256 and blocks per SM up to the occupancy limit (grids a
-// whole multiple of the SM count), pick the shape whose last round is
-// fullest, counting fewer than 24 resident warps per SM as proportionally
-// slower (measured on GB300: 24 warps at a 90 %-full last round beat 18 warps
-// at 99.8 %); ties go to more warps.  MLMC_BLOCK / MLMC_BLOCKS_PER_SM
-// restrict the search (ignored if no valid shape matches them).
+// Launch shape: a persistent grid of every resident block (256 threads, the
+// occupancy limit of blocks per SM) when the chunks outnumber the resident
+// warps, else one block per 8 chunks.  MLMC_BLOCK / MLMC_BLOCKS_PER_SM
+// override the block size and the blocks per SM.
 LaunchCfg level_launch_cfg(const DeviceState &d, LevelKernelFn fn, uint64_t npairs) {
-    LaunchCfg best = level_launch_search(d, fn, npairs, env_int("MLMC_BLOCK", 0), env_int("MLMC_BLOCKS_PER_SM", 0));
-    if (best.grid == 0) best = level_launch_search(d, fn, npairs, 0, 0);
-    return best;
+    LaunchCfg c;
+    int bt = env_int("MLMC_BLOCK", 256);
+    if (bt < 32 || bt > 256 || bt % 32) bt = 256;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, bt, 0) != cudaSuccess || occ < 1) occ = 1;
+    const int k = env_int("MLMC_BLOCKS_PER_SM", 0);
+    if (k > 0 && k < occ) occ = k;
+    const uint64_t chunks = (npairs + 31) / 32, per_block = (uint64_t)bt / 32;
+    const uint64_t resident = (uint64_t)occ * d.sm_count;
+    c.block = bt;
+    c.grid = (int)std::max<uint64_t>(1, std::min(resident, (chunks + per_block - 1) / per_block));
+    return c;
 }
 
-LaunchCfg level_launch_search(const DeviceState &d, LevelKernelFn fn, uint64_t npairs, int force_bt, int force_k) {
-    LaunchCfg best;
-    best.grid = 0;
-    const uint64_t chunks = (npairs + 31) / 32;
-    double best_score = -1.0;
-    uint64_t best_w = 0;
-    for (int bt = 256; bt >= 128; bt -= 32) {
-        if (force_bt && bt != force_bt) continue;
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, bt, 0) != cudaSuccess || occ < 1) occ = 1;
-        for (int k = 1; k <= occ; ++k) {
-            if (force_k && k != force_k) continue;
-            const uint64_t wps = (uint64_t)k * bt / 32, W = wps * d.sm_count;
-            uint64_t grid = (uint64_t)k * d.sm_count;
-            double score;
-            if (chunks <= W) {
-                // one round: only the blocks that have work
-                grid = (chunks * 32 + bt - 1) / bt;
-                score = 1.0 + (double)W * 1e-9;
-            } else {
-                const uint64_t rounds = (chunks + W - 1) / W;
-                const double eff = (double)chunks / (double)(rounds * W);
-                score = eff * std::min(1.0, (double)wps / 24.0);
-            }
-            if (score > best_score + 1e-9 || (fabs(score - best_score) <= 1e-9 && W > best_w)) {
-                best_score = score;
-                best_w = W;
-                best.block = bt;
-                best.grid = (int)std::max<uint64_t>(grid, 1);
-            }
-        }
-    }
-    return best;
-}
-
-// Chunks of 32 pairs up to which each chunk gets its own partial sum.
+// Chunk groups up to which each group gets its own partial sum.
 constexpr uint64_t MAX_CHUNK_PARTIALS = 1ull << 22;
 
 mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int prec, int kahan, int icdf,
@@ -218,18 +185,24 @@ mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int
     LevelArgs a = make_level_args(d, four, l, N, icdf, p, seed, path_offset, set_id);
     const LaunchCfg cfg = level_launch_cfg(d, fn, a.npairs);
     const uint64_t chunks = (a.npairs + 31) / 32;
-    a.chunk_partials = chunks <= MAX_CHUNK_PARTIALS ? 1 : 0;
-    const uint64_t slots = a.chunk_partials ? chunks : (uint64_t)cfg.grid;
+    const uint64_t groups = (chunks + chunk_group(l) - 1) / chunk_group(l);
+    a.chunk_partials = groups <= MAX_CHUNK_PARTIALS ? 1 : 0;
+    const uint64_t slots = a.chunk_partials ? groups : (uint64_t)cfg.grid;
+    const uint64_t fin = finalize_scratch(slots);
     double2 *partials = nullptr;
-    cudaError_t e = cudaMallocAsync(&partials, slots * sizeof(double2), s);
+    // partial slots, the chunk counter (zeroed), the finalize scratch
+    cudaError_t e = cudaMallocAsync(&partials, (slots + 1 + fin) * sizeof(double2), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(partials)");
     a.partials = partials;
+    a.counter = reinterpret_cast<unsigned long long *>(partials + slots);
+    if (a.chunk_partials && (e = cudaMemsetAsync(a.counter, 0, 8, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemsetAsync");
     a.paths_out = paths_dev;
     if (ev0) cudaEventRecord(ev0, s);
     fn<<<cfg.grid, cfg.block, 0, s>>>(a);
     e = cudaGetLastError();
     if (ev1) cudaEventRecord(ev1, s);
-    if (e == cudaSuccess && sums_dev) e = launch_finalize(partials, slots, sums_dev, s);
+    if (e == cudaSuccess && sums_dev) e = launch_finalize(partials, slots, sums_dev, partials + slots + 1, s);
     cudaError_t e2 = cudaFreeAsync(partials, s);
     if (e != cudaSuccess) return cuda_fail(e, "level kernel launch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");

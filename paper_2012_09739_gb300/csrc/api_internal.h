@@ -23,7 +23,9 @@ struct DeviceState {
     __half2 *tab16 = nullptr;
     MlpWeights *mlp = nullptr;
     bool mlp_ready = false;
-    BatchCache *batch = nullptr;
+    BatchCache *batch = nullptr;         // mlmc_batch: captured graph and buffers
+    BatchCache *run_cache = nullptr;     // mlmc_run: buffers of its batched rounds
+    cudaStream_t run_stream = nullptr;
 };
 
 struct LaunchCfg {
@@ -48,5 +50,10 @@ mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int
 mlmc_status level_sync(int four, int l, uint64_t N, int prec, int kahan, int icdf, const mlmc_sde_params *p,
                        uint64_t seed, uint64_t path_offset, mlmc_sums *out, void *stream);
 void release_device_extras(DeviceState &d);
+BatchCache *batch_cache_create();
+void batch_cache_destroy(BatchCache *c);
+mlmc_status batch_round(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed,
+                        cudaStream_t s);
+const double2 *batch_sums_host(const BatchCache &c);
 
 }  // namespace mlmc

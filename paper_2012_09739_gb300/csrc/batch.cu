@@ -144,6 +144,8 @@ struct BatchCache {
     size_t sums_cap = 0;
     double2 *sums_host = nullptr;
     size_t sums_host_cap = 0;
+    unsigned char *stage = nullptr;      // pinned staging of the descriptors
+    size_t stage_cap = 0;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t sig = 0;
@@ -151,8 +153,9 @@ struct BatchCache {
     std::map<uint64_t, int> tuned;       // item-list signature -> lane_work_log2
 };
 
-void release_device_extras(DeviceState &d) {
-    BatchCache *c = d.batch;
+BatchCache *batch_cache_create() { return new BatchCache(); }
+
+void batch_cache_destroy(BatchCache *c) {
     if (!c) return;
     if (c->exec) cudaGraphExecDestroy(c->exec);
     cudaFree(c->items);
@@ -163,22 +166,33 @@ void release_device_extras(DeviceState &d) {
     cudaFree(c->counters);
     cudaFree(c->sums);
     if (c->sums_host) cudaFreeHost(c->sums_host);
+    if (c->stage) cudaFreeHost(c->stage);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     delete c;
-    d.batch = nullptr;
+}
+
+void release_device_extras(DeviceState &d) {
+    batch_cache_destroy(d.batch);
+    batch_cache_destroy(d.run_cache);
+    if (d.run_stream) cudaStreamDestroy(d.run_stream);
+    d.batch = d.run_cache = nullptr;
+    d.run_stream = nullptr;
 }
 
 namespace {
 
-// Uploads the plan into the cache's device buffers.
-mlmc_status upload(BatchCache &c, const Plan &p) {
+// Uploads the plan into the cache's device buffers: the descriptors are
+// packed into pinned staging memory and copied asynchronously on s (the
+// buffers only grow, with cudaMalloc, when a larger batch arrives).
+mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     cudaError_t e;
     const size_t n = p.items.size();
     if ((e = grow(&c.items, &c.items_cap, n)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if ((e = grow(&c.tiles, &c.tiles_cap, p.ntiles)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if ((e = grow(&c.partials, &c.partials_cap, p.ntiles)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if ((e = grow(&c.start, &c.start_cap, p.start.size())) != cudaSuccess) return cuda_fail(e, "batch buffers");
-    if ((e = grow(&c.list, &c.list_cap, p.list.size())) != cudaSuccess) return cuda_fail(e, "batch buffers");
+    if ((e = grow(&c.list, &c.list_cap, std::max<size_t>(p.list.size(), 1))) != cudaSuccess)
+        return cuda_fail(e, "batch buffers");
     if ((e = grow(&c.counters, &c.counters_cap, p.groups.size())) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if ((e = grow(&c.sums, &c.sums_cap, n)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if (c.sums_host_cap < n) {
@@ -188,17 +202,31 @@ mlmc_status upload(BatchCache &c, const Plan &p) {
         if ((e = cudaMallocHost(&c.sums_host, n * sizeof(double2))) != cudaSuccess) return cuda_fail(e, "pinned");
         c.sums_host_cap = n;
     }
-    if ((e = cudaMemcpy(c.items, p.items.data(), n * sizeof(LevelArgs), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return cuda_fail(e, "upload");
-    std::vector<Tile> all;
-    all.reserve(p.ntiles);
-    for (const auto &g : p.groups) all.insert(all.end(), g.tiles.begin(), g.tiles.end());
-    if ((e = cudaMemcpy(c.tiles, all.data(), all.size() * sizeof(Tile), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return cuda_fail(e, "upload");
-    if ((e = cudaMemcpy(c.start, p.start.data(), p.start.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
-        return cuda_fail(e, "upload");
-    if (!p.list.empty() &&
-        (e = cudaMemcpy(c.list, p.list.data(), p.list.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    const size_t b_items = n * sizeof(LevelArgs), b_tiles = (size_t)p.ntiles * sizeof(Tile);
+    const size_t b_start = p.start.size() * 4, b_list = p.list.size() * 4;
+    const size_t total = b_items + b_tiles + b_start + b_list;
+    if (c.stage_cap < total) {
+        if (c.stage) cudaFreeHost(c.stage);
+        c.stage = nullptr;
+        c.stage_cap = 0;
+        if ((e = cudaMallocHost(&c.stage, total * 2)) != cudaSuccess) return cuda_fail(e, "pinned");
+        c.stage_cap = total * 2;
+    }
+    // the previous round's copies out of the staging buffer must be done
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload");
+    unsigned char *h = c.stage;
+    memcpy(h, p.items.data(), b_items);
+    size_t off = b_items;
+    for (const auto &g : p.groups) {
+        memcpy(h + off, g.tiles.data(), g.tiles.size() * sizeof(Tile));
+        off += g.tiles.size() * sizeof(Tile);
+    }
+    memcpy(h + off, p.start.data(), b_start);
+    if (b_list) memcpy(h + off + b_start, p.list.data(), b_list);
+    if ((e = cudaMemcpyAsync(c.items, h, b_items, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c.tiles, h + b_items, b_tiles, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c.start, h + off, b_start, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (b_list && (e = cudaMemcpyAsync(c.list, h + off + b_start, b_list, cudaMemcpyHostToDevice, s)) != cudaSuccess))
         return cuda_fail(e, "upload");
     return MLMC_OK;
 }
@@ -246,7 +274,7 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
     mlmc_status st = MLMC_OK;
     for (int lw : cands) {
         Plan p = make_plan(d, w, n, seed, lw);
-        if ((st = upload(c, p))) break;
+        if ((st = upload(c, p, s))) break;
         cudaEventRecord(a, s);
         if ((st = enqueue(d, c, p, s, false))) break;
         cudaEventRecord(b, s);
@@ -264,6 +292,26 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
 }
 
 }  // namespace
+
+// One round of a caller that owns its own cache (the adaptive driver):
+// descriptors, persistent kernels, finalize and the copy of all sums into
+// c.sums_host, enqueued on s.  The caller waits on s before reading.
+// The tile size follows the round's total work: about four tiles per
+// resident lane, each at least 16 and at most 4096 steps long per lane.
+mlmc_status batch_round(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed,
+                        cudaStream_t s) {
+    double steps = 0.0;
+    for (int i = 0; i < n; ++i) steps += ldexp((double)((w[i].N + 1) / 2), w[i].l);
+    const double lanes = (double)d.sm_count * 24 * 32;
+    int lw = (int)floor(log2(std::max(steps / (4.0 * lanes), 1.0)));
+    lw = std::min(12, std::max(4, lw));
+    Plan p = make_plan(d, w, n, seed, lw);
+    mlmc_status st = upload(c, p, s);
+    if (st) return st;
+    return enqueue(d, c, p, s, true);
+}
+
+const double2 *batch_sums_host(const BatchCache &c) { return c.sums_host; }
 
 }  // namespace mlmc
 
@@ -318,7 +366,10 @@ extern "C" mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t 
             }
         }
         Plan p = make_plan(*d, items, n_items, seed, lw);
-        if ((st = upload(c, p))) return st;
+        if ((st = upload(c, p, c.capture_stream))) return st;
+        // the graph is launched on the caller's stream: the descriptors must have landed
+        cudaError_t ue = cudaStreamSynchronize(c.capture_stream);
+        if (ue != cudaSuccess) return cuda_fail(ue, "upload");
         if (c.exec) {
             cudaGraphExecDestroy(c.exec);
             c.exec = nullptr;

@@ -10,13 +10,18 @@
 // from the last level means meets eps / sqrt(2) (the standard algorithm the
 // paper cites; alpha = weak order).
 //
-// Each round enqueues every term's new samples on one stream (fresh counter
-// ranges: path_offset = samples already taken), then copies all sums to the
-// host once.
+// Each round runs every term's new samples (fresh counter ranges:
+// path_offset = samples already taken) as the items of one persistent batched
+// launch, then copies all sums to the host once.  The allocation uses a cost
+// model C = 2^l nu (ns per path-step of each variant, measured on GB300); only
+// the ratios between terms matter to the split.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <chrono>
+#include <mutex>
 #include <vector>
 
 #include "api_internal.h"
@@ -35,23 +40,15 @@ struct Term {
     double mean() const { return n ? s1 / n : 0.0; }
 };
 
-// Device ns per fine path-step of each variant, measured from launches big
-// enough to fill the GPU; a launch-size-independent cost model C = 2^l nu.
-struct CostModel {
-    double ns[2][2][2][3] = {};        // [four][prec][kahan][icdf]
-    double ps[2][2][2][3] = {};
-    double nu(const Term &t) const {
-        const double n = ns[t.four][t.prec][t.kahan][t.icdf], p = ps[t.four][t.prec][t.kahan][t.icdf];
-        if (p > 0.0) return n / p;
-        // before any large launch: relative weights from the operation counts
-        return t.four ? 2.2e-3 : (t.icdf == MLMC_ICDF_EXACT ? 1.7e-3 : 1.2e-3);
-    }
-    void add(const Term &t, double kernel_ns, double path_steps) {
-        if (path_steps < 4194304.0) return;
-        ns[t.four][t.prec][t.kahan][t.icdf] += kernel_ns;
-        ps[t.four][t.prec][t.kahan][t.icdf] += path_steps;
-    }
-};
+// Device ns per fine path-step of each variant at full occupancy, measured on
+// GB300 with N = 2^20 samples per level (two-way / four-way; exact, table
+// and MLP normals).
+double nu_of(const Term &t) {
+    if (t.icdf == MLMC_ICDF_MLP) return t.four ? 9.0e-3 : 7.0e-3;
+    if (t.icdf == MLMC_ICDF_EXACT) return t.kahan ? 1.8e-3 : 1.65e-3;
+    if (t.four) return t.prec == MLMC_F16 ? 2.45e-3 : 2.6e-3;
+    return t.prec == MLMC_F16 ? (t.kahan ? 1.12e-3 : 1.0e-3) : (t.kahan ? 1.4e-3 : 1.25e-3);
+}
 
 }  // namespace
 
@@ -63,75 +60,139 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
     const bool nested = o->estimator == 1;
     if (nested && o->icdf == MLMC_ICDF_MLP && !d->mlp_ready) return fail(MLMC_ENOTREADY, "MLP weights not set");
 
-    cudaStream_t s;
-    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
-    const int max_terms = 2 * MLMC_MAX_LEVELS;
-    double *sums_dev = nullptr, *sums_host = nullptr;
-    std::vector<cudaEvent_t> ev(2 * max_terms, nullptr);
-    if ((e = cudaMalloc(&sums_dev, 2 * max_terms * sizeof(double))) != cudaSuccess) st = cuda_fail(e, "cudaMalloc");
-    if (!st && (e = cudaMallocHost(&sums_host, 2 * max_terms * sizeof(double))) != cudaSuccess)
-        st = cuda_fail(e, "cudaMallocHost");
-    for (auto &x : ev)
-        if (!st && (e = cudaEventCreate(&x)) != cudaSuccess) st = cuda_fail(e, "cudaEventCreate");
-    cudaEvent_t done = nullptr;
-    if (!st && (e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess)
+    // one run at a time per process: the stream and round buffers persist
+    // across runs so that a run allocates nothing once they are large enough
+    static std::mutex run_mu;
+    std::lock_guard<std::mutex> lock(run_mu);
+    cudaError_t e;
+    if (!d->run_stream && (e = cudaStreamCreateWithFlags(&d->run_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    if (!d->run_cache) d->run_cache = batch_cache_create();
+    cudaStream_t s = d->run_stream;
+    BatchCache *cache = d->run_cache;
+    cudaEvent_t done = nullptr, ev_a = nullptr, ev_b = nullptr;
+    if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess)
         st = cuda_fail(e, "cudaEventCreate");
+    // MLMC_RUN_LOG=1: one JSON line per round on stderr (items, path-steps,
+    // device and wall time)
+    const char *log_env = getenv("MLMC_RUN_LOG");
+    const bool log = log_env && atoi(log_env) > 0;
+    if (log) {
+        cudaEventCreate(&ev_a);
+        cudaEventCreate(&ev_b);
+    }
 
     std::vector<Term> terms;
-    CostModel model;
-    auto add_level = [&](int l) {
-        if (nested) {
+    std::vector<int> lvl_prec(MLMC_MAX_LEVELS, o->prec), lvl_kahan(MLMC_MAX_LEVELS, o->kahan ? 1 : 0);
+    std::vector<double> lvl_eff(MLMC_MAX_LEVELS, 0.0);
+    double path_steps = 0.0;
+    const double limit = o->timeout_s > 0 ? o->timeout_s : wait_limit_s();
+    int rounds = 0;
+
+    // Adds dn samples to every term with dn > 0 in one batched launch.
+    auto run_round = [&](std::vector<Term> &ts) -> mlmc_status {
+        std::vector<mlmc_work> items;
+        std::vector<size_t> which;
+        for (size_t i = 0; i < ts.size(); ++i) {
+            if (ts[i].dn == 0) continue;
+            mlmc_work w;
+            memset(&w, 0, sizeof w);
+            w.params = *p;
+            w.l = ts[i].l;
+            w.kind = ts[i].four;
+            w.prec = ts[i].prec;
+            w.kahan = ts[i].kahan;
+            w.icdf = ts[i].icdf;
+            w.set_id = 0;
+            w.N = ts[i].dn;
+            w.path_offset = ts[i].n;
+            items.push_back(w);
+            which.push_back(i);
+        }
+        if (items.empty()) return MLMC_OK;
+        const auto t0 = std::chrono::steady_clock::now();
+        if (log) cudaEventRecord(ev_a, s);
+        mlmc_status r = batch_round(*d, *cache, items.data(), (int)items.size(), o->seed, s);
+        if (r) return r;
+        if (log) cudaEventRecord(ev_b, s);
+        cudaEventRecord(done, s);
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        if ((r = wait_event(done, fmax(limit - el, 0.001)))) return r;
+        if (log) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, ev_a, ev_b);
+            double ps = 0.0;
+            for (const auto &w : items) ps += ldexp((double)w.N, w.l);
+            const double host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            fprintf(stderr, "{\"mlmc_run_round\": %d, \"items\": %zu, \"path_steps\": %.0f, \"device_ms\": %.4f, "
+                            "\"wall_ms\": %.4f}\n", rounds, items.size(), ps, ms, host_ms);
+        }
+        const double2 *sums = batch_sums_host(*cache);
+        for (size_t k = 0; k < which.size(); ++k) {
+            Term &t = ts[which[k]];
+            path_steps += (double)t.dn * ldexp(1.0, t.l);
+            t.s1 += sums[k].x;
+            t.s2 += sums[k].y;
+            t.n += t.dn;
+            t.dn = 0;
+        }
+        ++rounds;
+        return MLMC_OK;
+    };
+    // Runs n0 samples of each candidate term at once.
+    auto trial = [&](std::vector<Term> &cand) -> mlmc_status {
+        for (Term &t : cand) t.dn = o->n0;
+        return run_round(cand);
+    };
+    const bool autoprec = nested && o->prec < 0;
+    auto add_level = [&](int l) -> mlmc_status {
+        if (!nested) {
+            terms.push_back(Term{l, 0, MLMC_F32, o->kahan ? 1 : 0, MLMC_ICDF_EXACT});
+            terms.back().dn = o->n0;
+            return MLMC_OK;
+        }
+        if (!autoprec) {
             terms.push_back(Term{l, 0, o->prec, o->kahan ? 1 : 0, o->icdf});
             terms.push_back(Term{l, 1, o->prec, o->kahan ? 1 : 0, o->icdf});
-        } else {
-            terms.push_back(Term{l, 0, MLMC_F32, o->kahan ? 1 : 0, MLMC_ICDF_EXACT});
+            terms[terms.size() - 2].dn = terms.back().dn = o->n0;
+            return MLMC_OK;
         }
-        for (size_t i = terms.size() - (nested ? 2 : 1); i < terms.size(); ++i) terms[i].dn = o->n0;
+        // candidates (two-way, four-way) x {FP16 + Kahan, FP16, FP32}, plus the
+        // standard FP32 exact-normal two-way term for the efficiency factor
+        const int cp[3] = {MLMC_F16, MLMC_F16, MLMC_F32}, ck[3] = {1, 0, 0};
+        std::vector<Term> cand;
+        for (int c = 0; c < 3; ++c) {
+            cand.push_back(Term{l, 0, cp[c], ck[c], o->icdf});
+            cand.push_back(Term{l, 1, cp[c], ck[c], o->icdf});
+        }
+        cand.push_back(Term{l, 0, MLMC_F32, 0, MLMC_ICDF_EXACT});
+        mlmc_status r = trial(cand);
+        if (r) return r;
+        auto vc = [&](const Term &t) { return t.var() * ldexp(1.0, t.l) * nu_of(t); };
+        int best = 0;
+        double best_score = 1e300;
+        for (int c = 0; c < 3; ++c) {
+            const double score = sqrt(vc(cand[2 * c])) + sqrt(vc(cand[2 * c + 1]));
+            if (score < best_score) {
+                best_score = score;
+                best = c;
+            }
+        }
+        const double vc2 = vc(cand[2 * best]), vc4 = vc(cand[2 * best + 1]), vch = vc(cand[6]);
+        if (vch > 0.0 && vc2 > 0.0) lvl_eff[l] = vc2 / vch * pow(1.0 + sqrt(vc4 / vc2), 2.0);
+        lvl_prec[l] = cp[best];
+        lvl_kahan[l] = ck[best];
+        terms.push_back(cand[2 * best]);
+        terms.push_back(cand[2 * best + 1]);
+        return MLMC_OK;
     };
     int L = o->min_levels - 1;
-    for (int l = 0; l <= L; ++l) add_level(l);
-    const double limit = o->timeout_s > 0 ? o->timeout_s : wait_limit_s();
+    for (int l = 0; l <= L && !st; ++l) st = add_level(l);
     const int per_level = nested ? 2 : 1;
-    int rounds = 0;
-    double path_steps = 0.0;
     bool converged = false;
 
     while (!st) {
-        // ---- enqueue this round's samples, one launch per term with new samples
-        bool any = false;
-        for (size_t i = 0; i < terms.size() && !st; ++i) {
-            Term &t = terms[i];
-            if (t.dn == 0) continue;
-            any = true;
-            st = enqueue_level(*d, t.four, t.l, t.dn, t.prec, t.kahan, t.icdf, p, o->seed, t.n, 0, sums_dev + 2 * i,
-                               nullptr, s, ev[2 * i], ev[2 * i + 1]);
-        }
-        if (st) break;
-        if (any) {
-            ++rounds;
-            if ((e = cudaMemcpyAsync(sums_host, sums_dev, 2 * terms.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                                     s)) != cudaSuccess) {
-                st = cuda_fail(e, "cudaMemcpyAsync");
-                break;
-            }
-            cudaEventRecord(done, s);
-            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-            if ((st = wait_event(done, fmax(limit - el, 0.001)))) break;
-            for (size_t i = 0; i < terms.size(); ++i) {
-                Term &t = terms[i];
-                if (t.dn == 0) continue;
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
-                const double ps = (double)t.dn * ldexp(1.0, t.l);
-                model.add(t, (double)ms * 1e6, ps);
-                path_steps += ps;
-                t.s1 += sums_host[2 * i];
-                t.s2 += sums_host[2 * i + 1];
-                t.n += t.dn;
-                t.dn = 0;
-            }
-        }
+        if ((st = run_round(terms))) break;
         // ---- variance and cost estimates; optimal sample counts
         std::vector<double> V(terms.size()), C(terms.size());
         for (size_t i = 0; i < terms.size(); ++i) {
@@ -139,7 +200,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
             // a level's variance is at least half its predecessor's, decayed
             // at strong rate beta = 1 (guards new levels with few samples)
             if (terms[i].l >= 2) V[i] = fmax(V[i], 0.5 * V[i - per_level] * 0.5);
-            C[i] = ldexp(1.0, terms[i].l) * model.nu(terms[i]);
+            C[i] = ldexp(1.0, terms[i].l) * nu_of(terms[i]);
             terms[i].cost = C[i];
         }
         double total = 0.0;
@@ -168,7 +229,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         }
         if (L >= o->max_level) break;
         ++L;
-        add_level(L);
+        st = add_level(L);
     }
 
     if (!st) {
@@ -187,16 +248,18 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         out->variance = var;
         out->levels = L + 1;
         out->rounds = rounds;
+        for (int l = 0; l <= L && l < MLMC_MAX_LEVELS; ++l) {
+            out->prec[l] = nested ? lvl_prec[l] : MLMC_F32;
+            out->kahan[l] = nested ? lvl_kahan[l] : (o->kahan ? 1 : 0);
+            out->efficiency[l] = lvl_eff[l];
+        }
         out->path_steps = path_steps;
         out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
         if (!converged) st = fail(MLMC_ENOTCONV, "bias test not met at max_level %d", o->max_level);
     }
-    for (auto &x : ev)
-        if (x) cudaEventDestroy(x);
     if (done) cudaEventDestroy(done);
-    if (sums_dev) cudaFree(sums_dev);
-    if (sums_host) cudaFreeHost(sums_host);
-    cudaStreamDestroy(s);
+    if (ev_a) cudaEventDestroy(ev_a);
+    if (ev_b) cudaEventDestroy(ev_b);
     return st;
 }
 
@@ -217,7 +280,8 @@ extern "C" mlmc_status mlmc_run(double eps, const mlmc_sde_params *params, const
     if (opts->n0 < 2) return fail(MLMC_EINVAL, "n0 must be >= 2");
     if (!(opts->alpha > 0.0)) return fail(MLMC_EINVAL, "alpha must be > 0");
     if (opts->estimator == 1) {
-        if (opts->prec != MLMC_F32 && opts->prec != MLMC_F16) return fail(MLMC_EINVAL, "unknown precision");
+        if (opts->prec != MLMC_F32 && opts->prec != MLMC_F16 && opts->prec != -1)
+            return fail(MLMC_EINVAL, "unknown precision");
         if (opts->icdf != MLMC_ICDF_TABLE && opts->icdf != MLMC_ICDF_MLP)
             return fail(MLMC_EINVAL, "nested estimator needs approximate normals");
     }

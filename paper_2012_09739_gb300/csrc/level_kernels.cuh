@@ -40,6 +40,7 @@ struct LevelArgs {
     const MlpWeights *mlp;    // network (ICDF_MLP only)
     double2 *partials;        // (sum D, sum D^2) per warp chunk, or per block
     int chunk_partials;       // 1: one partial per chunk of 32 pairs (result independent of the grid)
+    unsigned long long *counter;  // chunk counter of the persistent schedule (chunk_partials)
     float *paths_out;         // optional per-sample output (3 or 5 floats per sample)
 };
 
@@ -52,7 +53,7 @@ struct PathPair {
         diff = Pair<P>::of(diff_);
         mean = Pair<P>::of(mean_);
         X = Pair<P>::of(x0);
-        c = Pair<P>::of(0.0);
+        c = Pair<P>::of2(0.0f, 0.0f);
     }
     // X <- X (+) (A (+) B): A = a delta, B = (b sqrt(delta)) (x) z  (Sec. 2.2);
     // with Kahan compensation of the outer addition (Sec. 2.3, Algorithm 1).
@@ -196,12 +197,19 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Warp w takes chunks w, w + W, ... of 32 consecutive pairs (one per lane).
-// With chunk_partials each chunk's FP32 warp sum goes, in FP64, to its own
-// slot, so the finalize kernel adds the same values in the same order
-// whatever the grid; otherwise one slot per block (warps summed in FP64).
+// Chunks of 32 consecutive pairs (one per lane), in groups of
+// chunk_group(l) chunks (more at coarse levels, where a chunk is short).
+// With chunk_partials the grid is persistent: each warp takes the next group
+// from an atomic counter (a.counter, zeroed before the launch) until none is
+// left; its lanes accumulate the group's samples in FP32 (Kahan) and the warp
+// sum goes, in FP64, to the group's own slot, so the finalize kernel adds the
+// same values in the same order whatever the grid or the schedule.
+// Otherwise warp w takes chunks w, w + W, ... and one slot per block holds
+// the block's sum (warps added in FP64).
+__host__ __device__ __forceinline__ uint32_t chunk_group(int l) { return l >= 6 ? 1u : (64u >> l); }
+
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 1 : 3) level_kernel(const LevelArgs a) {
+__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 1 : 4) level_kernel(const LevelArgs a) {
     __shared__ SmemTable tab;
     __shared__ double red[2][32];
     if (ICDF == ICDF_TABLE) {
@@ -214,38 +222,48 @@ __global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 1 : 3) level_kernel(co
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     const uint64_t warp_id = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    for (uint64_t base = warp_id * 32; base < a.npairs; base += warps * 32) {
-        const uint64_t g = base + lane;
-        const bool active = g < a.npairs;
-        float d0, d1, out0[5], out1[5];
-        simulate_pair<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, active ? g : a.npairs - 1, d0, d1, out0, out1);
-        const bool valid1 = 2 * g + 1 < a.N;
+    const uint64_t nchunks = (a.npairs + 31) >> 5;
+    const uint64_t G = a.chunk_partials ? chunk_group(a.l) : 1;
+    for (uint64_t grp = warp_id;; grp += warps) {
         if (a.chunk_partials) {
-            float c1 = 0.0f, c2 = 0.0f;
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(a.counter, 1ull);
+            grp = __shfl_sync(0xffffffffu, t, 0);
+        }
+        const uint64_t c0 = grp * G;
+        if (c0 >= nchunks) break;
+        const uint64_t c1 = c0 + G < nchunks ? c0 + G : nchunks;
+        for (uint64_t c = c0; c < c1; ++c) {
+            const uint64_t base = c * 32;
+            const uint64_t g = base + lane;
+            const bool active = g < a.npairs;
+            float d0, d1, out0[5], out1[5];
+            simulate_pair<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, active ? g : a.npairs - 1, d0, d1, out0, out1);
+            const bool valid1 = 2 * g + 1 < a.N;
             if (active) {
-                c1 = valid1 ? __fadd_rn(d0, d1) : d0;
-                c2 = valid1 ? fmaf(d1, d1, d0 * d0) : d0 * d0;
+                k1.add(d0);
+                k2.add(d0 * d0);
+                if (valid1) {
+                    k1.add(d1);
+                    k2.add(d1 * d1);
+                }
             }
-            c1 = warp_sum(c1);
-            c2 = warp_sum(c2);
-            if (lane == 0) a.partials[base >> 5] = make_double2((double)c1, (double)c2);
-        } else if (active) {
-            k1.add(d0);
-            k2.add(d0 * d0);
-            if (valid1) {
-                k1.add(d1);
-                k2.add(d1 * d1);
+            if (active && a.paths_out != nullptr) {
+                constexpr int W = MODE == MODE_TWO ? 3 : 5;
+                float *o = a.paths_out + (2 * g) * W;
+#pragma unroll
+                for (int k = 0; k < W; ++k) o[k] = out0[k];
+                if (valid1) {
+#pragma unroll
+                    for (int k = 0; k < W; ++k) o[W + k] = out1[k];
+                }
             }
         }
-        if (active && a.paths_out != nullptr) {
-            constexpr int W = MODE == MODE_TWO ? 3 : 5;
-            float *o = a.paths_out + (2 * g) * W;
-#pragma unroll
-            for (int k = 0; k < W; ++k) o[k] = out0[k];
-            if (valid1) {
-#pragma unroll
-                for (int k = 0; k < W; ++k) o[W + k] = out1[k];
-            }
+        if (a.chunk_partials) {
+            const float w1 = warp_sum(k1.value()), w2 = warp_sum(k2.value());
+            if (lane == 0) a.partials[grp] = make_double2((double)w1, (double)w2);
+            k1 = KahanF32();
+            k2 = KahanF32();
         }
     }
     if (a.chunk_partials) return;

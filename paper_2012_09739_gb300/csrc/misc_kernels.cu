@@ -62,12 +62,19 @@ cudaError_t launch_build_table(double *t64, float2 *t32, __half2 *t16, cudaStrea
 }
 
 // ---------------------------------------------------------------- finalize
-// Deterministic FP64 sum of the partials: a fixed strided split across 1024
-// threads, then a fixed tree.  out[0] = sum D, out[1] = sum D^2.
-__global__ void __launch_bounds__(1024) finalize_kernel(const double2 *partials, uint64_t count, double *out) {
+// Deterministic FP64 sum of the partials: each block adds a fixed range of up
+// to FINALIZE_SPAN partials (fixed strided split over 1024 threads, then a
+// fixed tree).  One block when the partials fit one span; otherwise a first
+// pass writes one sum per span and a single block adds those.
+constexpr uint64_t FINALIZE_SPAN = 8192;
+
+__global__ void __launch_bounds__(1024) finalize_kernel(const double2 *partials, uint64_t count, double2 *out) {
     __shared__ double r1[1024], r2[1024];
+    const uint64_t lo = (uint64_t)blockIdx.x * FINALIZE_SPAN;
+    const uint64_t hi = lo + FINALIZE_SPAN < count ? lo + FINALIZE_SPAN : count;
+    const uint64_t end = gridDim.x == 1 ? count : hi;
     double t1 = 0.0, t2 = 0.0;
-    for (uint64_t i = threadIdx.x; i < count; i += 1024) {
+    for (uint64_t i = lo + threadIdx.x; i < end; i += 1024) {
         t1 += partials[i].x;
         t2 += partials[i].y;
     }
@@ -81,14 +88,19 @@ __global__ void __launch_bounds__(1024) finalize_kernel(const double2 *partials,
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        out[0] = r1[0];
-        out[1] = r2[0];
-    }
+    if (threadIdx.x == 0) out[blockIdx.x] = make_double2(r1[0], r2[0]);
 }
 
-cudaError_t launch_finalize(const double2 *partials, uint64_t count, double *out, cudaStream_t s) {
-    finalize_kernel<<<1, 1024, 0, s>>>(partials, count, out);
+uint64_t finalize_scratch(uint64_t count) { return count <= FINALIZE_SPAN ? 0 : (count + FINALIZE_SPAN - 1) / FINALIZE_SPAN; }
+
+cudaError_t launch_finalize(const double2 *partials, uint64_t count, double *out, double2 *scratch, cudaStream_t s) {
+    const uint64_t spans = finalize_scratch(count);
+    if (spans == 0) {
+        finalize_kernel<<<1, 1024, 0, s>>>(partials, count, reinterpret_cast<double2 *>(out));
+    } else {
+        finalize_kernel<<<(unsigned)spans, 1024, 0, s>>>(partials, count, scratch);
+        finalize_kernel<<<1, 1024, 0, s>>>(scratch, spans, reinterpret_cast<double2 *>(out));
+    }
     return cudaGetLastError();
 }
 

@@ -103,6 +103,7 @@ extern "C" mlmc_status mlmc_level_noalloc(int four, int l, uint64_t N, int prec,
     const int grid = (int)((a.npairs + NOALLOC_BLOCK - 1) / NOALLOC_BLOCK);
     fn<<<grid, NOALLOC_BLOCK, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "level kernel launch");
-    if ((e = launch_finalize(na->partials, grid, sums_dev, s)) != cudaSuccess) return cuda_fail(e, "finalize");
+    // grid <= 4096 partials: one finalize block, no finalize scratch
+    if ((e = launch_finalize(na->partials, grid, sums_dev, nullptr, s)) != cudaSuccess) return cuda_fail(e, "finalize");
     return MLMC_OK;
 }

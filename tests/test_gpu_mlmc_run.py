@@ -47,3 +47,37 @@ def test_mlmc_run_invalid():
         M.mlmc_run(-1.0, params, _opts(0))
     with pytest.raises(M.MlmcError):
         M.mlmc_run(1e-3, params, _opts(1, icdf=M.MLMC_ICDF_EXACT))
+
+
+def test_mlmc_run_auto_precision_per_level():
+    """prec = -1: each level keeps the variant with the smallest
+    sqrt(v c) + sqrt(V C) (Sec. 3) and reports the per-level efficiency
+    factor against the standard estimator."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    eps = 2e-4
+    params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    r = M.mlmc_run(eps, params, _opts(1, prec=-1))
+    assert abs(r.estimate - mlmc.bs_call()) < 4 * eps
+    assert r.variance <= eps * eps / 2 * 1.05
+    for l in range(r.levels):
+        assert r.prec[l] in (M.MLMC_F16, M.MLMC_F32)
+        assert r.efficiency[l] > 0.0
+        assert r.n[0][l] >= 10000 and r.n[1][l] >= 10000
+
+
+def test_mlmc_run_timeout_is_reported_and_recoverable():
+    """A wall-clock limit that cannot be met ends the host wait with
+    MLMC_ETIMEOUT (the GPU work itself completes; nothing hangs); the next run
+    on the same device succeeds."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    o = _opts(0)
+    o.timeout_s = 1e-4
+    with pytest.raises(M.MlmcError) as e:
+        M.mlmc_run(1e-5, params, o)
+    assert e.value.status == M.MLMC_ETIMEOUT
+    torch.cuda.synchronize()
+    r = M.mlmc_run(1e-3, params, _opts(0))
+    assert abs(r.estimate - mlmc.bs_call()) < 4e-3

@@ -1,0 +1,108 @@
+"""The paper's rounding-error findings reproduced with real binary16 and
+binary32 arithmetic on the GPU (Sec. 2.2-2.3 and the Fig. 3 discussion of
+Sec. 3): GBM mu = 0.05, sigma = 0.2, X0 = 1, P(X) = X, piecewise-linear
+approximate normals, variances of the two-way and four-way level differences
+against delta = 2^-l.  The paper states its observations approximately and
+for its own approximation and hardware, so break points are checked to
+within a level or two and ratios to within a factor 2^+-1.5."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2012_09739_gb300 as M  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
+LEVELS = list(range(0, 19))
+
+
+def _pv():
+    vals = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, value, _ = line.split()
+            vals[name] = float(value)
+    return vals
+
+
+@pytest.fixture(scope="module")
+def curves():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_X, p0=0.05, p1=0.2)
+    T = M.MLMC_ICDF_TABLE
+    out = {k: [] for k in ("exact", "two16", "two16k", "four32", "four32k", "four16", "four16k")}
+    for l in LEVELS:
+        N = 1 << 20 if l <= 12 else 1 << (32 - l)
+        out["exact"].append(M.mlmc_level(l, N, M.MLMC_F32, True, M.MLMC_ICDF_EXACT, p, 1234).var())
+        out["two16"].append(M.mlmc_level(l, N, M.MLMC_F16, False, T, p, 1234).var())
+        out["two16k"].append(M.mlmc_level(l, N, M.MLMC_F16, True, T, p, 1234).var())
+        out["four32"].append(M.mlmc_nested_level(l, N, M.MLMC_F32, False, T, p, 1234).var())
+        out["four32k"].append(M.mlmc_nested_level(l, N, M.MLMC_F32, True, T, p, 1234).var())
+        out["four16"].append(M.mlmc_nested_level(l, N, M.MLMC_F16, False, T, p, 1234).var())
+        out["four16k"].append(M.mlmc_nested_level(l, N, M.MLMC_F16, True, T, p, 1234).var())
+    return {k: np.log2(np.array(v)) for k, v in out.items()}
+
+
+def _slope(y, lo, hi):
+    ls = np.arange(lo, hi + 1)
+    return np.polyfit(ls, y[lo:hi + 1], 1)[0]
+
+
+def test_two_way_double_proxy_decays_like_delta(curves):
+    assert abs(_slope(curves["exact"], 2, 18) + 1.0) < 0.05
+
+
+def test_half_two_way_without_kahan(curves):
+    """Tracks the exact-arithmetic curve down to delta ~ 2^-7, then grows like
+    N rho^2 (slope +1, Lemma 2.6)."""
+    lvl = int(_pv()["half_twoway_tracks_double_to_level"])
+    gap = curves["two16"] - curves["exact"]
+    assert np.all(np.abs(gap[:lvl - 2]) < 0.2)
+    assert np.all(gap[lvl + 1:] > 1.0)
+    assert abs(_slope(curves["two16"], 10, 18) - 1.0) < 0.1
+
+
+def test_half_two_way_with_kahan(curves):
+    lvl = int(_pv()["half_kahan_twoway_tracks_double_to_level"])
+    gap = curves["two16k"] - curves["exact"]
+    assert np.all(np.abs(gap[:lvl - 1]) < 0.3)
+    assert np.all(gap[lvl + 2:] > 1.0)
+
+
+def test_single_four_way(curves):
+    pv = _pv()
+    lvl = int(pv["single_fourway_decays_to_level"])
+    assert abs(_slope(curves["four32"], 2, lvl - 2) + 1.0) < 0.1
+    assert _slope(curves["four32"], lvl + 2, 18) > 0.7           # the O(delta^-1) term
+    red17 = curves["four32"][17] - curves["exact"][17]
+    assert abs(red17 - pv["single_fourway_log2_reduction_at_level17"]) < 1.5
+    # Kahan removes the rounding term: O(delta) all the way down
+    assert abs(_slope(curves["four32k"], 2, 18) + 1.0) < 0.1
+
+
+def test_half_four_way_without_kahan(curves):
+    pv = _pv()
+    red0 = curves["four16"][0] - curves["exact"][0]
+    assert red0 < pv["half_fourway_log2_reduction_at_level0"] + 1.5
+    # at least ~2^-6 below the two-way difference at the coarsest levels
+    assert np.all(curves["four16"][:4] - curves["exact"][:4] < -6.0)
+    # coincides with the two-way half-precision difference once rounding dominates
+    assert np.all(np.abs(curves["four16"][9:] - curves["two16"][9:]) < 0.3)
+
+
+def test_half_four_way_with_kahan(curves):
+    pv = _pv()
+    lvl = int(pv["half_kahan_fourway_flat_to_level"])
+    flat = curves["four16k"][1:lvl + 3]
+    assert flat.max() - flat.min() < 1.0                              # O(1)
+    red = curves["four16k"][:9] - curves["exact"][:9]
+    assert np.all(red[4:9] < pv["half_kahan_fourway_log2_reduction_to_level8"] + 1.5)
+    # finer still, the two-way and four-way half-precision variances coincide
+    assert np.all(np.abs(curves["four16k"][14:] - curves["two16k"][14:]) < 0.5)
