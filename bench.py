@@ -347,7 +347,7 @@ def time_to_eps(M, params, eps_list, repeats=3):
     return out
 
 
-def mlp_leg(M, torch, params):
+def mlp_leg(M, torch, params, steps=20000, level=10, n=1 << 20):
     """The learned part: train the FP16 tensor-core MLP surrogate on 2^20
     (u, |Phi^-1|) pairs (targets computed on the device in FP64), then its
     E|Z - Z~|^2 against the table's and the four-way throughput with it."""
@@ -355,7 +355,7 @@ def mlp_leg(M, torch, params):
     dev = torch.device("cuda")
     M.mlmc_mlp_set_weights(mlp_initial_weights(1234))
     u = torch.tensor(uniform_grid_sample(1 << 20, 31), dtype=torch.float32, device=dev)
-    opts = M.mlmc_train_opts(steps=20000, batch=8192, lr0=1e-2, lr_min=1e-5, beta1=0.9, beta2=0.999, eps=1e-8,
+    opts = M.mlmc_train_opts(steps=steps, batch=8192, lr0=1e-2, lr_min=1e-5, beta1=0.9, beta2=0.999, eps=1e-8,
                              seed=SEED)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -372,17 +372,17 @@ def mlp_leg(M, torch, params):
     s = torch.cuda.current_stream()
     rates = {}
     for name, kind in (("mlp", M.MLMC_ICDF_MLP), ("table", M.MLMC_ICDF_TABLE)):
-        M.mlmc_level_async(1, 10, 1 << 20, M.MLMC_F16, 1, kind, params, SEED, 0, sums, s.cuda_stream)
+        M.mlmc_level_async(1, level, n, M.MLMC_F16, 1, kind, params, SEED, 0, sums, s.cuda_stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
         for _ in range(3):
-            M.mlmc_level_async(1, 10, 1 << 20, M.MLMC_F16, 1, kind, params, SEED, 0, sums, s.cuda_stream)
+            M.mlmc_level_async(1, level, n, M.MLMC_F16, 1, kind, params, SEED, 0, sums, s.cuda_stream)
         e1.record(s)
         torch.cuda.synchronize()
-        rates[name] = 3 * (1 << 20) * (1 << 10) / (e0.elapsed_time(e1) / 1e3)
-    return {"train_seconds": train_s, "steps": 20000, "batch": 8192, "pairs": 1 << 20, "final_loss": loss,
+        rates[name] = 3 * n * (1 << level) / (e0.elapsed_time(e1) / 1e3)
+    return {"train_seconds": train_s, "steps": steps, "batch": 8192, "pairs": 1 << 20, "final_loss": loss,
             "l2_error_mlp": err["mlp"], "l2_error_table": err["table"],
-            "fourway_l10_path_steps_per_s": {"mlp": rates["mlp"], "table": rates["table"]}}
+            f"fourway_l{level}_path_steps_per_s": {"mlp": rates["mlp"], "table": rates["table"]}}
 
 
 def _cpu_sample(target_s: float, nthreads: int):
@@ -465,6 +465,8 @@ def main():
     ap.add_argument("--no-tte", action="store_true", help="skip the time-to-eps leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batching leg")
     ap.add_argument("--no-mlp", action="store_true", help="skip the MLP leg")
+    ap.add_argument("--mlp-only", action="store_true", help="run only the MLP leg (profiling)")
+    ap.add_argument("--mlp-steps", type=int, default=20000)
     ap.add_argument("--eps", type=float, default=1e-3)
     ap.add_argument("--levels", type=str, default=None, help="comma-separated levels (profiling runs)")
     ap.add_argument("--n", type=int, default=None, help="samples per level (profiling runs)")
@@ -476,6 +478,12 @@ def main():
         N_PER_LEVEL = args.n
     if args.impl == "reference":
         run_reference(args)
+    elif args.mlp_only:
+        # profiling mode: the learned part alone (training steps, one four-way MLP level)
+        import torch
+        import paper_2012_09739_gb300 as M
+        params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+        print(json.dumps(mlp_leg(M, torch, params, steps=args.mlp_steps, level=LEVELS[-1], n=N_PER_LEVEL)))
     else:
         run_gpu(args)
 
