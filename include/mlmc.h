@@ -47,8 +47,13 @@ typedef enum {
 
 typedef enum { MLMC_GBM = 0, MLMC_OU = 1 } mlmc_sde_kind;
 typedef enum { MLMC_PAYOFF_X = 0, MLMC_PAYOFF_CALL = 1 } mlmc_payoff;
-/* working precision of the approximate ("bar") paths and of Z~ */
-typedef enum { MLMC_F32 = 0, MLMC_F16 = 1 } mlmc_prec;
+/* working precision of the approximate ("bar") paths and of Z~: IEEE
+ * binary32, IEEE binary16 (10 stored significand bits), or bfloat16 (7
+ * stored significand bits, binary32's exponent range; Sec. 4.1 and 5.1
+ * compare it with binary16 through the rounding model).  All arithmetic on
+ * the bar paths rounds to nearest-even in that format after every
+ * operation. */
+typedef enum { MLMC_F32 = 0, MLMC_F16 = 1, MLMC_BF16 = 2 } mlmc_prec;
 typedef enum { MLMC_ICDF_EXACT = 0, MLMC_ICDF_TABLE = 1, MLMC_ICDF_MLP = 2 } mlmc_icdf;
 
 /* SDE dX = a(X) dt + b(X) dW on [0, T], X_0 = x0.
@@ -136,7 +141,8 @@ mlmc_status mlmc_level_paths(int four, int l, uint64_t N, int prec, int kahan, i
 
 /* Bulk approximate inverse CDF (Sec. 2.1): z_dev[i] = Phi~^-1(u_dev[i]) for
  * 0 < u < 1 (values outside give unspecified finite results).  z_dev is
- * float for prec = F32 and IEEE binary16 (uint16_t storage) for F16.
+ * float for prec = F32, IEEE binary16 (uint16_t storage) for F16 and
+ * bfloat16 (uint16_t storage, the upper half of a binary32) for BF16.
  * icdf = EXACT evaluates Phi^-1 in FP32. */
 mlmc_status approx_icdf(const float *u_dev, void *z_dev, size_t n, int icdf, int prec, void *stream);
 
@@ -149,8 +155,10 @@ mlmc_status mlmc_uniforms(const uint32_t *w_dev, float *u_dev, size_t n, void *s
 /* The piecewise-linear table as built on the device (FP64 closed-form L2
  * fit of Phi^-1 on the 16 dyadic intervals of v = min(u, 1-u), Sec. 2.1):
  * c_host[2i], c_host[2i+1] = (c0, c1) of interval i+1.  Any pointer may be
- * NULL.  c32_host / c16_host receive the binary32 / binary16 roundings. */
-mlmc_status mlmc_icdf_table(double *c_host, float *c32_host, uint16_t *c16_host);
+ * NULL.  c32_host / c16_host / cbf16_host receive the binary32 / binary16 /
+ * bfloat16 roundings (round to nearest-even from the FP64 value), in the
+ * same (c0, c1) order. */
+mlmc_status mlmc_icdf_table(double *c_host, float *c32_host, uint16_t *c16_host, uint16_t *cbf16_host);
 
 /* ---- MLP surrogate inverse CDF: 1 -> 32 -> 32 -> 1 tanh network on
  * t = sqrt(-2 ln v), v = min(u, 1-u); Z~ = -y for u <= 1/2, +y above.

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmlmc.so")
 MLMC_OK, MLMC_EINVAL, MLMC_ECUDA, MLMC_ETIMEOUT, MLMC_ENOMEM, MLMC_ENOTCONV, MLMC_ENOTREADY = range(7)
 MLMC_GBM, MLMC_OU = 0, 1
 MLMC_PAYOFF_X, MLMC_PAYOFF_CALL = 0, 1
-MLMC_F32, MLMC_F16 = 0, 1
+MLMC_F32, MLMC_F16, MLMC_BF16 = 0, 1, 2
 MLMC_ICDF_EXACT, MLMC_ICDF_TABLE, MLMC_ICDF_MLP = 0, 1, 2
 MLMC_MLP_PARAMS = 1153
 MLMC_MAX_LEVELS = 19
@@ -90,7 +90,7 @@ _SIGS = {
     "approx_icdf": [_vp, _vp, ctypes.c_size_t, _i32, _i32, _vp],
     "mlmc_philox4x32_10": [_vp, _vp, _vp, ctypes.c_size_t, _vp],
     "mlmc_uniforms": [_vp, _vp, ctypes.c_size_t, _vp],
-    "mlmc_icdf_table": [_vp, _vp, _vp],
+    "mlmc_icdf_table": [_vp, _vp, _vp, _vp],
     "mlmc_mlp_set_weights": [_vp, ctypes.c_size_t],
     "mlmc_mlp_get_weights": [_vp, ctypes.c_size_t],
     "mlmc_mlp_grad": [_vp, _vp, ctypes.c_size_t, _vp, _vp, _vp],
@@ -205,13 +205,15 @@ def mlmc_uniforms(w_dev, u_dev, stream=None):
 
 
 def mlmc_icdf_table():
-    """(c64 (16, 2) float64, c32 (16, 2) float32, c16 (16, 2) uint16 bits) as built on the device."""
+    """(c64, c32, c16 bits, bf16 bits), each (16, 2), as built on the device."""
     import numpy as np
     c64 = np.zeros(32, np.float64)
     c32 = np.zeros(32, np.float32)
     c16 = np.zeros(32, np.uint16)
-    _check(load().mlmc_icdf_table(c64.ctypes.data_as(_vp), c32.ctypes.data_as(_vp), c16.ctypes.data_as(_vp)))
-    return c64.reshape(16, 2), c32.reshape(16, 2), c16.reshape(16, 2)
+    cbf = np.zeros(32, np.uint16)
+    _check(load().mlmc_icdf_table(c64.ctypes.data_as(_vp), c32.ctypes.data_as(_vp), c16.ctypes.data_as(_vp),
+                                  cbf.ctypes.data_as(_vp)))
+    return c64.reshape(16, 2), c32.reshape(16, 2), c16.reshape(16, 2), cbf.reshape(16, 2)
 
 
 def mlmc_mlp_set_weights(w):

@@ -50,9 +50,11 @@ mlmc_status device_state(DeviceState **out) {
             return cuda_fail(e, "cudaMalloc(table)");
         if ((e = cudaMalloc(&d.tab16, TAB_ENTRIES * sizeof(__half2))) != cudaSuccess)
             return cuda_fail(e, "cudaMalloc(table)");
+        if ((e = cudaMalloc(&d.tabbf, TAB_ENTRIES * sizeof(uint32_t))) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(table)");
         if ((e = cudaMalloc(&d.mlp, sizeof(MlpWeights))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(mlp)");
         if ((e = cudaMemset(d.mlp, 0, sizeof(MlpWeights))) != cudaSuccess) return cuda_fail(e, "cudaMemset(mlp)");
-        if ((e = launch_build_table(d.tab64, d.tab32, d.tab16, 0)) != cudaSuccess)
+        if ((e = launch_build_table(d.tab64, d.tab32, d.tab16, d.tabbf, 0)) != cudaSuccess)
             return cuda_fail(e, "build_table");
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "build_table");
         d.device = dev;
@@ -103,7 +105,7 @@ mlmc_status check_level(int four, int l, uint64_t N, int prec, int icdf, const m
     if (l < 0 || l > 18) return fail(MLMC_EINVAL, "level %d outside 0..18", l);
     if (N == 0) return fail(MLMC_EINVAL, "N must be >= 1");
     if (N > (1ull << 40)) return fail(MLMC_EINVAL, "N too large");
-    if (prec != MLMC_F32 && prec != MLMC_F16) return fail(MLMC_EINVAL, "unknown precision %d", prec);
+    if (prec != MLMC_F32 && prec != MLMC_F16 && prec != MLMC_BF16) return fail(MLMC_EINVAL, "unknown precision %d", prec);
     if (icdf < 0 || icdf > 2) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
     if (four && icdf == MLMC_ICDF_EXACT) return fail(MLMC_EINVAL, "four-way difference needs approximate normals");
     return check_params(p);
@@ -142,12 +144,15 @@ LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int
     a.disc = p->disc;
     a.tab32 = d.tab32;
     a.tab16 = d.tab16;
+    a.tabbf = d.tabbf;
     a.mlp = d.mlp;
     return a;
 }
 
 LevelKernelFn pick_level_kernel(int four, int prec, int kahan, int icdf, int sde) {
-    return prec == MLMC_F32 ? level_kernel_f32(four, kahan, icdf, sde) : level_kernel_f16(four, kahan, icdf, sde);
+    return prec == MLMC_F32   ? level_kernel_f32(four, kahan, icdf, sde)
+           : prec == MLMC_F16 ? level_kernel_f16(four, kahan, icdf, sde)
+                              : level_kernel_bf16(four, kahan, icdf, sde);
 }
 
 static int env_int(const char *name, int dflt) {
@@ -301,14 +306,15 @@ mlmc_status mlmc_level_paths(int four, int l, uint64_t N, int prec, int kahan, i
 
 mlmc_status approx_icdf(const float *u_dev, void *z_dev, size_t n, int icdf, int prec, void *stream) {
     if (icdf < 0 || icdf > 2) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
-    if (prec != MLMC_F32 && prec != MLMC_F16) return fail(MLMC_EINVAL, "unknown precision %d", prec);
+    if (prec != MLMC_F32 && prec != MLMC_F16 && prec != MLMC_BF16) return fail(MLMC_EINVAL, "unknown precision %d", prec);
     if (n == 0) return MLMC_OK;
     if (!u_dev || !z_dev) return fail(MLMC_EINVAL, "NULL buffer");
     DeviceState *d;
     mlmc_status st = device_state(&d);
     if (st) return st;
     if (icdf == MLMC_ICDF_MLP && !d->mlp_ready) return fail(MLMC_ENOTREADY, "MLP weights not set");
-    cudaError_t e = launch_icdf_bulk(u_dev, z_dev, n, icdf, prec, d->tab32, d->tab16, d->mlp, (cudaStream_t)stream);
+    cudaError_t e = launch_icdf_bulk(u_dev, z_dev, n, icdf, prec, d->tab32, d->tab16, d->tabbf, d->mlp,
+                                     (cudaStream_t)stream);
     return e == cudaSuccess ? MLMC_OK : cuda_fail(e, "approx_icdf");
 }
 
@@ -329,14 +335,16 @@ mlmc_status mlmc_uniforms(const uint32_t *w_dev, float *u_dev, size_t n, void *s
     return e == cudaSuccess ? MLMC_OK : cuda_fail(e, "uniforms");
 }
 
-mlmc_status mlmc_icdf_table(double *c_host, float *c32_host, uint16_t *c16_host) {
+mlmc_status mlmc_icdf_table(double *c_host, float *c32_host, uint16_t *c16_host, uint16_t *cbf16_host) {
     DeviceState *d;
     mlmc_status st = device_state(&d);
     if (st) return st;
     double t64[32];
     float2 t32[TAB_ENTRIES];
     __half2 t16[TAB_ENTRIES];
+    uint32_t tbf[TAB_ENTRIES];
     cudaError_t e = cudaMemcpy(t64, d->tab64, sizeof t64, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(tbf, d->tabbf, sizeof tbf, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(t32, d->tab32, sizeof t32, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(t16, d->tab16, sizeof t16, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "mlmc_icdf_table");
@@ -355,6 +363,10 @@ mlmc_status mlmc_icdf_table(double *c_host, float *c32_host, uint16_t *c16_host)
             __half2_raw r = *reinterpret_cast<__half2_raw *>(&t16[entry]);
             c16_host[2 * i] = r.x;
             c16_host[2 * i + 1] = r.y;
+        }
+        if (cbf16_host) {
+            cbf16_host[2 * i] = (uint16_t)(tbf[entry] & 0xFFFFu);
+            cbf16_host[2 * i + 1] = (uint16_t)(tbf[entry] >> 16);
         }
     }
     return MLMC_OK;
@@ -405,6 +417,7 @@ mlmc_status mlmc_shutdown(void) {
         cudaFree(d.tab64);
         cudaFree(d.tab32);
         cudaFree(d.tab16);
+        cudaFree(d.tabbf);
         cudaFree(d.mlp);
         d = DeviceState();
     }

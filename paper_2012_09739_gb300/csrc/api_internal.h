@@ -21,6 +21,7 @@ struct DeviceState {
     double *tab64 = nullptr;
     float2 *tab32 = nullptr;
     __half2 *tab16 = nullptr;
+    uint32_t *tabbf = nullptr;
     MlpWeights *mlp = nullptr;
     bool mlp_ready = false;
     BatchCache *batch = nullptr;         // mlmc_batch: captured graph and buffers

@@ -18,6 +18,7 @@ namespace mlmc {
 
 BatchKernelFn batch_kernel_f32(int kahan, int icdf);
 BatchKernelFn batch_kernel_f16(int kahan, int icdf);
+BatchKernelFn batch_kernel_bf16(int kahan, int icdf);
 
 // Sums each item's tile partials in a fixed order, one warp per item, FP64.
 __global__ void batch_finalize_kernel(const double2 *tile_partials, const uint32_t *start, const uint32_t *list,
@@ -112,7 +113,8 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
 }
 
 BatchKernelFn pick_batch_kernel(int prec, int kahan, int icdf) {
-    return prec == MLMC_F32 ? batch_kernel_f32(kahan, icdf) : batch_kernel_f16(kahan, icdf);
+    return prec == MLMC_F32 ? batch_kernel_f32(kahan, icdf)
+                            : prec == MLMC_F16 ? batch_kernel_f16(kahan, icdf) : batch_kernel_bf16(kahan, icdf);
 }
 
 template <typename T>
@@ -245,7 +247,7 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         uint32_t grid = (uint32_t)bps * d.sm_count;
         grid = std::min<uint32_t>(grid, (warps_needed + 7) / 8);
         fn<<<grid ? grid : 1, 256, 0, s>>>(c.items, c.tiles + g.tile_base, (uint32_t)g.tiles.size(), c.counters + gi,
-                                           c.partials + g.tile_base, d.tab32, d.tab16);
+                                           c.partials + g.tile_base, d.tab32, d.tab16, d.tabbf);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch kernel");
     }
     const int n = (int)p.items.size();

@@ -6,6 +6,7 @@
 // (Sec. 2.1) staged in shared memory.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
 
@@ -68,6 +69,35 @@ __device__ __forceinline__ __half2 h2mul(__half2 a, __half2 b) {
     return r;
 }
 
+// bfloat16x2 arithmetic, each operation rounded to nearest even, never fused.
+__device__ __forceinline__ uint32_t b2add(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t b2sub(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("sub.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t b2mul(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+// binary64 -> bfloat16 with a single rounding to nearest even.
+__device__ __forceinline__ uint16_t f64_to_bf16(double v) {
+    unsigned short r;
+    asm("cvt.rn.bf16.f64 %0, %1;" : "=h"(r) : "d"(v));
+    return r;
+}
+// two binary32 -> bfloat16x2 (lo = a, hi = b), rounded to nearest even.
+__device__ __forceinline__ uint32_t f32x2_to_bf16x2(float a, float b) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
+
 // binary64 -> binary16 with a single rounding to nearest even.
 __device__ __forceinline__ __half f64_to_f16(double v) {
     unsigned short r;
@@ -76,8 +106,8 @@ __device__ __forceinline__ __half f64_to_f16(double v) {
 }
 
 // A pair of paths in working precision P: two binary32 values or one
-// packed binary16x2 register.
-enum { P_F32 = 0, P_F16 = 1 };
+// packed binary16x2 / bfloat16x2 register.
+enum { P_F32 = 0, P_F16 = 1, P_BF16 = 2 };
 
 template <int P> struct Pair;
 
@@ -94,12 +124,27 @@ template <> struct Pair<P_F16> {
     __device__ __forceinline__ float2 f32() const { return __half22float2(h); }
 };
 
+template <> struct Pair<P_BF16> {
+    uint32_t b;      // lo = path 0, hi = path 1
+    static __device__ __forceinline__ Pair of(double v) {
+        const uint32_t h = f64_to_bf16(v);
+        return {h | (h << 16)};
+    }
+    static __device__ __forceinline__ Pair of2(float a, float c) { return {f32x2_to_bf16x2(a, c)}; }
+    __device__ __forceinline__ float2 f32() const {
+        return make_float2(__uint_as_float(b << 16), __uint_as_float(b & 0xFFFF0000u));
+    }
+};
+
 __device__ __forceinline__ Pair<P_F32> add(Pair<P_F32> a, Pair<P_F32> b) { return {__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)}; }
 __device__ __forceinline__ Pair<P_F32> sub(Pair<P_F32> a, Pair<P_F32> b) { return {__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)}; }
 __device__ __forceinline__ Pair<P_F32> mul(Pair<P_F32> a, Pair<P_F32> b) { return {__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)}; }
 __device__ __forceinline__ Pair<P_F16> add(Pair<P_F16> a, Pair<P_F16> b) { return {h2add(a.h, b.h)}; }
 __device__ __forceinline__ Pair<P_F16> sub(Pair<P_F16> a, Pair<P_F16> b) { return {h2sub(a.h, b.h)}; }
 __device__ __forceinline__ Pair<P_F16> mul(Pair<P_F16> a, Pair<P_F16> b) { return {h2mul(a.h, b.h)}; }
+__device__ __forceinline__ Pair<P_BF16> add(Pair<P_BF16> a, Pair<P_BF16> b) { return {b2add(a.b, b.b)}; }
+__device__ __forceinline__ Pair<P_BF16> sub(Pair<P_BF16> a, Pair<P_BF16> b) { return {b2sub(a.b, b.b)}; }
+__device__ __forceinline__ Pair<P_BF16> mul(Pair<P_BF16> a, Pair<P_BF16> b) { return {b2mul(a.b, b.b)}; }
 
 // Kahan-compensated FP32 accumulator (Algorithm 1) for the per-thread sums
 // of D and D^2; value() is the compensated sum s - c.
@@ -125,6 +170,7 @@ constexpr int TAB_ENTRIES = 23;
 struct SmemTable {
     float2 c32[TAB_ENTRIES];     // (c0, c1) in binary32
     __half2 c16[TAB_ENTRIES];    // (c0, c1) in binary16
+    uint32_t cb16[TAB_ENTRIES];  // (c0, c1) in bfloat16 (c0 in the low half)
 };
 
 // Entry index of v; CLAMP widens it to any v in (0, 1/2] (bulk API).
@@ -164,6 +210,18 @@ __device__ __forceinline__ __half2 table_z16(const SmemTable &s, uint32_t w0, ui
     const uint32_t top = __byte_perm(w0, w1, 0x7030u);
     uint32_t zb = *reinterpret_cast<uint32_t *>(&z) ^ (top & 0x80008000u);
     return *reinterpret_cast<__half2 *>(&zb);
+}
+
+// Piecewise-linear Z~ for two paths in bfloat16x2, same operation order.
+template <bool CLAMP>
+__device__ __forceinline__ uint32_t table_zbf16(const SmemTable &s, uint32_t w0, uint32_t w1, float v0, float v1) {
+    const uint32_t t0 = s.cb16[tab_index<CLAMP>(v0)];
+    const uint32_t t1 = s.cb16[tab_index<CLAMP>(v1)];
+    const uint32_t c0 = __byte_perm(t0, t1, 0x5410u);     // lo halves
+    const uint32_t c1 = __byte_perm(t0, t1, 0x7632u);     // hi halves
+    const uint32_t z = b2add(c0, b2mul(c1, f32x2_to_bf16x2(v0, v1)));
+    const uint32_t top = __byte_perm(w0, w1, 0x7030u);
+    return z ^ (top & 0x80008000u);
 }
 
 }  // namespace mlmc

@@ -46,8 +46,9 @@ struct Term {
 double nu_of(const Term &t) {
     if (t.icdf == MLMC_ICDF_MLP) return t.four ? 9.0e-3 : 7.0e-3;
     if (t.icdf == MLMC_ICDF_EXACT) return t.kahan ? 1.8e-3 : 1.65e-3;
-    if (t.four) return t.prec == MLMC_F16 ? 2.45e-3 : 2.6e-3;
-    return t.prec == MLMC_F16 ? (t.kahan ? 1.12e-3 : 1.0e-3) : (t.kahan ? 1.4e-3 : 1.25e-3);
+    const bool half = t.prec != MLMC_F32;   // binary16 and bfloat16 share the f16x2-style packing
+    if (t.four) return half ? 2.45e-3 : 2.6e-3;
+    return half ? (t.kahan ? 1.12e-3 : 1.0e-3) : (t.kahan ? 1.4e-3 : 1.25e-3);
 }
 
 }  // namespace
@@ -280,7 +281,7 @@ extern "C" mlmc_status mlmc_run(double eps, const mlmc_sde_params *params, const
     if (opts->n0 < 2) return fail(MLMC_EINVAL, "n0 must be >= 2");
     if (!(opts->alpha > 0.0)) return fail(MLMC_EINVAL, "alpha must be > 0");
     if (opts->estimator == 1) {
-        if (opts->prec != MLMC_F32 && opts->prec != MLMC_F16 && opts->prec != -1)
+        if (opts->prec != MLMC_F32 && opts->prec != MLMC_F16 && opts->prec != MLMC_BF16 && opts->prec != -1)
             return fail(MLMC_EINVAL, "unknown precision");
         if (opts->icdf != MLMC_ICDF_TABLE && opts->icdf != MLMC_ICDF_MLP)
             return fail(MLMC_EINVAL, "nested estimator needs approximate normals");

@@ -37,6 +37,7 @@ struct LevelArgs {
     double K, disc;
     const float2 *tab32;      // table in binary32, TAB_ENTRIES entries
     const __half2 *tab16;     // table in binary16
+    const uint32_t *tabbf;    // table in bfloat16 (c0 in the low half)
     const MlpWeights *mlp;    // network (ICDF_MLP only)
     double2 *partials;        // (sum D, sum D^2) per warp chunk, or per block
     int chunk_partials;       // 1: one partial per chunk of 32 pairs (result independent of the grid)
@@ -86,8 +87,10 @@ __device__ __forceinline__ Pair<P> icdf_pair(const SmemTable &s, const MlpFrags 
         const float v0 = mirrored_v(w0), v1 = mirrored_v(w1);
         if constexpr (P == P_F32) {
             return Pair<P>::of2(table_z32<false>(s, w0, v0), table_z32<false>(s, w1, v1));
-        } else {
+        } else if constexpr (P == P_F16) {
             return Pair<P>{table_z16<false>(s, w0, w1, v0, v1)};
+        } else {
+            return Pair<P>{table_zbf16<false>(s, w0, w1, v0, v1)};
         }
     } else {
         const float2 z = mlp_z_warp(mlp, w0, w1);      // all 32 lanes together
@@ -183,10 +186,12 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
     }
 }
 
-__device__ __forceinline__ void stage_table(SmemTable &tab, const float2 *t32, const __half2 *t16) {
+__device__ __forceinline__ void stage_table(SmemTable &tab, const float2 *t32, const __half2 *t16,
+                                            const uint32_t *tbf) {
     for (int i = threadIdx.x; i < TAB_ENTRIES; i += blockDim.x) {
         tab.c32[i] = t32[i];
         tab.c16[i] = t16[i];
+        tab.cb16[i] = tbf[i];
     }
 }
 
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 1 : 4) level_kernel(co
     __shared__ SmemTable tab;
     __shared__ double red[2][32];
     if (ICDF == ICDF_TABLE) {
-        stage_table(tab, a.tab32, a.tab16);
+        stage_table(tab, a.tab32, a.tab16, a.tabbf);
         __syncthreads();
     }
     MlpFrags mlp;

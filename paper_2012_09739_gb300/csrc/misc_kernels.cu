@@ -17,7 +17,7 @@ namespace mlmc {
 //   int_a^b Phi^-1(v) dv   = phi(z_a) - phi(z_b)
 //   int_a^b v Phi^-1(v) dv = [ -phi(z) Phi(z) + Phi(sqrt(2) z) / (2 sqrt(pi)) ]_{z_a}^{z_b}
 // and the normal equations are solved in centred form.
-__global__ void build_table_kernel(double *t64, float2 *t32, __half2 *t16) {
+__global__ void build_table_kernel(double *t64, float2 *t32, __half2 *t16, uint32_t *tbf) {
     __shared__ double c[32];
     const int i = threadIdx.x;
     if (i < 16) {
@@ -53,11 +53,12 @@ __global__ void build_table_kernel(double *t64, float2 *t32, __half2 *t16) {
         const double c0 = c[2 * interval], c1 = c[2 * interval + 1];
         t32[i] = make_float2(__double2float_rn(c0), __double2float_rn(c1));
         t16[i] = __halves2half2(f64_to_f16(c0), f64_to_f16(c1));
+        tbf[i] = (uint32_t)f64_to_bf16(c0) | ((uint32_t)f64_to_bf16(c1) << 16);
     }
 }
 
-cudaError_t launch_build_table(double *t64, float2 *t32, __half2 *t16, cudaStream_t s) {
-    build_table_kernel<<<1, 32, 0, s>>>(t64, t32, t16);
+cudaError_t launch_build_table(double *t64, float2 *t32, __half2 *t16, uint32_t *tbf, cudaStream_t s) {
+    build_table_kernel<<<1, 32, 0, s>>>(t64, t32, t16, tbf);
     return cudaGetLastError();
 }
 
@@ -139,9 +140,9 @@ cudaError_t launch_uniform_bulk(const uint32_t *w, float *u, size_t n, cudaStrea
 // sees all 32 lanes.
 template <int P, int ICDF>
 __global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const float2 *tab32, const __half2 *tab16,
-                                 const MlpWeights *mlpw) {
+                                 const uint32_t *tabbf, const MlpWeights *mlpw) {
     __shared__ SmemTable tab;
-    stage_table(tab, tab32, tab16);
+    stage_table(tab, tab32, tab16, tabbf);
     __syncthreads();
     MlpFrags mlp;
     if (ICDF == ICDF_MLP) mlp.load(mlpw);
@@ -176,27 +177,35 @@ __global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const float2
                     static_cast<__half *>(z)[idx[h]] = __low2half(hz);
                     continue;
                 }
+                if (P == P_BF16) {
+                    static_cast<uint16_t *>(z)[idx[h]] = (uint16_t)table_zbf16<true>(tab, sg[h], sg[h], v[h], v[h]);
+                    continue;
+                }
                 r[h] = table_z32<true>(tab, sg[h], v[h]);
             }
             if (P == P_F32) static_cast<float *>(z)[idx[h]] = r[h];
-            else static_cast<__half *>(z)[idx[h]] = __float2half_rn(r[h]);
+            else if (P == P_F16) static_cast<__half *>(z)[idx[h]] = __float2half_rn(r[h]);
+            else static_cast<uint16_t *>(z)[idx[h]] = (uint16_t)f32x2_to_bf16x2(r[h], 0.0f);
         }
     }
 }
 
 cudaError_t launch_icdf_bulk(const float *u, void *z, size_t n, int icdf, int prec, const float2 *tab32,
-                             const __half2 *tab16, const MlpWeights *mlp, cudaStream_t s) {
+                             const __half2 *tab16, const uint32_t *tabbf, const MlpWeights *mlp, cudaStream_t s) {
     const int g = bulk_grid(n);
-#define MLMC_ICDF_CASE(PP, II) icdf_bulk_kernel<PP, II><<<g, 256, 0, s>>>(u, z, n, tab32, tab16, mlp)
+#define MLMC_ICDF_CASE(PP, II) icdf_bulk_kernel<PP, II><<<g, 256, 0, s>>>(u, z, n, tab32, tab16, tabbf, mlp)
+#define MLMC_ICDF_PREC(PP)                                  \
+    if (icdf == ICDF_EXACT) MLMC_ICDF_CASE(PP, ICDF_EXACT); \
+    else if (icdf == ICDF_TABLE) MLMC_ICDF_CASE(PP, ICDF_TABLE); \
+    else MLMC_ICDF_CASE(PP, ICDF_MLP)
     if (prec == P_F32) {
-        if (icdf == ICDF_EXACT) MLMC_ICDF_CASE(P_F32, ICDF_EXACT);
-        else if (icdf == ICDF_TABLE) MLMC_ICDF_CASE(P_F32, ICDF_TABLE);
-        else MLMC_ICDF_CASE(P_F32, ICDF_MLP);
+        MLMC_ICDF_PREC(P_F32);
+    } else if (prec == P_F16) {
+        MLMC_ICDF_PREC(P_F16);
     } else {
-        if (icdf == ICDF_EXACT) MLMC_ICDF_CASE(P_F16, ICDF_EXACT);
-        else if (icdf == ICDF_TABLE) MLMC_ICDF_CASE(P_F16, ICDF_TABLE);
-        else MLMC_ICDF_CASE(P_F16, ICDF_MLP);
+        MLMC_ICDF_PREC(P_BF16);
     }
+#undef MLMC_ICDF_PREC
 #undef MLMC_ICDF_CASE
     return cudaGetLastError();
 }

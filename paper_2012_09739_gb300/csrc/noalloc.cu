@@ -28,6 +28,7 @@ static __device__ __align__(256) double2 g_noalloc_partials[NOALLOC_MAX_BLOCKS];
 static __device__ __align__(256) double g_noalloc_tab64[32];
 static __device__ __align__(256) float2 g_noalloc_tab32[TAB_ENTRIES];
 static __device__ __align__(256) __half2 g_noalloc_tab16[TAB_ENTRIES];
+static __device__ __align__(256) uint32_t g_noalloc_tabbf[TAB_ENTRIES];
 
 // Device addresses of the arrays above, looked up once per device with that
 // device current.  In host code the array names are host-side stand-ins, not
@@ -38,6 +39,7 @@ struct NoallocState {
     double *tab64 = nullptr;
     float2 *tab32 = nullptr;
     __half2 *tab16 = nullptr;
+    uint32_t *tabbf = nullptr;
 };
 static std::mutex g_noalloc_mu;
 static NoallocState g_noalloc[MAX_DEVICES];
@@ -58,7 +60,9 @@ static mlmc_status noalloc_setup(int dev, cudaStream_t s, NoallocState **out) {
             return cuda_fail(e, "cudaGetSymbolAddress(table)");
         if ((e = cudaGetSymbolAddress((void **)&st.tab16, g_noalloc_tab16)) != cudaSuccess)
             return cuda_fail(e, "cudaGetSymbolAddress(table)");
-        if ((e = launch_build_table(st.tab64, st.tab32, st.tab16, s)) != cudaSuccess)
+        if ((e = cudaGetSymbolAddress((void **)&st.tabbf, g_noalloc_tabbf)) != cudaSuccess)
+            return cuda_fail(e, "cudaGetSymbolAddress(table)");
+        if ((e = launch_build_table(st.tab64, st.tab32, st.tab16, st.tabbf, s)) != cudaSuccess)
             return cuda_fail(e, "build_table");
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "build_table");
         st.ready = true;
@@ -97,6 +101,7 @@ extern "C" mlmc_status mlmc_level_noalloc(int four, int l, uint64_t N, int prec,
     view.tab64 = na->tab64;
     view.tab32 = na->tab32;
     view.tab16 = na->tab16;
+    view.tabbf = na->tabbf;
     LevelArgs a = make_level_args(view, four ? 1 : 0, l, N, icdf, params, seed, path_offset, 0);
     a.partials = na->partials;
     a.paths_out = nullptr;

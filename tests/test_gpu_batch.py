@@ -61,11 +61,13 @@ def test_single_item_batch_equals_level_kernel():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
-    for kind, l, N in [(0, 0, 1), (1, 3, 77777), (0, 7, 4097), (1, 12, 33), (0, 16, 1)]:
-        it = M.mlmc_work(p, l, kind, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 0, N, 5)
+    for kind, l, N, prec in [(0, 0, 1, M.MLMC_F16), (1, 3, 77777, M.MLMC_F16), (0, 7, 4097, M.MLMC_F16),
+                             (1, 12, 33, M.MLMC_F16), (0, 16, 1, M.MLMC_F16), (1, 5, 9999, M.MLMC_BF16),
+                             (0, 9, 3001, M.MLMC_BF16), (1, 4, 5000, M.MLMC_F32)]:
+        it = M.mlmc_work(p, l, kind, prec, 1, M.MLMC_ICDF_TABLE, 0, N, 5)
         g = M.mlmc_batch([it], SEED)[0]
         fn = M.mlmc_nested_level if kind else M.mlmc_level
-        ref = fn(l, N, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, p, SEED, 5)
+        ref = fn(l, N, prec, True, M.MLMC_ICDF_TABLE, p, SEED, 5)
         _close(g, ref)
 
 

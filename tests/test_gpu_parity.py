@@ -1,6 +1,6 @@
 """Parity of the CUDA library (through the C ABI) with the FP64 oracle.
 
-Bit-exact: Philox words, uniforms, the binary32/binary16 table coefficients,
+Bit-exact: Philox words, uniforms, the binary32/binary16/bfloat16 table coefficients,
 the approximate normals, and every per-path output of the low-precision
 ("bar") paths against the oracle's per-operation rounding emulation.
 Within tolerance: exact-normal FP32 paths against FP64 (1e-5 relative), and
@@ -44,8 +44,11 @@ def gpu_paths(four, l, N, prec, kahan, icdf, params, seed=SEED, offset=0):
     return out.cpu().numpy().astype(np.float64).reshape(N, w)
 
 
+_OPREC = {M.MLMC_F32: O.F32, M.MLMC_F16: O.F16, M.MLMC_BF16: O.BF16}
+
+
 def _bar_variant(prec, kahan, icdf=O.RV_TABLE):
-    return O.variant(prec=O.F16 if prec == M.MLMC_F16 else O.F32, kahan=kahan, rv=icdf)
+    return O.variant(prec=_OPREC[prec], kahan=kahan, rv=icdf)
 
 
 def _kind_tag(four, icdf, l):
@@ -86,13 +89,21 @@ def test_uniforms_bitexact():
 
 def test_table_matches_oracle(pl_table):
     _dev()
-    c64, c32, c16 = M.mlmc_icdf_table()
+    c64, c32, c16, cbf = M.mlmc_icdf_table()
     assert np.allclose(c64, pl_table, rtol=1e-11, atol=0)
     assert np.array_equal(c32.astype(np.float64), O.round_bits(pl_table, O.F32).reshape(16, 2))
     assert np.array_equal(c16.view(np.float16).astype(np.float64), O.round_bits(pl_table, O.F16).reshape(16, 2))
+    bf = (cbf.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    assert np.array_equal(bf, O.round_bits(pl_table, O.BF16).reshape(16, 2))
 
 
-@pytest.mark.parametrize("prec", [M.MLMC_F32, M.MLMC_F16])
+def _z_host(z, prec):
+    if prec == M.MLMC_BF16:
+        return (z.cpu().numpy().view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return z.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("prec", [M.MLMC_F32, M.MLMC_F16, M.MLMC_BF16])
 def test_approx_icdf_table_bitexact(prec, pl_table):
     dev = _dev()
     rng = np.random.default_rng(2)
@@ -100,12 +111,29 @@ def test_approx_icdf_table_bitexact(prec, pl_table):
                         [2.0 ** -24, 1 - 2.0 ** -24, 0.5 - 2.0 ** -24, 0.25, 0.75, 2.0 ** -16, 2.0 ** -17,
                          3e-9, 0.5]]).astype(np.float32)
     ut = torch.from_numpy(u).to(dev)
-    z = torch.empty(u.size, dtype=torch.float32 if prec == M.MLMC_F32 else torch.float16, device=dev)
+    z = torch.empty(u.size, dtype=torch.float32 if prec == M.MLMC_F32 else torch.int16, device=dev)
     M.approx_icdf(ut, z, M.MLMC_ICDF_TABLE, prec)
     torch.cuda.synchronize()
-    oprec = O.F32 if prec == M.MLMC_F32 else O.F16
-    ref = O.approx_icdf(u.astype(np.float64), O.RV_TABLE, prec=oprec, table=pl_table)
-    assert np.array_equal(z.cpu().numpy().astype(np.float64), ref)
+    ref = O.approx_icdf(u.astype(np.float64), O.RV_TABLE, prec=_OPREC[prec], table=pl_table)
+    if prec == M.MLMC_F16:
+        got = z.cpu().numpy().view(np.float16).astype(np.float64)
+    else:
+        got = _z_host(z, prec)
+    assert np.array_equal(got, ref)
+
+
+def test_approx_icdf_exact_bf16_is_rounded_fp32():
+    """bfloat16 output of the exact inverse CDF is the round-to-nearest-even
+    bfloat16 of the binary32 value."""
+    dev = _dev()
+    u = ((2 * np.arange(0, 1 << 23, 3) + 1) * 2.0 ** -24).astype(np.float32)
+    ut = torch.from_numpy(u).to(dev)
+    z32 = torch.empty(u.size, dtype=torch.float32, device=dev)
+    zb = torch.empty(u.size, dtype=torch.int16, device=dev)
+    M.approx_icdf(ut, z32, M.MLMC_ICDF_EXACT, M.MLMC_F32)
+    M.approx_icdf(ut, zb, M.MLMC_ICDF_EXACT, M.MLMC_BF16)
+    torch.cuda.synchronize()
+    assert np.array_equal(_z_host(zb, M.MLMC_BF16), O.round_bits(z32.cpu().numpy().astype(np.float64), O.BF16))
 
 
 def test_exact_icdf_fp32_accuracy():
@@ -130,7 +158,7 @@ GBM_X = dict(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_X, p0=0.05, p1=0.2)
 OU_X = dict(sde=M.MLMC_OU, payoff=M.MLMC_PAYOFF_X, p0=2.0, p1=0.3, p2=0.5, x0=1.0)
 
 
-@pytest.mark.parametrize("prec", [M.MLMC_F16, M.MLMC_F32])
+@pytest.mark.parametrize("prec", [M.MLMC_F16, M.MLMC_F32, M.MLMC_BF16])
 @pytest.mark.parametrize("kahan", [True, False])
 @pytest.mark.parametrize("l", [0, 1, 2, 5, 9])
 @pytest.mark.parametrize("sde", ["gbm_call", "ou_x"])
@@ -143,7 +171,7 @@ def test_twoway_table_paths_bitexact(prec, kahan, l, sde, pl_table):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("prec", [M.MLMC_F16, M.MLMC_F32])
+@pytest.mark.parametrize("prec", [M.MLMC_F16, M.MLMC_F32, M.MLMC_BF16])
 @pytest.mark.parametrize("kahan", [True, False])
 @pytest.mark.parametrize("l", [0, 1, 3, 8])
 def test_fourway_table_paths(prec, kahan, l, pl_table):
@@ -283,6 +311,10 @@ def test_edge_cases(pl_table):
     assert np.array_equal(got, ref)
     s = M.mlmc_level(0, 1, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, params, SEED)
     assert s.n == 1 and s.var() == 0.0
+    got = gpu_paths(0, 18, 3, M.MLMC_BF16, True, M.MLMC_ICDF_TABLE, params, offset=2 ** 40 + 3)
+    ref = O.twoway_paths(18, 2 ** 40 + 3 + np.arange(3), _bar_variant(M.MLMC_BF16, True), _orc_sde(params), SEED,
+                         _kind_tag(0, 1, 18), table=pl_table)
+    assert np.array_equal(got, ref)
 
 
 def test_invalid_arguments_raise():

@@ -106,3 +106,49 @@ def test_half_four_way_with_kahan(curves):
     assert np.all(red[4:9] < pv["half_kahan_fourway_log2_reduction_to_level8"] + 1.5)
     # finer still, the two-way and four-way half-precision variances coincide
     assert np.all(np.abs(curves["four16k"][14:] - curves["two16k"][14:]) < 0.5)
+
+
+@pytest.fixture(scope="module")
+def pair_errors():
+    """log2 Var(P_bar - P_ref) of the fine payoff, where P_bar is a 16-bit path
+    and P_ref the binary32 + Kahan path driven by the same approximate normals
+    (same counters): the rounding error alone, as in Sec. 2.2-2.3."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_X, p0=0.05, p1=0.2)
+    T, N = M.MLMC_ICDF_TABLE, 1 << 16
+    dev = torch.device("cuda:0")
+
+    def fine(l, prec, kahan):
+        out = torch.empty(N * 3, dtype=torch.float32, device=dev)
+        M.mlmc_level_paths(0, l, N, prec, kahan, T, p, 1234, 0, out)
+        return out.view(N, 3)[:, 0].double()
+
+    res = {k: [] for k in ("f16", "f16k", "bf16", "bf16k")}
+    for l in range(2, 13):
+        ref = fine(l, M.MLMC_F32, True)
+        for key, prec, kahan in (("f16", M.MLMC_F16, False), ("f16k", M.MLMC_F16, True),
+                                 ("bf16", M.MLMC_BF16, False), ("bf16k", M.MLMC_BF16, True)):
+            res[key].append(math.log2(torch.var(fine(l, prec, kahan) - ref).item()))
+    return {k: np.array(v) for k, v in res.items()}
+
+
+def test_bf16_rounding_error_growth_and_kahan(pair_errors):
+    """Lemma 2.6 in bfloat16 and binary16: without compensation the rounding
+    variance grows like N rho^2 (slope +1 in l); with Kahan it is O(rho^2)
+    (slope 0)."""
+    pv = _pv()
+    ls = np.arange(2, 13)
+    for key in ("f16", "bf16"):
+        assert abs(np.polyfit(ls, pair_errors[key], 1)[0] - pv["half_no_kahan_log2_slope"]) < 0.3, key
+    for key in ("f16k", "bf16k"):
+        assert abs(np.polyfit(ls, pair_errors[key], 1)[0] - pv["half_kahan_log2_slope"]) < 0.3, key
+
+
+def test_bf16_half_kahan_gap(pair_errors):
+    """With Kahan the binary16 rounding variance sits about 2^-6 below
+    bfloat16's, the ratio of the squared unit roundoffs (Sec. 2.3)."""
+    gap = np.mean(pair_errors["f16k"] - pair_errors["bf16k"])
+    assert abs(gap - _pv()["kahan_half_bf16_log2_gap"]) < 1.0, gap
+    # and without Kahan the same ratio holds level by level
+    assert abs(np.mean(pair_errors["f16"] - pair_errors["bf16"]) - _pv()["kahan_half_bf16_log2_gap"]) < 1.0
