@@ -37,7 +37,7 @@ _lib = None
 # precision codes (oracle.c)
 F64, F32, F16, BF16, PBITS = 0, 1, 2, 3, 4
 # random-variable kinds
-RV_EXACT, RV_TABLE, RV_MLP = 0, 1, 2
+RV_EXACT, RV_TABLE, RV_MLP, RV_TABLE16 = 0, 1, 2, 3
 # SDEs and payoffs
 GBM, OU = 0, 1
 PAYOFF_X, PAYOFF_CALL = 0, 1
@@ -139,6 +139,22 @@ def uniforms(words) -> np.ndarray:
     return u
 
 
+def uniforms16(halves) -> np.ndarray:
+    """u = (h + 1/2) 2^-16 for 16-bit values h (the low 16 bits are used)."""
+    h = np.ascontiguousarray(halves, dtype=np.uint32).ravel()
+    u = np.empty(h.shape, np.float64)
+    lib().orc_u16_to_uniform(_ptr(h, ctypes.c_uint32), _ptr(u, ctypes.c_double), h.size)
+    return u
+
+
+def q16(u) -> np.ndarray:
+    """Centre of the 2^-16-wide cell of (0, 1) that contains u."""
+    u = _f64(u).ravel()
+    q = np.empty_like(u)
+    lib().orc_q16(_ptr(u, ctypes.c_double), _ptr(q, ctypes.c_double), u.size)
+    return q
+
+
 def counters(path_idx, j, tag) -> np.ndarray:
     """Counter words (path lo32, path hi32, j, tag) for the given paths."""
     p = np.asarray(path_idx, dtype=np.uint64).ravel()
@@ -186,8 +202,9 @@ _NO_TABLE = np.zeros(32)
 
 
 def approx_icdf(u, rv: int, prec: int = F64, pbits: int = 53, table=None, mlp=None) -> np.ndarray:
-    """Phi^-1 (rv=RV_EXACT), piecewise-linear table (RV_TABLE) or MLP
-    (RV_MLP) evaluated with the rounding of precision prec."""
+    """Phi^-1 (rv=RV_EXACT), piecewise-linear table (RV_TABLE), the table at
+    the 16-bit cell centre q16(u) (RV_TABLE16) or MLP (RV_MLP) evaluated with
+    the rounding of precision prec."""
     u = _f64(u).ravel()
     z = np.empty_like(u)
     t = _f64(table if table is not None else _NO_TABLE)

@@ -82,6 +82,33 @@ void orc_u32_to_uniform(const uint32_t *w, double *u, int64_t n)
     for (int64_t i = 0; i < n; ++i) u[i] = uniform_of(w[i]);
 }
 
+/* 16-bit uniforms for the approximate normals (a reading, not the paper's:
+ * the paper leaves the generator open).  A 16-bit value h gives
+ * u = (h + 1/2) 2^-16, the centre of the h-th of 2^16 equal cells of (0, 1).
+ * q16(u) maps any u in (0, 1) to the centre of the cell that contains it,
+ * so q16 of a 24-bit uniform is distributed exactly like a 16-bit uniform
+ * (each cell holds 2^7 of the 2^23 grid points); this keeps the two-way
+ * approximate estimator and the four-way bar paths consistent (Sec. 3). */
+static double uniform16_of(uint32_t h)
+{
+    return ldexp((double)h + 0.5, -16);
+}
+
+static double q16(double u)
+{
+    return ldexp(floor(ldexp(u, 16)) + 0.5, -16);
+}
+
+void orc_u16_to_uniform(const uint32_t *h, double *u, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) u[i] = uniform16_of(h[i] & 0xFFFFu);
+}
+
+void orc_q16(const double *u, double *q, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) q[i] = q16(u[i]);
+}
+
 /* ------------------------------------------------------------------ */
 /* Exact inverse Gaussian CDF in FP64.                                 */
 /* Initial guess: Abramowitz & Stegun 26.2.23 (|error| < 4.5e-4), then */
@@ -226,12 +253,15 @@ static double mlp_icdf(double u, const double *w)
     return upper ? y : -y;
 }
 
-enum { ORC_RV_EXACT = 0, ORC_RV_TABLE = 1, ORC_RV_MLP = 2 };
+/* RV kinds.  TABLE16: the piecewise-linear table at the 16-bit uniform
+ * q16(u) (see uniform16_of). */
+enum { ORC_RV_EXACT = 0, ORC_RV_TABLE = 1, ORC_RV_MLP = 2, ORC_RV_TABLE16 = 3 };
 
 static double rv_of(double u, int rv, const double *table, const double *mlp, const rmode *m)
 {
     switch (rv) {
     case ORC_RV_TABLE: return table_icdf(u, table, m);
+    case ORC_RV_TABLE16: return table_icdf(q16(u), table, m);
     case ORC_RV_MLP: return round_p(mlp_icdf(u, mlp), m);
     default: return round_p(orc_ndtri1(u), m);
     }
@@ -327,13 +357,20 @@ static double payoff_of(double X, const orc_sde *p, int prec)
  * key = (seed lo32, seed hi32); fine step n of a path uses word n mod 4 of
  * call j = n / 4.  tag = kind | level << 8 | set << 16 with kind 0: standard
  * two-way with exact normals, 1: two-way with approximate normals, 2:
- * four-way.  (Reading: the paper is silent on the generator.) */
-static void draw4(uint64_t path, uint32_t j, uint32_t tag, uint64_t seed, double u[4])
+ * four-way.  (Reading: the paper is silent on the generator.)
+ * With 16-bit uniforms (RV TABLE16 on a two-way path) fine step n uses half
+ * n mod 2 (low half first) of word (n / 2) mod 4 of call j = n / 8. */
+static void draw4w(uint64_t path, uint32_t j, uint32_t tag, uint64_t seed, uint32_t w[4])
 {
     uint32_t ctr[4] = {(uint32_t)path, (uint32_t)(path >> 32), j, tag};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    uint32_t w[4];
     philox(ctr, key, w);
+}
+
+static void draw4(uint64_t path, uint32_t j, uint32_t tag, uint64_t seed, double u[4])
+{
+    uint32_t w[4];
+    draw4w(path, j, tag, seed, w);
     for (int i = 0; i < 4; ++i) u[i] = uniform_of(w[i]);
 }
 
@@ -350,9 +387,18 @@ static void twoway_one(int l, uint64_t path, const orc_variant *v, const orc_sde
     path_init(&fine, p, v->prec, v->pbits, v->kahan, delta_f, sq);
     path_init(&coarse, p, v->prec, v->pbits, v->kahan, 2.0 * delta_f, sq);
     double zprev = 0.0, u[4];
+    uint32_t w[4];
     for (int64_t n = 0; n < nf; ++n) {
-        if ((n & 3) == 0) draw4(path, (uint32_t)(n >> 2), tag, seed, u);
-        double z = rv_of(u[n & 3], v->rv, table, mlp, &fine.m);
+        double z;
+        if (v->rv == ORC_RV_TABLE16) {
+            if ((n & 7) == 0) draw4w(path, (uint32_t)(n >> 3), tag, seed, w);
+            uint32_t word = w[(n >> 1) & 3];
+            uint32_t h = (n & 1) ? word >> 16 : word & 0xFFFFu;
+            z = table_icdf(uniform16_of(h), table, &fine.m);
+        } else {
+            if ((n & 3) == 0) draw4(path, (uint32_t)(n >> 2), tag, seed, u);
+            z = rv_of(u[n & 3], v->rv, table, mlp, &fine.m);
+        }
         path_step(&fine, z);
         if (l > 0 && (n & 1)) path_step(&coarse, round_p(zprev + z, &coarse.m));
         zprev = z;
