@@ -99,12 +99,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def gpu_step_items(M):
+def gpu_step_items(M, icdf=None):
     """(four, level, prec, kahan, icdf) of every launch in one FP16+Kahan nested step."""
+    icdf = M.MLMC_ICDF_TABLE if icdf is None else icdf
     items = []
     for l in LEVELS:
-        items.append((0, l, M.MLMC_F16, True, M.MLMC_ICDF_TABLE))
-        items.append((1, l, M.MLMC_F16, True, M.MLMC_ICDF_TABLE))
+        items.append((0, l, M.MLMC_F16, True, icdf))
+        items.append((1, l, M.MLMC_F16, True, icdf))
     return items
 
 
@@ -148,6 +149,10 @@ def run_gpu(args):
         step()
         if not args.no_fp32:
             fp32_step()
+        if not args.no_table16:
+            for i, (four, l, prec, kahan, icdf) in enumerate(gpu_step_items(M, M.MLMC_ICDF_TABLE16)):
+                M.mlmc_level_async(four, l, N_PER_LEVEL, prec, kahan, icdf, params, SEED, offset, sums[2 * i:],
+                                   stream.cuda_stream)
     torch.cuda.synchronize()
 
     # --- device-timed FP16+Kahan nested step
@@ -191,6 +196,24 @@ def run_gpu(args):
         torch.cuda.synchronize()
         fp32_ms += e0.elapsed_time(e1)
     fp32_value = path_steps(LEVELS, N_PER_LEVEL) * args.steps * world / (fp32_ms / 1e3) if fp32_ms else None
+
+    # --- the same nested step with 16-bit uniforms for the approximate normals
+    t16_items = gpu_step_items(M, M.MLMC_ICDF_TABLE16)
+    t16_ms, t16_kind = 0.0, [0.0, 0.0]
+    for _ in range(0 if args.no_table16 else args.steps):
+        flush.fill_(1)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in t16_items]
+        for i, (four, l, prec, kahan, icdf) in enumerate(t16_items):
+            evs[i][0].record(stream)
+            M.mlmc_level_async(four, l, N_PER_LEVEL, prec, kahan, icdf, params, SEED, offset, sums[2 * i:],
+                               stream.cuda_stream)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        for i, (a, b) in enumerate(evs):
+            ms = a.elapsed_time(b)
+            t16_ms += ms
+            t16_kind[t16_items[i][0]] += ms
+    t16_value = ps_step * args.steps * world / (t16_ms / 1e3) if t16_ms else None
 
     # --- end to end through the synchronous C-ABI calls (sums to host memory)
     torch.cuda.synchronize()
@@ -245,6 +268,12 @@ def run_gpu(args):
                        "path_steps_per_step": path_steps(LEVELS, N_PER_LEVEL)},
         "kernel_ms_per_step": {"fourway_f16_kahan_table": four_ms / args.steps,
                                "twoway_f16_kahan_table": two_ms / args.steps},
+        "table16": None if not t16_ms else {
+            "value": t16_value, "unit": "path-steps/s", "ms_per_step": t16_ms / args.steps,
+            "ratio_vs_table": t16_value / value,
+            "kernel_ms_per_step": {"fourway_f16_kahan_table16": t16_kind[1] / args.steps,
+                                   "twoway_f16_kahan_table16": t16_kind[0] / args.steps},
+            "note": "approximate normals from 16-bit uniforms (two per Philox word on two-way paths)"},
         "roofline": {"bound": "alu", "kernel": "level_kernel<FOUR,F16,kahan,TABLE,GBM>",
                      "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
                      "traffic": None,
@@ -256,7 +285,7 @@ def run_gpu(args):
         "time_to_eps": tte,
         "batching": batch,
         "mlp": mlp,
-        "gpu_launches": 2 * len(items) * args.steps,
+        "gpu_launches": 2 * len(items) * args.steps,     # level + finalize per item, headline step
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -318,15 +347,17 @@ def time_to_eps(M, params, eps_list, repeats=3):
     with FP16 + Kahan table normals, FP32 table normals, and the per-level
     automatic choice.  Median of `repeats` runs with different seeds, after
     one untimed run."""
-    variants = (("plain_fp32_exact", 0, M.MLMC_F32, 0), ("nested_f16_kahan_table", 1, M.MLMC_F16, 1),
-                ("nested_f32_table", 1, M.MLMC_F32, 0), ("nested_auto_table", 1, -1, 0))
+    T, T16 = M.MLMC_ICDF_TABLE, M.MLMC_ICDF_TABLE16
+    variants = (("plain_fp32_exact", 0, M.MLMC_F32, 0, T), ("nested_f16_kahan_table", 1, M.MLMC_F16, 1, T),
+                ("nested_f32_table", 1, M.MLMC_F32, 0, T), ("nested_auto_table", 1, -1, 0, T),
+                ("nested_f16_kahan_table16", 1, M.MLMC_F16, 1, T16), ("nested_auto_table16", 1, -1, 0, T16))
     out = {}
     for eps in eps_list:
         row = {}
-        for name, est, prec, kahan in variants:
+        for name, est, prec, kahan, icdf in variants:
             times, res = [], None
             for rep in range(repeats + 1):
-                o = M.mlmc_run_opts(estimator=est, prec=prec, kahan=kahan, icdf=M.MLMC_ICDF_TABLE, max_level=18,
+                o = M.mlmc_run_opts(estimator=est, prec=prec, kahan=kahan, icdf=icdf, max_level=18,
                                     min_levels=3, n0=10000, seed=1000 + rep, alpha=1.0, timeout_s=600.0)
                 t0 = time.perf_counter()
                 r = M.mlmc_run(eps, params, o)
@@ -343,6 +374,8 @@ def time_to_eps(M, params, eps_list, repeats=3):
                 row[name]["kahan_per_level"] = [int(res.kahan[l]) for l in range(res.levels)]
                 row[name]["efficiency_per_level"] = [round(res.efficiency[l], 3) for l in range(res.levels)]
         row["speedup_f16_kahan_vs_plain"] = row["plain_fp32_exact"]["seconds"] / row["nested_f16_kahan_table"]["seconds"]
+        row["speedup_f16_kahan_table16_vs_plain"] = (row["plain_fp32_exact"]["seconds"]
+                                                     / row["nested_f16_kahan_table16"]["seconds"])
         out[f"{eps:g}"] = row
     return out
 
@@ -462,6 +495,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison leg (profiling runs)")
+    ap.add_argument("--no-table16", action="store_true", help="skip the 16-bit-uniform leg (profiling runs)")
     ap.add_argument("--no-tte", action="store_true", help="skip the time-to-eps leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batching leg")
     ap.add_argument("--no-mlp", action="store_true", help="skip the MLP leg")

@@ -54,7 +54,22 @@ typedef enum { MLMC_PAYOFF_X = 0, MLMC_PAYOFF_CALL = 1 } mlmc_payoff;
  * the bar paths rounds to nearest-even in that format after every
  * operation. */
 typedef enum { MLMC_F32 = 0, MLMC_F16 = 1, MLMC_BF16 = 2 } mlmc_prec;
-typedef enum { MLMC_ICDF_EXACT = 0, MLMC_ICDF_TABLE = 1, MLMC_ICDF_MLP = 2 } mlmc_icdf;
+/* How the normals of the approximate paths are formed from the Philox words
+ * (counter (path lo32, path hi32, j, tag), key = seed; 24-bit uniform
+ * u = (2 (w >> 9) + 1) 2^-24 from a word w; fine step n uses word n mod 4 of
+ * call j = n / 4):
+ *   EXACT    Phi^-1(u) in FP32 (no approximation);
+ *   TABLE    the 16-interval piecewise-linear Phi~^-1 of Sec. 2.1 at u;
+ *   MLP      the network of mlmc_mlp_set_weights / mlmc_mlp_train at u;
+ *   TABLE16  the same table at a 16-bit uniform u16 = (h + 1/2) 2^-16, a
+ *            design choice of this library (the paper leaves the generator
+ *            open).  On two-way paths each word gives two: fine step n uses
+ *            half n mod 2 (low half first) of word (n / 2) mod 4 of call
+ *            j = n / 8, halving the generator's work.  On four-way bar paths
+ *            h = w >> 16, the 2^-16 cell of the hat path's 24-bit u, so both
+ *            estimators see the same law of Z~ and the telescoping sum of
+ *            Sec. 3 keeps its expectation. */
+typedef enum { MLMC_ICDF_EXACT = 0, MLMC_ICDF_TABLE = 1, MLMC_ICDF_MLP = 2, MLMC_ICDF_TABLE16 = 3 } mlmc_icdf;
 
 /* SDE dX = a(X) dt + b(X) dW on [0, T], X_0 = x0.
  *   GBM: a = p0 X, b = p1 X            (mu = p0, sigma = p1)
@@ -140,7 +155,8 @@ mlmc_status mlmc_level_paths(int four, int l, uint64_t N, int prec, int kahan, i
                              float *out_dev, void *stream);
 
 /* Bulk approximate inverse CDF (Sec. 2.1): z_dev[i] = Phi~^-1(u_dev[i]) for
- * 0 < u < 1 (values outside give unspecified finite results).  z_dev is
+ * 0 < u < 1 (values outside give unspecified finite results); TABLE16
+ * evaluates the table at the centre of the 2^-16 cell that holds u.  z_dev is
  * float for prec = F32, IEEE binary16 (uint16_t storage) for F16 and
  * bfloat16 (uint16_t storage, the upper half of a binary32) for BF16.
  * icdf = EXACT evaluates Phi^-1 in FP32. */

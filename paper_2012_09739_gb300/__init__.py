@@ -21,7 +21,7 @@ MLMC_OK, MLMC_EINVAL, MLMC_ECUDA, MLMC_ETIMEOUT, MLMC_ENOMEM, MLMC_ENOTCONV, MLM
 MLMC_GBM, MLMC_OU = 0, 1
 MLMC_PAYOFF_X, MLMC_PAYOFF_CALL = 0, 1
 MLMC_F32, MLMC_F16, MLMC_BF16 = 0, 1, 2
-MLMC_ICDF_EXACT, MLMC_ICDF_TABLE, MLMC_ICDF_MLP = 0, 1, 2
+MLMC_ICDF_EXACT, MLMC_ICDF_TABLE, MLMC_ICDF_MLP, MLMC_ICDF_TABLE16 = 0, 1, 2, 3
 MLMC_MLP_PARAMS = 1153
 MLMC_MAX_LEVELS = 19
 

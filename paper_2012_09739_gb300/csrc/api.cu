@@ -106,7 +106,7 @@ mlmc_status check_level(int four, int l, uint64_t N, int prec, int icdf, const m
     if (N == 0) return fail(MLMC_EINVAL, "N must be >= 1");
     if (N > (1ull << 40)) return fail(MLMC_EINVAL, "N too large");
     if (prec != MLMC_F32 && prec != MLMC_F16 && prec != MLMC_BF16) return fail(MLMC_EINVAL, "unknown precision %d", prec);
-    if (icdf < 0 || icdf > 2) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
+    if (icdf < 0 || icdf > 3) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
     if (four && icdf == MLMC_ICDF_EXACT) return fail(MLMC_EINVAL, "four-way difference needs approximate normals");
     return check_params(p);
 }
@@ -305,7 +305,7 @@ mlmc_status mlmc_level_paths(int four, int l, uint64_t N, int prec, int kahan, i
 }
 
 mlmc_status approx_icdf(const float *u_dev, void *z_dev, size_t n, int icdf, int prec, void *stream) {
-    if (icdf < 0 || icdf > 2) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
+    if (icdf < 0 || icdf > 3) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
     if (prec != MLMC_F32 && prec != MLMC_F16 && prec != MLMC_BF16) return fail(MLMC_EINVAL, "unknown precision %d", prec);
     if (n == 0) return MLMC_OK;
     if (!u_dev || !z_dev) return fail(MLMC_EINVAL, "NULL buffer");

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const LevelArgs *items, cons
                                                     uint32_t *counter, double2 *tile_partials, const float2 *t32,
                                                     const __half2 *t16, const uint32_t *tbf) {
     __shared__ SmemTable tab;
-    if (ICDF == ICDF_TABLE) {
+    if (ICDF == ICDF_TABLE || ICDF == ICDF_TABLE16) {
         stage_table(tab, t32, t16, tbf);
         __syncthreads();
     }

@@ -47,6 +47,23 @@ __device__ __forceinline__ float mirrored_v(uint32_t w) {
     return __fsub_rn(0.5f, fabsf(s));
 }
 
+// 16-bit uniforms u = (h + 1/2) 2^-16.  half16_bits<HI>(w) places half h of
+// w (low or high 16 bits) under the binary32 exponent of 128 with one byte
+// permute: f = 128 + h 2^-16, so bit 15 of the result is the top bit of h
+// (set exactly when u > 1/2).
+template <bool HI>
+__device__ __forceinline__ uint32_t half16_bits(uint32_t w) {
+    return __byte_perm(w, 0x43000000u, HI ? 0x7432u : 0x7410u);
+}
+
+// v = min(u, 1 - u) of such a 16-bit uniform, exact:
+// s = (f - 128.5) + 2^-17 = u - 1/2, v = 1/2 - |s|.
+__device__ __forceinline__ float mirrored_v16(uint32_t fbits) {
+    const float s = __fadd_rn(__fsub_rn(__uint_as_float(fbits), 128.5f), 0x1p-17f);
+    return __fsub_rn(0.5f, fabsf(s));
+}
+
+
 // ---------------------------------------------------------------- arithmetic
 // Every operation is a single IEEE operation rounded to nearest even; none
 // is ever fused into an FMA (Sec. 2.2 models exactly this operation order).
@@ -160,7 +177,9 @@ struct KahanF32 {
 };
 
 // ---------------------------------------------------------------- inverse CDFs
-enum { ICDF_EXACT = 0, ICDF_TABLE = 1, ICDF_MLP = 2 };
+// TABLE16: the table at a 16-bit uniform (two per Philox word on two-way
+// paths; the cell centre of the 24-bit uniform on four-way bar paths).
+enum { ICDF_EXACT = 0, ICDF_TABLE = 1, ICDF_MLP = 2, ICDF_TABLE16 = 3 };
 
 // Shared-memory copy of the piecewise-linear table, indexed by the biased
 // binary32 exponent E of v: v in [2^(E-127), 2^(E-126)) lies in interval
@@ -189,16 +208,17 @@ __device__ __forceinline__ float exact_z(uint32_t w) {
 }
 
 // Piecewise-linear Z~ in binary32: z = R(c0 + R(c1 v)), negated for u > 1/2.
-template <bool CLAMP>
+// The sign is bit 31 of w (SIGN15: bit 15, for half16_bits words).
+template <bool CLAMP, bool SIGN15 = false>
 __device__ __forceinline__ float table_z32(const SmemTable &s, uint32_t w, float v) {
     const float2 c = s.c32[tab_index<CLAMP>(v)];
     const float z = __fadd_rn(c.x, __fmul_rn(c.y, v));
-    return __uint_as_float(__float_as_uint(z) ^ (w & 0x80000000u));
+    return __uint_as_float(__float_as_uint(z) ^ ((SIGN15 ? w << 16 : w) & 0x80000000u));
 }
 
 // Piecewise-linear Z~ for two paths in binary16x2:
 // z = R16(R16(c0) + R16(R16(c1) R16(v))), negated for u > 1/2.
-template <bool CLAMP>
+template <bool CLAMP, bool SIGN15 = false>
 __device__ __forceinline__ __half2 table_z16(const SmemTable &s, uint32_t w0, uint32_t w1, float v0, float v1) {
     const __half2 t0 = s.c16[tab_index<CLAMP>(v0)];
     const __half2 t1 = s.c16[tab_index<CLAMP>(v1)];
@@ -206,21 +226,22 @@ __device__ __forceinline__ __half2 table_z16(const SmemTable &s, uint32_t w0, ui
     const __half2 c1 = __highs2half2(t0, t1);
     const __half2 v = __floats2half2_rn(v0, v1);
     __half2 z = h2add(c0, h2mul(c1, v));
-    // sign bits of the two words into bits 15 and 31 (top bytes of w0, w1)
-    const uint32_t top = __byte_perm(w0, w1, 0x7030u);
+    // sign bits of the two words into bits 15 and 31 (top bytes of w0, w1;
+    // SIGN15: second bytes)
+    const uint32_t top = __byte_perm(w0, w1, SIGN15 ? 0x5010u : 0x7030u);
     uint32_t zb = *reinterpret_cast<uint32_t *>(&z) ^ (top & 0x80008000u);
     return *reinterpret_cast<__half2 *>(&zb);
 }
 
 // Piecewise-linear Z~ for two paths in bfloat16x2, same operation order.
-template <bool CLAMP>
+template <bool CLAMP, bool SIGN15 = false>
 __device__ __forceinline__ uint32_t table_zbf16(const SmemTable &s, uint32_t w0, uint32_t w1, float v0, float v1) {
     const uint32_t t0 = s.cb16[tab_index<CLAMP>(v0)];
     const uint32_t t1 = s.cb16[tab_index<CLAMP>(v1)];
     const uint32_t c0 = __byte_perm(t0, t1, 0x5410u);     // lo halves
     const uint32_t c1 = __byte_perm(t0, t1, 0x7632u);     // hi halves
     const uint32_t z = b2add(c0, b2mul(c1, f32x2_to_bf16x2(v0, v1)));
-    const uint32_t top = __byte_perm(w0, w1, 0x7030u);
+    const uint32_t top = __byte_perm(w0, w1, SIGN15 ? 0x5010u : 0x7030u);
     return z ^ (top & 0x80008000u);
 }
 

@@ -79,19 +79,32 @@ struct PathPair {
     }
 };
 
+// Table normals of two samples from their mirrored uniforms v0, v1 and the
+// words carrying their signs (bit 31, or bit 15 with SIGN15).
+template <int P, bool SIGN15>
+__device__ __forceinline__ Pair<P> table_pair(const SmemTable &s, uint32_t w0, uint32_t w1, float v0, float v1) {
+    if constexpr (P == P_F32) {
+        return Pair<P>::of2(table_z32<false, SIGN15>(s, w0, v0), table_z32<false, SIGN15>(s, w1, v1));
+    } else if constexpr (P == P_F16) {
+        return Pair<P>{table_z16<false, SIGN15>(s, w0, w1, v0, v1)};
+    } else {
+        return Pair<P>{table_zbf16<false, SIGN15>(s, w0, w1, v0, v1)};
+    }
+}
+
+// Approximate (or exact) normals of two samples from their Philox words.
+// TABLE16 (four-way bar paths): the table at the centre of the 2^-16 cell
+// that holds each word's 24-bit uniform, i.e. at the 16-bit uniform of the
+// word's top half (u24 = (2 (w >> 9) + 1) 2^-24 lies in cell w >> 16).
 template <int P, int ICDF>
 __device__ __forceinline__ Pair<P> icdf_pair(const SmemTable &s, const MlpFrags &mlp, uint32_t w0, uint32_t w1) {
     if constexpr (ICDF == ICDF_EXACT) {
         return Pair<P>::of2(exact_z(w0), exact_z(w1));
     } else if constexpr (ICDF == ICDF_TABLE) {
-        const float v0 = mirrored_v(w0), v1 = mirrored_v(w1);
-        if constexpr (P == P_F32) {
-            return Pair<P>::of2(table_z32<false>(s, w0, v0), table_z32<false>(s, w1, v1));
-        } else if constexpr (P == P_F16) {
-            return Pair<P>{table_z16<false>(s, w0, w1, v0, v1)};
-        } else {
-            return Pair<P>{table_zbf16<false>(s, w0, w1, v0, v1)};
-        }
+        return table_pair<P, false>(s, w0, w1, mirrored_v(w0), mirrored_v(w1));
+    } else if constexpr (ICDF == ICDF_TABLE16) {
+        const uint32_t f0 = half16_bits<true>(w0), f1 = half16_bits<true>(w1);
+        return table_pair<P, true>(s, f0, f1, mirrored_v16(f0), mirrored_v16(f1));
     } else {
         const float2 z = mlp_z_warp(mlp, w0, w1);      // all 32 lanes together
         return Pair<P>::of2(z.x, z.y);
@@ -139,17 +152,47 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
         }
     };
 
-    for (uint32_t j = 0; j < ncalls; ++j) {
-        const uint4 r0 = philox4x32_10(make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), j, a.tag), a.k0, a.k1);
-        const uint4 r1 = philox4x32_10(make_uint4((uint32_t)p1, (uint32_t)(p1 >> 32), j, a.tag), a.k0, a.k1);
-        if (nf >= 4) {
-            body(r0.x, r1.x, 0);
-            body(r0.y, r1.y, 1);
-            body(r0.z, r1.z, 2);
-            body(r0.w, r1.w, 3);
-        } else {
-            body(r0.x, r1.x, 0);
-            if (nf == 2) body(r0.y, r1.y, 1);
+    if constexpr (ICDF == ICDF_TABLE16 && MODE == MODE_TWO) {
+        // two 16-bit uniforms per word: fine step n takes half n mod 2 (low
+        // half first) of word (n / 2) mod 4 of call n / 8
+        auto body16 = [&](uint32_t f0, uint32_t f1, int q) {
+            const Pair<P> z = table_pair<P, true>(tab, f0, f1, mirrored_v16(f0), mirrored_v16(f1));
+            fine.step(z);
+            if (q & 1) coarse.step(add(zprev, z));
+            else zprev = z;
+        };
+        auto halves = [&](uint32_t x0, uint32_t x1, int q) {
+            body16(half16_bits<false>(x0), half16_bits<false>(x1), q);
+            body16(half16_bits<true>(x0), half16_bits<true>(x1), q + 1);
+        };
+        const uint32_t ncalls16 = (nf + 7u) >> 3;
+        for (uint32_t j = 0; j < ncalls16; ++j) {
+            const uint4 r0 = philox4x32_10(make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), j, a.tag), a.k0, a.k1);
+            const uint4 r1 = philox4x32_10(make_uint4((uint32_t)p1, (uint32_t)(p1 >> 32), j, a.tag), a.k0, a.k1);
+            if (nf >= 8) {
+                halves(r0.x, r1.x, 0);
+                halves(r0.y, r1.y, 2);
+                halves(r0.z, r1.z, 4);
+                halves(r0.w, r1.w, 6);
+            } else {
+                body16(half16_bits<false>(r0.x), half16_bits<false>(r1.x), 0);
+                if (nf >= 2) body16(half16_bits<true>(r0.x), half16_bits<true>(r1.x), 1);
+                if (nf >= 4) halves(r0.y, r1.y, 2);
+            }
+        }
+    } else {
+        for (uint32_t j = 0; j < ncalls; ++j) {
+            const uint4 r0 = philox4x32_10(make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), j, a.tag), a.k0, a.k1);
+            const uint4 r1 = philox4x32_10(make_uint4((uint32_t)p1, (uint32_t)(p1 >> 32), j, a.tag), a.k0, a.k1);
+            if (nf >= 4) {
+                body(r0.x, r1.x, 0);
+                body(r0.y, r1.y, 1);
+                body(r0.z, r1.z, 2);
+                body(r0.w, r1.w, 3);
+            } else {
+                body(r0.x, r1.x, 0);
+                if (nf == 2) body(r0.y, r1.y, 1);
+            }
         }
     }
 
@@ -213,11 +256,15 @@ __device__ __forceinline__ float warp_sum(float v) {
 // the block's sum (warps added in FP64).
 __host__ __device__ __forceinline__ uint32_t chunk_group(int l) { return l >= 6 ? 1u : (64u >> l); }
 
+// Register budget: two-way kernels fit 64 registers (4 blocks of 256 per
+// SM); four-way kernels carry four paths per sample and get 80 (3 blocks),
+// which removes their spills (measured 8 % faster on GB300 than 64 registers
+// with spills); the MLP kernels hold the network's fragments (1 block).
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 1 : 4) level_kernel(const LevelArgs a) {
+__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 1 : (MODE == MODE_FOUR ? 3 : 4)) level_kernel(const LevelArgs a) {
     __shared__ SmemTable tab;
     __shared__ double red[2][32];
-    if (ICDF == ICDF_TABLE) {
+    if (ICDF == ICDF_TABLE || ICDF == ICDF_TABLE16) {
         stage_table(tab, a.tab32, a.tab16, a.tabbf);
         __syncthreads();
     }

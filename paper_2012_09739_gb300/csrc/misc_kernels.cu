@@ -156,7 +156,9 @@ __global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const float2
         size_t idx[2];
         for (int h = 0; h < 2; ++h) {
             idx[h] = base + 2 * lane + h;
-            const float ui = u[idx[h] < n ? idx[h] : n - 1];
+            float ui = u[idx[h] < n ? idx[h] : n - 1];
+            // TABLE16: centre of the 2^-16 cell that holds u (exact steps)
+            if (ICDF == ICDF_TABLE16) ui = __fmul_rn(__fadd_rn(floorf(__fmul_rn(ui, 65536.0f)), 0.5f), 0x1p-16f);
             const bool upper = ui > 0.5f;
             v[h] = upper ? __fsub_rn(1.0f, ui) : ui;
             sg[h] = upper ? 0x80000000u : 0u;
@@ -171,7 +173,7 @@ __global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const float2
             if (idx[h] >= n) continue;
             if (ICDF == ICDF_EXACT) {
                 r[h] = __uint_as_float(__float_as_uint(normcdfinvf(v[h])) ^ sg[h]);
-            } else if (ICDF == ICDF_TABLE) {
+            } else if (ICDF == ICDF_TABLE || ICDF == ICDF_TABLE16) {
                 if (P == P_F16) {
                     const __half2 hz = table_z16<true>(tab, sg[h], sg[h], v[h], v[h]);
                     static_cast<__half *>(z)[idx[h]] = __low2half(hz);
@@ -197,6 +199,7 @@ cudaError_t launch_icdf_bulk(const float *u, void *z, size_t n, int icdf, int pr
 #define MLMC_ICDF_PREC(PP)                                  \
     if (icdf == ICDF_EXACT) MLMC_ICDF_CASE(PP, ICDF_EXACT); \
     else if (icdf == ICDF_TABLE) MLMC_ICDF_CASE(PP, ICDF_TABLE); \
+    else if (icdf == ICDF_TABLE16) MLMC_ICDF_CASE(PP, ICDF_TABLE16); \
     else MLMC_ICDF_CASE(PP, ICDF_MLP)
     if (prec == P_F32) {
         MLMC_ICDF_PREC(P_F32);

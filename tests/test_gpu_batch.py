@@ -64,11 +64,12 @@ def test_single_item_batch_equals_level_kernel():
     for kind, l, N, prec in [(0, 0, 1, M.MLMC_F16), (1, 3, 77777, M.MLMC_F16), (0, 7, 4097, M.MLMC_F16),
                              (1, 12, 33, M.MLMC_F16), (0, 16, 1, M.MLMC_F16), (1, 5, 9999, M.MLMC_BF16),
                              (0, 9, 3001, M.MLMC_BF16), (1, 4, 5000, M.MLMC_F32)]:
-        it = M.mlmc_work(p, l, kind, prec, 1, M.MLMC_ICDF_TABLE, 0, N, 5)
-        g = M.mlmc_batch([it], SEED)[0]
-        fn = M.mlmc_nested_level if kind else M.mlmc_level
-        ref = fn(l, N, prec, True, M.MLMC_ICDF_TABLE, p, SEED, 5)
-        _close(g, ref)
+        for icdf in (M.MLMC_ICDF_TABLE, M.MLMC_ICDF_TABLE16):
+            it = M.mlmc_work(p, l, kind, prec, 1, icdf, 0, N, 5)
+            g = M.mlmc_batch([it], SEED)[0]
+            fn = M.mlmc_nested_level if kind else M.mlmc_level
+            ref = fn(l, N, prec, True, icdf, p, SEED, 5)
+            _close(g, ref)
 
 
 def test_batch_config3_full_size_statistics():

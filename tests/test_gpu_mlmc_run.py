@@ -20,13 +20,16 @@ def _opts(estimator, prec=M.MLMC_F16, kahan=1, icdf=M.MLMC_ICDF_TABLE, seed=1234
                            n0=10000, seed=seed, alpha=1.0, timeout_s=300.0)
 
 
-@pytest.mark.parametrize("estimator", [0, 1])
-def test_mlmc_run_reaches_eps(estimator):
+@pytest.mark.parametrize("estimator,icdf,prec", [(0, M.MLMC_ICDF_TABLE, M.MLMC_F16),
+                                                 (1, M.MLMC_ICDF_TABLE, M.MLMC_F16),
+                                                 (1, M.MLMC_ICDF_TABLE16, M.MLMC_F16),
+                                                 (1, M.MLMC_ICDF_TABLE, M.MLMC_BF16)])
+def test_mlmc_run_reaches_eps(estimator, icdf, prec):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     eps = 1e-3
     params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
-    r = M.mlmc_run(eps, params, _opts(estimator))
+    r = M.mlmc_run(eps, params, _opts(estimator, prec=prec, icdf=icdf))
     bs = mlmc.bs_call()
     assert r.levels >= 3 and r.rounds >= 1
     assert r.variance <= eps * eps / 2 * 1.05

@@ -325,3 +325,85 @@ def test_invalid_arguments_raise():
     assert e.value.status == M.MLMC_EINVAL
     with pytest.raises(M.MlmcError):
         M.mlmc_nested_level(3, 10, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, params, SEED)
+
+
+# ------------------------------------------------------------------ 16-bit uniforms (TABLE16)
+
+
+@pytest.mark.parametrize("prec", [M.MLMC_F16, M.MLMC_F32, M.MLMC_BF16])
+@pytest.mark.parametrize("kahan", [True, False])
+@pytest.mark.parametrize("l", [0, 1, 2, 3, 4, 7, 10])
+def test_twoway_table16_paths_bitexact(prec, kahan, l, pl_table):
+    """Two 16-bit uniforms per Philox word; levels 0-2 use part of one call."""
+    params = M.sde_params(**GBM_CALL)
+    N = 1537
+    got = gpu_paths(0, l, N, prec, kahan, M.MLMC_ICDF_TABLE16, params, offset=123)
+    ref = O.twoway_paths(l, np.arange(123, 123 + N), _bar_variant(prec, kahan, O.RV_TABLE16), _orc_sde(params),
+                         SEED, _kind_tag(0, M.MLMC_ICDF_TABLE16, l), table=pl_table)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("sde", ["gbm_x", "ou_x"])
+def test_twoway_table16_ou_and_x(sde, pl_table):
+    params = M.sde_params(**(GBM_X if sde == "gbm_x" else OU_X))
+    got = gpu_paths(0, 6, 999, M.MLMC_F16, True, M.MLMC_ICDF_TABLE16, params)
+    ref = O.twoway_paths(6, np.arange(999), _bar_variant(M.MLMC_F16, True, O.RV_TABLE16), _orc_sde(params), SEED,
+                         _kind_tag(0, M.MLMC_ICDF_TABLE16, 6), table=pl_table)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("prec", [M.MLMC_F16, M.MLMC_BF16, M.MLMC_F32])
+@pytest.mark.parametrize("l", [0, 1, 4, 9])
+def test_fourway_table16_paths(prec, l, pl_table):
+    params = M.sde_params(**GBM_CALL)
+    N = 1025
+    got = gpu_paths(1, l, N, prec, True, M.MLMC_ICDF_TABLE16, params)
+    ref = O.fourway_paths(l, np.arange(N), O.variant(), _bar_variant(prec, True, O.RV_TABLE16), _orc_sde(params),
+                          SEED, _kind_tag(1, M.MLMC_ICDF_TABLE16, l), table=pl_table)
+    assert np.array_equal(got[:, 2:4], ref[:, 2:4])
+    scale = np.maximum(1.0, np.abs(ref[:, 0]))
+    assert np.all(np.abs(got[:, 0:2] - ref[:, 0:2]) <= TOL32 * scale[:, None])
+    # the hat pair is the same as with 24-bit table normals on the bar pair
+    hat = gpu_paths(1, l, N, prec, True, M.MLMC_ICDF_TABLE, params)
+    assert np.array_equal(got[:, 0:2], hat[:, 0:2])
+
+
+@pytest.mark.parametrize("prec", [M.MLMC_F32, M.MLMC_F16, M.MLMC_BF16])
+def test_approx_icdf_table16_bitexact(prec, pl_table):
+    dev = _dev()
+    rng = np.random.default_rng(4)
+    u = np.concatenate([rng.random(100000), (2 * rng.integers(0, 1 << 23, 100000) + 1) * 2.0 ** -24,
+                        [2.0 ** -24, 2.0 ** -16, 2.0 ** -16 - 2.0 ** -24, 0.5, 0.5 - 2.0 ** -24,
+                         1 - 2.0 ** -24]]).astype(np.float32)
+    u = u[(u > 0) & (u < 1)]
+    z = torch.empty(u.size, dtype=torch.float32 if prec == M.MLMC_F32 else torch.int16, device=dev)
+    M.approx_icdf(torch.from_numpy(u).to(dev), z, M.MLMC_ICDF_TABLE16, prec)
+    torch.cuda.synchronize()
+    ref = O.approx_icdf(u.astype(np.float64), O.RV_TABLE16, prec=_OPREC[prec], table=pl_table)
+    got = z.cpu().numpy().view(np.float16).astype(np.float64) if prec == M.MLMC_F16 else _z_host(z, prec)
+    assert np.array_equal(got, ref)
+
+
+def test_table16_level_sums_match_oracle(pl_table):
+    params = M.sde_params(**GBM_CALL)
+    for four, l, N in ((0, 5, 30001), (1, 4, 20001)):
+        fn = M.mlmc_nested_level if four else M.mlmc_level
+        s = fn(l, N, M.MLMC_F16, True, M.MLMC_ICDF_TABLE16, params, SEED)
+        bar = _bar_variant(M.MLMC_F16, True, O.RV_TABLE16)
+        o1, o2 = O.level_sums(l, N, 0, O.variant() if four else bar, _orc_sde(params), SEED,
+                              _kind_tag(four, M.MLMC_ICDF_TABLE16, l), table=pl_table, four=bool(four),
+                              var2=bar, nthreads=4)
+        assert abs(s.s1 - o1) <= 2e-5 * (abs(o1) + math.sqrt(o2 * N)), (four, s.s1, o1)
+        assert abs(s.s2 - o2) <= 1e-5 * o2
+
+
+def test_full_size_level12_table16_sampled(pl_table):
+    """N = 2^20 at l = 12, two-way TABLE16 (the bench's launch shape):
+    sampled per-path outputs against the oracle."""
+    params = M.sde_params(**GBM_CALL)
+    N, l = 1 << 20, 12
+    got = gpu_paths(0, l, N, M.MLMC_F16, True, M.MLMC_ICDF_TABLE16, params)
+    idx = np.unique(np.concatenate([np.random.default_rng(5).integers(0, N, 40), [0, 1, N - 2, N - 1]]))
+    ref = O.twoway_paths(l, idx, _bar_variant(M.MLMC_F16, True, O.RV_TABLE16), _orc_sde(params), SEED,
+                         _kind_tag(0, 1, l), table=pl_table)
+    assert np.array_equal(got[idx], ref)
