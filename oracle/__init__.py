@@ -37,7 +37,7 @@ _lib = None
 # precision codes (oracle.c)
 F64, F32, F16, BF16, PBITS = 0, 1, 2, 3, 4
 # random-variable kinds
-RV_EXACT, RV_TABLE, RV_MLP, RV_TABLE16 = 0, 1, 2, 3
+RV_EXACT, RV_TABLE, RV_MLP, RV_TABLE16, RV_CUBIC = 0, 1, 2, 3, 4
 # SDEs and payoffs
 GBM, OU = 0, 1
 PAYOFF_X, PAYOFF_CALL = 0, 1
@@ -199,15 +199,26 @@ def round_bits(x, prec: int, pbits: int = 53) -> np.ndarray:
 
 _NO_MLP = np.zeros(1153)
 _NO_TABLE = np.zeros(32)
+_NO_CUBIC = np.zeros(64)
 
 
-def approx_icdf(u, rv: int, prec: int = F64, pbits: int = 53, table=None, mlp=None) -> np.ndarray:
+def _tables(table, cubic):
+    """The linear table (16 x 2) followed by the cubic one (16 x 4), as the C
+    entry points take them."""
+    t = _f64(table if table is not None else _NO_TABLE).ravel()
+    c = _f64(cubic if cubic is not None else _NO_CUBIC).ravel()
+    assert t.size == 32 and c.size == 64
+    return np.ascontiguousarray(np.concatenate([t, c]))
+
+
+def approx_icdf(u, rv: int, prec: int = F64, pbits: int = 53, table=None, mlp=None, cubic=None) -> np.ndarray:
     """Phi^-1 (rv=RV_EXACT), piecewise-linear table (RV_TABLE), the table at
-    the 16-bit cell centre q16(u) (RV_TABLE16) or MLP (RV_MLP) evaluated with
-    the rounding of precision prec."""
+    the 16-bit cell centre q16(u) (RV_TABLE16), piecewise cubic (RV_CUBIC,
+    coefficients `cubic`) or MLP (RV_MLP) evaluated with the rounding of
+    precision prec."""
     u = _f64(u).ravel()
     z = np.empty_like(u)
-    t = _f64(table if table is not None else _NO_TABLE)
+    t = _tables(table, cubic)
     w = _f64(mlp if mlp is not None else _NO_MLP)
     lib().orc_approx_icdf(_ptr(u, ctypes.c_double), _ptr(z, ctypes.c_double), u.size, rv, prec, pbits,
                           _ptr(t, ctypes.c_double), _ptr(w, ctypes.c_double))
@@ -218,11 +229,11 @@ def variant(prec=F64, kahan=False, rv=RV_EXACT, pbits=53) -> np.ndarray:
     return np.array([prec, pbits, int(bool(kahan)), rv], dtype=np.int32)
 
 
-def twoway_paths(l, idx, var, sde: SDE, seed, tag, table=None, mlp=None) -> np.ndarray:
+def twoway_paths(l, idx, var, sde: SDE, seed, tag, table=None, mlp=None, cubic=None) -> np.ndarray:
     """Per-path (P_fine, P_coarse, D) of the two-way difference at level l."""
     idx = np.ascontiguousarray(idx, dtype=np.uint64).ravel()
     out = np.empty((idx.size, 3), np.float64)
-    t = _f64(table if table is not None else _NO_TABLE)
+    t = _tables(table, cubic)
     w = _f64(mlp if mlp is not None else _NO_MLP)
     var = np.ascontiguousarray(var, dtype=np.int32)
     lib().orc_twoway_paths(l, _ptr(idx, ctypes.c_uint64), idx.size, _ptr(var, ctypes.c_int), ctypes.byref(sde),
@@ -231,11 +242,11 @@ def twoway_paths(l, idx, var, sde: SDE, seed, tag, table=None, mlp=None) -> np.n
     return out
 
 
-def fourway_paths(l, idx, hat, bar, sde: SDE, seed, tag, table=None, mlp=None) -> np.ndarray:
+def fourway_paths(l, idx, hat, bar, sde: SDE, seed, tag, table=None, mlp=None, cubic=None) -> np.ndarray:
     """Per-path (P^_f, P^_c, P-_f, P-_c, D) of the four-way difference."""
     idx = np.ascontiguousarray(idx, dtype=np.uint64).ravel()
     out = np.empty((idx.size, 5), np.float64)
-    t = _f64(table if table is not None else _NO_TABLE)
+    t = _tables(table, cubic)
     w = _f64(mlp if mlp is not None else _NO_MLP)
     hat = np.ascontiguousarray(hat, dtype=np.int32)
     bar = np.ascontiguousarray(bar, dtype=np.int32)
@@ -245,10 +256,10 @@ def fourway_paths(l, idx, hat, bar, sde: SDE, seed, tag, table=None, mlp=None) -
     return out
 
 
-def level_sums(l, N, path_offset, var, sde: SDE, seed, tag, table=None, mlp=None, four=False, var2=None,
+def level_sums(l, N, path_offset, var, sde: SDE, seed, tag, table=None, mlp=None, cubic=None, four=False, var2=None,
                nthreads=1) -> tuple[float, float]:
     """(sum D, sum D^2) over paths path_offset .. path_offset+N-1."""
-    t = _f64(table if table is not None else _NO_TABLE)
+    t = _tables(table, cubic)
     w = _f64(mlp if mlp is not None else _NO_MLP)
     var = np.ascontiguousarray(var, dtype=np.int32)
     var2 = np.ascontiguousarray(var2 if var2 is not None else var, dtype=np.int32)
@@ -259,9 +270,9 @@ def level_sums(l, N, path_offset, var, sde: SDE, seed, tag, table=None, mlp=None
     return float(sums[0]), float(sums[1])
 
 
-def rounding_pairs(l, N, path_offset, var, sde: SDE, seed, tag, table=None, mlp=None) -> np.ndarray:
+def rounding_pairs(l, N, path_offset, var, sde: SDE, seed, tag, table=None, mlp=None, cubic=None) -> np.ndarray:
     """(X_T in FP64, X_T in working precision) driven by the same normals."""
-    t = _f64(table if table is not None else _NO_TABLE)
+    t = _tables(table, cubic)
     w = _f64(mlp if mlp is not None else _NO_MLP)
     var = np.ascontiguousarray(var, dtype=np.int32)
     out = np.empty((N, 2), np.float64)

@@ -226,6 +226,31 @@ static double table_icdf(double u, const double *table, const rmode *m)
     return upper ? -z : z;
 }
 
+/* Piecewise cubic (the high-fidelity approximation of the Sec. 2.2
+ * experiments): same intervals and mirroring; on interval k the local
+ * variable s = A v - B lies in [-1, 1] (A = 2^(k+2), B = 3 for k <= 15;
+ * A = 2^17, B = 1 for k = 16) and g = d0 + d1 s + d2 s^2 + d3 s^3.
+ * cubic[4i + j] = d_j of interval i+1.  Working precision: s = R(A v - B)
+ * (exact on the uniform grid), then Horner with a rounding after every
+ * operation: z = R(d0 + R(s R(d1 + R(s R(d2 + R(s d3)))))). */
+static double cubic_icdf(double u, const double *cubic, const rmode *m)
+{
+    int upper = u > 0.5;
+    double v = upper ? 1.0 - u : u;
+    int i = interval_of(v);
+    double A = i < 15 ? ldexp(1.0, i + 3) : ldexp(1.0, 17);
+    double B = i < 15 ? 3.0 : 1.0;
+    double s = round_p(v * A - B, m);
+    const double *d = cubic + 4 * i;
+    double z = round_p(s * round_p(d[3], m), m);
+    z = round_p(round_p(d[2], m) + z, m);
+    z = round_p(s * z, m);
+    z = round_p(round_p(d[1], m) + z, m);
+    z = round_p(s * z, m);
+    z = round_p(round_p(d[0], m) + z, m);
+    return upper ? -z : z;
+}
+
 /* MLP surrogate: t = sqrt(-2 ln v), y = W3 tanh(W2 tanh(W1 t + b1) + b2)
  * + b3 approximates |Phi^-1(v)|; Phi~^-1(u) = -y for u <= 1/2, +y above.
  * Weight layout (1153 values): W1[32], b1[32], W2[32][32] (row = output
@@ -254,14 +279,17 @@ static double mlp_icdf(double u, const double *w)
 }
 
 /* RV kinds.  TABLE16: the piecewise-linear table at the 16-bit uniform
- * q16(u) (see uniform16_of). */
-enum { ORC_RV_EXACT = 0, ORC_RV_TABLE = 1, ORC_RV_MLP = 2, ORC_RV_TABLE16 = 3 };
+ * q16(u) (see uniform16_of).  CUBIC: the piecewise cubic.  The `table`
+ * argument of the entry points holds the linear table (32 values) followed
+ * by the cubic one (64 values). */
+enum { ORC_RV_EXACT = 0, ORC_RV_TABLE = 1, ORC_RV_MLP = 2, ORC_RV_TABLE16 = 3, ORC_RV_CUBIC = 4 };
 
 static double rv_of(double u, int rv, const double *table, const double *mlp, const rmode *m)
 {
     switch (rv) {
     case ORC_RV_TABLE: return table_icdf(u, table, m);
     case ORC_RV_TABLE16: return table_icdf(q16(u), table, m);
+    case ORC_RV_CUBIC: return cubic_icdf(u, table + 32, m);
     case ORC_RV_MLP: return round_p(mlp_icdf(u, mlp), m);
     default: return round_p(orc_ndtri1(u), m);
     }

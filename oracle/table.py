@@ -1,4 +1,6 @@
-"""Piecewise-linear approximate inverse Gaussian CDF (Sec. 2.1, Fig. 1).
+"""Piecewise-linear and piecewise-cubic approximate inverse Gaussian CDFs
+(Sec. 2.1, Fig. 1; the cubic is the high-fidelity approximation the paper
+uses for its rounding-error experiments in Sec. 2.2, Fig. 2).
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
@@ -7,6 +9,11 @@ on v = min(u, 1-u) the 16 intervals are I_k = [2^-(k+1), 2^-k) for
 k = 1..15 and I_16 = (0, 2^-16); on each interval g(v) = c0 + c1 v is the
 least-squares (L2 in the uniform measure) linear fit of Phi^-1, and the
 approximation is mirrored: Phi~^-1(u) = g(u) for u <= 1/2, -g(1-u) above.
+The cubic uses the same intervals and mirroring with the L2 fit of degree 3,
+written in the interval's own variable s in [-1, 1] (s = v 2^(k+2) - 3 on
+I_k, k <= 15, s = v 2^17 - 1 on I_16): g(v) = d0 + d1 s + d2 s^2 + d3 s^3.
+(Readings: the paper takes the cubic from its cited work; the interval set,
+the L2 criterion and the local variable s are this oracle's.)
 
 The moments are computed by 24-point Gauss-Legendre quadrature on dyadic
 sub-intervals (Phi^-1 is smooth on each; the logarithmic singularity at 0
@@ -74,4 +81,49 @@ def l2_error(tab: np.ndarray) -> float:
             half, mid = 0.5 * (hi - lo), 0.5 * (hi + lo)
             v = mid + half * _GL_X
             total += (half * _GL_W * (ndtri(v) - c0 - c1 * v) ** 2).sum()
+    return 2.0 * total
+
+
+def cubic_map(k: int) -> tuple[float, float]:
+    """(A, B) of the local variable s = A v - B on interval k = 1..16."""
+    if k < N_INTERVALS:
+        return 2.0 ** (k + 2), 3.0
+    return 2.0 ** (N_INTERVALS + 1), 1.0
+
+
+def build_cubic_table() -> np.ndarray:
+    """(16, 4) array of (d0, d1, d2, d3): the L2 cubic fit of Phi^-1 on each
+    interval in its variable s.  Computed as the orthogonal projection on
+    the Legendre polynomials P0..P3 of s (a_j = (2j+1)/2 int f P_j ds), then
+    expanded in powers of s."""
+    tab = np.zeros((N_INTERVALS, 4))
+    for k in range(1, N_INTERVALS + 1):
+        A, B = cubic_map(k)
+        a_lo, b_hi = interval_bounds(k)
+        proj = np.zeros(4)
+        for lo, hi in _pieces(a_lo, b_hi):
+            half, mid = 0.5 * (hi - lo), 0.5 * (hi + lo)
+            v = mid + half * _GL_X
+            w = half * _GL_W * A            # ds = A dv
+            s = A * v - B
+            fv = ndtri(v)
+            leg = np.array([np.ones_like(s), s, 0.5 * (3 * s * s - 1), 0.5 * (5 * s ** 3 - 3 * s)])
+            proj += (leg * (w * fv)).sum(axis=1)
+        a = proj * (2 * np.arange(4) + 1) / 2.0
+        tab[k - 1] = (a[0] - 0.5 * a[2], a[1] - 1.5 * a[3], 1.5 * a[2], 2.5 * a[3])
+    return tab
+
+
+def cubic_l2_error(tab: np.ndarray) -> float:
+    """E|Z - Z~|^2 of the piecewise cubic for U uniform on (0, 1)."""
+    total = 0.0
+    for k in range(1, N_INTERVALS + 1):
+        A, B = cubic_map(k)
+        d = tab[k - 1]
+        for lo, hi in _pieces(*interval_bounds(k)):
+            half, mid = 0.5 * (hi - lo), 0.5 * (hi + lo)
+            v = mid + half * _GL_X
+            s = A * v - B
+            g = d[0] + s * (d[1] + s * (d[2] + s * d[3]))
+            total += (half * _GL_W * (ndtri(v) - g) ** 2).sum()
     return 2.0 * total
