@@ -68,8 +68,21 @@ typedef enum { MLMC_F32 = 0, MLMC_F16 = 1, MLMC_BF16 = 2 } mlmc_prec;
  *            j = n / 8, halving the generator's work.  On four-way bar paths
  *            h = w >> 16, the 2^-16 cell of the hat path's 24-bit u, so both
  *            estimators see the same law of Z~ and the telescoping sum of
- *            Sec. 3 keeps its expectation. */
-typedef enum { MLMC_ICDF_EXACT = 0, MLMC_ICDF_TABLE = 1, MLMC_ICDF_MLP = 2, MLMC_ICDF_TABLE16 = 3 } mlmc_icdf;
+ *            Sec. 3 keeps its expectation.
+ *   CUBIC    the piecewise cubic at u: the L2 cubic fit of Phi^-1 on the
+ *            same 16 intervals (the high-fidelity approximation of the
+ *            Sec. 2.2 experiments), g = d0 + d1 s + d2 s^2 + d3 s^3 in the
+ *            interval's variable s = A v - B in [-1, 1] (A = 2^(k+2), B = 3
+ *            on interval k <= 15; A = 2^17, B = 1 on interval 16), evaluated
+ *            by Horner in the working precision with every operation
+ *            rounded. */
+typedef enum {
+    MLMC_ICDF_EXACT = 0,
+    MLMC_ICDF_TABLE = 1,
+    MLMC_ICDF_MLP = 2,
+    MLMC_ICDF_TABLE16 = 3,
+    MLMC_ICDF_CUBIC = 4
+} mlmc_icdf;
 
 /* SDE dX = a(X) dt + b(X) dW on [0, T], X_0 = x0.
  *   GBM: a = p0 X, b = p1 X            (mu = p0, sigma = p1)
@@ -156,7 +169,9 @@ mlmc_status mlmc_level_paths(int four, int l, uint64_t N, int prec, int kahan, i
 
 /* Bulk approximate inverse CDF (Sec. 2.1): z_dev[i] = Phi~^-1(u_dev[i]) for
  * 0 < u < 1 (values outside give unspecified finite results); TABLE16
- * evaluates the table at the centre of the 2^-16 cell that holds u.  z_dev is
+ * evaluates the table at the centre of the 2^-16 cell that holds u.  For
+ * CUBIC in binary16 / bfloat16 the local variable s is rounded to binary32
+ * first (exact for u on the 24-bit grid).  z_dev is
  * float for prec = F32, IEEE binary16 (uint16_t storage) for F16 and
  * bfloat16 (uint16_t storage, the upper half of a binary32) for BF16.
  * icdf = EXACT evaluates Phi^-1 in FP32. */
@@ -175,6 +190,12 @@ mlmc_status mlmc_uniforms(const uint32_t *w_dev, float *u_dev, size_t n, void *s
  * bfloat16 roundings (round to nearest-even from the FP64 value), in the
  * same (c0, c1) order. */
 mlmc_status mlmc_icdf_table(double *c_host, float *c32_host, uint16_t *c16_host, uint16_t *cbf16_host);
+
+/* The piecewise cubic as built on the device (FP64 Legendre projection by
+ * Gauss-Legendre quadrature): d_host[4i + j] = d_j of interval i+1, and its
+ * binary32 / binary16 / bfloat16 roundings in the same order.  Any pointer
+ * may be NULL. */
+mlmc_status mlmc_icdf_cubic(double *d_host, float *d32_host, uint16_t *d16_host, uint16_t *dbf16_host);
 
 /* ---- MLP surrogate inverse CDF: 1 -> 32 -> 32 -> 1 tanh network on
  * t = sqrt(-2 ln v), v = min(u, 1-u); Z~ = -y for u <= 1/2, +y above.

@@ -21,7 +21,7 @@ MLMC_OK, MLMC_EINVAL, MLMC_ECUDA, MLMC_ETIMEOUT, MLMC_ENOMEM, MLMC_ENOTCONV, MLM
 MLMC_GBM, MLMC_OU = 0, 1
 MLMC_PAYOFF_X, MLMC_PAYOFF_CALL = 0, 1
 MLMC_F32, MLMC_F16, MLMC_BF16 = 0, 1, 2
-MLMC_ICDF_EXACT, MLMC_ICDF_TABLE, MLMC_ICDF_MLP, MLMC_ICDF_TABLE16 = 0, 1, 2, 3
+MLMC_ICDF_EXACT, MLMC_ICDF_TABLE, MLMC_ICDF_MLP, MLMC_ICDF_TABLE16, MLMC_ICDF_CUBIC = 0, 1, 2, 3, 4
 MLMC_MLP_PARAMS = 1153
 MLMC_MAX_LEVELS = 19
 
@@ -91,6 +91,7 @@ _SIGS = {
     "mlmc_philox4x32_10": [_vp, _vp, _vp, ctypes.c_size_t, _vp],
     "mlmc_uniforms": [_vp, _vp, ctypes.c_size_t, _vp],
     "mlmc_icdf_table": [_vp, _vp, _vp, _vp],
+    "mlmc_icdf_cubic": [_vp, _vp, _vp, _vp],
     "mlmc_mlp_set_weights": [_vp, ctypes.c_size_t],
     "mlmc_mlp_get_weights": [_vp, ctypes.c_size_t],
     "mlmc_mlp_grad": [_vp, _vp, ctypes.c_size_t, _vp, _vp, _vp],
@@ -214,6 +215,18 @@ def mlmc_icdf_table():
     _check(load().mlmc_icdf_table(c64.ctypes.data_as(_vp), c32.ctypes.data_as(_vp), c16.ctypes.data_as(_vp),
                                   cbf.ctypes.data_as(_vp)))
     return c64.reshape(16, 2), c32.reshape(16, 2), c16.reshape(16, 2), cbf.reshape(16, 2)
+
+
+def mlmc_icdf_cubic():
+    """(d64, d32, d16 bits, bf16 bits), each (16, 4), as built on the device."""
+    import numpy as np
+    d64 = np.zeros(64, np.float64)
+    d32 = np.zeros(64, np.float32)
+    d16 = np.zeros(64, np.uint16)
+    dbf = np.zeros(64, np.uint16)
+    _check(load().mlmc_icdf_cubic(d64.ctypes.data_as(_vp), d32.ctypes.data_as(_vp), d16.ctypes.data_as(_vp),
+                                  dbf.ctypes.data_as(_vp)))
+    return d64.reshape(16, 4), d32.reshape(16, 4), d16.reshape(16, 4), dbf.reshape(16, 4)
 
 
 def mlmc_mlp_set_weights(w):

@@ -45,16 +45,10 @@ mlmc_status device_state(DeviceState **out) {
     if (!d.ready) {
         if ((e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
             return cuda_fail(e, "cudaDeviceGetAttribute");
-        if ((e = cudaMalloc(&d.tab64, 32 * sizeof(double))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(table)");
-        if ((e = cudaMalloc(&d.tab32, TAB_ENTRIES * sizeof(float2))) != cudaSuccess)
-            return cuda_fail(e, "cudaMalloc(table)");
-        if ((e = cudaMalloc(&d.tab16, TAB_ENTRIES * sizeof(__half2))) != cudaSuccess)
-            return cuda_fail(e, "cudaMalloc(table)");
-        if ((e = cudaMalloc(&d.tabbf, TAB_ENTRIES * sizeof(uint32_t))) != cudaSuccess)
-            return cuda_fail(e, "cudaMalloc(table)");
+        if ((e = cudaMalloc(&d.tabs, sizeof(DevTables))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(table)");
         if ((e = cudaMalloc(&d.mlp, sizeof(MlpWeights))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(mlp)");
         if ((e = cudaMemset(d.mlp, 0, sizeof(MlpWeights))) != cudaSuccess) return cuda_fail(e, "cudaMemset(mlp)");
-        if ((e = launch_build_table(d.tab64, d.tab32, d.tab16, d.tabbf, 0)) != cudaSuccess)
+        if ((e = launch_build_table(d.tabs, 0)) != cudaSuccess)
             return cuda_fail(e, "build_table");
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "build_table");
         d.device = dev;
@@ -106,7 +100,7 @@ mlmc_status check_level(int four, int l, uint64_t N, int prec, int icdf, const m
     if (N == 0) return fail(MLMC_EINVAL, "N must be >= 1");
     if (N > (1ull << 40)) return fail(MLMC_EINVAL, "N too large");
     if (prec != MLMC_F32 && prec != MLMC_F16 && prec != MLMC_BF16) return fail(MLMC_EINVAL, "unknown precision %d", prec);
-    if (icdf < 0 || icdf > 3) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
+    if (icdf < 0 || icdf > 4) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
     if (four && icdf == MLMC_ICDF_EXACT) return fail(MLMC_EINVAL, "four-way difference needs approximate normals");
     return check_params(p);
 }
@@ -142,9 +136,7 @@ LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int
     a.x0 = p->x0;
     a.K = p->K;
     a.disc = p->disc;
-    a.tab32 = d.tab32;
-    a.tab16 = d.tab16;
-    a.tabbf = d.tabbf;
+    a.tabs = d.tabs;
     a.mlp = d.mlp;
     return a;
 }
@@ -305,7 +297,7 @@ mlmc_status mlmc_level_paths(int four, int l, uint64_t N, int prec, int kahan, i
 }
 
 mlmc_status approx_icdf(const float *u_dev, void *z_dev, size_t n, int icdf, int prec, void *stream) {
-    if (icdf < 0 || icdf > 3) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
+    if (icdf < 0 || icdf > 4) return fail(MLMC_EINVAL, "unknown icdf %d", icdf);
     if (prec != MLMC_F32 && prec != MLMC_F16 && prec != MLMC_BF16) return fail(MLMC_EINVAL, "unknown precision %d", prec);
     if (n == 0) return MLMC_OK;
     if (!u_dev || !z_dev) return fail(MLMC_EINVAL, "NULL buffer");
@@ -313,8 +305,7 @@ mlmc_status approx_icdf(const float *u_dev, void *z_dev, size_t n, int icdf, int
     mlmc_status st = device_state(&d);
     if (st) return st;
     if (icdf == MLMC_ICDF_MLP && !d->mlp_ready) return fail(MLMC_ENOTREADY, "MLP weights not set");
-    cudaError_t e = launch_icdf_bulk(u_dev, z_dev, n, icdf, prec, d->tab32, d->tab16, d->tabbf, d->mlp,
-                                     (cudaStream_t)stream);
+    cudaError_t e = launch_icdf_bulk(u_dev, z_dev, n, icdf, prec, d->tabs, d->mlp, (cudaStream_t)stream);
     return e == cudaSuccess ? MLMC_OK : cuda_fail(e, "approx_icdf");
 }
 
@@ -335,38 +326,61 @@ mlmc_status mlmc_uniforms(const uint32_t *w_dev, float *u_dev, size_t n, void *s
     return e == cudaSuccess ? MLMC_OK : cuda_fail(e, "uniforms");
 }
 
-mlmc_status mlmc_icdf_table(double *c_host, float *c32_host, uint16_t *c16_host, uint16_t *cbf16_host) {
+// Table entry (biased binary32 exponent E of v, minus 103) that holds
+// 0-based interval i: E = 125 - i for i < 15, any E <= 110 for the last.
+static int interval_entry(int i) { return i < 15 ? 22 - i : 0; }
+
+static mlmc_status fetch_tables(DevTables *h) {
     DeviceState *d;
     mlmc_status st = device_state(&d);
     if (st) return st;
-    double t64[32];
-    float2 t32[TAB_ENTRIES];
-    __half2 t16[TAB_ENTRIES];
-    uint32_t tbf[TAB_ENTRIES];
-    cudaError_t e = cudaMemcpy(t64, d->tab64, sizeof t64, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(tbf, d->tabbf, sizeof tbf, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(t32, d->tab32, sizeof t32, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(t16, d->tab16, sizeof t16, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(e, "mlmc_icdf_table");
+    cudaError_t e = cudaMemcpy(h, d->tabs, sizeof(DevTables), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? MLMC_OK : cuda_fail(e, "copy of the tables");
+}
+
+mlmc_status mlmc_icdf_table(double *c_host, float *c32_host, uint16_t *c16_host, uint16_t *cbf16_host) {
+    DevTables t;
+    mlmc_status st = fetch_tables(&t);
+    if (st) return st;
     for (int i = 0; i < 16; ++i) {
-        // interval i+1 sits in entry E - 103 with E = 125 - i (i < 15), E = 103 for the last
-        const int entry = i < 15 ? 22 - i : 0;
+        const int entry = interval_entry(i);
         if (c_host) {
-            c_host[2 * i] = t64[2 * i];
-            c_host[2 * i + 1] = t64[2 * i + 1];
+            c_host[2 * i] = t.lin64[2 * i];
+            c_host[2 * i + 1] = t.lin64[2 * i + 1];
         }
         if (c32_host) {
-            c32_host[2 * i] = t32[entry].x;
-            c32_host[2 * i + 1] = t32[entry].y;
+            c32_host[2 * i] = t.e.c32[entry].x;
+            c32_host[2 * i + 1] = t.e.c32[entry].y;
         }
         if (c16_host) {
-            __half2_raw r = *reinterpret_cast<__half2_raw *>(&t16[entry]);
+            __half2_raw r = *reinterpret_cast<__half2_raw *>(&t.e.c16[entry]);
             c16_host[2 * i] = r.x;
             c16_host[2 * i + 1] = r.y;
         }
         if (cbf16_host) {
-            cbf16_host[2 * i] = (uint16_t)(tbf[entry] & 0xFFFFu);
-            cbf16_host[2 * i + 1] = (uint16_t)(tbf[entry] >> 16);
+            cbf16_host[2 * i] = (uint16_t)(t.e.cb16[entry] & 0xFFFFu);
+            cbf16_host[2 * i + 1] = (uint16_t)(t.e.cb16[entry] >> 16);
+        }
+    }
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_icdf_cubic(double *d_host, float *d32_host, uint16_t *d16_host, uint16_t *dbf16_host) {
+    DevTables t;
+    mlmc_status st = fetch_tables(&t);
+    if (st) return st;
+    for (int i = 0; i < 16; ++i) {
+        const int entry = interval_entry(i);
+        const float4 q = t.e.q32[entry];
+        const float q32[4] = {q.x, q.y, q.z, q.w};
+        const uint2 h = t.e.q16[entry], b = t.e.qbf[entry];
+        const uint32_t h16[4] = {h.x & 0xFFFFu, h.x >> 16, h.y & 0xFFFFu, h.y >> 16};
+        const uint32_t b16[4] = {b.x & 0xFFFFu, b.x >> 16, b.y & 0xFFFFu, b.y >> 16};
+        for (int j = 0; j < 4; ++j) {
+            if (d_host) d_host[4 * i + j] = t.cub64[4 * i + j];
+            if (d32_host) d32_host[4 * i + j] = q32[j];
+            if (d16_host) d16_host[4 * i + j] = (uint16_t)h16[j];
+            if (dbf16_host) dbf16_host[4 * i + j] = (uint16_t)b16[j];
         }
     }
     return MLMC_OK;
@@ -414,10 +428,7 @@ mlmc_status mlmc_shutdown(void) {
         if (!d.ready) continue;
         cudaSetDevice(i);
         release_device_extras(d);
-        cudaFree(d.tab64);
-        cudaFree(d.tab32);
-        cudaFree(d.tab16);
-        cudaFree(d.tabbf);
+        cudaFree(d.tabs);
         cudaFree(d.mlp);
         d = DeviceState();
     }

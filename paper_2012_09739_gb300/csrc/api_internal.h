@@ -12,16 +12,14 @@ constexpr int MAX_DEVICES = 16;
 
 struct BatchCache;   // batch.cu: captured graph of the last batch shape
 
-// Per-device library state: the piecewise-linear table (FP64 and its
-// binary32/binary16 roundings), the MLP weights, cached graphs.
+// Per-device library state: the piecewise-linear and cubic tables (FP64 and
+// their binary32 / binary16 / bfloat16 roundings), the MLP weights, cached
+// graphs.
 struct DeviceState {
     bool ready = false;
     int device = -1;
     int sm_count = 0;
-    double *tab64 = nullptr;
-    float2 *tab32 = nullptr;
-    __half2 *tab16 = nullptr;
-    uint32_t *tabbf = nullptr;
+    DevTables *tabs = nullptr;
     MlpWeights *mlp = nullptr;
     bool mlp_ready = false;
     BatchCache *batch = nullptr;         // mlmc_batch: captured graph and buffers

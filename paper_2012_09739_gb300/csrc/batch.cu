@@ -247,7 +247,7 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         uint32_t grid = (uint32_t)bps * d.sm_count;
         grid = std::min<uint32_t>(grid, (warps_needed + 7) / 8);
         fn<<<grid ? grid : 1, 256, 0, s>>>(c.items, c.tiles + g.tile_base, (uint32_t)g.tiles.size(), c.counters + gi,
-                                           c.partials + g.tile_base, d.tab32, d.tab16, d.tabbf);
+                                           c.partials + g.tile_base, d.tabs);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch kernel");
     }
     const int n = (int)p.items.size();

@@ -3,15 +3,17 @@
 
 namespace mlmc {
 
-static const BatchKernelFn k_batch[2][4] = {
+static const BatchKernelFn k_batch[2][5] = {
     {&batch_kernel<P_F32, false, ICDF_EXACT>, &batch_kernel<P_F32, false, ICDF_TABLE>, &batch_kernel<P_F32, false, ICDF_MLP>,
-     &batch_kernel<P_F32, false, ICDF_TABLE16>},
+     &batch_kernel<P_F32, false, ICDF_TABLE16>,
+     &batch_kernel<P_F32, false, ICDF_CUBIC>},
     {&batch_kernel<P_F32, true, ICDF_EXACT>, &batch_kernel<P_F32, true, ICDF_TABLE>, &batch_kernel<P_F32, true, ICDF_MLP>,
-     &batch_kernel<P_F32, true, ICDF_TABLE16>},
+     &batch_kernel<P_F32, true, ICDF_TABLE16>,
+     &batch_kernel<P_F32, true, ICDF_CUBIC>},
 };
 
 BatchKernelFn batch_kernel_f32(int kahan, int icdf) {
-    if (icdf < 0 || icdf > 3) return nullptr;
+    if (icdf < 0 || icdf > 4) return nullptr;
     return k_batch[kahan ? 1 : 0][icdf];
 }
 

@@ -22,11 +22,11 @@ struct Tile {
 
 template <int P, bool KAHAN, int ICDF>
 __global__ void __launch_bounds__(256) batch_kernel(const LevelArgs *items, const Tile *tiles, uint32_t ntiles,
-                                                    uint32_t *counter, double2 *tile_partials, const float2 *t32,
-                                                    const __half2 *t16, const uint32_t *tbf) {
+                                                    uint32_t *counter, double2 *tile_partials,
+                                                    const DevTables *tabs) {
     __shared__ SmemTable tab;
-    if (ICDF == ICDF_TABLE || ICDF == ICDF_TABLE16) {
-        stage_table(tab, t32, t16, tbf);
+    if (ICDF == ICDF_TABLE || ICDF == ICDF_TABLE16 || ICDF == ICDF_CUBIC) {
+        stage_table(tab, tabs);
         __syncthreads();
     }
     MlpFrags mlp;
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const LevelArgs *items, cons
     }
 }
 
-using BatchKernelFn = void (*)(const LevelArgs *, const Tile *, uint32_t, uint32_t *, double2 *, const float2 *,
-                               const __half2 *, const uint32_t *);
+using BatchKernelFn = void (*)(const LevelArgs *, const Tile *, uint32_t, uint32_t *, double2 *,
+                               const DevTables *);
 
 }  // namespace mlmc

@@ -179,7 +179,8 @@ struct KahanF32 {
 // ---------------------------------------------------------------- inverse CDFs
 // TABLE16: the table at a 16-bit uniform (two per Philox word on two-way
 // paths; the cell centre of the 24-bit uniform on four-way bar paths).
-enum { ICDF_EXACT = 0, ICDF_TABLE = 1, ICDF_MLP = 2, ICDF_TABLE16 = 3 };
+// CUBIC: the piecewise cubic.
+enum { ICDF_EXACT = 0, ICDF_TABLE = 1, ICDF_MLP = 2, ICDF_TABLE16 = 3, ICDF_CUBIC = 4 };
 
 // Shared-memory copy of the piecewise-linear table, indexed by the biased
 // binary32 exponent E of v: v in [2^(E-127), 2^(E-126)) lies in interval
@@ -187,9 +188,21 @@ enum { ICDF_EXACT = 0, ICDF_TABLE = 1, ICDF_MLP = 2, ICDF_TABLE16 = 3 };
 // for E = 103..125 (v >= 2^-24 on the uniform grid).
 constexpr int TAB_ENTRIES = 23;
 struct SmemTable {
-    float2 c32[TAB_ENTRIES];     // (c0, c1) in binary32
-    __half2 c16[TAB_ENTRIES];    // (c0, c1) in binary16
-    uint32_t cb16[TAB_ENTRIES];  // (c0, c1) in bfloat16 (c0 in the low half)
+    float2 c32[TAB_ENTRIES];     // linear (c0, c1) in binary32
+    __half2 c16[TAB_ENTRIES];    // linear (c0, c1) in binary16
+    uint32_t cb16[TAB_ENTRIES];  // linear (c0, c1) in bfloat16 (c0 in the low half)
+    float4 q32[TAB_ENTRIES];     // cubic (d0, d1, d2, d3) in binary32
+    uint2 q16[TAB_ENTRIES];      // cubic in binary16: (d0 | d1 << 16, d2 | d3 << 16)
+    uint2 qbf[TAB_ENTRIES];      // cubic in bfloat16, same packing
+    float2 qab[TAB_ENTRIES];     // cubic local variable s = A v - B as (A, -B)
+};
+
+// The per-device tables: the entries staged by the kernels, and the FP64
+// coefficients in interval order (intervals 1..16) for export.
+struct DevTables {
+    SmemTable e;
+    double lin64[32];            // linear (c0, c1)
+    double cub64[64];            // cubic (d0, d1, d2, d3)
 };
 
 // Entry index of v; CLAMP widens it to any v in (0, 1/2] (bulk API).
@@ -242,6 +255,68 @@ __device__ __forceinline__ uint32_t table_zbf16(const SmemTable &s, uint32_t w0,
     const uint32_t c1 = __byte_perm(t0, t1, 0x7632u);     // hi halves
     const uint32_t z = b2add(c0, b2mul(c1, f32x2_to_bf16x2(v0, v1)));
     const uint32_t top = __byte_perm(w0, w1, SIGN15 ? 0x5010u : 0x7030u);
+    return z ^ (top & 0x80008000u);
+}
+
+}  // namespace mlmc
+
+namespace mlmc {
+
+// Piecewise-cubic Z~ (the high-fidelity approximation of Sec. 2.2): on the
+// interval of v the local variable s = A v - B lies in [-1, 1]; it is formed
+// with one rounding of the exact value (exact on the uniform grid), then
+// Horner with every operation rounded:
+//   z = R(d0 + R(s R(d1 + R(s R(d2 + R(s d3)))))),  negated for u > 1/2.
+template <bool CLAMP>
+__device__ __forceinline__ float cubic_z32(const SmemTable &t, uint32_t w, float v) {
+    const int i = tab_index<CLAMP>(v);
+    const float2 ab = t.qab[i];
+    const float4 d = t.q32[i];
+    const float s = __fmaf_rn(v, ab.x, ab.y);
+    float z = __fmul_rn(s, d.w);
+    z = __fadd_rn(d.z, z);
+    z = __fmul_rn(s, z);
+    z = __fadd_rn(d.y, z);
+    z = __fmul_rn(s, z);
+    z = __fadd_rn(d.x, z);
+    return __uint_as_float(__float_as_uint(z) ^ (w & 0x80000000u));
+}
+
+// Two samples in binary16x2 (lo = sample of w0/v0, hi = w1/v1).
+template <bool CLAMP>
+__device__ __forceinline__ __half2 cubic_z16(const SmemTable &t, uint32_t w0, uint32_t w1, float v0, float v1) {
+    const int i0 = tab_index<CLAMP>(v0), i1 = tab_index<CLAMP>(v1);
+    const float2 ab0 = t.qab[i0], ab1 = t.qab[i1];
+    const uint2 q0 = t.q16[i0], q1 = t.q16[i1];
+    const __half2 s = __floats2half2_rn(__fmaf_rn(v0, ab0.x, ab0.y), __fmaf_rn(v1, ab1.x, ab1.y));
+    uint32_t d[4] = {__byte_perm(q0.x, q1.x, 0x5410u), __byte_perm(q0.x, q1.x, 0x7632u),
+                     __byte_perm(q0.y, q1.y, 0x5410u), __byte_perm(q0.y, q1.y, 0x7632u)};
+    const __half2 *dh = reinterpret_cast<const __half2 *>(d);
+    __half2 z = h2mul(s, dh[3]);
+    z = h2add(dh[2], z);
+    z = h2mul(s, z);
+    z = h2add(dh[1], z);
+    z = h2mul(s, z);
+    z = h2add(dh[0], z);
+    const uint32_t top = __byte_perm(w0, w1, 0x7030u);
+    uint32_t zb = *reinterpret_cast<uint32_t *>(&z) ^ (top & 0x80008000u);
+    return *reinterpret_cast<__half2 *>(&zb);
+}
+
+// Two samples in bfloat16x2, same operation order.
+template <bool CLAMP>
+__device__ __forceinline__ uint32_t cubic_zbf16(const SmemTable &t, uint32_t w0, uint32_t w1, float v0, float v1) {
+    const int i0 = tab_index<CLAMP>(v0), i1 = tab_index<CLAMP>(v1);
+    const float2 ab0 = t.qab[i0], ab1 = t.qab[i1];
+    const uint2 q0 = t.qbf[i0], q1 = t.qbf[i1];
+    const uint32_t s = f32x2_to_bf16x2(__fmaf_rn(v0, ab0.x, ab0.y), __fmaf_rn(v1, ab1.x, ab1.y));
+    uint32_t z = b2mul(s, __byte_perm(q0.y, q1.y, 0x7632u));
+    z = b2add(__byte_perm(q0.y, q1.y, 0x5410u), z);
+    z = b2mul(s, z);
+    z = b2add(__byte_perm(q0.x, q1.x, 0x7632u), z);
+    z = b2mul(s, z);
+    z = b2add(__byte_perm(q0.x, q1.x, 0x5410u), z);
+    const uint32_t top = __byte_perm(w0, w1, 0x7030u);
     return z ^ (top & 0x80008000u);
 }
 

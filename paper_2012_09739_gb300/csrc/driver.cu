@@ -49,9 +49,10 @@ double nu_of(const Term &t) {
     const bool half = t.prec != MLMC_F32;   // binary16 and bfloat16 share the f16x2-style packing
     // 16-bit uniforms: half the Philox calls per two-way fine step; one more
     // uniform conversion per four-way step
-    const bool u16 = t.icdf == MLMC_ICDF_TABLE16;
-    if (t.four) return (u16 ? 1.08 : 1.0) * (half ? 2.15e-3 : 2.4e-3);
-    return (u16 ? 0.8 : 1.0) * (half ? (t.kahan ? 1.12e-3 : 1.0e-3) : (t.kahan ? 1.4e-3 : 1.25e-3));
+    // the cubic adds a Horner evaluation per normal
+    const bool u16 = t.icdf == MLMC_ICDF_TABLE16, cub = t.icdf == MLMC_ICDF_CUBIC;
+    if (t.four) return (u16 ? 1.08 : cub ? 1.12 : 1.0) * (half ? 2.15e-3 : 2.4e-3);
+    return (u16 ? 0.8 : cub ? 1.3 : 1.0) * (half ? (t.kahan ? 1.12e-3 : 1.0e-3) : (t.kahan ? 1.4e-3 : 1.25e-3));
 }
 
 }  // namespace
@@ -286,7 +287,8 @@ extern "C" mlmc_status mlmc_run(double eps, const mlmc_sde_params *params, const
     if (opts->estimator == 1) {
         if (opts->prec != MLMC_F32 && opts->prec != MLMC_F16 && opts->prec != MLMC_BF16 && opts->prec != -1)
             return fail(MLMC_EINVAL, "unknown precision");
-        if (opts->icdf != MLMC_ICDF_TABLE && opts->icdf != MLMC_ICDF_MLP && opts->icdf != MLMC_ICDF_TABLE16)
+        if (opts->icdf != MLMC_ICDF_TABLE && opts->icdf != MLMC_ICDF_MLP && opts->icdf != MLMC_ICDF_TABLE16 &&
+            opts->icdf != MLMC_ICDF_CUBIC)
             return fail(MLMC_EINVAL, "nested estimator needs approximate normals");
     }
     return run_impl(eps, params, opts, out);

@@ -35,9 +35,7 @@ struct LevelArgs {
     // mean = m.
     double drift_f, drift_c, diff, mean, x0;
     double K, disc;
-    const float2 *tab32;      // table in binary32, TAB_ENTRIES entries
-    const __half2 *tab16;     // table in binary16
-    const uint32_t *tabbf;    // table in bfloat16 (c0 in the low half)
+    const DevTables *tabs;    // piecewise-linear and cubic tables
     const MlpWeights *mlp;    // network (ICDF_MLP only)
     double2 *partials;        // (sum D, sum D^2) per warp chunk, or per block
     int chunk_partials;       // 1: one partial per chunk of 32 pairs (result independent of the grid)
@@ -102,6 +100,15 @@ __device__ __forceinline__ Pair<P> icdf_pair(const SmemTable &s, const MlpFrags 
         return Pair<P>::of2(exact_z(w0), exact_z(w1));
     } else if constexpr (ICDF == ICDF_TABLE) {
         return table_pair<P, false>(s, w0, w1, mirrored_v(w0), mirrored_v(w1));
+    } else if constexpr (ICDF == ICDF_CUBIC) {
+        const float v0 = mirrored_v(w0), v1 = mirrored_v(w1);
+        if constexpr (P == P_F32) {
+            return Pair<P>::of2(cubic_z32<false>(s, w0, v0), cubic_z32<false>(s, w1, v1));
+        } else if constexpr (P == P_F16) {
+            return Pair<P>{cubic_z16<false>(s, w0, w1, v0, v1)};
+        } else {
+            return Pair<P>{cubic_zbf16<false>(s, w0, w1, v0, v1)};
+        }
     } else if constexpr (ICDF == ICDF_TABLE16) {
         const uint32_t f0 = half16_bits<true>(w0), f1 = half16_bits<true>(w1);
         return table_pair<P, true>(s, f0, f1, mirrored_v16(f0), mirrored_v16(f1));
@@ -229,13 +236,11 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
     }
 }
 
-__device__ __forceinline__ void stage_table(SmemTable &tab, const float2 *t32, const __half2 *t16,
-                                            const uint32_t *tbf) {
-    for (int i = threadIdx.x; i < TAB_ENTRIES; i += blockDim.x) {
-        tab.c32[i] = t32[i];
-        tab.c16[i] = t16[i];
-        tab.cb16[i] = tbf[i];
-    }
+__device__ __forceinline__ void stage_table(SmemTable &tab, const DevTables *t) {
+    static_assert(sizeof(SmemTable) % 4 == 0, "table size");
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&t->e);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&tab);
+    for (int i = threadIdx.x; i < (int)(sizeof(SmemTable) / 4); i += blockDim.x) dst[i] = src[i];
 }
 
 // Warp sum in FP32.
@@ -264,8 +269,8 @@ template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
 __global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 1 : (MODE == MODE_FOUR ? 3 : 4)) level_kernel(const LevelArgs a) {
     __shared__ SmemTable tab;
     __shared__ double red[2][32];
-    if (ICDF == ICDF_TABLE || ICDF == ICDF_TABLE16) {
-        stage_table(tab, a.tab32, a.tab16, a.tabbf);
+    if (ICDF == ICDF_TABLE || ICDF == ICDF_TABLE16 || ICDF == ICDF_CUBIC) {
+        stage_table(tab, a.tabs);
         __syncthreads();
     }
     MlpFrags mlp;

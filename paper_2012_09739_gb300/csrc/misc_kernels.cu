@@ -8,18 +8,56 @@
 
 namespace mlmc {
 
-// ---------------------------------------------------------------- table
-// L2 (uniform-measure) linear fit of Phi^-1 on each interval [a, b) of
-// v = min(u, 1-u): I_k = [2^-(k+1), 2^-k) for k = 1..15, I_16 = (0, 2^-16)
-// (Sec. 2.1; the construction is deferred by the paper to its cited work,
-// this is the least-squares reading).  The moments have closed forms in
-// z = Phi^-1(v):
+// ---------------------------------------------------------------- tables
+// Piecewise-linear table: L2 (uniform-measure) linear fit of Phi^-1 on each
+// interval [a, b) of v = min(u, 1-u): I_k = [2^-(k+1), 2^-k) for k = 1..15,
+// I_16 = (0, 2^-16) (Sec. 2.1; the construction is deferred by the paper to
+// its cited work, this is the least-squares reading).  The moments have
+// closed forms in z = Phi^-1(v):
 //   int_a^b Phi^-1(v) dv   = phi(z_a) - phi(z_b)
 //   int_a^b v Phi^-1(v) dv = [ -phi(z) Phi(z) + Phi(sqrt(2) z) / (2 sqrt(pi)) ]_{z_a}^{z_b}
 // and the normal equations are solved in centred form.
-__global__ void build_table_kernel(double *t64, float2 *t32, __half2 *t16, uint32_t *tbf) {
-    __shared__ double c[32];
+//
+// Piecewise-cubic table (the high-fidelity approximation of Sec. 2.2): the
+// L2 cubic fit on the same intervals in the local variable s = A v - B in
+// [-1, 1] (A = 2^(k+2), B = 3 for k <= 15; A = 2^17, B = 1 for k = 16),
+// computed as the projection on the Legendre polynomials P0..P3 of s by
+// Gauss-Legendre quadrature (24 nodes per piece; I_16 is split into dyadic
+// pieces down to 2^-76, below which the moments change by < 1e-17), then
+// expanded in powers of s.
+constexpr int GL_N = 24;
+constexpr int CUBIC_TAIL_PIECES = 60;
+
+// Gauss-Legendre nodes and weights on [-1, 1]: node i is the root of P_n
+// found by Newton's method from cos(pi (i + 3/4) / (n + 1/2)), with the
+// three-term recurrence for P_n and P_n' = n (x P_n - P_{n-1}) / (x^2 - 1);
+// weight 2 / ((1 - x^2) P_n'(x)^2).  At most 100 iterations.
+__device__ void gauss_legendre_node(int i, double &x, double &w) {
+    x = cos(3.14159265358979323846 * (i + 0.75) / (GL_N + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = x;
+        for (int n = 2; n <= GL_N; ++n) {
+            const double p2 = ((2 * n - 1) * x * p1 - (n - 1) * p0) / n;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = GL_N * (x * p1 - p0) / (x * x - 1.0);
+        const double dx = p1 / dp;
+        x -= dx;
+        if (fabs(dx) < 1e-16) break;
+    }
+    w = 2.0 / ((1.0 - x * x) * dp * dp);
+}
+
+__device__ __forceinline__ int entry_interval(int entry) {     // 0-based interval of table entry E - 103
+    return min(126 - (103 + entry), 16) - 1;
+}
+
+__global__ void build_table_kernel(DevTables *out) {
+    __shared__ double lin[32], cub[64], glx[GL_N], glw[GL_N];
     const int i = threadIdx.x;
+    if (i < GL_N) gauss_legendre_node(i, glx[i], glw[i]);
     if (i < 16) {
         const int k = i + 1;
         const double b = ldexp(1.0, -k);
@@ -41,24 +79,59 @@ __global__ void build_table_kernel(double *t64, float2 *t32, __half2 *t16, uint3
         const double Svv = M0 * M0 * M0 / 12.0;
         const double c1 = (F1 - vbar * F0) / Svv;
         const double c0 = F0 / M0 - c1 * vbar;
-        c[2 * i] = c0;
-        c[2 * i + 1] = c1;
-        t64[2 * i] = c0;
-        t64[2 * i + 1] = c1;
+        lin[2 * i] = c0;
+        lin[2 * i + 1] = c1;
     }
     __syncthreads();
+    if (i < 16) {
+        const int k = i + 1;
+        const double A = k < 16 ? ldexp(1.0, k + 2) : ldexp(1.0, 17);
+        const double B = k < 16 ? 3.0 : 1.0;
+        const int pieces = k < 16 ? 1 : CUBIC_TAIL_PIECES;
+        double pr[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int j = 0; j < pieces; ++j) {
+            const double hi = k < 16 ? ldexp(1.0, -k) : ldexp(1.0, -16 - j);
+            const double lo = k < 16 ? ldexp(1.0, -k - 1) : ldexp(1.0, -17 - j);
+            const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+            for (int q = 0; q < GL_N; ++q) {
+                const double v = mid + half * glx[q];
+                const double s = A * v - B;
+                const double wf = half * glw[q] * A * normcdfinv(v);     // ds = A dv
+                pr[0] += wf;
+                pr[1] += wf * s;
+                pr[2] += wf * 0.5 * (3.0 * s * s - 1.0);
+                pr[3] += wf * 0.5 * (5.0 * s * s * s - 3.0 * s);
+            }
+        }
+        const double a0 = 0.5 * pr[0], a1 = 1.5 * pr[1], a2 = 2.5 * pr[2], a3 = 3.5 * pr[3];
+        cub[4 * i] = a0 - 0.5 * a2;
+        cub[4 * i + 1] = a1 - 1.5 * a3;
+        cub[4 * i + 2] = 1.5 * a2;
+        cub[4 * i + 3] = 2.5 * a3;
+    }
+    __syncthreads();
+    if (i < 32) out->lin64[i] = lin[i];
+    for (int j = i; j < 64; j += blockDim.x) out->cub64[j] = cub[j];
     if (i < TAB_ENTRIES) {
-        const int E = 103 + i;                       // biased exponent of v
-        const int interval = min(126 - E, 16) - 1;   // 0-based
-        const double c0 = c[2 * interval], c1 = c[2 * interval + 1];
-        t32[i] = make_float2(__double2float_rn(c0), __double2float_rn(c1));
-        t16[i] = __halves2half2(f64_to_f16(c0), f64_to_f16(c1));
-        tbf[i] = (uint32_t)f64_to_bf16(c0) | ((uint32_t)f64_to_bf16(c1) << 16);
+        const int iv = entry_interval(i);
+        const double c0 = lin[2 * iv], c1 = lin[2 * iv + 1];
+        out->e.c32[i] = make_float2(__double2float_rn(c0), __double2float_rn(c1));
+        out->e.c16[i] = __halves2half2(f64_to_f16(c0), f64_to_f16(c1));
+        out->e.cb16[i] = (uint32_t)f64_to_bf16(c0) | ((uint32_t)f64_to_bf16(c1) << 16);
+        const double *d = cub + 4 * iv;
+        out->e.q32[i] = make_float4(__double2float_rn(d[0]), __double2float_rn(d[1]), __double2float_rn(d[2]),
+                                    __double2float_rn(d[3]));
+        auto h16 = [](double x) { return (uint32_t)__half_as_ushort(f64_to_f16(x)); };
+        out->e.q16[i] = make_uint2(h16(d[0]) | (h16(d[1]) << 16), h16(d[2]) | (h16(d[3]) << 16));
+        out->e.qbf[i] = make_uint2((uint32_t)f64_to_bf16(d[0]) | ((uint32_t)f64_to_bf16(d[1]) << 16),
+                                   (uint32_t)f64_to_bf16(d[2]) | ((uint32_t)f64_to_bf16(d[3]) << 16));
+        const int k = iv + 1;
+        out->e.qab[i] = make_float2(k < 16 ? ldexpf(1.0f, k + 2) : 131072.0f, k < 16 ? -3.0f : -1.0f);
     }
 }
 
-cudaError_t launch_build_table(double *t64, float2 *t32, __half2 *t16, uint32_t *tbf, cudaStream_t s) {
-    build_table_kernel<<<1, 32, 0, s>>>(t64, t32, t16, tbf);
+cudaError_t launch_build_table(DevTables *out, cudaStream_t s) {
+    build_table_kernel<<<1, 32, 0, s>>>(out);
     return cudaGetLastError();
 }
 
@@ -139,10 +212,9 @@ cudaError_t launch_uniform_bulk(const uint32_t *w, float *u, size_t n, cudaStrea
 // values per round (two per lane), so the MLP's warp-cooperative evaluation
 // sees all 32 lanes.
 template <int P, int ICDF>
-__global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const float2 *tab32, const __half2 *tab16,
-                                 const uint32_t *tabbf, const MlpWeights *mlpw) {
+__global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const DevTables *tabs, const MlpWeights *mlpw) {
     __shared__ SmemTable tab;
-    stage_table(tab, tab32, tab16, tabbf);
+    stage_table(tab, tabs);
     __syncthreads();
     MlpFrags mlp;
     if (ICDF == ICDF_MLP) mlp.load(mlpw);
@@ -173,6 +245,16 @@ __global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const float2
             if (idx[h] >= n) continue;
             if (ICDF == ICDF_EXACT) {
                 r[h] = __uint_as_float(__float_as_uint(normcdfinvf(v[h])) ^ sg[h]);
+            } else if (ICDF == ICDF_CUBIC) {
+                if (P == P_F16) {
+                    static_cast<__half *>(z)[idx[h]] = __low2half(cubic_z16<true>(tab, sg[h], sg[h], v[h], v[h]));
+                    continue;
+                }
+                if (P == P_BF16) {
+                    static_cast<uint16_t *>(z)[idx[h]] = (uint16_t)cubic_zbf16<true>(tab, sg[h], sg[h], v[h], v[h]);
+                    continue;
+                }
+                r[h] = cubic_z32<true>(tab, sg[h], v[h]);
             } else if (ICDF == ICDF_TABLE || ICDF == ICDF_TABLE16) {
                 if (P == P_F16) {
                     const __half2 hz = table_z16<true>(tab, sg[h], sg[h], v[h], v[h]);
@@ -192,14 +274,15 @@ __global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const float2
     }
 }
 
-cudaError_t launch_icdf_bulk(const float *u, void *z, size_t n, int icdf, int prec, const float2 *tab32,
-                             const __half2 *tab16, const uint32_t *tabbf, const MlpWeights *mlp, cudaStream_t s) {
+cudaError_t launch_icdf_bulk(const float *u, void *z, size_t n, int icdf, int prec, const DevTables *tabs,
+                             const MlpWeights *mlp, cudaStream_t s) {
     const int g = bulk_grid(n);
-#define MLMC_ICDF_CASE(PP, II) icdf_bulk_kernel<PP, II><<<g, 256, 0, s>>>(u, z, n, tab32, tab16, tabbf, mlp)
+#define MLMC_ICDF_CASE(PP, II) icdf_bulk_kernel<PP, II><<<g, 256, 0, s>>>(u, z, n, tabs, mlp)
 #define MLMC_ICDF_PREC(PP)                                  \
     if (icdf == ICDF_EXACT) MLMC_ICDF_CASE(PP, ICDF_EXACT); \
     else if (icdf == ICDF_TABLE) MLMC_ICDF_CASE(PP, ICDF_TABLE); \
     else if (icdf == ICDF_TABLE16) MLMC_ICDF_CASE(PP, ICDF_TABLE16); \
+    else if (icdf == ICDF_CUBIC) MLMC_ICDF_CASE(PP, ICDF_CUBIC); \
     else MLMC_ICDF_CASE(PP, ICDF_MLP)
     if (prec == P_F32) {
         MLMC_ICDF_PREC(P_F32);

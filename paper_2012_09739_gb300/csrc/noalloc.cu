@@ -24,11 +24,8 @@ constexpr int NOALLOC_MAX_BLOCKS = 4096;
 constexpr uint64_t NOALLOC_MAX_N = (uint64_t)NOALLOC_MAX_BLOCKS * NOALLOC_BLOCK * 2;
 
 static __device__ __align__(256) double2 g_noalloc_partials[NOALLOC_MAX_BLOCKS];
-// Private table (same construction as the per-device table of the other entry points).
-static __device__ __align__(256) double g_noalloc_tab64[32];
-static __device__ __align__(256) float2 g_noalloc_tab32[TAB_ENTRIES];
-static __device__ __align__(256) __half2 g_noalloc_tab16[TAB_ENTRIES];
-static __device__ __align__(256) uint32_t g_noalloc_tabbf[TAB_ENTRIES];
+// Private tables (same construction as the per-device tables of the other entry points).
+static __device__ __align__(256) DevTables g_noalloc_tabs;
 
 // Device addresses of the arrays above, looked up once per device with that
 // device current.  In host code the array names are host-side stand-ins, not
@@ -36,10 +33,7 @@ static __device__ __align__(256) uint32_t g_noalloc_tabbf[TAB_ENTRIES];
 struct NoallocState {
     bool ready = false;
     double2 *partials = nullptr;
-    double *tab64 = nullptr;
-    float2 *tab32 = nullptr;
-    __half2 *tab16 = nullptr;
-    uint32_t *tabbf = nullptr;
+    DevTables *tabs = nullptr;
 };
 static std::mutex g_noalloc_mu;
 static NoallocState g_noalloc[MAX_DEVICES];
@@ -54,15 +48,9 @@ static mlmc_status noalloc_setup(int dev, cudaStream_t s, NoallocState **out) {
         cudaError_t e;
         if ((e = cudaGetSymbolAddress((void **)&st.partials, g_noalloc_partials)) != cudaSuccess)
             return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-        if ((e = cudaGetSymbolAddress((void **)&st.tab64, g_noalloc_tab64)) != cudaSuccess)
+        if ((e = cudaGetSymbolAddress((void **)&st.tabs, g_noalloc_tabs)) != cudaSuccess)
             return cuda_fail(e, "cudaGetSymbolAddress(table)");
-        if ((e = cudaGetSymbolAddress((void **)&st.tab32, g_noalloc_tab32)) != cudaSuccess)
-            return cuda_fail(e, "cudaGetSymbolAddress(table)");
-        if ((e = cudaGetSymbolAddress((void **)&st.tab16, g_noalloc_tab16)) != cudaSuccess)
-            return cuda_fail(e, "cudaGetSymbolAddress(table)");
-        if ((e = cudaGetSymbolAddress((void **)&st.tabbf, g_noalloc_tabbf)) != cudaSuccess)
-            return cuda_fail(e, "cudaGetSymbolAddress(table)");
-        if ((e = launch_build_table(st.tab64, st.tab32, st.tab16, st.tabbf, s)) != cudaSuccess)
+        if ((e = launch_build_table(st.tabs, s)) != cudaSuccess)
             return cuda_fail(e, "build_table");
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "build_table");
         st.ready = true;
@@ -98,10 +86,7 @@ extern "C" mlmc_status mlmc_level_noalloc(int four, int l, uint64_t N, int prec,
     if (!fn) return fail(MLMC_EINVAL, "no kernel for this variant");
     // make_level_args only reads the table pointers from the state it is given
     DeviceState view;
-    view.tab64 = na->tab64;
-    view.tab32 = na->tab32;
-    view.tab16 = na->tab16;
-    view.tabbf = na->tabbf;
+    view.tabs = na->tabs;
     LevelArgs a = make_level_args(view, four ? 1 : 0, l, N, icdf, params, seed, path_offset, 0);
     a.partials = na->partials;
     a.paths_out = nullptr;

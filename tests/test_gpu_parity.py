@@ -407,3 +407,77 @@ def test_full_size_level12_table16_sampled(pl_table):
     ref = O.twoway_paths(l, idx, _bar_variant(M.MLMC_F16, True, O.RV_TABLE16), _orc_sde(params), SEED,
                          _kind_tag(0, 1, l), table=pl_table)
     assert np.array_equal(got[idx], ref)
+
+
+# ------------------------------------------------------------------ piecewise cubic (CUBIC)
+
+
+@pytest.fixture(scope="module")
+def cubic_table():
+    from oracle import table
+    return table.build_cubic_table()
+
+
+def test_cubic_table_matches_oracle(cubic_table):
+    _dev()
+    d64, d32, d16, dbf = M.mlmc_icdf_cubic()
+    assert np.allclose(d64, cubic_table, rtol=1e-11, atol=1e-13)
+    assert np.array_equal(d32.astype(np.float64), O.round_bits(cubic_table, O.F32).reshape(16, 4))
+    assert np.array_equal(d16.view(np.float16).astype(np.float64), O.round_bits(cubic_table, O.F16).reshape(16, 4))
+    bf = (dbf.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    assert np.array_equal(bf, O.round_bits(cubic_table, O.BF16).reshape(16, 4))
+
+
+@pytest.mark.parametrize("prec", [M.MLMC_F32, M.MLMC_F16, M.MLMC_BF16])
+def test_approx_icdf_cubic_bitexact(prec, pl_table, cubic_table):
+    dev = _dev()
+    rng = np.random.default_rng(6)
+    u = np.concatenate([(2 * rng.integers(0, 1 << 23, 200000) + 1) * 2.0 ** -24,
+                        [2.0 ** -24, 1 - 2.0 ** -24, 0.5 - 2.0 ** -24, 0.5 + 2.0 ** -24, 0.25 + 2.0 ** -24,
+                         0.25 - 2.0 ** -24, 2.0 ** -16 + 2.0 ** -24, 2.0 ** -16 - 2.0 ** -24]]).astype(np.float32)
+    z = torch.empty(u.size, dtype=torch.float32 if prec == M.MLMC_F32 else torch.int16, device=dev)
+    M.approx_icdf(torch.from_numpy(u).to(dev), z, M.MLMC_ICDF_CUBIC, prec)
+    torch.cuda.synchronize()
+    ref = O.approx_icdf(u.astype(np.float64), O.RV_CUBIC, prec=_OPREC[prec], table=pl_table, cubic=cubic_table)
+    got = z.cpu().numpy().view(np.float16).astype(np.float64) if prec == M.MLMC_F16 else _z_host(z, prec)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("prec", [M.MLMC_F16, M.MLMC_F32, M.MLMC_BF16])
+@pytest.mark.parametrize("kahan", [True, False])
+@pytest.mark.parametrize("l", [0, 1, 2, 5, 9])
+@pytest.mark.parametrize("sde", ["gbm_call", "ou_x"])
+def test_twoway_cubic_paths_bitexact(prec, kahan, l, sde, pl_table, cubic_table):
+    params = M.sde_params(**(GBM_CALL if sde == "gbm_call" else OU_X))
+    N = 1537
+    got = gpu_paths(0, l, N, prec, kahan, M.MLMC_ICDF_CUBIC, params, offset=31)
+    ref = O.twoway_paths(l, np.arange(31, 31 + N), _bar_variant(prec, kahan, O.RV_CUBIC), _orc_sde(params), SEED,
+                         _kind_tag(0, M.MLMC_ICDF_CUBIC, l), table=pl_table, cubic=cubic_table)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("prec", [M.MLMC_F16, M.MLMC_BF16, M.MLMC_F32])
+@pytest.mark.parametrize("kahan", [True, False])
+@pytest.mark.parametrize("l", [0, 3, 8])
+def test_fourway_cubic_paths(prec, kahan, l, pl_table, cubic_table):
+    params = M.sde_params(**GBM_CALL)
+    N = 1025
+    got = gpu_paths(1, l, N, prec, kahan, M.MLMC_ICDF_CUBIC, params)
+    ref = O.fourway_paths(l, np.arange(N), O.variant(), _bar_variant(prec, kahan, O.RV_CUBIC), _orc_sde(params),
+                          SEED, _kind_tag(1, M.MLMC_ICDF_CUBIC, l), table=pl_table, cubic=cubic_table)
+    assert np.array_equal(got[:, 2:4], ref[:, 2:4])
+    scale = np.maximum(1.0, np.abs(ref[:, 0]))
+    assert np.all(np.abs(got[:, 0:2] - ref[:, 0:2]) <= TOL32 * scale[:, None])
+
+
+def test_cubic_level_sums_match_oracle(pl_table, cubic_table):
+    params = M.sde_params(**GBM_CALL)
+    for four, l, N in ((0, 6, 30001), (1, 5, 20001)):
+        fn = M.mlmc_nested_level if four else M.mlmc_level
+        s = fn(l, N, M.MLMC_F16, True, M.MLMC_ICDF_CUBIC, params, SEED)
+        bar = _bar_variant(M.MLMC_F16, True, O.RV_CUBIC)
+        o1, o2 = O.level_sums(l, N, 0, O.variant() if four else bar, _orc_sde(params), SEED,
+                              _kind_tag(four, M.MLMC_ICDF_CUBIC, l), table=pl_table, cubic=cubic_table,
+                              four=bool(four), var2=bar, nthreads=4)
+        assert abs(s.s1 - o1) <= 2e-5 * (abs(o1) + math.sqrt(o2 * N)), (four, s.s1, o1)
+        assert abs(s.s2 - o2) <= 1e-5 * o2

@@ -152,3 +152,55 @@ def test_bf16_half_kahan_gap(pair_errors):
     assert abs(gap - _pv()["kahan_half_bf16_log2_gap"]) < 1.0, gap
     # and without Kahan the same ratio holds level by level
     assert abs(np.mean(pair_errors["f16"] - pair_errors["bf16"]) - _pv()["kahan_half_bf16_log2_gap"]) < 1.0
+
+
+@pytest.fixture(scope="module")
+def fig2_curves():
+    """log2 Var(X^_N - X-_N) of Fig. 2 with real arithmetic: X^ the FP32 +
+    Kahan path with exact normals, X- the path with the piecewise-cubic
+    normals in binary16 / bfloat16 / binary32, both driven by the same
+    uniforms (the four-way per-sample outputs), N = 2^18 samples per level."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_X, p0=0.05, p1=0.2)
+    N = 1 << 18
+    dev = torch.device("cuda:0")
+    out = {}
+    for key, prec, kahan in (("f16", M.MLMC_F16, False), ("bf16", M.MLMC_BF16, False), ("f32", M.MLMC_F32, False),
+                             ("f16k", M.MLMC_F16, True), ("bf16k", M.MLMC_BF16, True), ("f32k", M.MLMC_F32, True)):
+        row = []
+        for l in range(2, 15):
+            buf = torch.empty(N * 5, dtype=torch.float32, device=dev)
+            M.mlmc_level_paths(1, l, N, prec, kahan, M.MLMC_ICDF_CUBIC, p, 1234, 0, buf)
+            b = buf.view(N, 5).double()
+            row.append(math.log2(torch.var(b[:, 0] - b[:, 2]).item()))
+        out[key] = np.array(row)
+    return out
+
+
+def test_fig2_half_and_bf16_grow_single_flat(fig2_curves):
+    """Sec. 2.2, Fig. 2: without compensation binary16 grows like N rho^2
+    (slope 1 in l), bfloat16 sits about 2^6 above it, and binary32 is O(1):
+    its variance is the cubic's approximation error, sigma^2 T E|Z - Z~|^2."""
+    ls = np.arange(2, 15)
+    assert abs(np.polyfit(ls, fig2_curves["f16"], 1)[0] - 1.0) < 0.15
+    assert abs(np.polyfit(ls, fig2_curves["bf16"], 1)[0] - 1.0) < 0.2
+    assert np.all(np.abs(fig2_curves["bf16"] - fig2_curves["f16"] - 6.0) < 1.0)
+    assert abs(np.polyfit(ls, fig2_curves["f32"], 1)[0]) < 0.15
+    approx = math.log2(0.04 * 7.6923e-8 * 1.105)
+    assert np.all(np.abs(fig2_curves["f32"] - approx) < 1.5)
+
+
+def test_fig2_kahan_flat_with_2pow6_gap(fig2_curves):
+    """Sec. 2.3: with Kahan all precisions are O(1); binary16 sits about
+    2^-6 below bfloat16; binary32 stays at the approximation error.  The
+    compensated sum's error bound is (2 rho + O(N rho^2)) sum |x|: for
+    bfloat16 (rho = 2^-8) the second term reaches the first near
+    N = 2^8..2^10 steps, and the curve rises beyond l = 11, so its
+    flatness is checked over l = 2..10."""
+    ls = np.arange(2, 15)
+    for key in ("f16k", "f32k"):
+        assert abs(np.polyfit(ls, fig2_curves[key], 1)[0]) < 0.2, key
+    assert abs(np.polyfit(ls[:9], fig2_curves["bf16k"][:9], 1)[0]) < 0.2
+    assert abs(np.mean(fig2_curves["f16k"][:9] - fig2_curves["bf16k"][:9]) + 6.0) < 1.0
+    assert np.all(np.abs(fig2_curves["f32k"] - fig2_curves["f32"]) < 0.5)
