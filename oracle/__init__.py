@@ -63,19 +63,20 @@ def build(force: bool = False) -> str:
 
 class SDE(ctypes.Structure):
     """Mirror of orc_sde: GBM (p0, p1) = (mu, sigma); OU (p0, p1, p2) =
-    (theta, m, s).  Call payoff disc * max(X_T - K, 0)."""
+    (theta, m, s).  Call payoff disc * max(X_T - K, 0).  scheme 0: Euler,
+    1: Milstein."""
     _fields_ = [("sde", ctypes.c_int), ("payoff", ctypes.c_int),
                 ("p0", ctypes.c_double), ("p1", ctypes.c_double), ("p2", ctypes.c_double),
                 ("x0", ctypes.c_double), ("T", ctypes.c_double), ("K", ctypes.c_double),
-                ("disc", ctypes.c_double)]
+                ("disc", ctypes.c_double), ("scheme", ctypes.c_int)]
 
 
-def gbm(mu=0.05, sigma=0.2, x0=1.0, T=1.0, payoff=PAYOFF_X, K=1.0, disc=None) -> SDE:
+def gbm(mu=0.05, sigma=0.2, x0=1.0, T=1.0, payoff=PAYOFF_X, K=1.0, disc=None, scheme=0) -> SDE:
     """GBM dX = mu X dt + sigma X dW (Sec. 2.2 experiments); call payoff
-    discounted at r = mu unless disc is given."""
+    discounted at r = mu unless disc is given; scheme 1: Milstein."""
     if disc is None:
         disc = float(np.exp(-mu * T))
-    return SDE(GBM, payoff, mu, sigma, 0.0, x0, T, K, disc)
+    return SDE(GBM, payoff, mu, sigma, 0.0, x0, T, K, disc, scheme)
 
 
 def ou(theta, m, s, x0=1.0, T=1.0, payoff=PAYOFF_X, K=0.0, disc=1.0) -> SDE:

@@ -113,3 +113,98 @@ def weak_converged(Y, eps, alpha=1.0):
     r = 2.0 ** alpha
     bias = max(abs(Y[-1]), abs(Y[-2]) / r, abs(Y[-3]) / (r * r)) / (r - 1.0)
     return bias <= eps / math.sqrt(2.0)
+
+
+# ---------------------------------------------------------------- GBM step polynomials
+# Per coarse step (two fine steps), each of the four coupled paths multiplies
+# X by a polynomial in the step's normals: variables (Z1, W1, Z2, W2), with
+# Z the exact normal and W = Z~ the approximate one of the same uniform.
+#   fine (Euler):     (1 + mu d + s Z1)(1 + mu d + s Z2),  s = sigma sqrt(d)
+#   fine (Milstein):  each factor + m (Z^2 - 1),           m = sigma^2 d / 2
+#   coarse (Euler):   1 + 2 mu d + s (Z1 + Z2)
+#   coarse (Milstein): + m ((Z1 + Z2)^2 - 2)
+# and the same with W for the approximate paths.  Expectations use the
+# joint moments mom(a, b) = E[Z^a W^b] of one step, steps being independent.
+
+def _pmul(p, q):
+    out = {}
+    for ep, cp in p.items():
+        for eq, cq in q.items():
+            e = tuple(x + y for x, y in zip(ep, eq))
+            out[e] = out.get(e, 0.0) + cp * cq
+    return out
+
+
+def _unit(i, power=1):
+    e = [0, 0, 0, 0]
+    e[i] = power
+    return tuple(e)
+
+
+def _step_polys(mu, sigma, delta, milstein):
+    s = sigma * math.sqrt(delta)
+    m = 0.5 * sigma * sigma * delta if milstein else 0.0
+    zero = (0, 0, 0, 0)
+
+    def fine_factor(i):
+        return {zero: 1.0 + mu * delta - m, _unit(i): s, _unit(i, 2): m}
+
+    def coarse(i, j):
+        ij = tuple(a + b for a, b in zip(_unit(i), _unit(j)))
+        return {zero: 1.0 + 2.0 * mu * delta - 2.0 * m, _unit(i): s, _unit(j): s,
+                _unit(i, 2): m, _unit(j, 2): m, ij: 2.0 * m}
+
+    return {"hf": _pmul(fine_factor(0), fine_factor(2)), "hc": coarse(0, 2),
+            "bf": _pmul(fine_factor(1), fine_factor(3)), "bc": coarse(1, 3)}
+
+
+def _expect(p, mom):
+    return sum(c * mom(e[0], e[1]) * mom(e[2], e[3]) for e, c in p.items())
+
+
+def gaussian_moment(a, b=0):
+    """E[Z^(a+b)] for W = Z (exact normals in both slots)."""
+    k = a + b
+    return 0.0 if k % 2 else float(np.prod(np.arange(k - 1, 0, -2))) if k else 1.0
+
+
+def gbm_level_moments(l, mom=gaussian_moment, four=False, milstein=False, mu=0.05, sigma=0.2, x0=1.0, T=1.0):
+    """(E D, Var D) of the level-l difference for GBM with P(X) = X in exact
+    arithmetic: two-way D = X_f - X_c on the approximate normals W (W = Z by
+    default), or four-way D = X^_f - X^_c - X-_f + X-_c (hat on Z, bar on
+    W); Euler or Milstein.  mom(a, b) = E[Z^a W^b] for one step."""
+    if l == 0:
+        m = 0.5 * sigma * sigma * T if milstein else 0.0
+        s = sigma * math.sqrt(T)
+        zero = (0, 0, 0, 0)
+        h = {zero: 1.0 + mu * T - m, _unit(0): s, _unit(0, 2): m}
+        b = {zero: 1.0 + mu * T - m, _unit(1): s, _unit(1, 2): m}
+        if four:
+            d = dict(h)
+            for e, c in b.items():
+                d[e] = d.get(e, 0.0) - c
+        else:
+            d = b
+        mean = x0 * _expect(d, mom)
+        return mean, x0 * x0 * _expect(_pmul(d, d), mom) - mean * mean
+    delta = T * 2.0 ** -l
+    n = 2 ** (l - 1)
+    P = _step_polys(mu, sigma, delta, milstein)
+    sign = {"hf": 1, "hc": -1, "bf": -1, "bc": 1} if four else {"bf": 1, "bc": -1}
+    names = list(sign)
+    mean = x0 * sum(sign[p] * _expect(P[p], mom) ** n for p in names)
+    second = 0.0
+    for i, p in enumerate(names):
+        for q in names[i:]:
+            mult = 1 if p == q else 2
+            second += mult * sign[p] * sign[q] * _expect(_pmul(P[p], P[q]), mom) ** n
+    return mean, x0 * x0 * second - mean * mean
+
+
+def grid_joint_moments(z, w, max_order=4):
+    """mom(a, b) = mean of z^a w^b over a grid (the uniform's law)."""
+    table = {}
+    for a in range(max_order + 1):
+        for b in range(max_order + 1 - a):
+            table[(a, b)] = float(np.mean(z ** a * w ** b))
+    return lambda a, b: table[(a, b)]

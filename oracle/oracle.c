@@ -312,6 +312,7 @@ typedef struct {
     int sde, payoff;
     double p0, p1, p2;      /* GBM: mu, sigma, -;  OU: theta, m, s */
     double x0, T, K, disc;  /* call payoff: disc * max(X_T - K, 0) */
+    int scheme;             /* 0: Euler-Maruyama; 1: Milstein (GBM; OU's b' = 0 makes it Euler) */
 } orc_sde;
 
 /* Per-level constants of one path, each rounded once to the working
@@ -320,16 +321,20 @@ typedef struct {
  * s sqrt(delta). */
 typedef struct {
     rmode m;
-    int kahan, sde;
+    int kahan, sde, milstein;
     double drift, diff, mean;   /* drift: mu*delta or theta*delta; diff: sigma*sqrt(delta_f) or s*sqrt(delta_f) */
+    double mil, mconst;         /* Milstein: R(sigma^2 delta_f / 2), and 1 (fine) or 2 (coarse) */
     double X, c;                /* state and Kahan compensation */
 } path_state;
 
-static void path_init(path_state *s, const orc_sde *p, int prec, int pbits, int kahan, double delta, double sqrt_delta_f)
+/* delta = delta_f (fine path) or 2 delta_f (coarse path, coarse = 1). */
+static void path_init(path_state *s, const orc_sde *p, int prec, int pbits, int kahan, double delta, double sqrt_delta_f,
+                      int coarse)
 {
     s->m = mode_of(prec, pbits);
     s->kahan = kahan;
     s->sde = p->sde;
+    s->milstein = p->sde == ORC_GBM && p->scheme == 1;
     s->drift = round_p(p->p0 * delta, &s->m);
     s->diff = round_p(p->p1 * sqrt_delta_f, &s->m);
     s->mean = 0.0;
@@ -337,14 +342,21 @@ static void path_init(path_state *s, const orc_sde *p, int prec, int pbits, int 
         s->diff = round_p(p->p2 * sqrt_delta_f, &s->m);
         s->mean = round_p(p->p1, &s->m);
     }
+    /* the coarse step (delta = 2 delta_f) uses Z1 + Z2 with the fine
+     * sqrt(delta_f): (dW_c)^2 - delta_c = delta_f ((Z1 + Z2)^2 - 2) */
+    s->mil = round_p(0.5 * p->p1 * p->p1 * (coarse ? 0.5 * delta : delta), &s->m);
+    s->mconst = coarse ? 2.0 : 1.0;
     s->X = round_p(p->x0, &s->m);
     s->c = 0.0;
 }
 
-/* One step X <- X (+) (A (+) B) (Sec. 2.2), with Kahan (Algorithm 1) if on.
- * dW is the normal increment multiplier: Z for a fine step, Z1 (+) Z2 for
- * a coarse step (the coarse Wiener increment is the pairwise sum of the
- * two fine ones, Sec. 3). */
+/* One step X <- X (+) (A (+) B), or with the Milstein term of GBM
+ * X <- X (+) ((A (+) B) (+) M), M = (mil (x) X) (x) ((z (x) z) (-) mconst),
+ * i.e. 1/2 b b' ((dW)^2 - delta) with b = sigma X (the scheme the paper
+ * names in its conclusions; order of operations a reading).  Kahan
+ * (Algorithm 1) on the outer addition if on.  dW is the normal increment
+ * multiplier: Z for a fine step, Z1 (+) Z2 for a coarse step (the coarse
+ * Wiener increment is the pairwise sum of the two fine ones, Sec. 3). */
 static void path_step(path_state *s, double z)
 {
     const rmode *m = &s->m;
@@ -357,6 +369,10 @@ static void path_step(path_state *s, double z)
         B = round_p(s->diff * z, m);
     }
     double inc = round_p(A + B, m);
+    if (s->milstein) {
+        double w = round_p(round_p(z * z, m) - s->mconst, m);
+        inc = round_p(inc + round_p(round_p(s->mil * s->X, m) * w, m), m);
+    }
     if (s->kahan) {
         double y = round_p(inc - s->c, m);
         double t = round_p(s->X + y, m);
@@ -412,8 +428,8 @@ static void twoway_one(int l, uint64_t path, const orc_variant *v, const orc_sde
     double delta_f = ldexp(p->T, -l);
     double sq = sqrt(delta_f);
     path_state fine, coarse;
-    path_init(&fine, p, v->prec, v->pbits, v->kahan, delta_f, sq);
-    path_init(&coarse, p, v->prec, v->pbits, v->kahan, 2.0 * delta_f, sq);
+    path_init(&fine, p, v->prec, v->pbits, v->kahan, delta_f, sq, 0);
+    path_init(&coarse, p, v->prec, v->pbits, v->kahan, 2.0 * delta_f, sq, 1);
     double zprev = 0.0, u[4];
     uint32_t w[4];
     for (int64_t n = 0; n < nf; ++n) {
@@ -449,10 +465,10 @@ static void fourway_one(int l, uint64_t path, const orc_variant *hat, const orc_
     double delta_f = ldexp(p->T, -l);
     double sq = sqrt(delta_f);
     path_state hf, hc, bf, bc;
-    path_init(&hf, p, hat->prec, hat->pbits, hat->kahan, delta_f, sq);
-    path_init(&hc, p, hat->prec, hat->pbits, hat->kahan, 2.0 * delta_f, sq);
-    path_init(&bf, p, bar->prec, bar->pbits, bar->kahan, delta_f, sq);
-    path_init(&bc, p, bar->prec, bar->pbits, bar->kahan, 2.0 * delta_f, sq);
+    path_init(&hf, p, hat->prec, hat->pbits, hat->kahan, delta_f, sq, 0);
+    path_init(&hc, p, hat->prec, hat->pbits, hat->kahan, 2.0 * delta_f, sq, 1);
+    path_init(&bf, p, bar->prec, bar->pbits, bar->kahan, delta_f, sq, 0);
+    path_init(&bc, p, bar->prec, bar->pbits, bar->kahan, 2.0 * delta_f, sq, 1);
     double zh_prev = 0.0, zb_prev = 0.0, u[4];
     for (int64_t n = 0; n < nf; ++n) {
         if ((n & 3) == 0) draw4(path, (uint32_t)(n >> 2), tag, seed, u);
@@ -537,8 +553,8 @@ void orc_rounding_pairs(int l, uint64_t N, uint64_t path_offset, const int *var,
     double sq = sqrt(delta_f);
     for (int64_t i = 0; i < (int64_t)N; ++i) {
         path_state hi, lo;
-        path_init(&hi, p, ORC_F64, 53, 0, delta_f, sq);
-        path_init(&lo, p, v.prec, v.pbits, v.kahan, delta_f, sq);
+        path_init(&hi, p, ORC_F64, 53, 0, delta_f, sq, 0);
+        path_init(&lo, p, v.prec, v.pbits, v.kahan, delta_f, sq, 0);
         double u[4];
         rmode exact = mode_of(ORC_F64, 0);
         for (int64_t n = 0; n < nf; ++n) {
