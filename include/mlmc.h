@@ -84,6 +84,15 @@ typedef enum {
     MLMC_ICDF_CUBIC = 4
 } mlmc_icdf;
 
+/* Time-stepping scheme.  EULER: Euler-Maruyama.  MILSTEIN: adds the term
+ * b b' ((dW)^2 - delta) / 2 (the scheme of order 1 strong convergence the
+ * paper's conclusions name); for GBM each fine step adds
+ * (mil (x) X) (x) ((Z (x) Z) (-) 1) with mil = R(sigma^2 delta_f / 2), the
+ * coarse step (mil (x) X) (x) ((Zc (x) Zc) (-) 2) with Zc = Z1 (+) Z2, added
+ * after A (+) B: X <- X (+) ((A (+) B) (+) M).  For OU b' = 0 and the two
+ * schemes coincide. */
+typedef enum { MLMC_EULER = 0, MLMC_MILSTEIN = 1 } mlmc_scheme;
+
 /* SDE dX = a(X) dt + b(X) dW on [0, T], X_0 = x0.
  *   GBM: a = p0 X, b = p1 X            (mu = p0, sigma = p1)
  *   OU:  a = p0 (p1 - X), b = p2       (theta = p0, m = p1, s = p2)
@@ -93,6 +102,8 @@ typedef struct {
     int32_t payoff;   /* mlmc_payoff */
     double p0, p1, p2;
     double x0, T, K, disc;
+    int32_t scheme;   /* mlmc_scheme */
+    int32_t reserved; /* must be 0 */
 } mlmc_sde_params;
 
 /* Sums of one level estimator: s1 = sum D, s2 = sum D^2 over n samples

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmlmc.so")
 # enums (include/mlmc.h)
 MLMC_OK, MLMC_EINVAL, MLMC_ECUDA, MLMC_ETIMEOUT, MLMC_ENOMEM, MLMC_ENOTCONV, MLMC_ENOTREADY = range(7)
 MLMC_GBM, MLMC_OU = 0, 1
+MLMC_EULER, MLMC_MILSTEIN = 0, 1
 MLMC_PAYOFF_X, MLMC_PAYOFF_CALL = 0, 1
 MLMC_F32, MLMC_F16, MLMC_BF16 = 0, 1, 2
 MLMC_ICDF_EXACT, MLMC_ICDF_TABLE, MLMC_ICDF_MLP, MLMC_ICDF_TABLE16, MLMC_ICDF_CUBIC = 0, 1, 2, 3, 4
@@ -35,7 +36,8 @@ class MlmcError(RuntimeError):
 class mlmc_sde_params(ctypes.Structure):
     _fields_ = [("sde", ctypes.c_int32), ("payoff", ctypes.c_int32),
                 ("p0", ctypes.c_double), ("p1", ctypes.c_double), ("p2", ctypes.c_double),
-                ("x0", ctypes.c_double), ("T", ctypes.c_double), ("K", ctypes.c_double), ("disc", ctypes.c_double)]
+                ("x0", ctypes.c_double), ("T", ctypes.c_double), ("K", ctypes.c_double), ("disc", ctypes.c_double),
+                ("scheme", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class mlmc_sums(ctypes.Structure):
@@ -144,13 +146,14 @@ def _dptr(t):
 
 
 def sde_params(sde=MLMC_GBM, payoff=MLMC_PAYOFF_X, p0=0.05, p1=0.2, p2=0.0, x0=1.0, T=1.0, K=1.0,
-               disc=None) -> mlmc_sde_params:
+               disc=None, scheme=0) -> mlmc_sde_params:
     """GBM: (p0, p1) = (mu, sigma); OU: (p0, p1, p2) = (theta, m, s).  The call
-    is discounted by disc (default e^{-p0 T} for GBM, 1 for OU)."""
+    is discounted by disc (default e^{-p0 T} for GBM, 1 for OU).  scheme:
+    MLMC_EULER or MLMC_MILSTEIN."""
     import math
     if disc is None:
         disc = math.exp(-p0 * T) if sde == MLMC_GBM else 1.0
-    return mlmc_sde_params(sde, payoff, p0, p1, p2, x0, T, K, disc)
+    return mlmc_sde_params(sde, payoff, p0, p1, p2, x0, T, K, disc, scheme, 0)
 
 
 def mlmc_level(l, N, prec, kahan, icdf, params, seed, path_offset=0, stream=None) -> mlmc_sums:

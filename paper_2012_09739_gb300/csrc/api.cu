@@ -86,6 +86,8 @@ mlmc_status check_params(const mlmc_sde_params *p) {
     if (!p) return fail(MLMC_EINVAL, "params is NULL");
     if (p->sde != MLMC_GBM && p->sde != MLMC_OU) return fail(MLMC_EINVAL, "unknown sde %d", p->sde);
     if (p->payoff != MLMC_PAYOFF_X && p->payoff != MLMC_PAYOFF_CALL) return fail(MLMC_EINVAL, "unknown payoff");
+    if (p->scheme != MLMC_EULER && p->scheme != MLMC_MILSTEIN) return fail(MLMC_EINVAL, "unknown scheme %d", p->scheme);
+    if (p->reserved != 0) return fail(MLMC_EINVAL, "reserved field must be 0");
     const double v[] = {p->p0, p->p1, p->p2, p->x0, p->T, p->K, p->disc};
     for (double x : v)
         if (!isfinite(x)) return fail(MLMC_EINVAL, "non-finite SDE parameter");
@@ -116,7 +118,7 @@ LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int
     a.l = l;
     a.payoff = p->payoff;
     a.mode = four ? MODE_FOUR : MODE_TWO;
-    a.sde = p->sde == MLMC_OU ? SDE_OU : SDE_GBM;
+    a.sde = kernel_sde(p);
     a.N = N;
     a.npairs = (N + 1) / 2;
     a.path_offset = path_offset;
@@ -129,6 +131,7 @@ LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int
     if (p->sde == MLMC_GBM) {
         a.diff = p->p1 * sq;
         a.mean = 0.0;
+        a.mil = 0.5 * p->p1 * p->p1 * delta_f;
     } else {
         a.diff = p->p2 * sq;
         a.mean = p->p1;
@@ -139,6 +142,12 @@ LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int
     a.tabs = d.tabs;
     a.mlp = d.mlp;
     return a;
+}
+
+// Kernel SDE kind: Milstein only changes GBM (b' = 0 for OU).
+int kernel_sde(const mlmc_sde_params *p) {
+    if (p->sde == MLMC_OU) return SDE_OU;
+    return p->scheme == MLMC_MILSTEIN ? SDE_GBM_MIL : SDE_GBM;
 }
 
 LevelKernelFn pick_level_kernel(int four, int prec, int kahan, int icdf, int sde) {
@@ -177,7 +186,7 @@ constexpr uint64_t MAX_CHUNK_PARTIALS = 1ull << 22;
 mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int prec, int kahan, int icdf,
                           const mlmc_sde_params *p, uint64_t seed, uint64_t path_offset, uint32_t set_id,
                           double *sums_dev, float *paths_dev, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
-    LevelKernelFn fn = pick_level_kernel(four, prec, kahan, icdf, p->sde);
+    LevelKernelFn fn = pick_level_kernel(four, prec, kahan, icdf, kernel_sde(p));
     if (!fn) return fail(MLMC_EINVAL, "no kernel for this variant");
     LevelArgs a = make_level_args(d, four, l, N, icdf, p, seed, path_offset, set_id);
     const LaunchCfg cfg = level_launch_cfg(d, fn, a.npairs);

@@ -48,10 +48,12 @@ __global__ void __launch_bounds__(256) batch_kernel(const LevelArgs *items, cons
             float d0, d1, o0[5], o1[5];
             if (a.mode == MODE_TWO) {
                 if (a.sde == SDE_GBM) simulate_pair<MODE_TWO, P, KAHAN, ICDF, SDE_GBM>(a, tab, mlp, g, d0, d1, o0, o1);
-                else simulate_pair<MODE_TWO, P, KAHAN, ICDF, SDE_OU>(a, tab, mlp, g, d0, d1, o0, o1);
+                else if (a.sde == SDE_OU) simulate_pair<MODE_TWO, P, KAHAN, ICDF, SDE_OU>(a, tab, mlp, g, d0, d1, o0, o1);
+                else simulate_pair<MODE_TWO, P, KAHAN, ICDF, SDE_GBM_MIL>(a, tab, mlp, g, d0, d1, o0, o1);
             } else {
                 if (a.sde == SDE_GBM) simulate_pair<MODE_FOUR, P, KAHAN, ICDF, SDE_GBM>(a, tab, mlp, g, d0, d1, o0, o1);
-                else simulate_pair<MODE_FOUR, P, KAHAN, ICDF, SDE_OU>(a, tab, mlp, g, d0, d1, o0, o1);
+                else if (a.sde == SDE_OU) simulate_pair<MODE_FOUR, P, KAHAN, ICDF, SDE_OU>(a, tab, mlp, g, d0, d1, o0, o1);
+                else simulate_pair<MODE_FOUR, P, KAHAN, ICDF, SDE_GBM_MIL>(a, tab, mlp, g, d0, d1, o0, o1);
             }
             if (!active) continue;
             s1.add(d0);

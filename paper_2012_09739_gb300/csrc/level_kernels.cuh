@@ -18,7 +18,7 @@
 namespace mlmc {
 
 enum { MODE_TWO = 0, MODE_FOUR = 1 };
-enum { SDE_GBM = 0, SDE_OU = 1 };
+enum { SDE_GBM = 0, SDE_OU = 1, SDE_GBM_MIL = 2 };   // GBM with Milstein
 enum { PAYOFF_X = 0, PAYOFF_CALL = 1 };
 
 struct LevelArgs {
@@ -31,9 +31,9 @@ struct LevelArgs {
     uint32_t tag, k0, k1;     // Philox counter tag and key (seed)
     // per-level coefficients in FP64, rounded once to the working precision
     // in the kernel: GBM drift = mu delta_f (fine) / mu 2 delta_f (coarse),
-    // diff = sigma sqrt(delta_f); OU drift = theta delta, diff = s sqrt(delta_f),
-    // mean = m.
-    double drift_f, drift_c, diff, mean, x0;
+    // diff = sigma sqrt(delta_f), Milstein mil = sigma^2 delta_f / 2; OU
+    // drift = theta delta, diff = s sqrt(delta_f), mean = m.
+    double drift_f, drift_c, diff, mean, x0, mil;
     double K, disc;
     const DevTables *tabs;    // piecewise-linear and cubic tables
     const MlpWeights *mlp;    // network (ICDF_MLP only)
@@ -45,27 +45,36 @@ struct LevelArgs {
 
 template <int P, bool KAHAN, int SDE>
 struct PathPair {
-    Pair<P> X, c, drift, diff, mean;
+    Pair<P> X, c, drift, diff, mean, mil, mconst;
 
-    __device__ __forceinline__ void init(double drift_, double diff_, double mean_, double x0) {
+    // mconst: 1 on a fine path, 2 on a coarse one (Milstein only)
+    __device__ __forceinline__ void init(double drift_, double diff_, double mean_, double x0, double mil_ = 0.0,
+                                         double mconst_ = 1.0) {
         drift = Pair<P>::of(drift_);
         diff = Pair<P>::of(diff_);
         mean = Pair<P>::of(mean_);
         X = Pair<P>::of(x0);
         c = Pair<P>::of2(0.0f, 0.0f);
+        if (SDE == SDE_GBM_MIL) {
+            mil = Pair<P>::of(mil_);
+            mconst = Pair<P>::of(mconst_);
+        }
     }
     // X <- X (+) (A (+) B): A = a delta, B = (b sqrt(delta)) (x) z  (Sec. 2.2);
-    // with Kahan compensation of the outer addition (Sec. 2.3, Algorithm 1).
+    // Milstein (GBM): X <- X (+) ((A (+) B) (+) M), M = (mil (x) X) (x)
+    // ((z (x) z) (-) mconst); with Kahan compensation of the outer addition
+    // (Sec. 2.3, Algorithm 1).
     __device__ __forceinline__ void step(Pair<P> z) {
         Pair<P> A, B;
-        if (SDE == SDE_GBM) {
+        if (SDE == SDE_GBM || SDE == SDE_GBM_MIL) {
             A = mul(drift, X);
             B = mul(mul(diff, X), z);
         } else {
             A = mul(drift, sub(mean, X));
             B = mul(diff, z);
         }
-        const Pair<P> inc = add(A, B);
+        Pair<P> inc = add(A, B);
+        if (SDE == SDE_GBM_MIL) inc = add(inc, mul(mul(mil, X), sub(mul(z, z), mconst)));
         if (KAHAN) {
             const Pair<P> y = sub(inc, c);
             const Pair<P> t = add(X, y);
@@ -136,12 +145,12 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
     const float K = __double2float_rn(a.K), disc = __double2float_rn(a.disc);
     const uint64_t p0 = a.path_offset + 2 * g, p1 = p0 + 1;
     PathPair<P, KAHAN, SDE> fine, coarse;
-    fine.init(a.drift_f, a.diff, a.mean, a.x0);
-    coarse.init(a.drift_c, a.diff, a.mean, a.x0);
+    fine.init(a.drift_f, a.diff, a.mean, a.x0, a.mil, 1.0);
+    coarse.init(a.drift_c, a.diff, a.mean, a.x0, a.mil, 2.0);
     PathPair<P_F32, true, SDE> hfine, hcoarse;       // exact-normal pair (four-way only)
     if (MODE == MODE_FOUR) {
-        hfine.init(a.drift_f, a.diff, a.mean, a.x0);
-        hcoarse.init(a.drift_c, a.diff, a.mean, a.x0);
+        hfine.init(a.drift_f, a.diff, a.mean, a.x0, a.mil, 1.0);
+        hcoarse.init(a.drift_c, a.diff, a.mean, a.x0, a.mil, 2.0);
     }
     Pair<P> zprev;
     Pair<P_F32> zhprev;

@@ -82,7 +82,7 @@ extern "C" mlmc_status mlmc_level_noalloc(int four, int l, uint64_t N, int prec,
     NoallocState *na;
     if ((st = noalloc_setup(dev, s, &na))) return st;
 
-    LevelKernelFn fn = pick_level_kernel(four ? 1 : 0, prec, kahan, icdf, params->sde);
+    LevelKernelFn fn = pick_level_kernel(four ? 1 : 0, prec, kahan, icdf, kernel_sde(params));
     if (!fn) return fail(MLMC_EINVAL, "no kernel for this variant");
     // make_level_args only reads the table pointers from the state it is given
     DeviceState view;

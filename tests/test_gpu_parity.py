@@ -33,7 +33,7 @@ def _u32(t):
 
 
 def _orc_sde(p):
-    return O.SDE(p.sde, p.payoff, p.p0, p.p1, p.p2, p.x0, p.T, p.K, p.disc)
+    return O.SDE(p.sde, p.payoff, p.p0, p.p1, p.p2, p.x0, p.T, p.K, p.disc, p.scheme)
 
 
 def gpu_paths(four, l, N, prec, kahan, icdf, params, seed=SEED, offset=0):
