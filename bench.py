@@ -345,22 +345,29 @@ def time_to_eps(M, params, eps_list, repeats=3):
     """Wall time of mlmc_run to RMSE eps (Sec. 3 adaptive MLMC): the standard
     estimator (FP32, exact normals, plain Euler) against the nested estimator
     with FP16 + Kahan table normals, FP32 table normals, and the per-level
-    automatic choice.  Median of `repeats` runs with different seeds, after
-    one untimed run."""
+    automatic choice; the same with 16-bit uniforms for the approximate
+    normals, and with the Milstein scheme.  Median of `repeats` runs with
+    different seeds, after one untimed run."""
     T, T16 = M.MLMC_ICDF_TABLE, M.MLMC_ICDF_TABLE16
-    variants = (("plain_fp32_exact", 0, M.MLMC_F32, 0, T), ("nested_f16_kahan_table", 1, M.MLMC_F16, 1, T),
-                ("nested_f32_table", 1, M.MLMC_F32, 0, T), ("nested_auto_table", 1, -1, 0, T),
-                ("nested_f16_kahan_table16", 1, M.MLMC_F16, 1, T16), ("nested_auto_table16", 1, -1, 0, T16))
+    E, MIL = M.MLMC_EULER, M.MLMC_MILSTEIN
+    variants = (("plain_fp32_exact", 0, M.MLMC_F32, 0, T, E), ("nested_f16_kahan_table", 1, M.MLMC_F16, 1, T, E),
+                ("nested_f32_table", 1, M.MLMC_F32, 0, T, E), ("nested_auto_table", 1, -1, 0, T, E),
+                ("nested_f16_kahan_table16", 1, M.MLMC_F16, 1, T16, E), ("nested_auto_table16", 1, -1, 0, T16, E),
+                ("plain_fp32_exact_milstein", 0, M.MLMC_F32, 0, T, MIL),
+                ("nested_f16_kahan_table16_milstein", 1, M.MLMC_F16, 1, T16, MIL),
+                ("nested_auto_table16_milstein", 1, -1, 0, T16, MIL))
     out = {}
     for eps in eps_list:
         row = {}
-        for name, est, prec, kahan, icdf in variants:
+        for name, est, prec, kahan, icdf, scheme in variants:
             times, res = [], None
+            p = M.mlmc_sde_params.from_buffer_copy(params)
+            p.scheme = scheme
             for rep in range(repeats + 1):
                 o = M.mlmc_run_opts(estimator=est, prec=prec, kahan=kahan, icdf=icdf, max_level=18,
                                     min_levels=3, n0=10000, seed=1000 + rep, alpha=1.0, timeout_s=600.0)
                 t0 = time.perf_counter()
-                r = M.mlmc_run(eps, params, o)
+                r = M.mlmc_run(eps, p, o)
                 dt = time.perf_counter() - t0
                 if rep > 0:
                     times.append(dt)
@@ -376,6 +383,8 @@ def time_to_eps(M, params, eps_list, repeats=3):
         row["speedup_f16_kahan_vs_plain"] = row["plain_fp32_exact"]["seconds"] / row["nested_f16_kahan_table"]["seconds"]
         row["speedup_f16_kahan_table16_vs_plain"] = (row["plain_fp32_exact"]["seconds"]
                                                      / row["nested_f16_kahan_table16"]["seconds"])
+        row["speedup_milstein_f16_kahan_table16_vs_plain_milstein"] = (
+            row["plain_fp32_exact_milstein"]["seconds"] / row["nested_f16_kahan_table16_milstein"]["seconds"])
         out[f"{eps:g}"] = row
     return out
 
