@@ -254,9 +254,11 @@ typedef struct {
     int32_t estimator;    /* 0: standard theta^ (FP32, exact normals, plain Euler);
                              1: nested theta- (two-way approximate + four-way) */
     int32_t prec, kahan, icdf;   /* variant of the approximate paths (estimator 1); prec = -1:
-                                    choose per level among FP16 + Kahan, FP16 and FP32 (kahan
-                                    ignored) the variant with the smallest sqrt(v c) + sqrt(V C)
-                                    measured on n0 warm-up samples of each (Sec. 3) */
+                                    choose per level, by the smallest sqrt(v c) + sqrt(V C) measured
+                                    on n0 warm-up samples of each (Sec. 3), among the nested pairs in
+                                    FP16 + Kahan, FP16 and FP32 (kahan ignored) and the standard FP32
+                                    exact-normal two-way difference alone (FP32 + Kahan, the hat
+                                    paths' arithmetic, so the level differences still telescope) */
     int32_t max_level;    /* <= 18 */
     int32_t min_levels;   /* levels 0 .. min_levels-1 always present (>= 3) */
     uint64_t n0;          /* warm-up samples per level and estimator */
@@ -284,6 +286,10 @@ typedef struct {
      * exact-normal two-way difference measured on n0 samples (< 1: saving);
      * 0 when not measured (estimator 0, or levels added without warm-up). */
     double efficiency[MLMC_MAX_LEVELS];
+    /* 1: the level uses the nested pair (two-way approximate + four-way);
+     * 0: the standard FP32 exact-normal two-way difference alone (estimator
+     * 0, or prec = -1 when that is cheaper for the level). */
+    int32_t nested[MLMC_MAX_LEVELS];
 } mlmc_run_result;
 
 mlmc_status mlmc_run(double eps, const mlmc_sde_params *params, const mlmc_run_opts *opts, mlmc_run_result *out);

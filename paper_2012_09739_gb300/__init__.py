@@ -77,7 +77,7 @@ class mlmc_run_result(ctypes.Structure):
                 ("n", (ctypes.c_uint64 * MLMC_MAX_LEVELS) * 2), ("mean", (ctypes.c_double * MLMC_MAX_LEVELS) * 2),
                 ("var", (ctypes.c_double * MLMC_MAX_LEVELS) * 2), ("cost", (ctypes.c_double * MLMC_MAX_LEVELS) * 2),
                 ("prec", ctypes.c_int32 * MLMC_MAX_LEVELS), ("kahan", ctypes.c_int32 * MLMC_MAX_LEVELS),
-                ("efficiency", ctypes.c_double * MLMC_MAX_LEVELS)]
+                ("efficiency", ctypes.c_double * MLMC_MAX_LEVELS), ("nested", ctypes.c_int32 * MLMC_MAX_LEVELS)]
 
 
 # exported symbols and their signatures

@@ -108,8 +108,26 @@ mlmc_status check_level(int four, int l, uint64_t N, int prec, int icdf, const m
 }
 
 // ---------------------------------------------------------------- launches
-LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int icdf, const mlmc_sde_params *p,
-                          uint64_t seed, uint64_t path_offset, uint32_t set_id) {
+// A binary64 constant rounded once to nearest even, as the pair bits of the
+// working precision (CUDA's host conversions to binary16 / bfloat16 round
+// directly from binary64).
+static uint32_t pair_bits(double v, int prec) {
+    if (prec == MLMC_F16) {
+        const __half_raw h = __double2half(v);
+        return (uint32_t)h.x | ((uint32_t)h.x << 16);
+    }
+    if (prec == MLMC_BF16) {
+        const __nv_bfloat16_raw b = __double2bfloat16(v);
+        return (uint32_t)b.x | ((uint32_t)b.x << 16);
+    }
+    const float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    return u;
+}
+
+LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int prec, int icdf,
+                          const mlmc_sde_params *p, uint64_t seed, uint64_t path_offset, uint32_t set_id) {
     (void)icdf;
     LevelArgs a;
     memset(&a, 0, sizeof a);
@@ -139,6 +157,13 @@ LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int
     a.x0 = p->x0;
     a.K = p->K;
     a.disc = p->disc;
+    const double cv[8] = {a.drift_f, a.drift_c, a.diff, a.mean, a.x0, a.mil, 1.0, 2.0};
+    for (int i = 0; i < 8; ++i) {
+        a.cw[i] = pair_bits(cv[i], prec);
+        a.c32[i] = (float)cv[i];
+    }
+    a.K32 = (float)p->K;
+    a.disc32 = (float)p->disc;
     a.tabs = d.tabs;
     a.mlp = d.mlp;
     return a;
@@ -188,7 +213,7 @@ mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int
                           double *sums_dev, float *paths_dev, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
     LevelKernelFn fn = pick_level_kernel(four, prec, kahan, icdf, kernel_sde(p));
     if (!fn) return fail(MLMC_EINVAL, "no kernel for this variant");
-    LevelArgs a = make_level_args(d, four, l, N, icdf, p, seed, path_offset, set_id);
+    LevelArgs a = make_level_args(d, four, l, N, prec, icdf, p, seed, path_offset, set_id);
     const LaunchCfg cfg = level_launch_cfg(d, fn, a.npairs);
     const uint64_t chunks = (a.npairs + 31) / 32;
     const uint64_t groups = (chunks + chunk_group(l) - 1) / chunk_group(l);

@@ -39,7 +39,7 @@ double wait_limit_s();
 double *host_staging();
 mlmc_status check_params(const mlmc_sde_params *p);
 mlmc_status check_level(int four, int l, uint64_t N, int prec, int icdf, const mlmc_sde_params *p);
-LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int icdf, const mlmc_sde_params *p,
+LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int prec, int icdf, const mlmc_sde_params *p,
                           uint64_t seed, uint64_t path_offset, uint32_t set_id);
 int kernel_sde(const mlmc_sde_params *p);
 LevelKernelFn pick_level_kernel(int four, int prec, int kahan, int icdf, int sde);

@@ -74,7 +74,7 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
     double total = 0.0;
     for (int i = 0; i < n; ++i) total += item_work(w[i]);
     for (int i = 0; i < n; ++i) {
-        plan.items[i] = make_level_args(d, w[i].kind, w[i].l, w[i].N, w[i].icdf, &w[i].params, seed,
+        plan.items[i] = make_level_args(d, w[i].kind, w[i].l, w[i].N, w[i].prec, w[i].icdf, &w[i].params, seed,
                                         w[i].path_offset, (uint32_t)w[i].set_id);
         plan.weight.push_back(total > 0 ? item_work(w[i]) / total : 0.0);
         Group *g = nullptr;

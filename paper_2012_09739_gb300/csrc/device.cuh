@@ -132,12 +132,16 @@ template <> struct Pair<P_F32> {
     float x, y;
     static __device__ __forceinline__ Pair of(double v) { float f = __double2float_rn(v); return {f, f}; }
     static __device__ __forceinline__ Pair of2(float a, float b) { return {a, b}; }
+    // a constant from its binary32 bits
+    static __device__ __forceinline__ Pair bits(uint32_t b) { return {__uint_as_float(b), __uint_as_float(b)}; }
     __device__ __forceinline__ float2 f32() const { return make_float2(x, y); }
 };
 template <> struct Pair<P_F16> {
     __half2 h;
     static __device__ __forceinline__ Pair of(double v) { __half t = f64_to_f16(v); return {__halves2half2(t, t)}; }
     static __device__ __forceinline__ Pair of2(float a, float b) { return {__floats2half2_rn(a, b)}; }
+    // a constant from its packed binary16x2 bits
+    static __device__ __forceinline__ Pair bits(uint32_t b) { return {*reinterpret_cast<const __half2 *>(&b)}; }
     __device__ __forceinline__ float2 f32() const { return __half22float2(h); }
 };
 
@@ -148,6 +152,7 @@ template <> struct Pair<P_BF16> {
         return {h | (h << 16)};
     }
     static __device__ __forceinline__ Pair of2(float a, float c) { return {f32x2_to_bf16x2(a, c)}; }
+    static __device__ __forceinline__ Pair bits(uint32_t b) { return {b}; }
     __device__ __forceinline__ float2 f32() const {
         return make_float2(__uint_as_float(b << 16), __uint_as_float(b & 0xFFFF0000u));
     }

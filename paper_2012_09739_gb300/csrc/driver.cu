@@ -20,6 +20,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <mutex>
 #include <vector>
@@ -32,6 +33,7 @@ namespace {
 
 struct Term {
     int l, four, prec, kahan, icdf;
+    bool off = false;            // placeholder four-way slot of a level run by the standard estimator
     uint64_t n = 0;              // samples taken
     uint64_t dn = 0;             // samples to add this round
     double s1 = 0.0, s2 = 0.0;
@@ -40,20 +42,24 @@ struct Term {
     double mean() const { return n ? s1 / n : 0.0; }
 };
 
-// Device ns per fine path-step of each variant at full occupancy, measured on
-// GB300 with N = 2^20 samples per level (two-way / four-way; exact, table
-// and MLP normals).
+// Device cost of one sample of a term: C = nu 2^l + kappa, with nu the ns
+// per fine path-step of the variant and kappa the per-sample cost (uniform
+// generation at l < 2, payoff, accumulation), measured on GB300 with the
+// level kernels at full occupancy (N = 2^24 for l <= 6, 2^(30-l) above;
+// fitted on l = 0..10).
 double nu_of(const Term &t) {
     if (t.icdf == MLMC_ICDF_MLP) return t.four ? 9.0e-3 : 7.0e-3;
-    if (t.icdf == MLMC_ICDF_EXACT) return t.kahan ? 1.8e-3 : 1.65e-3;
+    if (t.icdf == MLMC_ICDF_EXACT) return t.kahan ? 1.69e-3 : 1.53e-3;
     const bool half = t.prec != MLMC_F32;   // binary16 and bfloat16 share the f16x2-style packing
-    // 16-bit uniforms: half the Philox calls per two-way fine step; one more
-    // uniform conversion per four-way step
-    // the cubic adds a Horner evaluation per normal
+    // 16-bit uniforms: half the Philox calls per two-way fine step, one more
+    // uniform conversion per four-way step; the cubic adds a Horner evaluation
     const bool u16 = t.icdf == MLMC_ICDF_TABLE16, cub = t.icdf == MLMC_ICDF_CUBIC;
-    if (t.four) return (u16 ? 1.08 : cub ? 1.12 : 1.0) * (half ? 2.15e-3 : 2.4e-3);
-    return (u16 ? 0.8 : cub ? 1.3 : 1.0) * (half ? (t.kahan ? 1.12e-3 : 1.0e-3) : (t.kahan ? 1.4e-3 : 1.25e-3));
+    if (t.four) return (u16 ? 1.06 : cub ? 1.12 : 1.0) * (half ? 2.10e-3 : 2.15e-3);
+    const double base = half ? (t.kahan ? 1.07e-3 : 0.94e-3) : (t.kahan ? 1.2e-3 : 1.065e-3);
+    return (u16 ? 0.81 : cub ? 1.3 : 1.0) * base;
 }
+
+double cost_of(const Term &t) { return ldexp(1.0, t.l) * nu_of(t) + (t.four ? 5.5e-3 : 5.2e-3); }
 
 }  // namespace
 
@@ -90,6 +96,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
     std::vector<Term> terms;
     std::vector<int> lvl_prec(MLMC_MAX_LEVELS, o->prec), lvl_kahan(MLMC_MAX_LEVELS, o->kahan ? 1 : 0);
     std::vector<double> lvl_eff(MLMC_MAX_LEVELS, 0.0);
+    std::vector<int> lvl_nested(MLMC_MAX_LEVELS, nested ? 1 : 0);
     double path_steps = 0.0;
     const double limit = o->timeout_s > 0 ? o->timeout_s : wait_limit_s();
     int rounds = 0;
@@ -150,6 +157,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         return run_round(cand);
     };
     const bool autoprec = nested && o->prec < 0;
+    bool half_done = false;      // a coarser level already chose FP32 or the standard estimator
     auto add_level = [&](int l) -> mlmc_status {
         if (!nested) {
             terms.push_back(Term{l, 0, MLMC_F32, o->kahan ? 1 : 0, MLMC_ICDF_EXACT});
@@ -163,20 +171,28 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
             return MLMC_OK;
         }
         // candidates (two-way, four-way) x {FP16 + Kahan, FP16, FP32}, plus the
-        // standard FP32 exact-normal two-way term for the efficiency factor
+        // standard FP32 exact-normal two-way term (with Kahan, the four-way
+        // hat paths' arithmetic): the efficiency reference and a candidate.
+        // Once a level has chosen FP32 (or the standard estimator) the
+        // binary16 candidates are not tried again: their rounding variance
+        // does not decay with delta while the level variance does (Sec. 3),
+        // so they only lose further on finer levels.
         const int cp[3] = {MLMC_F16, MLMC_F16, MLMC_F32}, ck[3] = {1, 0, 0};
+        const int first = half_done ? 2 : 0;
         std::vector<Term> cand;
         for (int c = 0; c < 3; ++c) {
             cand.push_back(Term{l, 0, cp[c], ck[c], o->icdf});
             cand.push_back(Term{l, 1, cp[c], ck[c], o->icdf});
         }
-        cand.push_back(Term{l, 0, MLMC_F32, 0, MLMC_ICDF_EXACT});
-        mlmc_status r = trial(cand);
+        cand.push_back(Term{l, 0, MLMC_F32, 1, MLMC_ICDF_EXACT});
+        std::vector<Term> tried(cand.begin() + 2 * first, cand.end());
+        mlmc_status r = trial(tried);
         if (r) return r;
-        auto vc = [&](const Term &t) { return t.var() * ldexp(1.0, t.l) * nu_of(t); };
-        int best = 0;
+        std::copy(tried.begin(), tried.end(), cand.begin() + 2 * first);
+        auto vc = [&](const Term &t) { return t.var() * cost_of(t); };
+        int best = first;
         double best_score = 1e300;
-        for (int c = 0; c < 3; ++c) {
+        for (int c = first; c < 3; ++c) {
             const double score = sqrt(vc(cand[2 * c])) + sqrt(vc(cand[2 * c + 1]));
             if (score < best_score) {
                 best_score = score;
@@ -185,8 +201,24 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         }
         const double vc2 = vc(cand[2 * best]), vc4 = vc(cand[2 * best + 1]), vch = vc(cand[6]);
         if (vch > 0.0 && vc2 > 0.0) lvl_eff[l] = vc2 / vch * pow(1.0 + sqrt(vc4 / vc2), 2.0);
+        if (vch > 0.0 && sqrt(vch) < best_score) {
+            // the standard estimator alone is cheaper for this level; the
+            // four-way slot stays empty (both estimate E[P^_l - P^_{l-1}])
+            lvl_prec[l] = MLMC_F32;
+            lvl_kahan[l] = 1;
+            lvl_nested[l] = 0;
+            half_done = true;
+            terms.push_back(cand[6]);
+            Term slot = cand[1];
+            slot.off = true;
+            slot.n = 0;
+            slot.s1 = slot.s2 = 0.0;
+            terms.push_back(slot);
+            return MLMC_OK;
+        }
         lvl_prec[l] = cp[best];
         lvl_kahan[l] = ck[best];
+        if (cp[best] == MLMC_F32) half_done = true;
         terms.push_back(cand[2 * best]);
         terms.push_back(cand[2 * best + 1]);
         return MLMC_OK;
@@ -201,11 +233,12 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         // ---- variance and cost estimates; optimal sample counts
         std::vector<double> V(terms.size()), C(terms.size());
         for (size_t i = 0; i < terms.size(); ++i) {
-            V[i] = terms[i].var();
+            V[i] = terms[i].off ? 0.0 : terms[i].var();
             // a level's variance is at least half its predecessor's, decayed
             // at strong rate beta = 1 (guards new levels with few samples)
-            if (terms[i].l >= 2) V[i] = fmax(V[i], 0.5 * V[i - per_level] * 0.5);
-            C[i] = ldexp(1.0, terms[i].l) * nu_of(terms[i]);
+            if (terms[i].l >= 2 && !terms[i].off && !terms[i - per_level].off)
+                V[i] = fmax(V[i], 0.5 * V[i - per_level] * 0.5);
+            C[i] = cost_of(terms[i]);
             terms[i].cost = C[i];
         }
         double total = 0.0;
@@ -257,6 +290,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
             out->prec[l] = nested ? lvl_prec[l] : MLMC_F32;
             out->kahan[l] = nested ? lvl_kahan[l] : (o->kahan ? 1 : 0);
             out->efficiency[l] = lvl_eff[l];
+            out->nested[l] = lvl_nested[l];
         }
         out->path_steps = path_steps;
         out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();

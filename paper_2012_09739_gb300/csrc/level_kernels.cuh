@@ -20,6 +20,7 @@ namespace mlmc {
 enum { MODE_TWO = 0, MODE_FOUR = 1 };
 enum { SDE_GBM = 0, SDE_OU = 1, SDE_GBM_MIL = 2 };   // GBM with Milstein
 enum { PAYOFF_X = 0, PAYOFF_CALL = 1 };
+enum { CI_DRIFT_F = 0, CI_DRIFT_C = 1, CI_DIFF = 2, CI_MEAN = 3, CI_X0 = 4, CI_MIL = 5, CI_ONE = 6, CI_TWO = 7 };
 
 struct LevelArgs {
     int l;                    // level: 2^l fine steps
@@ -35,6 +36,13 @@ struct LevelArgs {
     // drift = theta delta, diff = s sqrt(delta_f), mean = m.
     double drift_f, drift_c, diff, mean, x0, mil;
     double K, disc;
+    // The same coefficients rounded once, on the host, to nearest even from
+    // FP64: cw in the approximate paths' working precision as pair bits
+    // (binary32: the value's bits; binary16 / bfloat16: the value in both
+    // halves), c32 in binary32 for the exact-normal paths.  Index: CI_*.
+    uint32_t cw[8];
+    float c32[8];
+    float K32, disc32;
     const DevTables *tabs;    // piecewise-linear and cubic tables
     const MlpWeights *mlp;    // network (ICDF_MLP only)
     double2 *partials;        // (sum D, sum D^2) per warp chunk, or per block
@@ -47,17 +55,23 @@ template <int P, bool KAHAN, int SDE>
 struct PathPair {
     Pair<P> X, c, drift, diff, mean, mil, mconst;
 
-    // mconst: 1 on a fine path, 2 on a coarse one (Milstein only)
-    __device__ __forceinline__ void init(double drift_, double diff_, double mean_, double x0, double mil_ = 0.0,
-                                         double mconst_ = 1.0) {
-        drift = Pair<P>::of(drift_);
-        diff = Pair<P>::of(diff_);
-        mean = Pair<P>::of(mean_);
-        X = Pair<P>::of(x0);
+    // Constants from the launch arguments, already rounded on the host (no
+    // FP64 conversion per sample): HAT selects the binary32 copies of the
+    // exact-normal paths; mconst is 1 on a fine path, 2 on a coarse one.
+    template <bool HAT>
+    __device__ __forceinline__ void init(const LevelArgs &a, bool coarse_path) {
+        auto k = [&](int i) {
+            if constexpr (HAT) return Pair<P>::bits(__float_as_uint(a.c32[i]));
+            else return Pair<P>::bits(a.cw[i]);
+        };
+        drift = k(coarse_path ? CI_DRIFT_C : CI_DRIFT_F);
+        diff = k(CI_DIFF);
+        mean = k(CI_MEAN);
+        X = k(CI_X0);
         c = Pair<P>::of2(0.0f, 0.0f);
         if (SDE == SDE_GBM_MIL) {
-            mil = Pair<P>::of(mil_);
-            mconst = Pair<P>::of(mconst_);
+            mil = k(CI_MIL);
+            mconst = k(coarse_path ? CI_TWO : CI_ONE);
         }
     }
     // X <- X (+) (A (+) B): A = a delta, B = (b sqrt(delta)) (x) z  (Sec. 2.2);
@@ -142,15 +156,15 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
                                               uint64_t g, float &d0, float &d1, float *out0, float *out1) {
     const uint32_t nf = 1u << a.l;
     const uint32_t ncalls = (nf + 3u) >> 2;
-    const float K = __double2float_rn(a.K), disc = __double2float_rn(a.disc);
+    const float K = a.K32, disc = a.disc32;
     const uint64_t p0 = a.path_offset + 2 * g, p1 = p0 + 1;
     PathPair<P, KAHAN, SDE> fine, coarse;
-    fine.init(a.drift_f, a.diff, a.mean, a.x0, a.mil, 1.0);
-    coarse.init(a.drift_c, a.diff, a.mean, a.x0, a.mil, 2.0);
+    fine.template init<false>(a, false);
+    coarse.template init<false>(a, true);
     PathPair<P_F32, true, SDE> hfine, hcoarse;       // exact-normal pair (four-way only)
     if (MODE == MODE_FOUR) {
-        hfine.init(a.drift_f, a.diff, a.mean, a.x0, a.mil, 1.0);
-        hcoarse.init(a.drift_c, a.diff, a.mean, a.x0, a.mil, 2.0);
+        hfine.template init<true>(a, false);
+        hcoarse.template init<true>(a, true);
     }
     Pair<P> zprev;
     Pair<P_F32> zhprev;

@@ -54,8 +54,13 @@ __device__ __forceinline__ int entry_interval(int entry) {     // 0-based interv
     return min(126 - (103 + entry), 16) - 1;
 }
 
-__global__ void build_table_kernel(DevTables *out) {
-    __shared__ double lin[32], cub[64], glx[GL_N], glw[GL_N];
+// One block of BUILD_THREADS threads: thread k-1 fits linear interval k; for the cubic,
+// thread j < 75 integrates one piece (pieces 0..14: intervals 1..15; pieces
+// 15..74: the dyadic pieces of interval 16), and the pieces of interval 16
+// are added in a fixed order.
+constexpr int BUILD_THREADS = 96;
+__global__ void __launch_bounds__(BUILD_THREADS) build_table_kernel(DevTables *out) {
+    __shared__ double lin[32], cub[64], glx[GL_N], glw[GL_N], piece[15 + CUBIC_TAIL_PIECES][4];
     const int i = threadIdx.x;
     if (i < GL_N) gauss_legendre_node(i, glx[i], glw[i]);
     if (i < 16) {
@@ -83,26 +88,33 @@ __global__ void build_table_kernel(DevTables *out) {
         lin[2 * i + 1] = c1;
     }
     __syncthreads();
-    if (i < 16) {
-        const int k = i + 1;
+    if (i < 15 + CUBIC_TAIL_PIECES) {
+        const int k = i < 15 ? i + 1 : 16;
+        const int j = i - 15;                                     // tail piece index
         const double A = k < 16 ? ldexp(1.0, k + 2) : ldexp(1.0, 17);
         const double B = k < 16 ? 3.0 : 1.0;
-        const int pieces = k < 16 ? 1 : CUBIC_TAIL_PIECES;
+        const double hi = k < 16 ? ldexp(1.0, -k) : ldexp(1.0, -16 - j);
+        const double lo = k < 16 ? ldexp(1.0, -k - 1) : ldexp(1.0, -17 - j);
+        const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
         double pr[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int j = 0; j < pieces; ++j) {
-            const double hi = k < 16 ? ldexp(1.0, -k) : ldexp(1.0, -16 - j);
-            const double lo = k < 16 ? ldexp(1.0, -k - 1) : ldexp(1.0, -17 - j);
-            const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
-            for (int q = 0; q < GL_N; ++q) {
-                const double v = mid + half * glx[q];
-                const double s = A * v - B;
-                const double wf = half * glw[q] * A * normcdfinv(v);     // ds = A dv
-                pr[0] += wf;
-                pr[1] += wf * s;
-                pr[2] += wf * 0.5 * (3.0 * s * s - 1.0);
-                pr[3] += wf * 0.5 * (5.0 * s * s * s - 3.0 * s);
-            }
+        for (int q = 0; q < GL_N; ++q) {
+            const double v = mid + half * glx[q];
+            const double s = A * v - B;
+            const double wf = half * glw[q] * A * normcdfinv(v);     // ds = A dv
+            pr[0] += wf;
+            pr[1] += wf * s;
+            pr[2] += wf * 0.5 * (3.0 * s * s - 1.0);
+            pr[3] += wf * 0.5 * (5.0 * s * s * s - 3.0 * s);
         }
+        for (int m = 0; m < 4; ++m) piece[i][m] = pr[m];
+    }
+    __syncthreads();
+    if (i < 16) {
+        double pr[4];
+        for (int m = 0; m < 4; ++m) pr[m] = i < 15 ? piece[i][m] : 0.0;
+        if (i == 15)
+            for (int j = 0; j < CUBIC_TAIL_PIECES; ++j)
+                for (int m = 0; m < 4; ++m) pr[m] += piece[15 + j][m];
         const double a0 = 0.5 * pr[0], a1 = 1.5 * pr[1], a2 = 2.5 * pr[2], a3 = 3.5 * pr[3];
         cub[4 * i] = a0 - 0.5 * a2;
         cub[4 * i + 1] = a1 - 1.5 * a3;
@@ -131,7 +143,7 @@ __global__ void build_table_kernel(DevTables *out) {
 }
 
 cudaError_t launch_build_table(DevTables *out, cudaStream_t s) {
-    build_table_kernel<<<1, 32, 0, s>>>(out);
+    build_table_kernel<<<1, BUILD_THREADS, 0, s>>>(out);
     return cudaGetLastError();
 }
 

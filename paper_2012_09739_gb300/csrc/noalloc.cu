@@ -87,7 +87,7 @@ extern "C" mlmc_status mlmc_level_noalloc(int four, int l, uint64_t N, int prec,
     // make_level_args only reads the table pointers from the state it is given
     DeviceState view;
     view.tabs = na->tabs;
-    LevelArgs a = make_level_args(view, four ? 1 : 0, l, N, icdf, params, seed, path_offset, 0);
+    LevelArgs a = make_level_args(view, four ? 1 : 0, l, N, prec, icdf, params, seed, path_offset, 0);
     a.partials = na->partials;
     a.paths_out = nullptr;
     const int grid = (int)((a.npairs + NOALLOC_BLOCK - 1) / NOALLOC_BLOCK);

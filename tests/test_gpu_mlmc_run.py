@@ -66,7 +66,27 @@ def test_mlmc_run_auto_precision_per_level():
     for l in range(r.levels):
         assert r.prec[l] in (M.MLMC_F16, M.MLMC_F32)
         assert r.efficiency[l] > 0.0
-        assert r.n[0][l] >= 10000 and r.n[1][l] >= 10000
+        assert r.n[0][l] >= 10000
+        # a level either runs the nested pair or the standard estimator alone
+        assert (r.n[1][l] >= 10000) if r.nested[l] else (r.n[1][l] == 0)
+
+
+def test_mlmc_run_auto_with_milstein():
+    """Milstein with the per-level choice: each level runs either the nested
+    pair or the standard estimator alone (whichever the measured variances
+    and the cost model favour); the mixed telescoping sum reaches eps around
+    the Black-Scholes price."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    eps = 2e-5
+    params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0,
+                          scheme=M.MLMC_MILSTEIN)
+    r = M.mlmc_run(eps, params, _opts(1, prec=-1, icdf=M.MLMC_ICDF_TABLE16))
+    assert abs(r.estimate - mlmc.bs_call()) < 4 * eps + 2e-5      # plus the l <= L weak bias allowance
+    assert r.variance <= eps * eps / 2 * 1.05
+    for l in range(r.levels):
+        assert r.nested[l] in (0, 1) and r.n[0][l] >= 10000
+        assert (r.n[1][l] >= 10000) if r.nested[l] else (r.n[1][l] == 0)
 
 
 def test_mlmc_run_timeout_is_reported_and_recoverable():
