@@ -403,7 +403,11 @@ static double payoff_of(double X, const orc_sde *p, int prec)
  * two-way with exact normals, 1: two-way with approximate normals, 2:
  * four-way.  (Reading: the paper is silent on the generator.)
  * With 16-bit uniforms (RV TABLE16 on a two-way path) fine step n uses half
- * n mod 2 (low half first) of word (n / 2) mod 4 of call j = n / 8. */
+ * n mod 2 (low half first) of word (n / 2) mod 4 of call j = n / 8.
+ * Coarsest levels (a path needs at most half a call: 2^l <= 2 words, or
+ * 2^l <= 4 halves with 16-bit uniforms): paths 2k and 2k+1 share call 0 of
+ * counter path field k; path p takes the words (halves) from
+ * (p mod 2) 2^l on. */
 static void draw4w(uint64_t path, uint32_t j, uint32_t tag, uint64_t seed, uint32_t w[4])
 {
     uint32_t ctr[4] = {(uint32_t)path, (uint32_t)(path >> 32), j, tag};
@@ -432,16 +436,21 @@ static void twoway_one(int l, uint64_t path, const orc_variant *v, const orc_sde
     path_init(&coarse, p, v->prec, v->pbits, v->kahan, 2.0 * delta_f, sq, 1);
     double zprev = 0.0, u[4];
     uint32_t w[4];
+    const int u16 = v->rv == ORC_RV_TABLE16;
+    const int shared = u16 ? l <= 2 : l <= 1;
+    const uint64_t cpath = shared ? path >> 1 : path;
+    const int64_t off = shared ? (int64_t)(path & 1) << l : 0;   /* first word (half) of this path */
     for (int64_t n = 0; n < nf; ++n) {
         double z;
-        if (v->rv == ORC_RV_TABLE16) {
-            if ((n & 7) == 0) draw4w(path, (uint32_t)(n >> 3), tag, seed, w);
-            uint32_t word = w[(n >> 1) & 3];
-            uint32_t h = (n & 1) ? word >> 16 : word & 0xFFFFu;
+        const int64_t q = off + n;
+        if (u16) {
+            if (n == 0 || (q & 7) == 0) draw4w(cpath, (uint32_t)(q >> 3), tag, seed, w);
+            uint32_t word = w[(q >> 1) & 3];
+            uint32_t h = (q & 1) ? word >> 16 : word & 0xFFFFu;
             z = table_icdf(uniform16_of(h), table, &fine.m);
         } else {
-            if ((n & 3) == 0) draw4(path, (uint32_t)(n >> 2), tag, seed, u);
-            z = rv_of(u[n & 3], v->rv, table, mlp, &fine.m);
+            if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);
+            z = rv_of(u[q & 3], v->rv, table, mlp, &fine.m);
         }
         path_step(&fine, z);
         if (l > 0 && (n & 1)) path_step(&coarse, round_p(zprev + z, &coarse.m));
@@ -470,10 +479,14 @@ static void fourway_one(int l, uint64_t path, const orc_variant *hat, const orc_
     path_init(&bf, p, bar->prec, bar->pbits, bar->kahan, delta_f, sq, 0);
     path_init(&bc, p, bar->prec, bar->pbits, bar->kahan, 2.0 * delta_f, sq, 1);
     double zh_prev = 0.0, zb_prev = 0.0, u[4];
+    const int shared = l <= 1;
+    const uint64_t cpath = shared ? path >> 1 : path;
+    const int64_t off = shared ? (int64_t)(path & 1) << l : 0;   /* see draw4w */
     for (int64_t n = 0; n < nf; ++n) {
-        if ((n & 3) == 0) draw4(path, (uint32_t)(n >> 2), tag, seed, u);
-        double zh = rv_of(u[n & 3], hat->rv, table, mlp, &hf.m);
-        double zb = rv_of(u[n & 3], bar->rv, table, mlp, &bf.m);
+        const int64_t q = off + n;
+        if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);
+        double zh = rv_of(u[q & 3], hat->rv, table, mlp, &hf.m);
+        double zb = rv_of(u[q & 3], bar->rv, table, mlp, &bf.m);
         path_step(&hf, zh);
         path_step(&bf, zb);
         if (l > 0 && (n & 1)) {
@@ -557,9 +570,14 @@ void orc_rounding_pairs(int l, uint64_t N, uint64_t path_offset, const int *var,
         path_init(&lo, p, v.prec, v.pbits, v.kahan, delta_f, sq, 0);
         double u[4];
         rmode exact = mode_of(ORC_F64, 0);
+        const uint64_t path = path_offset + (uint64_t)i;
+        const int shared = l <= 1;
+        const uint64_t cpath = shared ? path >> 1 : path;
+        const int64_t off = shared ? (int64_t)(path & 1) << l : 0;   /* see draw4w */
         for (int64_t n = 0; n < nf; ++n) {
-            if ((n & 3) == 0) draw4(path_offset + (uint64_t)i, (uint32_t)(n >> 2), tag, seed, u);
-            double z64 = rv_of(u[n & 3], v.rv, table, mlp, &exact);
+            const int64_t q = off + n;
+            if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);
+            double z64 = rv_of(u[q & 3], v.rv, table, mlp, &exact);
             path_step(&hi, z64);
             path_step(&lo, round_p(z64, &lo.m));
         }

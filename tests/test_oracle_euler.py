@@ -72,14 +72,38 @@ def test_per_path_components_consistent(pl_table):
 
 
 def test_level0_single_step_by_hand():
-    # l = 0: one step X1 = x0 + mu x0 T + sigma x0 sqrt(T) Z with Z from word 0 of call 0
+    # l = 0: one step X1 = x0 + mu x0 T + sigma x0 sqrt(T) Z; paths 6 and 7
+    # share call 0 of counter path field 3 and take words 0 and 1
     sde = O.gbm(mu=0.05, sigma=0.2, payoff=O.PAYOFF_X)
     tag = O.make_tag(O.KIND_STD, 0)
-    w = O.philox4x32_10(O.counters([7], 0, tag), O.seed_key(SEED))[0]
-    z = O.ndtri(O.uniforms(w[:1]))[0]
-    out = O.twoway_paths(0, [7], O.variant(), sde, SEED, tag)[0]
-    assert out[1] == 0.0 and out[2] == out[0]
-    assert abs(out[0] - (1 + 0.05 + 0.2 * z)) < 1e-15
+    w = O.philox4x32_10(O.counters([3], 0, tag), O.seed_key(SEED))[0]
+    z = O.ndtri(O.uniforms(w[:2]))
+    out = O.twoway_paths(0, [6, 7], O.variant(), sde, SEED, tag)
+    for k in range(2):
+        assert out[k, 1] == 0.0 and out[k, 2] == out[k, 0]
+        assert abs(out[k, 0] - (1 + 0.05 + 0.2 * z[k])) < 1e-15
+
+
+def test_level1_paths_share_a_call_by_hand():
+    # l = 1: paths 4 and 5 share call 0 of counter path field 2: path 4 takes
+    # words 0, 1 and path 5 words 2, 3; the coarse step adds the pair
+    mu, sigma = 0.07, 0.3
+    sde = O.gbm(mu=mu, sigma=sigma, payoff=O.PAYOFF_X)
+    tag = O.make_tag(O.KIND_STD, 1)
+    w = O.philox4x32_10(O.counters([2], 0, tag), O.seed_key(SEED))[0]
+    z = O.ndtri(O.uniforms(w))
+    out = O.twoway_paths(1, [4, 5], O.variant(), sde, SEED, tag)
+    d = 0.5
+    for k in range(2):
+        za, zb = z[2 * k], z[2 * k + 1]
+        xf = 1.0
+        for zz in (za, zb):
+            xf = xf + (mu * d * xf + (sigma * math.sqrt(d) * xf) * zz)
+        xc = 1.0 + (mu * 2 * d * 1.0 + (sigma * math.sqrt(d) * 1.0) * (za + zb))
+        assert out[k, 0] == xf and out[k, 1] == xc
+    # and the four-way paths of the same counters share the words the same way
+    four = O.fourway_paths(1, [4, 5], O.variant(), O.variant(rv=O.RV_TABLE), sde, SEED, tag)
+    assert np.array_equal(four[:, 0:2], out[:, 0:2])
 
 
 def test_level2_coarse_uses_pairwise_sums():

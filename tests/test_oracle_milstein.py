@@ -61,7 +61,8 @@ def test_milstein_level1_by_hand():
     mu, sigma = 0.07, 0.3
     sde = O.gbm(mu=mu, sigma=sigma, payoff=O.PAYOFF_X, scheme=1)
     tag = O.make_tag(O.KIND_STD, 1)
-    w = O.philox4x32_10(O.counters([4], 0, tag), O.seed_key(SEED))[0]
+    # path 4 at l = 1: words 0, 1 of call 0 of counter path field 2
+    w = O.philox4x32_10(O.counters([2], 0, tag), O.seed_key(SEED))[0]
     z = O.ndtri(O.uniforms(w))
     d = 0.5
     drift, diff, mil = mu * d, sigma * math.sqrt(d), 0.5 * sigma * sigma * d
