@@ -182,6 +182,16 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
         }
     };
 
+    auto call_of = [&](uint64_t cp, uint32_t j) {
+        return philox4x32_10(make_uint4((uint32_t)cp, (uint32_t)(cp >> 32), j, a.tag), a.k0, a.k1);
+    };
+    // Coarsest levels (a path needs at most half a call): paths 2k and 2k+1
+    // share call 0 of counter path field k, path p starting at word (or
+    // half) (p mod 2) 2^l.  p0 = path_offset + 2g has the launch's parity,
+    // so whether the pair's two paths share one call is uniform.
+    const uint64_t c0 = p0 >> 1, c1 = p1 >> 1;
+    const uint32_t o0 = (uint32_t)(p0 & 1) << a.l, o1 = (uint32_t)(p1 & 1) << a.l;
+
     if constexpr (ICDF == ICDF_TABLE16 && MODE == MODE_TWO) {
         // two 16-bit uniforms per word: fine step n takes half n mod 2 (low
         // half first) of word (n / 2) mod 4 of call n / 8
@@ -195,34 +205,39 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
             body16(half16_bits<false>(x0), half16_bits<false>(x1), q);
             body16(half16_bits<true>(x0), half16_bits<true>(x1), q + 1);
         };
-        const uint32_t ncalls16 = (nf + 7u) >> 3;
+        auto half_of = [](const uint4 &r, uint32_t h) {
+            const uint32_t w = word(r, (int)(h >> 1));
+            return (h & 1) ? half16_bits<true>(w) : half16_bits<false>(w);
+        };
+        if (nf <= 4) {
+            const uint4 ra = call_of(c0, 0);
+            const uint4 rb = c1 == c0 ? ra : call_of(c1, 0);
+            for (uint32_t n = 0; n < nf; ++n) body16(half_of(ra, o0 + n), half_of(rb, o1 + n), (int)n);
+        }
+        const uint32_t ncalls16 = nf <= 4 ? 0u : (nf + 7u) >> 3;
         for (uint32_t j = 0; j < ncalls16; ++j) {
             const uint4 r0 = philox4x32_10(make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), j, a.tag), a.k0, a.k1);
             const uint4 r1 = philox4x32_10(make_uint4((uint32_t)p1, (uint32_t)(p1 >> 32), j, a.tag), a.k0, a.k1);
-            if (nf >= 8) {
-                halves(r0.x, r1.x, 0);
-                halves(r0.y, r1.y, 2);
-                halves(r0.z, r1.z, 4);
-                halves(r0.w, r1.w, 6);
-            } else {
-                body16(half16_bits<false>(r0.x), half16_bits<false>(r1.x), 0);
-                if (nf >= 2) body16(half16_bits<true>(r0.x), half16_bits<true>(r1.x), 1);
-                if (nf >= 4) halves(r0.y, r1.y, 2);
-            }
+            halves(r0.x, r1.x, 0);
+            halves(r0.y, r1.y, 2);
+            halves(r0.z, r1.z, 4);
+            halves(r0.w, r1.w, 6);
         }
     } else {
-        for (uint32_t j = 0; j < ncalls; ++j) {
-            const uint4 r0 = philox4x32_10(make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), j, a.tag), a.k0, a.k1);
-            const uint4 r1 = philox4x32_10(make_uint4((uint32_t)p1, (uint32_t)(p1 >> 32), j, a.tag), a.k0, a.k1);
-            if (nf >= 4) {
-                body(r0.x, r1.x, 0);
-                body(r0.y, r1.y, 1);
-                body(r0.z, r1.z, 2);
-                body(r0.w, r1.w, 3);
-            } else {
-                body(r0.x, r1.x, 0);
-                if (nf == 2) body(r0.y, r1.y, 1);
-            }
+        if (nf <= 2) {
+            const uint4 ra = call_of(c0, 0);
+            const uint4 rb = c1 == c0 ? ra : call_of(c1, 0);
+            body(word(ra, (int)o0), word(rb, (int)o1), 0);
+            if (nf == 2) body(word(ra, (int)o0 + 1), word(rb, (int)o1 + 1), 1);
+        }
+        const uint32_t ncalls_full = nf <= 2 ? 0u : ncalls;
+        for (uint32_t j = 0; j < ncalls_full; ++j) {
+            const uint4 r0 = call_of(p0, j);
+            const uint4 r1 = call_of(p1, j);
+            body(r0.x, r1.x, 0);
+            body(r0.y, r1.y, 1);
+            body(r0.z, r1.z, 2);
+            body(r0.w, r1.w, 3);
         }
     }
 
