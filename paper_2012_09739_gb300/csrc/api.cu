@@ -216,7 +216,8 @@ mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int
     LevelArgs a = make_level_args(d, four, l, N, prec, icdf, p, seed, path_offset, set_id);
     const LaunchCfg cfg = level_launch_cfg(d, fn, a.npairs);
     const uint64_t chunks = (a.npairs + 31) / 32;
-    const uint64_t groups = (chunks + chunk_group(l) - 1) / chunk_group(l);
+    const uint64_t G = chunk_group(l, chunks);
+    const uint64_t groups = (chunks + G - 1) / G;
     a.chunk_partials = groups <= MAX_CHUNK_PARTIALS ? 1 : 0;
     const uint64_t slots = a.chunk_partials ? groups : (uint64_t)cfg.grid;
     const uint64_t fin = finalize_scratch(slots);

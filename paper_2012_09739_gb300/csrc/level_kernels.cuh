@@ -289,15 +289,26 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Chunks of 32 consecutive pairs (one per lane), in groups of
-// chunk_group(l) chunks (more at coarse levels, where a chunk is short).
-// With chunk_partials the grid is persistent: each warp takes the next group
-// from an atomic counter (a.counter, zeroed before the launch) until none is
-// left; its lanes accumulate the group's samples in FP32 (Kahan) and the warp
-// sum goes, in FP64, to the group's own slot, so the finalize kernel adds the
-// same values in the same order whatever the grid or the schedule.
-// Otherwise warp w takes chunks w, w + W, ... and one slot per block holds
-// the block's sum (warps added in FP64).
-__host__ __device__ __forceinline__ uint32_t chunk_group(int l) { return l >= 6 ? 1u : (64u >> l); }
+// chunk_group(l, chunks) chunks.  With chunk_partials the grid is persistent:
+// each warp takes the next group from an atomic counter (a.counter, zeroed
+// before the launch) until none is left; its lanes accumulate the group's
+// samples in FP32
+// (Kahan) and the warp sum goes, in FP64, to the group's own slot, so the
+// finalize kernel adds the same values in the same order whatever the grid
+// or the schedule.  Otherwise warp w takes chunks w, w + W, ... and one slot
+// per block holds the block's sum (warps added in FP64).
+//
+// Group size: up to 64 >> l chunks at coarse levels (where a chunk is
+// short), but at least GROUP_TARGET groups when there are enough chunks, so
+// that every resident warp gets several groups.  It depends on (l, N) only,
+// never on the device or the launch shape.
+constexpr uint64_t GROUP_TARGET = 16384;
+__host__ __device__ __forceinline__ uint32_t chunk_group(int l, uint64_t chunks) {
+    if (l >= 6) return 1u;
+    const uint64_t by_count = chunks / GROUP_TARGET;
+    const uint64_t g = by_count < (64u >> l) ? by_count : (64u >> l);
+    return g > 1 ? (uint32_t)g : 1u;
+}
 
 // Register budget: two-way kernels fit 64 registers (4 blocks of 256 per
 // SM); four-way kernels carry four paths per sample and get 80 (3 blocks),
@@ -318,7 +329,7 @@ __global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 1 : (MODE == MODE_FOUR
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     const uint64_t warp_id = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const uint64_t nchunks = (a.npairs + 31) >> 5;
-    const uint64_t G = a.chunk_partials ? chunk_group(a.l) : 1;
+    const uint64_t G = a.chunk_partials ? chunk_group(a.l, nchunks) : 1;
     for (uint64_t grp = warp_id;; grp += warps) {
         if (a.chunk_partials) {
             unsigned long long t = 0;
