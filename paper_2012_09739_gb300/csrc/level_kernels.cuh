@@ -148,6 +148,46 @@ __device__ __forceinline__ float payoff_of(float X, int payoff, float K, float d
     return __fmul_rn(disc, t > 0.0f ? t : 0.0f);
 }
 
+// Payoffs and differences of a simulated pair: D = P_f - P_c (two-way) or
+// (P^_f - P^_c) - (P-_f - P-_c) (four-way), in binary32; out0/out1 receive
+// the per-sample outputs (P_f, P_c, D) or (P^_f, P^_c, P-_f, P-_c, D).
+template <int MODE, class PP, class HP>
+__device__ __forceinline__ void pair_result(const LevelArgs &a, const PP &fine, const PP &coarse, const HP &hfine,
+                                            const HP &hcoarse, float &d0, float &d1, float *out0, float *out1) {
+    const float K = a.K32, disc = a.disc32;
+    const float2 xf = fine.X.f32(), xc = coarse.X.f32();
+    if (MODE == MODE_TWO) {
+        const float pf0 = payoff_of(xf.x, a.payoff, K, disc), pf1 = payoff_of(xf.y, a.payoff, K, disc);
+        float pc0 = 0.0f, pc1 = 0.0f;
+        if (a.l > 0) {
+            pc0 = payoff_of(xc.x, a.payoff, K, disc);
+            pc1 = payoff_of(xc.y, a.payoff, K, disc);
+            d0 = __fsub_rn(pf0, pc0);
+            d1 = __fsub_rn(pf1, pc1);
+        } else {
+            d0 = pf0;
+            d1 = pf1;
+        }
+        out0[0] = pf0; out0[1] = pc0; out0[2] = d0;
+        out1[0] = pf1; out1[1] = pc1; out1[2] = d1;
+    } else {
+        const float2 hf = hfine.X.f32(), hc = hcoarse.X.f32();
+        const float phf0 = payoff_of(hf.x, a.payoff, K, disc), phf1 = payoff_of(hf.y, a.payoff, K, disc);
+        const float pbf0 = payoff_of(xf.x, a.payoff, K, disc), pbf1 = payoff_of(xf.y, a.payoff, K, disc);
+        float phc0 = 0.0f, phc1 = 0.0f, pbc0 = 0.0f, pbc1 = 0.0f;
+        if (a.l > 0) {
+            phc0 = payoff_of(hc.x, a.payoff, K, disc);
+            phc1 = payoff_of(hc.y, a.payoff, K, disc);
+            pbc0 = payoff_of(xc.x, a.payoff, K, disc);
+            pbc1 = payoff_of(xc.y, a.payoff, K, disc);
+        }
+        d0 = __fsub_rn(__fsub_rn(phf0, phc0), __fsub_rn(pbf0, pbc0));
+        d1 = __fsub_rn(__fsub_rn(phf1, phc1), __fsub_rn(pbf1, pbc1));
+        out0[0] = phf0; out0[1] = phc0; out0[2] = pbf0; out0[3] = pbc0; out0[4] = d0;
+        out1[0] = phf1; out1[1] = phc1; out1[2] = pbf1; out1[3] = pbc1; out1[4] = d1;
+    }
+}
+
 // Simulates samples 2g and 2g+1 of the level described by `a` and returns
 // their differences D (d0, d1); out0/out1 receive the per-sample outputs
 // (P_f, P_c, D) or (P^_f, P^_c, P-_f, P-_c, D).
@@ -156,7 +196,6 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
                                               uint64_t g, float &d0, float &d1, float *out0, float *out1) {
     const uint32_t nf = 1u << a.l;
     const uint32_t ncalls = (nf + 3u) >> 2;
-    const float K = a.K32, disc = a.disc32;
     const uint64_t p0 = a.path_offset + 2 * g, p1 = p0 + 1;
     PathPair<P, KAHAN, SDE> fine, coarse;
     fine.template init<false>(a, false);
@@ -241,37 +280,7 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
         }
     }
 
-    const float2 xf = fine.X.f32(), xc = coarse.X.f32();
-    if (MODE == MODE_TWO) {
-        const float pf0 = payoff_of(xf.x, a.payoff, K, disc), pf1 = payoff_of(xf.y, a.payoff, K, disc);
-        float pc0 = 0.0f, pc1 = 0.0f;
-        if (a.l > 0) {
-            pc0 = payoff_of(xc.x, a.payoff, K, disc);
-            pc1 = payoff_of(xc.y, a.payoff, K, disc);
-            d0 = __fsub_rn(pf0, pc0);
-            d1 = __fsub_rn(pf1, pc1);
-        } else {
-            d0 = pf0;
-            d1 = pf1;
-        }
-        out0[0] = pf0; out0[1] = pc0; out0[2] = d0;
-        out1[0] = pf1; out1[1] = pc1; out1[2] = d1;
-    } else {
-        const float2 hf = hfine.X.f32(), hc = hcoarse.X.f32();
-        const float phf0 = payoff_of(hf.x, a.payoff, K, disc), phf1 = payoff_of(hf.y, a.payoff, K, disc);
-        const float pbf0 = payoff_of(xf.x, a.payoff, K, disc), pbf1 = payoff_of(xf.y, a.payoff, K, disc);
-        float phc0 = 0.0f, phc1 = 0.0f, pbc0 = 0.0f, pbc1 = 0.0f;
-        if (a.l > 0) {
-            phc0 = payoff_of(hc.x, a.payoff, K, disc);
-            phc1 = payoff_of(hc.y, a.payoff, K, disc);
-            pbc0 = payoff_of(xc.x, a.payoff, K, disc);
-            pbc1 = payoff_of(xc.y, a.payoff, K, disc);
-        }
-        d0 = __fsub_rn(__fsub_rn(phf0, phc0), __fsub_rn(pbf0, pbc0));
-        d1 = __fsub_rn(__fsub_rn(phf1, phc1), __fsub_rn(pbf1, pbc1));
-        out0[0] = phf0; out0[1] = phc0; out0[2] = pbf0; out0[3] = pbc0; out0[4] = d0;
-        out1[0] = phf1; out1[1] = phc1; out1[2] = pbf1; out1[3] = pbc1; out1[4] = d1;
-    }
+    pair_result<MODE>(a, fine, coarse, hfine, hcoarse, d0, d1, out0, out1);
 }
 
 __device__ __forceinline__ void stage_table(SmemTable &tab, const DevTables *t) {

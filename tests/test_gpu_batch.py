@@ -88,3 +88,24 @@ def test_batch_config3_full_size_statistics():
         var = sum(max(g.s2 / g.n - (g.s1 / g.n) ** 2, 0.0) / g.n for g in got[k * per:(k + 1) * per])
         bs = mlmc.bs_call(mu=s["mu"], sigma=s["sigma"], K=s["K"])
         assert abs(est - bs) < 5 * math.sqrt(var) + 2e-3
+
+
+@pytest.mark.parametrize("prec,icdf,scheme", [(M.MLMC_F16, M.MLMC_ICDF_TABLE, 0), (M.MLMC_F32, M.MLMC_ICDF_TABLE16, 0),
+                                              (M.MLMC_BF16, M.MLMC_ICDF_CUBIC, 0), (M.MLMC_F16, M.MLMC_ICDF_TABLE16, 1)])
+def test_single_pair_deep_items_exact(prec, icdf, scheme):
+    """Items of one pair at deep levels run warp-cooperatively (the lanes
+    generate 32 steps' normals, one lane steps the paths): their sums equal
+    the level kernels' exactly, two-way and four-way, even and odd path
+    offsets."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0, scheme=scheme)
+    po = M.sde_params(sde=M.MLMC_OU, payoff=M.MLMC_PAYOFF_X, p0=2.0, p1=0.3, p2=0.5)
+    cases = [(p, 0, 16, 1, 0), (p, 1, 16, 1, 3), (p, 1, 14, 2, 8), (p, 0, 12, 2, 5), (po, 1, 11, 1, 2),
+             (po, 0, 10, 2, 7)]
+    items = [M.mlmc_work(pp, l, kind, prec, 1, icdf, 0, N, off) for pp, kind, l, N, off in cases]
+    got = M.mlmc_batch(items, SEED)
+    for (pp, kind, l, N, off), g in zip(cases, got):
+        fn = M.mlmc_nested_level if kind else M.mlmc_level
+        ref = fn(l, N, prec, True, icdf, pp, SEED, off)
+        assert g.n == ref.n and g.s1 == ref.s1 and g.s2 == ref.s2, (kind, l, N, off, g.s1, ref.s1)
