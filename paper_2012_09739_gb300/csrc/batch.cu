@@ -132,16 +132,16 @@ cudaError_t grow(T **p, size_t *cap, size_t n) {
 }  // namespace
 
 struct BatchCache {
+    // descriptors, uploaded by one copy: items, tiles, per-item tile lists
+    // and the schedule counters (zeroed by the same copy), 16-byte aligned
+    unsigned char *blob = nullptr;
+    size_t blob_cap = 0;
     LevelArgs *items = nullptr;
-    size_t items_cap = 0;
     Tile *tiles = nullptr;
-    size_t tiles_cap = 0;
+    uint32_t *start = nullptr, *list = nullptr;
+    uint32_t *counters = nullptr;
     double2 *partials = nullptr;
     size_t partials_cap = 0;
-    uint32_t *start = nullptr, *list = nullptr;
-    size_t start_cap = 0, list_cap = 0;
-    uint32_t *counters = nullptr;
-    size_t counters_cap = 0;
     double2 *sums = nullptr;
     size_t sums_cap = 0;
     double2 *sums_host = nullptr;
@@ -153,6 +153,7 @@ struct BatchCache {
     uint64_t sig = 0;
     std::vector<double> weight;
     std::map<uint64_t, int> tuned;       // item-list signature -> lane_work_log2
+    std::map<const void *, int> occupancy;   // batch kernel -> resident blocks per SM
 };
 
 BatchCache *batch_cache_create() { return new BatchCache(); }
@@ -160,12 +161,8 @@ BatchCache *batch_cache_create() { return new BatchCache(); }
 void batch_cache_destroy(BatchCache *c) {
     if (!c) return;
     if (c->exec) cudaGraphExecDestroy(c->exec);
-    cudaFree(c->items);
-    cudaFree(c->tiles);
+    cudaFree(c->blob);
     cudaFree(c->partials);
-    cudaFree(c->start);
-    cudaFree(c->list);
-    cudaFree(c->counters);
     cudaFree(c->sums);
     if (c->sums_host) cudaFreeHost(c->sums_host);
     if (c->stage) cudaFreeHost(c->stage);
@@ -189,13 +186,7 @@ namespace {
 mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     cudaError_t e;
     const size_t n = p.items.size();
-    if ((e = grow(&c.items, &c.items_cap, n)) != cudaSuccess) return cuda_fail(e, "batch buffers");
-    if ((e = grow(&c.tiles, &c.tiles_cap, p.ntiles)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if ((e = grow(&c.partials, &c.partials_cap, p.ntiles)) != cudaSuccess) return cuda_fail(e, "batch buffers");
-    if ((e = grow(&c.start, &c.start_cap, p.start.size())) != cudaSuccess) return cuda_fail(e, "batch buffers");
-    if ((e = grow(&c.list, &c.list_cap, std::max<size_t>(p.list.size(), 1))) != cudaSuccess)
-        return cuda_fail(e, "batch buffers");
-    if ((e = grow(&c.counters, &c.counters_cap, p.groups.size())) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if ((e = grow(&c.sums, &c.sums_cap, n)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if (c.sums_host_cap < n) {
         if (c.sums_host) cudaFreeHost(c.sums_host);
@@ -204,9 +195,18 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
         if ((e = cudaMallocHost(&c.sums_host, n * sizeof(double2))) != cudaSuccess) return cuda_fail(e, "pinned");
         c.sums_host_cap = n;
     }
+    auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const size_t b_items = n * sizeof(LevelArgs), b_tiles = (size_t)p.ntiles * sizeof(Tile);
-    const size_t b_start = p.start.size() * 4, b_list = p.list.size() * 4;
-    const size_t total = b_items + b_tiles + b_start + b_list;
+    const size_t b_start = p.start.size() * 4, b_list = std::max<size_t>(p.list.size(), 1) * 4;
+    const size_t b_cnt = p.groups.size() * 4;
+    const size_t o_tiles = up16(b_items), o_start = o_tiles + up16(b_tiles), o_list = o_start + up16(b_start);
+    const size_t o_cnt = o_list + up16(b_list), total = o_cnt + up16(b_cnt);
+    if ((e = grow(&c.blob, &c.blob_cap, total)) != cudaSuccess) return cuda_fail(e, "batch buffers");
+    c.items = reinterpret_cast<LevelArgs *>(c.blob);
+    c.tiles = reinterpret_cast<Tile *>(c.blob + o_tiles);
+    c.start = reinterpret_cast<uint32_t *>(c.blob + o_start);
+    c.list = reinterpret_cast<uint32_t *>(c.blob + o_list);
+    c.counters = reinterpret_cast<uint32_t *>(c.blob + o_cnt);
     if (c.stage_cap < total) {
         if (c.stage) cudaFreeHost(c.stage);
         c.stage = nullptr;
@@ -214,35 +214,41 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
         if ((e = cudaMallocHost(&c.stage, total * 2)) != cudaSuccess) return cuda_fail(e, "pinned");
         c.stage_cap = total * 2;
     }
-    // the previous round's copies out of the staging buffer must be done
+    // the previous round's copy out of the staging buffer must be done
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload");
     unsigned char *h = c.stage;
+    memset(h, 0, total);
     memcpy(h, p.items.data(), b_items);
-    size_t off = b_items;
+    size_t off = o_tiles;
     for (const auto &g : p.groups) {
         memcpy(h + off, g.tiles.data(), g.tiles.size() * sizeof(Tile));
         off += g.tiles.size() * sizeof(Tile);
     }
-    memcpy(h + off, p.start.data(), b_start);
-    if (b_list) memcpy(h + off + b_start, p.list.data(), b_list);
-    if ((e = cudaMemcpyAsync(c.items, h, b_items, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(c.tiles, h + b_items, b_tiles, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(c.start, h + off, b_start, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (b_list && (e = cudaMemcpyAsync(c.list, h + off + b_start, b_list, cudaMemcpyHostToDevice, s)) != cudaSuccess))
-        return cuda_fail(e, "upload");
+    memcpy(h + o_start, p.start.data(), b_start);
+    if (!p.list.empty()) memcpy(h + o_list, p.list.data(), p.list.size() * 4);
+    if ((e = cudaMemcpyAsync(c.blob, h, total, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(e, "upload");
     return MLMC_OK;
 }
 
 // Enqueues the whole batch on stream s (also used inside graph capture).
-mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStream_t s, bool copy_out) {
+// zero_counters: reset the schedule counters on the stream (a replayed graph
+// needs it; a fresh upload has zeroed them already).
+mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStream_t s, bool copy_out,
+                    bool zero_counters) {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(c.counters, 0, p.groups.size() * sizeof(uint32_t), s)) != cudaSuccess)
+    if (zero_counters && (e = cudaMemsetAsync(c.counters, 0, p.groups.size() * sizeof(uint32_t), s)) != cudaSuccess)
         return cuda_fail(e, "memset");
     for (size_t gi = 0; gi < p.groups.size(); ++gi) {
         const Group &g = p.groups[gi];
         BatchKernelFn fn = pick_batch_kernel(g.prec, g.kahan, g.icdf);
         int bps = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 256, 0) != cudaSuccess || bps < 1) bps = 1;
+        auto it = c.occupancy.find((const void *)fn);
+        if (it != c.occupancy.end()) {
+            bps = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 256, 0) != cudaSuccess || bps < 1) bps = 1;
+            c.occupancy[(const void *)fn] = bps;
+        }
         const uint32_t warps_needed = (uint32_t)g.tiles.size();
         uint32_t grid = (uint32_t)bps * d.sm_count;
         grid = std::min<uint32_t>(grid, (warps_needed + 7) / 8);
@@ -278,7 +284,7 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
         Plan p = make_plan(d, w, n, seed, lw);
         if ((st = upload(c, p, s))) break;
         cudaEventRecord(a, s);
-        if ((st = enqueue(d, c, p, s, false))) break;
+        if ((st = enqueue(d, c, p, s, false, true))) break;
         cudaEventRecord(b, s);
         if ((st = wait_event(b, wait_limit_s()))) break;
         float ms = 0.0f;
@@ -310,7 +316,7 @@ mlmc_status batch_round(const DeviceState &d, BatchCache &c, const mlmc_work *w,
     Plan p = make_plan(d, w, n, seed, lw);
     mlmc_status st = upload(c, p, s);
     if (st) return st;
-    return enqueue(d, c, p, s, true);
+    return enqueue(d, c, p, s, true, false);
 }
 
 const double2 *batch_sums_host(const BatchCache &c) { return c.sums_host; }
@@ -379,7 +385,7 @@ extern "C" mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t 
         cudaGraph_t g;
         cudaError_t e = cudaStreamBeginCapture(c.capture_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        st = enqueue(*d, c, p, c.capture_stream, true);
+        st = enqueue(*d, c, p, c.capture_stream, true, true);
         e = cudaStreamEndCapture(c.capture_stream, &g);
         if (st) return st;
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
