@@ -259,22 +259,25 @@ mlmc_status level_sync(int four, int l, uint64_t N, int prec, int kahan, int icd
     if ((st = device_state(&d))) return st;
     if (icdf == MLMC_ICDF_MLP && !d->mlp_ready) return fail(MLMC_ENOTREADY, "MLP weights not set");
     cudaStream_t s = (cudaStream_t)stream;
+    // the finalize kernel writes the two sums straight into pinned host
+    // memory (device-accessible under unified addressing); the events are
+    // the calling thread's own, created once
     double *host = host_staging();
     if (!host) return fail(MLMC_ENOMEM, "cudaMallocHost");
-    double *sums_dev = nullptr;
-    cudaError_t e = cudaMallocAsync(&sums_dev, 2 * sizeof(double), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
-    cudaEvent_t ev0, ev1;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
-    st = enqueue_level(*d, four, l, N, prec, kahan, icdf, p, seed, path_offset, 0, sums_dev, nullptr, s, ev0, ev1);
-    if (st == MLMC_OK) {
-        e = cudaMemcpyAsync(host, sums_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync");
+    struct Events {
+        cudaEvent_t t0 = nullptr, t1 = nullptr, done = nullptr;
+    };
+    static thread_local Events evs[MAX_DEVICES];
+    Events &E = evs[d->device];
+    if (!E.done) {
+        if (cudaEventCreate(&E.t0) != cudaSuccess || cudaEventCreate(&E.t1) != cudaSuccess ||
+            cudaEventCreateWithFlags(&E.done, cudaEventDisableTiming) != cudaSuccess) {
+            E.done = nullptr;
+            return fail(MLMC_ECUDA, "cudaEventCreate");
+        }
     }
-    cudaFreeAsync(sums_dev, s);
-    cudaEvent_t done;
-    cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    cudaEvent_t ev0 = E.t0, ev1 = E.t1, done = E.done;
+    st = enqueue_level(*d, four, l, N, prec, kahan, icdf, p, seed, path_offset, 0, host, nullptr, s, ev0, ev1);
     cudaEventRecord(done, s);
     if (st == MLMC_OK) st = wait_event(done, wait_limit_s());
     if (st == MLMC_OK) {
@@ -285,9 +288,6 @@ mlmc_status level_sync(int four, int l, uint64_t N, int prec, int kahan, int icd
         out->n = N;
         out->cost_ns = (double)ms * 1e6;
     }
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-    cudaEventDestroy(done);
     return st;
 }
 

@@ -257,11 +257,11 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch kernel");
     }
     const int n = (int)p.items.size();
-    batch_finalize_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(c.partials, c.start, c.list, n, c.sums);
+    // copy_out: the finalize kernel writes the sums straight into the pinned
+    // host buffer (device-accessible under unified addressing), no copy
+    double2 *dst = copy_out ? c.sums_host : c.sums;
+    batch_finalize_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(c.partials, c.start, c.list, n, dst);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch finalize");
-    if (copy_out &&
-        (e = cudaMemcpyAsync(c.sums_host, c.sums, n * sizeof(double2), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_fail(e, "copy");
     return MLMC_OK;
 }
 
