@@ -34,9 +34,23 @@ SEED = 1234
 WORKLOAD = "GBM call, levels 0..12, N=2^20 per level, two-way + four-way, FP16+Kahan table vs FP32"
 
 # Algorithmic lane-instructions per fine path-step (one sample of one
-# estimator), counted from the method's operations; derivation in the design doc.
+# estimator), counted from the method's operations in their minimal form on
+# this ISA (a wide 32x32 multiply and a three-input XOR count one each;
+# binary16 work per f16x2 operation, i.e. half per sample):
+#   Philox (1/4 call x 10 rounds x (2 multiplies + 2 XOR))      10
+#   uniform and mirror (funnel shift, three adds)                 4
+#   table normal (exponent, lookup, v -> f16, mul, add, sign)     4
+#   fine Euler + Kahan (8 f16x2 ops per pair)                     4
+#   coarse Euler + Kahan (9 per pair per 2 fine steps)            2.25
+#   four-way only: exact normal in FP32                          17
+#   four-way only: hat fine + coarse Euler + Kahan in FP32       12.5
 OPS_FOURWAY_F16K_TABLE = 53.75
 OPS_TWOWAY_F16K_TABLE = 24.25
+# DRAM bytes (read + write) of one four-way level launch, from an ncu
+# capture of the kernel (l = 10, N = 2^18): the launch arguments and the
+# table; the per-group partial sums stay in L2.  The traffic does not grow
+# with the path-steps, so it is reported as measured, not scaled.
+TRAFFIC_FOURWAY_BYTES = 34304
 
 
 def _env_rank():
@@ -276,7 +290,9 @@ def run_gpu(args):
             "note": "approximate normals from 16-bit uniforms (two per Philox word on two-way paths)"},
         "roofline": {"bound": "alu", "kernel": "level_kernel<FOUR,F16,kahan,TABLE,GBM>",
                      "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-                     "traffic": None,
+                     "traffic": TRAFFIC_FOURWAY_BYTES,
+                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (l=10, N=2^18); "
+                                      "independent of the path-steps",
                      "ops_per_path_step": OPS_FOURWAY_F16K_TABLE,
                      "peak_basis": f"{sm_count} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock sampled)",
                      "launches": four_launches},
