@@ -42,9 +42,10 @@ WORKLOAD = "GBM call, levels 0..12, N=2^20 per level, two-way + four-way, FP16+K
 #   table normal (exponent, lookup, v -> f16, mul, add, sign)     4
 #   fine Euler + Kahan (8 f16x2 ops per pair)                     4
 #   coarse Euler + Kahan (9 per pair per 2 fine steps)            2.25
-#   four-way only: exact normal in FP32                          17
+#   four-way only: exact normal in FP32 (binade lookup, local
+#     variable, 7 FMA Horner, centring, sign)                    14
 #   four-way only: hat fine + coarse Euler + Kahan in FP32       12.5
-OPS_FOURWAY_F16K_TABLE = 53.75
+OPS_FOURWAY_F16K_TABLE = 50.75
 OPS_TWOWAY_F16K_TABLE = 24.25
 # DRAM bytes (read + write) of one four-way level launch, from an ncu
 # capture of the kernel (l = 10, N = 2^18): the launch arguments and the

@@ -74,7 +74,7 @@ __device__ void simulate_pair_seq(const LevelArgs &a, const SmemTable &tab, cons
         } else {
             const uint32_t w0 = sc.w[0][lane], w1 = sc.w[1][lane];
             sc.zb[lane] = icdf_pair<P, ICDF>(tab, mlp, w0, w1);
-            if (MODE == MODE_FOUR) sc.zh[lane] = Pair<P_F32>::of2(exact_z(w0), exact_z(w1));
+            if (MODE == MODE_FOUR) sc.zh[lane] = Pair<P_F32>::of2(exact_z(tab, w0), exact_z(tab, w1));
         }
         __syncwarp();
         if (lane == 0) {
@@ -103,10 +103,8 @@ __global__ void __launch_bounds__(256) batch_kernel(const LevelArgs *items, cons
                                                     const DevTables *tabs) {
     __shared__ SmemTable tab;
     __shared__ SeqScratch<P> seq[8];           // one per warp (warp-cooperative single pairs)
-    if (ICDF == ICDF_TABLE || ICDF == ICDF_TABLE16 || ICDF == ICDF_CUBIC) {
-        stage_table(tab, tabs);
-        __syncthreads();
-    }
+    stage_table(tab, tabs);
+    __syncthreads();
     MlpFrags mlp;
     if (ICDF == ICDF_MLP) mlp.load(items[0].mlp);
     const uint32_t lane = threadIdx.x & 31;

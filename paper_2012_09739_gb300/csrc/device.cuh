@@ -200,6 +200,7 @@ struct SmemTable {
     uint2 q16[TAB_ENTRIES];      // cubic in binary16: (d0 | d1 << 16, d2 | d3 << 16)
     uint2 qbf[TAB_ENTRIES];      // cubic in bfloat16, same packing
     float2 qab[TAB_ENTRIES];     // cubic local variable s = A v - B as (A, -B)
+    float4 ex[TAB_ENTRIES][2];   // exact normal: q0..q7 of Phi^-1(v) = (v - 1/2) q(s), one binade each
 };
 
 // The per-device tables: the entries staged by the kernels, and the FP64
@@ -218,12 +219,30 @@ __device__ __forceinline__ int tab_index(float v) {
     return e - 103;
 }
 
-// Exact normal in FP32: Phi^-1(v) (CUDA's normcdfinvf) with the sign of the
+// Exact normal in binary32 on the uniform grid (v >= 2^-24): on the binade
+// [2^(E-127), 2^(E-126)) of v, Phi^-1(v) = (v - 1/2) q(s) with s = v 2^(128-E)
+// - 3 in [-1, 1) (exact: v's significand under the exponent of 2, minus 3)
+// and q of degree 7 interpolating Phi^-1(v)/(v - 1/2) at the Chebyshev
+// points (built on the device from FP64 Phi^-1); FMA Horner.  Measured
+// against FP64 over the whole grid: at most 2.5 ulp.  The sign is the
 // word's half.
-__device__ __forceinline__ float exact_z(uint32_t w) {
-    const float z = normcdfinvf(mirrored_v(w));
+__device__ __forceinline__ float exact_zv(const SmemTable &t, uint32_t w, float v) {
+    const uint32_t vb = __float_as_uint(v);
+    const int i = (int)(vb >> 23) - 103;
+    const float s = __fsub_rn(__uint_as_float((vb & 0x007FFFFFu) | 0x40000000u), 3.0f);
+    const float4 a = t.ex[i][0], b = t.ex[i][1];
+    float q = __fmaf_rn(b.w, s, b.z);
+    q = __fmaf_rn(q, s, b.y);
+    q = __fmaf_rn(q, s, b.x);
+    q = __fmaf_rn(q, s, a.w);
+    q = __fmaf_rn(q, s, a.z);
+    q = __fmaf_rn(q, s, a.y);
+    q = __fmaf_rn(q, s, a.x);
+    const float z = __fmul_rn(__fsub_rn(v, 0.5f), q);
     return __uint_as_float(__float_as_uint(z) ^ (w & 0x80000000u));
 }
+
+__device__ __forceinline__ float exact_z(const SmemTable &t, uint32_t w) { return exact_zv(t, w, mirrored_v(w)); }
 
 // Piecewise-linear Z~ in binary32: z = R(c0 + R(c1 v)), negated for u > 1/2.
 // The sign is bit 31 of w (SIGN15: bit 15, for half16_bits words).

@@ -120,7 +120,7 @@ __device__ __forceinline__ Pair<P> table_pair(const SmemTable &s, uint32_t w0, u
 template <int P, int ICDF>
 __device__ __forceinline__ Pair<P> icdf_pair(const SmemTable &s, const MlpFrags &mlp, uint32_t w0, uint32_t w1) {
     if constexpr (ICDF == ICDF_EXACT) {
-        return Pair<P>::of2(exact_z(w0), exact_z(w1));
+        return Pair<P>::of2(exact_z(s, w0), exact_z(s, w1));
     } else if constexpr (ICDF == ICDF_TABLE) {
         return table_pair<P, false>(s, w0, w1, mirrored_v(w0), mirrored_v(w1));
     } else if constexpr (ICDF == ICDF_CUBIC) {
@@ -214,7 +214,7 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
         if (q & 1) coarse.step(add(zprev, z));
         else zprev = z;
         if (MODE == MODE_FOUR) {
-            const Pair<P_F32> zh = Pair<P_F32>::of2(exact_z(w0), exact_z(w1));
+            const Pair<P_F32> zh = Pair<P_F32>::of2(exact_z(tab, w0), exact_z(tab, w1));
             hfine.step(zh);
             if (q & 1) hcoarse.step(add(zhprev, zh));
             else zhprev = zh;
@@ -327,7 +327,7 @@ template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
 __global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 1 : (MODE == MODE_FOUR ? 3 : 4)) level_kernel(const LevelArgs a) {
     __shared__ SmemTable tab;
     __shared__ double red[2][32];
-    if (ICDF == ICDF_TABLE || ICDF == ICDF_TABLE16 || ICDF == ICDF_CUBIC) {
+    if (ICDF != ICDF_MLP || MODE == MODE_FOUR) {
         stage_table(tab, a.tabs);
         __syncthreads();
     }

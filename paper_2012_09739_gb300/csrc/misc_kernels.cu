@@ -50,6 +50,42 @@ __device__ void gauss_legendre_node(int i, double &x, double &w) {
     w = 2.0 / ((1.0 - x * x) * dp * dp);
 }
 
+// Exact-normal polynomial of table entry i (binade E = 103 + i of v):
+// Phi^-1(v) / (v - 1/2) interpolated at the 8 Chebyshev points of
+// s = v 2^(128-E) - 3 in [-1, 1], returned as monomial coefficients in s.
+__device__ void exact_poly(int i, double q[8]) {
+    constexpr int n = 8;
+    const double A = ldexp(1.0, 128 - (103 + i));
+    double y[n], x[n];
+    for (int k = 0; k < n; ++k) {
+        x[k] = cos(3.14159265358979323846 * (k + 0.5) / n);
+        const double v = (x[k] + 3.0) / A;
+        y[k] = normcdfinv(v) / (v - 0.5);
+    }
+    // Chebyshev coefficients c_j = (2/n) sum_k y_k T_j(x_k), c_0 halved
+    double c[n];
+    for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc += y[k] * cos(j * acos(x[k]));
+        c[j] = acc * 2.0 / n;
+    }
+    c[0] *= 0.5;
+    // sum_j c_j T_j(s) in powers of s (T_{j+1} = 2 s T_j - T_{j-1})
+    double tm[n], t0[n], t1[n];
+    for (int m = 0; m < n; ++m) q[m] = t0[m] = t1[m] = 0.0;
+    t0[0] = 1.0;
+    t1[1] = 1.0;
+    for (int m = 0; m < n; ++m) q[m] += c[0] * t0[m] + c[1] * t1[m];
+    for (int j = 2; j < n; ++j) {
+        for (int m = 0; m < n; ++m) tm[m] = (m > 0 ? 2.0 * t1[m - 1] : 0.0) - t0[m];
+        for (int m = 0; m < n; ++m) {
+            q[m] += c[j] * tm[m];
+            t0[m] = t1[m];
+            t1[m] = tm[m];
+        }
+    }
+}
+
 __device__ __forceinline__ int entry_interval(int entry) {     // 0-based interval of table entry E - 103
     return min(126 - (103 + entry), 16) - 1;
 }
@@ -139,6 +175,12 @@ __global__ void __launch_bounds__(BUILD_THREADS) build_table_kernel(DevTables *o
                                    (uint32_t)f64_to_bf16(d[2]) | ((uint32_t)f64_to_bf16(d[3]) << 16));
         const int k = iv + 1;
         out->e.qab[i] = make_float2(k < 16 ? ldexpf(1.0f, k + 2) : 131072.0f, k < 16 ? -3.0f : -1.0f);
+        double q[8];
+        exact_poly(i, q);
+        out->e.ex[i][0] = make_float4(__double2float_rn(q[0]), __double2float_rn(q[1]), __double2float_rn(q[2]),
+                                      __double2float_rn(q[3]));
+        out->e.ex[i][1] = make_float4(__double2float_rn(q[4]), __double2float_rn(q[5]), __double2float_rn(q[6]),
+                                      __double2float_rn(q[7]));
     }
 }
 
@@ -256,7 +298,9 @@ __global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const DevTab
         for (int h = 0; h < 2; ++h) {
             if (idx[h] >= n) continue;
             if (ICDF == ICDF_EXACT) {
-                r[h] = __uint_as_float(__float_as_uint(normcdfinvf(v[h])) ^ sg[h]);
+                // the kernels' polynomial on the grid's range, CUDA's normcdfinvf below it
+                r[h] = v[h] >= 0x1p-24f ? exact_zv(tab, sg[h], v[h])
+                                        : __uint_as_float(__float_as_uint(normcdfinvf(v[h])) ^ sg[h]);
             } else if (ICDF == ICDF_CUBIC) {
                 if (P == P_F16) {
                     static_cast<__half *>(z)[idx[h]] = __low2half(cubic_z16<true>(tab, sg[h], sg[h], v[h], v[h]));
