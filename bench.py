@@ -51,7 +51,7 @@ OPS_TWOWAY_F16K_TABLE = 24.25
 # capture of the kernel (l = 10, N = 2^18): the launch arguments and the
 # table; the per-group partial sums stay in L2.  The traffic does not grow
 # with the path-steps, so it is reported as measured, not scaled.
-TRAFFIC_FOURWAY_BYTES = 34304
+TRAFFIC_FOURWAY_BYTES = 29440
 
 
 def _env_rank():

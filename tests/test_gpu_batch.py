@@ -109,3 +109,22 @@ def test_single_pair_deep_items_exact(prec, icdf, scheme):
         fn = M.mlmc_nested_level if kind else M.mlmc_level
         ref = fn(l, N, prec, True, icdf, pp, SEED, off)
         assert g.n == ref.n and g.s1 == ref.s1 and g.s2 == ref.s2, (kind, l, N, off, g.s1, ref.s1)
+
+
+def test_single_pair_deep_items_with_mlp_exact():
+    """The MLP normals in the warp-cooperative mode: every lane evaluates the
+    network for a different step instead of a different sample; each row of
+    the tensor-core products is computed alone, so the sums still equal the
+    level kernels' exactly."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from workloads import mlp_initial_weights
+    M.mlmc_mlp_set_weights(mlp_initial_weights(7))
+    p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    cases = [(0, 12, 1, 0), (1, 13, 2, 4), (1, 10, 1, 1)]
+    items = [M.mlmc_work(p, l, kind, M.MLMC_F16, 1, M.MLMC_ICDF_MLP, 0, N, off) for kind, l, N, off in cases]
+    got = M.mlmc_batch(items, SEED)
+    for (kind, l, N, off), g in zip(cases, got):
+        fn = M.mlmc_nested_level if kind else M.mlmc_level
+        ref = fn(l, N, M.MLMC_F16, True, M.MLMC_ICDF_MLP, p, SEED, off)
+        assert g.n == ref.n and g.s1 == ref.s1 and g.s2 == ref.s2, (kind, l, N, off)

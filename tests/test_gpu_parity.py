@@ -136,6 +136,25 @@ def test_approx_icdf_exact_bf16_is_rounded_fp32():
     assert np.array_equal(_z_host(zb, M.MLMC_BF16), O.round_bits(z32.cpu().numpy().astype(np.float64), O.BF16))
 
 
+def test_exact_icdf_whole_grid_within_3_ulp():
+    """The kernels' exact normal (per-binade polynomial) at every point of the
+    24-bit uniform grid against the oracle's FP64 inverse CDF: within 3 ulp
+    of the result, exactly antisymmetric."""
+    dev = _dev()
+    lower = (2 * np.arange(1 << 22) + 1) * 2.0 ** -24          # all 2^22 grid points below 1/2
+    u = np.concatenate([lower, 1.0 - lower]).astype(np.float32)
+    z = torch.empty(u.size, dtype=torch.float32, device=dev)
+    M.approx_icdf(torch.from_numpy(u).to(dev), z, M.MLMC_ICDF_EXACT, M.MLMC_F32)
+    torch.cuda.synchronize()
+    zz = z.cpu().numpy()
+    ref = O.ndtri(u.astype(np.float64))
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    err_ulp = np.abs(zz.astype(np.float64) - ref) / ulp
+    assert err_ulp.max() <= 3.0, err_ulp.max()
+    assert err_ulp.mean() < 0.8
+    assert np.all(zz[lower.size:] == -zz[:lower.size])
+
+
 def test_exact_icdf_fp32_accuracy():
     dev = _dev()
     lower = (2 * np.arange(0, 1 << 22, 7) + 1) * 2.0 ** -24          # grid points below 1/2
