@@ -248,8 +248,8 @@ def run_gpu(args):
     batch = None if args.no_batch else batch_leg(M, torch, stream)
 
     # --- time to RMSE eps through mlmc_run: nested FP16+Kahan vs plain FP32
-    tte = None if args.no_tte else time_to_eps(M, params, [args.eps, 1e-5])
     mlp = None if args.no_mlp else mlp_leg(M, torch, params)
+    tte = None if args.no_tte else time_to_eps(M, params, [args.eps, 3e-4, 1e-5], with_mlp=mlp is not None)
 
     # --- roofline of the dominant kernel (four-way FP16+Kahan table)
     clk = clocks.summary()
@@ -358,7 +358,7 @@ def batch_leg(M, torch, stream, repeats=5):
                       "device_seconds from CUDA events around the graph launch"}
 
 
-def time_to_eps(M, params, eps_list, repeats=3):
+def time_to_eps(M, params, eps_list, repeats=3, with_mlp=False):
     """Wall time of mlmc_run to RMSE eps (Sec. 3 adaptive MLMC): the standard
     estimator (FP32, exact normals, plain Euler) against the nested estimator
     with FP16 + Kahan table normals, FP32 table normals, and the per-level
@@ -373,6 +373,8 @@ def time_to_eps(M, params, eps_list, repeats=3):
                 ("plain_fp32_exact_milstein", 0, M.MLMC_F32, 0, T, MIL),
                 ("nested_f16_kahan_table16_milstein", 1, M.MLMC_F16, 1, T16, MIL),
                 ("nested_auto_table16_milstein", 1, -1, 0, T16, MIL))
+    if with_mlp:       # the network trained by the MLP leg
+        variants += (("nested_f16_kahan_mlp", 1, M.MLMC_F16, 1, M.MLMC_ICDF_MLP, E),)
     out = {}
     for eps in eps_list:
         row = {}
@@ -407,13 +409,16 @@ def time_to_eps(M, params, eps_list, repeats=3):
 
 
 def mlp_leg(M, torch, params, steps=20000, level=10, n=1 << 20):
-    """The learned part: train the FP16 tensor-core MLP surrogate on 2^20
+    """The learned part: train the FP16 tensor-core MLP surrogate on 2^24
     (u, |Phi^-1|) pairs (targets computed on the device in FP64), then its
-    E|Z - Z~|^2 against the table's and the four-way throughput with it."""
+    E|Z - Z~|^2 against the table's, the four-way throughput with it, and the
+    learned-part workload: the nested step (two-way + four-way, FP16+Kahan)
+    over levels 0..10 with N = 2^22 per level with the network and with the
+    table, beside the plain FP32 exact two-way over the same levels."""
     from workloads import mlp_initial_weights, uniform_grid_sample
     dev = torch.device("cuda")
     M.mlmc_mlp_set_weights(mlp_initial_weights(1234))
-    u = torch.tensor(uniform_grid_sample(1 << 20, 31), dtype=torch.float32, device=dev)
+    u = torch.tensor(uniform_grid_sample(1 << 24, 31), dtype=torch.float32, device=dev)
     opts = M.mlmc_train_opts(steps=steps, batch=8192, lr0=1e-2, lr_min=1e-5, beta1=0.9, beta2=0.999, eps=1e-8,
                              seed=SEED)
     torch.cuda.synchronize()
@@ -439,9 +444,30 @@ def mlp_leg(M, torch, params, steps=20000, level=10, n=1 << 20):
         e1.record(s)
         torch.cuda.synchronize()
         rates[name] = 3 * n * (1 << level) / (e0.elapsed_time(e1) / 1e3)
-    return {"train_seconds": train_s, "steps": steps, "batch": 8192, "pairs": 1 << 20, "final_loss": loss,
+    # learned-part workload: levels 0..10, N = 2^22
+    n4, levels4 = 1 << 22, range(0, 11)
+    steps4 = sum(n4 * (1 << l) for l in levels4)
+    legs = {}
+    for name, kind, prec, kahan, icdf in (("nested_f16_kahan_mlp", 2, M.MLMC_F16, 1, M.MLMC_ICDF_MLP),
+                                          ("nested_f16_kahan_table", 2, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE),
+                                          ("plain_fp32_exact", 1, M.MLMC_F32, 0, M.MLMC_ICDF_EXACT)):
+        def one():
+            for l in levels4:
+                M.mlmc_level_async(0, l, n4, prec, kahan, icdf, params, SEED, 0, sums, s.cuda_stream)
+                if kind == 2:
+                    M.mlmc_level_async(1, l, n4, prec, kahan, icdf, params, SEED, 0, sums, s.cuda_stream)
+        one()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        one()
+        e1.record(s)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        legs[name] = {"seconds": sec, "path_steps": kind * steps4, "path_steps_per_s": kind * steps4 / sec}
+    return {"train_seconds": train_s, "steps": steps, "batch": 8192, "pairs": 1 << 24, "final_loss": loss,
             "l2_error_mlp": err["mlp"], "l2_error_table": err["table"],
-            f"fourway_l{level}_path_steps_per_s": {"mlp": rates["mlp"], "table": rates["table"]}}
+            f"fourway_l{level}_path_steps_per_s": {"mlp": rates["mlp"], "table": rates["table"]},
+            "levels_0_10_N_2e22": legs}
 
 
 def _cpu_sample(target_s: float, nthreads: int):
