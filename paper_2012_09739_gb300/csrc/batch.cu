@@ -183,7 +183,10 @@ namespace {
 // Uploads the plan into the cache's device buffers: the descriptors are
 // packed into pinned staging memory and copied asynchronously on s (the
 // buffers only grow, with cudaMalloc, when a larger batch arrives).
-mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
+// zero_copy: leave the descriptors in the pinned staging buffer, where the
+// kernels read them under unified addressing, instead of copying them to the
+// device (only the schedule counters stay in device memory).
+mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s, bool zero_copy) {
     cudaError_t e;
     const size_t n = p.items.size();
     if ((e = grow(&c.partials, &c.partials_cap, p.ntiles)) != cudaSuccess) return cuda_fail(e, "batch buffers");
@@ -202,11 +205,6 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     const size_t o_tiles = up16(b_items), o_start = o_tiles + up16(b_tiles), o_list = o_start + up16(b_start);
     const size_t o_cnt = o_list + up16(b_list), total = o_cnt + up16(b_cnt);
     if ((e = grow(&c.blob, &c.blob_cap, total)) != cudaSuccess) return cuda_fail(e, "batch buffers");
-    c.items = reinterpret_cast<LevelArgs *>(c.blob);
-    c.tiles = reinterpret_cast<Tile *>(c.blob + o_tiles);
-    c.start = reinterpret_cast<uint32_t *>(c.blob + o_start);
-    c.list = reinterpret_cast<uint32_t *>(c.blob + o_list);
-    c.counters = reinterpret_cast<uint32_t *>(c.blob + o_cnt);
     if (c.stage_cap < total) {
         if (c.stage) cudaFreeHost(c.stage);
         c.stage = nullptr;
@@ -214,8 +212,14 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
         if ((e = cudaMallocHost(&c.stage, total * 2)) != cudaSuccess) return cuda_fail(e, "pinned");
         c.stage_cap = total * 2;
     }
-    // the previous round's copy out of the staging buffer must be done
+    // the previous round's reads of (or copy out of) the staging buffer must be done
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload");
+    unsigned char *base = zero_copy ? c.stage : c.blob;
+    c.items = reinterpret_cast<LevelArgs *>(base);
+    c.tiles = reinterpret_cast<Tile *>(base + o_tiles);
+    c.start = reinterpret_cast<uint32_t *>(base + o_start);
+    c.list = reinterpret_cast<uint32_t *>(base + o_list);
+    c.counters = reinterpret_cast<uint32_t *>(c.blob + o_cnt);
     unsigned char *h = c.stage;
     memset(h, 0, total);
     memcpy(h, p.items.data(), b_items);
@@ -226,7 +230,8 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     }
     memcpy(h + o_start, p.start.data(), b_start);
     if (!p.list.empty()) memcpy(h + o_list, p.list.data(), p.list.size() * 4);
-    if ((e = cudaMemcpyAsync(c.blob, h, total, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(e, "upload");
+    if (!zero_copy && (e = cudaMemcpyAsync(c.blob, h, total, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "upload");
     return MLMC_OK;
 }
 
@@ -271,10 +276,22 @@ int env_int(const char *name, int dflt) {
 }
 
 // Times each candidate tile size once on the real batch and keeps the fastest.
+// Tile size (log2 of the path-steps per lane) for a batch's total work:
+// about four tiles per resident lane, clamped to [4, 12].
+int work_lane_log2(const DeviceState &d, const mlmc_work *w, int n) {
+    double steps = 0.0;
+    for (int i = 0; i < n; ++i) steps += ldexp((double)((w[i].N + 1) / 2), w[i].l);
+    const double lanes = (double)d.sm_count * 24 * 32;
+    const int lw = (int)floor(log2(std::max(steps / (4.0 * lanes), 1.0)));
+    return std::min(12, std::max(4, lw));
+}
+
 mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed, int *best) {
-    const int cands[] = {10, 11, 12, 13};
+    // candidates around the work-based size (large batches favour longer tiles)
+    const int base = work_lane_log2(d, w, n);
+    const int cands[] = {base - 1, base, base + 1, base + 2};
     float best_ms = 1e30f;
-    *best = 12;
+    *best = base;
     cudaStream_t s = c.capture_stream;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -282,7 +299,7 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
     mlmc_status st = MLMC_OK;
     for (int lw : cands) {
         Plan p = make_plan(d, w, n, seed, lw);
-        if ((st = upload(c, p, s))) break;
+        if ((st = upload(c, p, s, false))) break;
         cudaEventRecord(a, s);
         if ((st = enqueue(d, c, p, s, false, true))) break;
         cudaEventRecord(b, s);
@@ -308,13 +325,8 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
 // resident lane, each at least 16 and at most 4096 steps long per lane.
 mlmc_status batch_round(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed,
                         cudaStream_t s) {
-    double steps = 0.0;
-    for (int i = 0; i < n; ++i) steps += ldexp((double)((w[i].N + 1) / 2), w[i].l);
-    const double lanes = (double)d.sm_count * 24 * 32;
-    int lw = (int)floor(log2(std::max(steps / (4.0 * lanes), 1.0)));
-    lw = std::min(12, std::max(4, lw));
-    Plan p = make_plan(d, w, n, seed, lw);
-    mlmc_status st = upload(c, p, s);
+    Plan p = make_plan(d, w, n, seed, work_lane_log2(d, w, n));
+    mlmc_status st = upload(c, p, s, false);
     if (st) return st;
     return enqueue(d, c, p, s, true, false);
 }
@@ -374,7 +386,7 @@ extern "C" mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t 
             }
         }
         Plan p = make_plan(*d, items, n_items, seed, lw);
-        if ((st = upload(c, p, c.capture_stream))) return st;
+        if ((st = upload(c, p, c.capture_stream, false))) return st;
         // the graph is launched on the caller's stream: the descriptors must have landed
         cudaError_t ue = cudaStreamSynchronize(c.capture_stream);
         if (ue != cudaSuccess) return cuda_fail(ue, "upload");
