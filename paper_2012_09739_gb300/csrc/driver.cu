@@ -228,31 +228,55 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
     const int per_level = nested ? 2 : 1;
     bool converged = false;
 
-    while (!st) {
-        if ((st = run_round(terms))) break;
-        // ---- variance and cost estimates; optimal sample counts
+    // Optimal sample counts from the current estimates (Sec. 3).  When the
+    // estimated variance sum V_t / N_t of the terms already sampled exceeds
+    // eps^2 / 2, each term's dn grows to its shortfall against the optimal
+    // split; returns whether a round is needed (a shortfall, or a new level's
+    // pending warm-up).  A term without samples yet (a new level) takes an
+    // extrapolated variance, so the re-optimisation of all levels can share
+    // the new level's warm-up round.
+    auto plan_samples = [&]() -> bool {
         std::vector<double> V(terms.size()), C(terms.size());
         for (size_t i = 0; i < terms.size(); ++i) {
             V[i] = terms[i].off ? 0.0 : terms[i].var();
-            // a level's variance is at least half its predecessor's, decayed
-            // at strong rate beta = 1 (guards new levels with few samples)
-            if (terms[i].l >= 2 && !terms[i].off && !terms[i - per_level].off)
-                V[i] = fmax(V[i], 0.5 * V[i - per_level] * 0.5);
+            const bool prev_on = terms[i].l >= 2 && !terms[i].off && !terms[i - per_level].off;
+            if (prev_on && terms[i].n == 0 && terms[i].l >= 3 && !terms[i - 2 * per_level].off &&
+                V[i - 2 * per_level] > 0.0) {
+                // a level without samples yet: extrapolate the decay of the
+                // two levels below it (between 1/4 and 1 per level)
+                const double ratio = V[i - per_level] / V[i - 2 * per_level];
+                V[i] = V[i - per_level] * fmin(fmax(ratio, 0.25), 1.0);
+            } else if (prev_on) {
+                // a level's variance is at least a quarter of its
+                // predecessor's (guards levels with few samples)
+                V[i] = fmax(V[i], 0.25 * V[i - per_level]);
+            }
             C[i] = cost_of(terms[i]);
             terms[i].cost = C[i];
         }
-        double total = 0.0;
-        for (size_t i = 0; i < terms.size(); ++i) total += sqrt(V[i] * C[i]);
-        bool need = false;
+        double total = 0.0, var_sum = 0.0;
+        bool pending = false;
+        for (size_t i = 0; i < terms.size(); ++i) {
+            total += sqrt(V[i] * C[i]);
+            if (terms[i].n) var_sum += V[i] / (double)terms[i].n;
+            if (terms[i].dn) pending = true;
+        }
+        if (var_sum <= 0.5 * eps * eps && !pending) return false;
+        bool need = pending;
         for (size_t i = 0; i < terms.size(); ++i) {
             const double Nopt = ceil(2.0 / (eps * eps) * sqrt(V[i] / C[i]) * total);
-            const double dn = Nopt - (double)terms[i].n;
-            if (dn > 0.01 * (double)terms[i].n) {
-                terms[i].dn = (uint64_t)dn;
+            const double dn = Nopt - (double)(terms[i].n + terms[i].dn);
+            if (dn > 0.0) {
+                terms[i].dn += (uint64_t)dn;
                 need = true;
             }
         }
-        if (need) continue;
+        return need;
+    };
+
+    while (!st) {
+        if ((st = run_round(terms))) break;
+        if (plan_samples()) continue;
         // ---- weak-error test on the last three level means
         std::vector<double> Y(L + 1, 0.0);
         for (const Term &t : terms) Y[t.l] += t.mean();
@@ -268,6 +292,8 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         if (L >= o->max_level) break;
         ++L;
         st = add_level(L);
+        // the new level's warm-up and the other levels' top-ups in one round
+        if (!st) plan_samples();
     }
 
     if (!st) {
