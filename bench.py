@@ -140,6 +140,9 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
     stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    M.mlmc_icdf_table()                  # first call on the device: state and tables
+    init_s = time.perf_counter() - t0
     items = gpu_step_items(M)
     sums = torch.zeros(len(items) * 2, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # 256 MiB > 129 MB L2
@@ -302,6 +305,10 @@ def run_gpu(args):
         "time_to_eps": tte,
         "batching": batch,
         "mlp": mlp,
+        "setup": {"library_init_seconds": init_s,
+                  "batch_tune_and_capture_seconds": batch["first_call_seconds"] if batch else None,
+                  "mlp_train_seconds": mlp["train_seconds"] if mlp else None,
+                  "note": "one-time costs, outside every timed region"},
         "gpu_launches": 2 * len(items) * args.steps,     # level + finalize per item, headline step
         "clocks": clk,
     }
@@ -331,7 +338,9 @@ def batch_leg(M, torch, stream, repeats=5):
             for kind in (0, 1):
                 items.append(M.mlmc_work(p, l, kind, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, k, Ns[l], 0))
     ps = sum(it.N * (1 << it.l) for it in items)
+    t0 = time.perf_counter()
     M.mlmc_batch(items, SEED)            # tunes, captures the graph
+    first_s = time.perf_counter() - t0
     M.mlmc_batch(items, SEED)
     times = []
     for _ in range(repeats):
@@ -352,6 +361,7 @@ def batch_leg(M, torch, stream, repeats=5):
         seq.append(time.perf_counter() - t0)
     t_seq = min(seq)
     return {"items": len(items), "path_steps": ps, "seconds": t_batch, "path_steps_per_s": ps / t_batch,
+            "first_call_seconds": first_s,
             "device_seconds": dev_s,
             "one_launch_per_item_seconds": t_seq, "speedup_vs_one_launch_per_item": t_seq / t_batch,
             "timing": "wall clock around the synchronous mlmc_batch call (graph replay), median of 5; "

@@ -180,13 +180,11 @@ void release_device_extras(DeviceState &d) {
 
 namespace {
 
-// Uploads the plan into the cache's device buffers: the descriptors are
-// packed into pinned staging memory and copied asynchronously on s (the
-// buffers only grow, with cudaMalloc, when a larger batch arrives).
-// zero_copy: leave the descriptors in the pinned staging buffer, where the
-// kernels read them under unified addressing, instead of copying them to the
-// device (only the schedule counters stay in device memory).
-mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s, bool zero_copy) {
+// Uploads the plan into the cache's device buffers: the descriptors and the
+// zeroed schedule counters are packed into pinned staging memory and copied
+// to the device in one asynchronous copy on s (the buffers only grow, with
+// cudaMalloc, when a larger batch arrives).
+mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     cudaError_t e;
     const size_t n = p.items.size();
     if ((e = grow(&c.partials, &c.partials_cap, p.ntiles)) != cudaSuccess) return cuda_fail(e, "batch buffers");
@@ -212,13 +210,12 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s, bool zero_copy)
         if ((e = cudaMallocHost(&c.stage, total * 2)) != cudaSuccess) return cuda_fail(e, "pinned");
         c.stage_cap = total * 2;
     }
-    // the previous round's reads of (or copy out of) the staging buffer must be done
+    // the previous round's copy out of the staging buffer must be done
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload");
-    unsigned char *base = zero_copy ? c.stage : c.blob;
-    c.items = reinterpret_cast<LevelArgs *>(base);
-    c.tiles = reinterpret_cast<Tile *>(base + o_tiles);
-    c.start = reinterpret_cast<uint32_t *>(base + o_start);
-    c.list = reinterpret_cast<uint32_t *>(base + o_list);
+    c.items = reinterpret_cast<LevelArgs *>(c.blob);
+    c.tiles = reinterpret_cast<Tile *>(c.blob + o_tiles);
+    c.start = reinterpret_cast<uint32_t *>(c.blob + o_start);
+    c.list = reinterpret_cast<uint32_t *>(c.blob + o_list);
     c.counters = reinterpret_cast<uint32_t *>(c.blob + o_cnt);
     unsigned char *h = c.stage;
     memset(h, 0, total);
@@ -230,8 +227,7 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s, bool zero_copy)
     }
     memcpy(h + o_start, p.start.data(), b_start);
     if (!p.list.empty()) memcpy(h + o_list, p.list.data(), p.list.size() * 4);
-    if (!zero_copy && (e = cudaMemcpyAsync(c.blob, h, total, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return cuda_fail(e, "upload");
+    if ((e = cudaMemcpyAsync(c.blob, h, total, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(e, "upload");
     return MLMC_OK;
 }
 
@@ -299,7 +295,7 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
     mlmc_status st = MLMC_OK;
     for (int lw : cands) {
         Plan p = make_plan(d, w, n, seed, lw);
-        if ((st = upload(c, p, s, false))) break;
+        if ((st = upload(c, p, s))) break;
         cudaEventRecord(a, s);
         if ((st = enqueue(d, c, p, s, false, true))) break;
         cudaEventRecord(b, s);
@@ -326,7 +322,7 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
 mlmc_status batch_round(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed,
                         cudaStream_t s) {
     Plan p = make_plan(d, w, n, seed, work_lane_log2(d, w, n));
-    mlmc_status st = upload(c, p, s, false);
+    mlmc_status st = upload(c, p, s);
     if (st) return st;
     return enqueue(d, c, p, s, true, false);
 }
@@ -386,7 +382,7 @@ extern "C" mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t 
             }
         }
         Plan p = make_plan(*d, items, n_items, seed, lw);
-        if ((st = upload(c, p, c.capture_stream, false))) return st;
+        if ((st = upload(c, p, c.capture_stream))) return st;
         // the graph is launched on the caller's stream: the descriptors must have landed
         cudaError_t ue = cudaStreamSynchronize(c.capture_stream);
         if (ue != cudaSuccess) return cuda_fail(ue, "upload");
