@@ -322,9 +322,12 @@ __host__ __device__ __forceinline__ uint32_t chunk_group(int l, uint64_t chunks)
 // Register budget: two-way kernels fit 64 registers (4 blocks of 256 per
 // SM); four-way kernels carry four paths per sample and get 80 (3 blocks),
 // which removes their spills (measured 8 % faster on GB300 than 64 registers
-// with spills); the MLP kernels hold the network's fragments (1 block).
+// with spills); the MLP kernels hold the network's fragments and get 128 (2
+// blocks): they spill 120-170 bytes per thread to L1 but run 18 % faster than
+// with one block at 199 registers, the second block hiding the tensor-core
+// and MUFU latencies.
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 1 : (MODE == MODE_FOUR ? 3 : 4)) level_kernel(const LevelArgs a) {
+__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 2 : (MODE == MODE_FOUR ? 3 : 4)) level_kernel(const LevelArgs a) {
     __shared__ SmemTable tab;
     __shared__ double red[2][32];
     if (ICDF != ICDF_MLP || MODE == MODE_FOUR) {
