@@ -418,7 +418,7 @@ def time_to_eps(M, params, eps_list, repeats=3, with_mlp=False):
     return out
 
 
-def mlp_leg(M, torch, params, steps=20000, level=10, n=1 << 20):
+def mlp_leg(M, torch, params, steps=20000, level=10, n=1 << 20, workload=True):
     """The learned part: train the FP16 tensor-core MLP surrogate on 2^24
     (u, |Phi^-1|) pairs (targets computed on the device in FP64), then its
     E|Z - Z~|^2 against the table's, the four-way throughput with it, and the
@@ -455,7 +455,7 @@ def mlp_leg(M, torch, params, steps=20000, level=10, n=1 << 20):
         torch.cuda.synchronize()
         rates[name] = 3 * n * (1 << level) / (e0.elapsed_time(e1) / 1e3)
     # learned-part workload: levels 0..10, N = 2^22
-    n4, levels4 = 1 << 22, range(0, 11)
+    n4, levels4 = 1 << 22, (range(0, 11) if workload else range(0))
     steps4 = sum(n4 * (1 << l) for l in levels4)
     legs = {}
     for name, kind, prec, kahan, icdf in (("nested_f16_kahan_mlp", 2, M.MLMC_F16, 1, M.MLMC_ICDF_MLP),
@@ -579,7 +579,8 @@ def main():
         import torch
         import paper_2012_09739_gb300 as M
         params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
-        print(json.dumps(mlp_leg(M, torch, params, steps=args.mlp_steps, level=LEVELS[-1], n=N_PER_LEVEL)))
+        print(json.dumps(mlp_leg(M, torch, params, steps=args.mlp_steps, level=LEVELS[-1], n=N_PER_LEVEL,
+                                 workload=args.n is None)))
     else:
         run_gpu(args)
 
