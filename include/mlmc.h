@@ -58,7 +58,10 @@ typedef enum { MLMC_F32 = 0, MLMC_F16 = 1, MLMC_BF16 = 2 } mlmc_prec;
  * (counter (path lo32, path hi32, j, tag), key = seed; 24-bit uniform
  * u = (2 (w >> 9) + 1) 2^-24 from a word w; fine step n uses word n mod 4 of
  * call j = n / 4):
- *   EXACT    Phi^-1(u) in FP32 (no approximation);
+ *   EXACT    Phi^-1(u) in FP32 (no approximation beyond binary32: on each
+ *            binade of v = min(u, 1-u) a degree-7 polynomial of the
+ *            binade's local variable times (v - 1/2), built on the device
+ *            from FP64 values; within 2.5 ulp of Phi^-1 on the 24-bit grid);
  *   TABLE    the 16-interval piecewise-linear Phi~^-1 of Sec. 2.1 at u;
  *   MLP      the network of mlmc_mlp_set_weights / mlmc_mlp_train at u;
  *   TABLE16  the same table at a 16-bit uniform u16 = (h + 1/2) 2^-16, a
@@ -185,7 +188,8 @@ mlmc_status mlmc_level_paths(int four, int l, uint64_t N, int prec, int kahan, i
  * first (exact for u on the 24-bit grid).  z_dev is
  * float for prec = F32, IEEE binary16 (uint16_t storage) for F16 and
  * bfloat16 (uint16_t storage, the upper half of a binary32) for BF16.
- * icdf = EXACT evaluates Phi^-1 in FP32. */
+ * icdf = EXACT evaluates Phi^-1 in FP32 (the kernels' polynomial for
+ * v >= 2^-24, CUDA's normcdfinvf below). */
 mlmc_status approx_icdf(const float *u_dev, void *z_dev, size_t n, int icdf, int prec, void *stream);
 
 /* Philox4x32-10 of n counters: ctr_dev (n x 4 uint32), key_dev (n x 2),
