@@ -124,6 +124,17 @@ def gpu_step_items(M, icdf=None):
     return items
 
 
+def launches_per_level_call(l, n):
+    """Kernel launches of one mlmc_level_async call: the level kernel and a
+    one- or two-pass finalize (two passes above 8192 group partials; groups
+    of up to 64 >> l chunks of 32 sample pairs below l = 6, at least 16384
+    groups when there are enough chunks)."""
+    chunks = ((n + 1) // 2 + 31) // 32
+    g = 1 if l >= 6 else max(1, min(chunks // 16384, 64 >> l))
+    groups = (chunks + g - 1) // g
+    return 1 + (1 if groups <= 8192 else 2)
+
+
 def path_steps(levels, n):
     return sum(n * (1 << l) for l in levels)
 
@@ -309,7 +320,7 @@ def run_gpu(args):
                   "batch_tune_and_capture_seconds": batch["first_call_seconds"] if batch else None,
                   "mlp_train_seconds": mlp["train_seconds"] if mlp else None,
                   "note": "one-time costs, outside every timed region"},
-        "gpu_launches": 2 * len(items) * args.steps,     # level + finalize per item, headline step
+        "gpu_launches": args.steps * sum(launches_per_level_call(l, N_PER_LEVEL) for _, l, _, _, _ in items),
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -30,12 +30,17 @@ def test_noalloc_matches_allocating_entry_point_twice():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dev = torch.device("cuda:0")
-    params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
-    cases = [  # (four, l, N, prec, kahan, icdf, offset)
-        (1, 8, 1 << 20, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, 0),
-        (0, 5, 300001, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, 12345),
+    gbm = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    mil = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0, scheme=M.MLMC_MILSTEIN)
+    ou = M.sde_params(sde=M.MLMC_OU, payoff=M.MLMC_PAYOFF_X, p0=2.0, p1=0.3, p2=0.5)
+    cases = [  # (four, l, N, prec, kahan, icdf, offset, params)
+        (1, 8, 1 << 20, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, 0, gbm),
+        (0, 5, 300001, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, 12345, gbm),
+        (0, 6, 200001, M.MLMC_BF16, True, M.MLMC_ICDF_CUBIC, 3, gbm),
+        (1, 7, 100000, M.MLMC_F16, True, M.MLMC_ICDF_TABLE16, 0, mil),
+        (0, 9, 65536, M.MLMC_F32, True, M.MLMC_ICDF_TABLE, 1, ou),
     ]
-    for four, l, N, prec, kahan, icdf, off in cases:
+    for four, l, N, prec, kahan, icdf, off, params in cases:
         got = torch.zeros(2, dtype=torch.float64, device=dev)
         ref = torch.zeros(2, dtype=torch.float64, device=dev)
         M.mlmc_level_noalloc(four, l, N, prec, kahan, icdf, params, 1234, off, got)
