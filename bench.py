@@ -8,10 +8,15 @@ table) and the four-way nested difference (exact FP32 + Kahan vs FP16 + Kahan
 table).  One step = 2 x 2^20 x (2^13 - 1) = 1.718e10 fine Euler path-steps.
 Beside it, the plain FP32 exact-normal two-way MLMC over the same levels.
 
-value: fine path-steps per second of the FP16 + Kahan nested step, timed on
-the device with CUDA events; e2e: the same through the synchronous C-ABI
-calls that return the sums to host memory.  `--impl reference` times the CPU
-oracle on a bounded sample of the same workload.
+A step is two batched launches (mlmc_batch_async): the 13 two-way items and
+the 13 four-way items, each one persistent kernel over all levels, longest
+tiles first, replayed from a captured graph.  value: fine path-steps per
+second of that step, timed on the device with CUDA events; e2e: the same
+through the synchronous mlmc_batch call with host items and host sums, new
+path offsets every step (the descriptors are re-staged).  The same step
+through one mlmc_level_async call per level and estimator is reported beside
+it.  `--impl reference` times the CPU oracle on a bounded sample of the same
+workload.
 """
 from __future__ import annotations
 
@@ -47,11 +52,9 @@ WORKLOAD = "GBM call, levels 0..12, N=2^20 per level, two-way + four-way, FP16+K
 #   four-way only: hat fine + coarse Euler + Kahan in FP32       12.5
 OPS_FOURWAY_F16K_TABLE = 50.75
 OPS_TWOWAY_F16K_TABLE = 24.25
-# DRAM bytes (read + write) of one four-way level launch, from an ncu
-# capture of the kernel (l = 10, N = 2^18): the launch arguments and the
-# table; the per-group partial sums stay in L2.  The traffic does not grow
-# with the path-steps, so it is reported as measured, not scaled.
-TRAFFIC_FOURWAY_BYTES = 29440
+# DRAM bytes (read + write) of one four-way batched launch over levels 0..12
+# from an ncu capture; None until captured for the current kernel.
+TRAFFIC_FOURWAY_BYTES = None
 
 
 def _env_rank():
@@ -115,13 +118,18 @@ class ClockSampler:
 
 
 def gpu_step_items(M, icdf=None):
-    """(four, level, prec, kahan, icdf) of every launch in one FP16+Kahan nested step."""
+    """(four, level, prec, kahan, icdf) of every level in one FP16+Kahan nested step."""
     icdf = M.MLMC_ICDF_TABLE if icdf is None else icdf
     items = []
     for l in LEVELS:
         items.append((0, l, M.MLMC_F16, True, icdf))
         items.append((1, l, M.MLMC_F16, True, icdf))
     return items
+
+
+def batch_items(M, params, kind, prec, kahan, icdf, offset):
+    """The step's items of one estimator (kind 0 two-way, 1 four-way), levels 0..12."""
+    return [M.mlmc_work(params, l, kind, prec, int(kahan), icdf, 0, N_PER_LEVEL, offset) for l in LEVELS]
 
 
 def launches_per_level_call(l, n):
@@ -133,6 +141,14 @@ def launches_per_level_call(l, n):
     g = 1 if l >= 6 else max(1, min(chunks // 16384, 64 >> l))
     groups = (chunks + g - 1) // g
     return 1 + (1 if groups <= 8192 else 2)
+
+
+def launches_per_batch_call(items):
+    """Kernel launches of one mlmc_batch(_async) replay: one persistent batch
+    kernel per group of items sharing estimator, variant and SDE scheme, and
+    the finalize kernel."""
+    groups = {(w.kind, w.prec, w.kahan, w.icdf, w.params.sde, w.params.scheme) for w in items}
+    return len(groups) + 1
 
 
 def path_steps(levels, n):
@@ -154,54 +170,57 @@ def run_gpu(args):
     t0 = time.perf_counter()
     M.mlmc_icdf_table()                  # first call on the device: state and tables
     init_s = time.perf_counter() - t0
-    items = gpu_step_items(M)
-    sums = torch.zeros(len(items) * 2, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # 256 MiB > 129 MB L2
     # each rank simulates its own disjoint path range (weak scaling)
     offset = rank * N_PER_LEVEL
+    F16, T, T16 = M.MLMC_F16, M.MLMC_ICDF_TABLE, M.MLMC_ICDF_TABLE16
+    two = batch_items(M, params, 0, F16, True, T, offset)
+    four = batch_items(M, params, 1, F16, True, T, offset)
+    plain = batch_items(M, params, 0, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, offset)
+    two16 = batch_items(M, params, 0, F16, True, T16, offset)
+    four16 = batch_items(M, params, 1, F16, True, T16, offset)
+    sums = torch.zeros(2 * 2 * len(LEVELS), dtype=torch.float64, device=dev)
+    n2 = 2 * len(LEVELS)
 
-    def step(ev_pairs=None):
-        for i, (four, l, prec, kahan, icdf) in enumerate(items):
-            if ev_pairs is not None:
-                ev_pairs[i][0].record(stream)
-            M.mlmc_level_async(four, l, N_PER_LEVEL, prec, kahan, icdf, params, SEED, offset, sums[2 * i:],
-                               stream.cuda_stream)
-            if ev_pairs is not None:
-                ev_pairs[i][1].record(stream)
+    def step(e=None):
+        """One step: the two-way and the four-way batched launches."""
+        if e:
+            e[0].record(stream)
+        M.mlmc_batch_async(two, SEED, sums[:n2], stream.cuda_stream)
+        if e:
+            e[1].record(stream)
+        M.mlmc_batch_async(four, SEED, sums[n2:], stream.cuda_stream)
+        if e:
+            e[2].record(stream)
 
-    def fp32_step():
-        for l in LEVELS:
-            M.mlmc_level_async(0, l, N_PER_LEVEL, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, params, SEED, offset,
-                               sums[2 * l:], stream.cuda_stream)
-
+    # warm-up; the first call of each item-list shape tunes and captures its graph
+    t0 = time.perf_counter()
+    step()
+    torch.cuda.synchronize()
+    capture_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         step()
         if not args.no_fp32:
-            fp32_step()
+            M.mlmc_batch_async(plain, SEED, sums[:n2], stream.cuda_stream)
         if not args.no_table16:
-            for i, (four, l, prec, kahan, icdf) in enumerate(gpu_step_items(M, M.MLMC_ICDF_TABLE16)):
-                M.mlmc_level_async(four, l, N_PER_LEVEL, prec, kahan, icdf, params, SEED, offset, sums[2 * i:],
-                                   stream.cuda_stream)
+            M.mlmc_batch_async(two16, SEED, sums[:n2], stream.cuda_stream)
+            M.mlmc_batch_async(four16, SEED, sums[n2:], stream.cuda_stream)
     torch.cuda.synchronize()
 
     # --- device-timed FP16+Kahan nested step
-    step_ms, per_item = [], [[0.0, 0] for _ in items]
+    step_ms, two_ms, four_ms = [], 0.0, 0.0
     with ClockSampler(local) as clocks:
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         for _ in range(args.steps):
             flush.fill_(1)
-            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in items]
-            step(evs)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            step(e)
             torch.cuda.synchronize()
-            tot = 0.0
-            for i, (a, b) in enumerate(evs):
-                ms = a.elapsed_time(b)
-                per_item[i][0] += ms
-                per_item[i][1] += 1
-                tot += ms
-            step_ms.append(tot)
+            two_ms += e[0].elapsed_time(e[1])
+            four_ms += e[1].elapsed_time(e[2])
+            step_ms.append(e[0].elapsed_time(e[2]))
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -213,50 +232,70 @@ def run_gpu(args):
     ps_step = 2 * path_steps(LEVELS, N_PER_LEVEL)
     value = ps_step * args.steps * world / (ms_total / 1e3)
 
+    def timed(calls):
+        """Device time (ms) of `calls` per step, summed over the steps, L2 flushed before each."""
+        total = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            calls()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        return total
+
     # --- plain FP32 exact-normal MLMC over the same levels (comparison)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fp32_ms = 0.0
-    for _ in range(0 if args.no_fp32 else args.steps):
-        flush.fill_(1)
-        e0.record(stream)
-        fp32_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fp32_ms += e0.elapsed_time(e1)
+    fp32_ms = 0.0 if args.no_fp32 else timed(
+        lambda: M.mlmc_batch_async(plain, SEED, sums[:n2], stream.cuda_stream))
     fp32_value = path_steps(LEVELS, N_PER_LEVEL) * args.steps * world / (fp32_ms / 1e3) if fp32_ms else None
 
     # --- the same nested step with 16-bit uniforms for the approximate normals
-    t16_items = gpu_step_items(M, M.MLMC_ICDF_TABLE16)
-    t16_ms, t16_kind = 0.0, [0.0, 0.0]
+    t16_kind = [0.0, 0.0]
     for _ in range(0 if args.no_table16 else args.steps):
         flush.fill_(1)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in t16_items]
-        for i, (four, l, prec, kahan, icdf) in enumerate(t16_items):
-            evs[i][0].record(stream)
-            M.mlmc_level_async(four, l, N_PER_LEVEL, prec, kahan, icdf, params, SEED, offset, sums[2 * i:],
-                               stream.cuda_stream)
-            evs[i][1].record(stream)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        M.mlmc_batch_async(two16, SEED, sums[:n2], stream.cuda_stream)
+        e[1].record(stream)
+        M.mlmc_batch_async(four16, SEED, sums[n2:], stream.cuda_stream)
+        e[2].record(stream)
         torch.cuda.synchronize()
-        for i, (a, b) in enumerate(evs):
-            ms = a.elapsed_time(b)
-            t16_ms += ms
-            t16_kind[t16_items[i][0]] += ms
+        t16_kind[0] += e[0].elapsed_time(e[1])
+        t16_kind[1] += e[1].elapsed_time(e[2])
+    t16_ms = sum(t16_kind)
     t16_value = ps_step * args.steps * world / (t16_ms / 1e3) if t16_ms else None
 
-    # --- end to end through the synchronous C-ABI calls (sums to host memory)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(0 if args.no_e2e else args.steps):
-        for four, l, prec, kahan, icdf in items:
-            fn = M.mlmc_nested_level if four else M.mlmc_level
-            fn(l, N_PER_LEVEL, prec, kahan, icdf, params, SEED, offset, stream.cuda_stream)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ps_step * args.steps * world / e2e_s if not args.no_e2e else None
+    # --- the same step through one mlmc_level_async call per level and estimator
+    lvl_items = gpu_step_items(M)
+
+    def level_step():
+        for i, (k, l, prec, kahan, icdf) in enumerate(lvl_items):
+            M.mlmc_level_async(k, l, N_PER_LEVEL, prec, kahan, icdf, params, SEED, offset, sums[2 * i:],
+                               stream.cuda_stream)
+    level_step()
+    lvl_ms = 0.0 if args.no_level_calls else timed(level_step)
+    lvl_value = ps_step * args.steps * world / (lvl_ms / 1e3) if lvl_ms else None
+
+    # --- end to end through the synchronous C-ABI call: host items in, host
+    # sums out, new path offsets every step (the descriptors are re-staged)
+    e2e_value, h2d = None, 0
+    if not args.no_e2e:
+        def e2e_items(k):
+            off = (k * world + rank + 1) * N_PER_LEVEL
+            return (batch_items(M, params, 0, F16, True, T, off) + batch_items(M, params, 1, F16, True, T, off))
+        M.mlmc_batch(e2e_items(args.steps + 1), SEED)          # tunes and captures this shape (setup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            M.mlmc_batch(e2e_items(k), SEED, stream.cuda_stream)
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e_value = ps_step * args.steps * world / e2e_s
+        h2d = 2 * len(LEVELS) * M.mlmc_batch_descriptor_bytes()
 
     # --- batching workload: 128 sets x 17 levels x (two-way + four-way), one launch
     batch = None if args.no_batch else batch_leg(M, torch, stream)
@@ -265,16 +304,13 @@ def run_gpu(args):
     mlp = None if args.no_mlp else mlp_leg(M, torch, params)
     tte = None if args.no_tte else time_to_eps(M, params, [args.eps, 3e-4, 1e-5], with_mlp=mlp is not None)
 
-    # --- roofline of the dominant kernel (four-way FP16+Kahan table)
+    # --- roofline of the dominant kernel (four-way FP16+Kahan table, all levels in one launch)
     clk = clocks.summary()
-    four_ms = sum(per_item[i][0] for i, it in enumerate(items) if it[0] == 1)
-    four_launches = sum(per_item[i][1] for i, it in enumerate(items) if it[0] == 1)
     four_ps = path_steps(LEVELS, N_PER_LEVEL) * args.steps
     achieved = OPS_FOURWAY_F16K_TABLE * four_ps / (four_ms / 1e3) / 1e9     # Gop/s (lane-instructions)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_mhz = clk["sm_mhz"] or 1477.0
     peak = sm_count * 128 * clk_mhz * 1e6 / 1e9                              # Gop/s issue peak
-    two_ms = sum(per_item[i][0] for i, it in enumerate(items) if it[0] == 0)
 
     line = {
         "metric": "EM path-steps/s and time-to-RMSE 1e-3: FP16+Kahan vs plain FP32, one GB300",
@@ -291,36 +327,43 @@ def run_gpu(args):
         "data": "synthetic (Philox4x32-10 seed 1234; counter-based, generated in-kernel)",
         "config": {"workload": WORKLOAD, "levels": [min(LEVELS), max(LEVELS)], "N_per_level": N_PER_LEVEL,
                    "path_steps_per_step": ps_step, "estimators": "two-way FP16+Kahan table + four-way nested",
+                   "launch": "one batched persistent launch per estimator over all levels (mlmc_batch_async, "
+                             "graph replay)",
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "fp32_plain": {"value": fp32_value, "unit": "path-steps/s", "ms_per_step": fp32_ms / args.steps,
                        "ratio": (value / fp32_value) if fp32_value else None,
                        "path_steps_per_step": path_steps(LEVELS, N_PER_LEVEL)},
         "kernel_ms_per_step": {"fourway_f16_kahan_table": four_ms / args.steps,
                                "twoway_f16_kahan_table": two_ms / args.steps},
+        "level_calls": None if not lvl_ms else {
+            "value": lvl_value, "unit": "path-steps/s", "ms_per_step": lvl_ms / args.steps,
+            "note": "the same step as one mlmc_level_async call per level and estimator (26 launches of "
+                    "the level kernels plus finalizes)"},
         "table16": None if not t16_ms else {
             "value": t16_value, "unit": "path-steps/s", "ms_per_step": t16_ms / args.steps,
             "ratio_vs_table": t16_value / value,
             "kernel_ms_per_step": {"fourway_f16_kahan_table16": t16_kind[1] / args.steps,
                                    "twoway_f16_kahan_table16": t16_kind[0] / args.steps},
             "note": "approximate normals from 16-bit uniforms (two per Philox word on two-way paths)"},
-        "roofline": {"bound": "alu", "kernel": "level_kernel<FOUR,F16,kahan,TABLE,GBM>",
+        "roofline": {"bound": "alu", "kernel": "batch_kernel<FOUR,F16,kahan,TABLE,GBM> (levels 0..12)",
                      "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
                      "traffic": TRAFFIC_FOURWAY_BYTES,
-                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (l=10, N=2^18); "
-                                      "independent of the path-steps",
+                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch",
                      "ops_per_path_step": OPS_FOURWAY_F16K_TABLE,
                      "peak_basis": f"{sm_count} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock sampled)",
-                     "launches": four_launches},
-        "e2e": {"value": e2e_value, "unit": "path-steps/s", "h2d_bytes_per_step": len(items) * 64,
-                "d2h_bytes_per_step": len(items) * 16},
+                     "launches": args.steps},
+        "e2e": {"value": e2e_value, "unit": "path-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 2 * len(LEVELS) * 16,
+                "note": "synchronous mlmc_batch over the 26 items; new path offsets each step"},
         "time_to_eps": tte,
         "batching": batch,
         "mlp": mlp,
         "setup": {"library_init_seconds": init_s,
+                  "step_tune_and_capture_seconds": capture_s,
                   "batch_tune_and_capture_seconds": batch["first_call_seconds"] if batch else None,
                   "mlp_train_seconds": mlp["train_seconds"] if mlp else None,
                   "note": "one-time costs, outside every timed region"},
-        "gpu_launches": args.steps * sum(launches_per_level_call(l, N_PER_LEVEL) for _, l, _, _, _ in items),
+        "gpu_launches": args.steps * (launches_per_batch_call(two) + launches_per_batch_call(four)),
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -569,6 +612,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 comparison leg (profiling runs)")
     ap.add_argument("--no-table16", action="store_true", help="skip the 16-bit-uniform leg (profiling runs)")
+    ap.add_argument("--no-level-calls", action="store_true", help="skip the per-level-call leg (profiling runs)")
     ap.add_argument("--no-tte", action="store_true", help="skip the time-to-eps leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batching leg")
     ap.add_argument("--no-mlp", action="store_true", help="skip the MLP leg")

@@ -248,10 +248,34 @@ typedef struct {
     uint64_t N, path_offset;
 } mlmc_work;
 
-/* Runs all items, longest first, in one persistent kernel captured in a
- * CUDA graph (re-used while the item list's shape is unchanged), followed by
- * one finalize kernel.  out_host[i] receives the sums of items[i]. */
+/* Runs all items, longest first: one persistent kernel per group of items
+ * that share estimator, working precision, Kahan flag, inverse CDF and SDE
+ * scheme (the same per-sample code as the level kernels), then one finalize
+ * kernel, all captured in a CUDA graph.  out_host[i] receives the sums of
+ * items[i]; the call waits for them.  The library keeps the graphs of up to
+ * 8 item-list shapes (the level, kind, prec, kahan, icdf, N, SDE type and
+ * scheme of every item), least recently used evicted; the first call with a
+ * shape tunes the tile size, captures and instantiates (hundreds of ms).  A
+ * call with a known shape but other parameter values, payoffs, set ids, path
+ * offsets or seed uploads n_items * mlmc_batch_descriptor_bytes() bytes of
+ * descriptors and replays the graph.  The sums of one item are a fixed-order
+ * FP64 sum of its tiles' FP32 partials: the same for every call with the
+ * same items and seed.  Errors: MLMC_EINVAL for an invalid item (before any
+ * launch), MLMC_ENOTREADY for MLP items without weights, MLMC_ECUDA,
+ * MLMC_ETIMEOUT. */
 mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t seed, mlmc_sums *out_host, void *stream);
+
+/* mlmc_batch without the wait: enqueues the batch on `stream` and returns.
+ * sums_dev (caller-owned device or pinned host memory, 2 * n_items doubles)
+ * receives (sum D, sum D^2) of every item when the stream reaches that
+ * point.  Launches of the same shape on different streams are ordered by the
+ * library (each waits for the previous one on the device).  Same errors as
+ * mlmc_batch, plus MLMC_EINVAL for a NULL sums_dev. */
+mlmc_status mlmc_batch_async(const mlmc_work *items, int n_items, uint64_t seed, double *sums_dev, void *stream);
+
+/* Bytes of device descriptors uploaded per item when a batch of a known
+ * shape is re-staged. */
+size_t mlmc_batch_descriptor_bytes(void);
 
 /* ---- Adaptive MLMC to a target RMSE (Sec. 3 cost model). */
 typedef struct {

@@ -99,6 +99,8 @@ _SIGS = {
     "mlmc_mlp_grad": [_vp, _vp, ctypes.c_size_t, _vp, _vp, _vp],
     "mlmc_mlp_train": [_vp, _vp, ctypes.c_size_t, _P(mlmc_train_opts), _vp, _vp],
     "mlmc_batch": [_P(mlmc_work), _i32, _u64, _P(mlmc_sums), _vp],
+    "mlmc_batch_async": [_P(mlmc_work), _i32, _u64, _vp, _vp],
+    "mlmc_batch_descriptor_bytes": [],
     "mlmc_run": [ctypes.c_double, _P(mlmc_sde_params), _P(mlmc_run_opts), _P(mlmc_run_result)],
     "mlmc_optimal_samples": [_vp, _vp, _i32, ctypes.c_double, _vp],
     "mlmc_peak_probe": [_i32, _vp, _vp],
@@ -108,6 +110,7 @@ _SIGS = {
     "mlmc_shutdown": [],
 }
 _CHAR_RET = {"mlmc_strerror", "mlmc_last_error", "mlmc_version"}
+_SIZE_RET = {"mlmc_batch_descriptor_bytes"}
 
 _lock = threading.Lock()
 _lib = None
@@ -124,7 +127,8 @@ def load(path: str = LIB_PATH):
             for name, args in _SIGS.items():
                 fn = getattr(lib, name)
                 fn.argtypes = args
-                fn.restype = ctypes.c_char_p if name in _CHAR_RET else ctypes.c_int
+                fn.restype = (ctypes.c_char_p if name in _CHAR_RET
+                              else ctypes.c_size_t if name in _SIZE_RET else ctypes.c_int)
             _lib = lib
     return _lib
 
@@ -265,6 +269,16 @@ def mlmc_batch(items, seed, stream=None):
     out = (mlmc_sums * len(items))()
     _check(load().mlmc_batch(arr, len(items), seed, out, _stream(stream)))
     return list(out)
+
+
+def mlmc_batch_async(items, seed, sums_dev, stream=None):
+    """sums_dev: float64 CUDA tensor with >= 2 * len(items) elements."""
+    arr = (mlmc_work * len(items))(*items)
+    _check(load().mlmc_batch_async(arr, len(items), seed, _dptr(sums_dev), _stream(stream)))
+
+
+def mlmc_batch_descriptor_bytes() -> int:
+    return int(load().mlmc_batch_descriptor_bytes())
 
 
 def mlmc_run(eps, params, opts: mlmc_run_opts) -> mlmc_run_result:

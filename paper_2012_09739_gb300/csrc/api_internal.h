@@ -10,7 +10,8 @@ namespace mlmc {
 
 constexpr int MAX_DEVICES = 16;
 
-struct BatchCache;   // batch.cu: captured graph of the last batch shape
+struct BatchCache;   // batch.cu: device buffers of one batch plan (and its captured graph)
+struct BatchGraphs;  // batch.cu: the captured graphs of mlmc_batch, by item-list shape
 
 // Per-device library state: the piecewise-linear and cubic tables (FP64 and
 // their binary32 / binary16 / bfloat16 roundings), the MLP weights, cached
@@ -22,7 +23,7 @@ struct DeviceState {
     DevTables *tabs = nullptr;
     MlpWeights *mlp = nullptr;
     bool mlp_ready = false;
-    BatchCache *batch = nullptr;         // mlmc_batch: captured graph and buffers
+    BatchGraphs *batch = nullptr;        // mlmc_batch: captured graphs and their buffers
     BatchCache *run_cache = nullptr;     // mlmc_run: buffers of its batched rounds
     cudaStream_t run_stream = nullptr;
 };

@@ -1,7 +1,8 @@
-// Host side of mlmc_batch: warp tiles in longest-first order, one persistent
-// launch per working-precision variant, a finalize kernel, all captured in a
-// CUDA graph that is replayed while the item list is unchanged, and an
-// autotuner for the tile size.
+// Host side of mlmc_batch: warp tiles in longest-first order (one span of
+// tiles per item, never listed one by one); one persistent launch per group
+// of items sharing estimator, working-precision variant and SDE scheme, the
+// groups running concurrently; a finalize kernel; CUDA graphs of recent
+// item-list shapes, replayed; and an autotuner for the tile size.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -16,18 +17,22 @@
 
 namespace mlmc {
 
-BatchKernelFn batch_kernel_f32(int kahan, int icdf);
-BatchKernelFn batch_kernel_f16(int kahan, int icdf);
-BatchKernelFn batch_kernel_bf16(int kahan, int icdf);
+BatchKernelFn batch_kernel_f32_two(int kahan, int icdf, int sde);
+BatchKernelFn batch_kernel_f16_two(int kahan, int icdf, int sde);
+BatchKernelFn batch_kernel_bf16_two(int kahan, int icdf, int sde);
+BatchKernelFn batch_kernel_f32_four(int kahan, int icdf, int sde);
+BatchKernelFn batch_kernel_f16_four(int kahan, int icdf, int sde);
+BatchKernelFn batch_kernel_bf16_four(int kahan, int icdf, int sde);
 
-// Sums each item's tile partials in a fixed order, one warp per item, FP64.
-__global__ void batch_finalize_kernel(const double2 *tile_partials, const uint32_t *start, const uint32_t *list,
-                                      int nitems, double2 *sums) {
+// Sums each item's tile partials (a contiguous range, fin[2i] .. + fin[2i+1])
+// in a fixed order, one warp per item, FP64.
+__global__ void batch_finalize_kernel(const double2 *tile_partials, const uint32_t *fin, int nitems, double2 *sums) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= nitems) return;
+    const uint32_t first = fin[2 * warp], count = fin[2 * warp + 1];
     double s1 = 0.0, s2 = 0.0;
-    for (uint32_t i = start[warp] + lane; i < start[warp + 1]; i += 32) {
-        const double2 p = tile_partials[list[i]];
+    for (uint32_t i = lane; i < count; i += 32) {
+        const double2 p = tile_partials[first + i];
         s1 += p.x;
         s2 += p.y;
     }
@@ -42,17 +47,23 @@ __global__ void batch_finalize_kernel(const double2 *tile_partials, const uint32
 namespace {
 
 struct Group {
-    int prec, kahan, icdf;
-    std::vector<Tile> tiles;
-    uint32_t tile_base = 0;        // offset of this group's tiles in the device array
+    int mode, prec, kahan, icdf, sde;
+    std::vector<TileSpan> spans;   // longest tiles first
+    std::vector<double> tile_cost;  // per span: cost of one full tile
+    uint32_t span_base = 0;        // offset of this group's spans in the device array
+    uint32_t tile_base = 0;        // offset of this group's tiles in the partials
+    uint32_t ntiles = 0;
+    double work = 0.0;
 };
 
 struct Plan {
     std::vector<LevelArgs> items;
     std::vector<Group> groups;
-    std::vector<uint32_t> start, list;   // per-item tile lists (global tile indices)
+    std::vector<uint32_t> fin;           // per item: first tile (global), tile count
     std::vector<double> weight;          // share of the launch's work per item
-    uint32_t ntiles = 0;
+    uint32_t ntiles = 0, nspans = 0;
+    double work = 0.0;
+    bool too_many_tiles = false;         // more than 2^32 - 1 tiles
 };
 
 uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
@@ -61,60 +72,89 @@ uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
     return h;
 }
 
-double item_work(const mlmc_work &w) {
-    return ldexp((double)((w.N + 1) / 2), w.l) * (w.kind ? 2.2 : 1.0);
-}
+// Cost of one sample pair on one lane in fine-step units: 2^l steps plus the
+// per-sample work (counter set-up, payoffs, accumulation), which at level 0
+// is about three steps' worth; a four-way pair costs about 2.2 two-way pairs.
+constexpr double PAIR_OVERHEAD_STEPS = 3.0;
+double pair_cost(int l, int four) { return (ldexp(1.0, l) + PAIR_OVERHEAD_STEPS) * (four ? 2.2 : 1.0); }
 
-// Tiles of `lane_pairs_log2` controls the work per lane per tile: a lane takes
-// max(1, 2^lane_work_log2 / 2^l) pairs of an item at level l.
+double item_work(const mlmc_work &w) { return (double)((w.N + 1) / 2) * pair_cost(w.l, w.kind); }
+
+// Tiles: a lane takes max(1, 2^lane_work_log2 / (2^l + overhead)) pairs of an
+// item at level l, a tile is 32 such lanes.  Every item is one span of
+// consecutive tiles; each group's spans are ordered by the cost of their
+// tiles, longest first, so the host work is per item, not per tile.
 Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, int lane_work_log2) {
     Plan plan;
     plan.items.resize(n);
-    std::vector<std::vector<uint32_t>> per_item(n);
-    double total = 0.0;
-    for (int i = 0; i < n; ++i) total += item_work(w[i]);
+    plan.fin.assign(2 * (size_t)n, 0);
+    std::vector<uint32_t> group_of(n);
+    for (int i = 0; i < n; ++i) plan.work += item_work(w[i]);
     for (int i = 0; i < n; ++i) {
         plan.items[i] = make_level_args(d, w[i].kind, w[i].l, w[i].N, w[i].prec, w[i].icdf, &w[i].params, seed,
                                         w[i].path_offset, (uint32_t)w[i].set_id);
-        plan.weight.push_back(total > 0 ? item_work(w[i]) / total : 0.0);
-        Group *g = nullptr;
-        for (auto &gg : plan.groups)
-            if (gg.prec == w[i].prec && gg.kahan == (w[i].kahan ? 1 : 0) && gg.icdf == w[i].icdf) g = &gg;
-        if (!g) {
-            plan.groups.push_back(Group{w[i].prec, w[i].kahan ? 1 : 0, w[i].icdf, {}, 0});
-            g = &plan.groups.back();
+        plan.weight.push_back(plan.work > 0 ? item_work(w[i]) / plan.work : 0.0);
+        const int mode = w[i].kind, kahan = w[i].kahan ? 1 : 0, sde = plan.items[i].sde;
+        size_t gi = 0;
+        while (gi < plan.groups.size()) {
+            const Group &g = plan.groups[gi];
+            if (g.mode == mode && g.prec == w[i].prec && g.kahan == kahan && g.icdf == w[i].icdf && g.sde == sde) break;
+            ++gi;
         }
+        if (gi == plan.groups.size()) plan.groups.push_back(Group{mode, w[i].prec, kahan, w[i].icdf, sde});
+        Group &g = plan.groups[gi];
+        group_of[i] = (uint32_t)gi;
         const uint64_t np = (w[i].N + 1) / 2;
-        const uint64_t per_lane = std::max<uint64_t>(1, (1ull << lane_work_log2) >> w[i].l);
+        const double pc = pair_cost(w[i].l, w[i].kind);
+        const uint64_t per_lane = std::max<uint64_t>(1, (uint64_t)(ldexp(1.0, lane_work_log2) / (pc / (w[i].kind ? 2.2 : 1.0))));
         const uint64_t per_tile = 32 * per_lane;
-        for (uint64_t first = 0; first < np; first += per_tile)
-            g->tiles.push_back(Tile{(uint32_t)i, (uint32_t)std::min<uint64_t>(per_tile, np - first), first});
+        const uint64_t count = (np + per_tile - 1) / per_tile;
+        const uint64_t rounds = (std::min(per_tile, np) + 31) / 32;
+        g.spans.push_back(TileSpan{(uint32_t)i, (uint32_t)per_tile, 0, (uint32_t)count});
+        g.tile_cost.push_back((double)rounds * pc);
+        g.work += item_work(w[i]);
     }
-    uint32_t base = 0;
+    uint64_t tile_base = 0;
+    uint32_t span_base = 0;
     for (auto &g : plan.groups) {
-        // longest first: lane rounds x steps per pair, four-way weighted
-        std::stable_sort(g.tiles.begin(), g.tiles.end(), [&](const Tile &a, const Tile &b) {
-            const LevelArgs &ia = plan.items[a.item], &ib = plan.items[b.item];
-            const double ca = ldexp((double)((a.npairs + 31) / 32), ia.l) * (ia.mode ? 2.2 : 1.0);
-            const double cb = ldexp((double)((b.npairs + 31) / 32), ib.l) * (ib.mode ? 2.2 : 1.0);
-            return ca > cb;
-        });
-        g.tile_base = base;
-        for (uint32_t k = 0; k < g.tiles.size(); ++k) per_item[g.tiles[k].item].push_back(base + k);
-        base += (uint32_t)g.tiles.size();
+        std::vector<uint32_t> order(g.spans.size());
+        for (uint32_t k = 0; k < order.size(); ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](uint32_t a, uint32_t b) { return g.tile_cost[a] > g.tile_cost[b]; });
+        std::vector<TileSpan> spans;
+        std::vector<double> cost;
+        uint64_t begin = 0;
+        for (uint32_t k : order) {
+            TileSpan sp = g.spans[k];
+            sp.begin = (uint32_t)begin;
+            begin += sp.count;
+            plan.fin[2 * sp.item] = (uint32_t)(tile_base + sp.begin);
+            plan.fin[2 * sp.item + 1] = sp.count;
+            spans.push_back(sp);
+            cost.push_back(g.tile_cost[k]);
+        }
+        g.spans.swap(spans);
+        g.tile_cost.swap(cost);
+        g.ntiles = (uint32_t)begin;
+        g.tile_base = (uint32_t)tile_base;
+        g.span_base = span_base;
+        tile_base += begin;
+        span_base += (uint32_t)g.spans.size();
+        if (tile_base > 0xFFFFFFFFull) plan.too_many_tiles = true;
     }
-    plan.ntiles = base;
-    plan.start.push_back(0);
-    for (int i = 0; i < n; ++i) {
-        for (uint32_t t : per_item[i]) plan.list.push_back(t);
-        plan.start.push_back((uint32_t)plan.list.size());
-    }
+    plan.ntiles = (uint32_t)tile_base;
+    plan.nspans = span_base;
     return plan;
 }
 
-BatchKernelFn pick_batch_kernel(int prec, int kahan, int icdf) {
-    return prec == MLMC_F32 ? batch_kernel_f32(kahan, icdf)
-                            : prec == MLMC_F16 ? batch_kernel_f16(kahan, icdf) : batch_kernel_bf16(kahan, icdf);
+BatchKernelFn pick_batch_kernel(const Group &g) {
+    if (g.mode == MODE_TWO)
+        return g.prec == MLMC_F32   ? batch_kernel_f32_two(g.kahan, g.icdf, g.sde)
+               : g.prec == MLMC_F16 ? batch_kernel_f16_two(g.kahan, g.icdf, g.sde)
+                                    : batch_kernel_bf16_two(g.kahan, g.icdf, g.sde);
+    return g.prec == MLMC_F32   ? batch_kernel_f32_four(g.kahan, g.icdf, g.sde)
+           : g.prec == MLMC_F16 ? batch_kernel_f16_four(g.kahan, g.icdf, g.sde)
+                                : batch_kernel_bf16_four(g.kahan, g.icdf, g.sde);
 }
 
 template <typename T>
@@ -132,13 +172,14 @@ cudaError_t grow(T **p, size_t *cap, size_t n) {
 }  // namespace
 
 struct BatchCache {
-    // descriptors, uploaded by one copy: items, tiles, per-item tile lists
-    // and the schedule counters (zeroed by the same copy), 16-byte aligned
+    // descriptors, uploaded by one copy: items, tile spans, per-item tile
+    // ranges and the schedule counters (zeroed by the same copy), 16-byte
+    // aligned
     unsigned char *blob = nullptr;
     size_t blob_cap = 0;
     LevelArgs *items = nullptr;
-    Tile *tiles = nullptr;
-    uint32_t *start = nullptr, *list = nullptr;
+    TileSpan *spans = nullptr;
+    uint32_t *fin = nullptr;             // per item: first tile, tile count
     uint32_t *counters = nullptr;
     double2 *partials = nullptr;
     size_t partials_cap = 0;
@@ -148,33 +189,64 @@ struct BatchCache {
     size_t sums_host_cap = 0;
     unsigned char *stage = nullptr;      // pinned staging of the descriptors
     size_t stage_cap = 0;
-    cudaStream_t capture_stream = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    uint64_t sig = 0;
-    std::vector<double> weight;
-    std::map<uint64_t, int> tuned;       // item-list signature -> lane_work_log2
     std::map<const void *, int> occupancy;   // batch kernel -> resident blocks per SM
+    // streams of the concurrent groups (created on first use)
+    static constexpr size_t MAX_SIDE = 7;
+    cudaStream_t side[MAX_SIDE] = {};
+    cudaEvent_t fork = nullptr, join[MAX_SIDE] = {};
+    // mlmc_batch graph entry: the captured graph of one item-list shape
+    cudaGraphExec_t exec = nullptr;
+    uint64_t shape = 0;          // signature of the items without path offsets and seed
+    uint64_t full = 0;           // signature of the items and seed the device descriptors hold
+    uint64_t last_use = 0;
+    size_t items_bytes = 0;      // the LevelArgs part of the descriptors
+    cudaEvent_t done = nullptr;  // after the entry's last launch and sums copy
+    cudaEvent_t staged = nullptr;    // after the last descriptor copy out of `stage`
+    bool launched = false, restaged = false;
+    std::vector<double> weight;
+};
+
+// The graph entries of mlmc_batch / mlmc_batch_async on one device.
+struct BatchGraphs {
+    std::vector<BatchCache *> entries;   // at most MAX_ENTRIES, least recently used evicted
+    cudaStream_t capture_stream = nullptr;
+    std::map<uint64_t, int> tuned;       // item-list shape -> lane_work_log2
+    uint64_t clock = 0;
+    static constexpr size_t MAX_ENTRIES = 8;
 };
 
 BatchCache *batch_cache_create() { return new BatchCache(); }
 
 void batch_cache_destroy(BatchCache *c) {
     if (!c) return;
+    if (c->done) cudaEventSynchronize(c->done);
     if (c->exec) cudaGraphExecDestroy(c->exec);
     cudaFree(c->blob);
     cudaFree(c->partials);
     cudaFree(c->sums);
     if (c->sums_host) cudaFreeHost(c->sums_host);
     if (c->stage) cudaFreeHost(c->stage);
-    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    if (c->done) cudaEventDestroy(c->done);
+    if (c->staged) cudaEventDestroy(c->staged);
+    for (size_t k = 0; k < BatchCache::MAX_SIDE; ++k) {
+        if (c->side[k]) cudaStreamSynchronize(c->side[k]);
+        if (c->side[k]) cudaStreamDestroy(c->side[k]);
+        if (c->join[k]) cudaEventDestroy(c->join[k]);
+    }
+    if (c->fork) cudaEventDestroy(c->fork);
     delete c;
 }
 
 void release_device_extras(DeviceState &d) {
-    batch_cache_destroy(d.batch);
+    if (d.batch) {
+        for (BatchCache *c : d.batch->entries) batch_cache_destroy(c);
+        if (d.batch->capture_stream) cudaStreamDestroy(d.batch->capture_stream);
+        delete d.batch;
+    }
     batch_cache_destroy(d.run_cache);
     if (d.run_stream) cudaStreamDestroy(d.run_stream);
-    d.batch = d.run_cache = nullptr;
+    d.batch = nullptr;
+    d.run_cache = nullptr;
     d.run_stream = nullptr;
 }
 
@@ -187,6 +259,7 @@ namespace {
 mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     cudaError_t e;
     const size_t n = p.items.size();
+    if (p.too_many_tiles) return fail(MLMC_EINVAL, "batch needs more than 2^32 - 1 tiles");
     if ((e = grow(&c.partials, &c.partials_cap, p.ntiles)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if ((e = grow(&c.sums, &c.sums_cap, n)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if (c.sums_host_cap < n) {
@@ -197,11 +270,10 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
         c.sums_host_cap = n;
     }
     auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
-    const size_t b_items = n * sizeof(LevelArgs), b_tiles = (size_t)p.ntiles * sizeof(Tile);
-    const size_t b_start = p.start.size() * 4, b_list = std::max<size_t>(p.list.size(), 1) * 4;
-    const size_t b_cnt = p.groups.size() * 4;
-    const size_t o_tiles = up16(b_items), o_start = o_tiles + up16(b_tiles), o_list = o_start + up16(b_start);
-    const size_t o_cnt = o_list + up16(b_list), total = o_cnt + up16(b_cnt);
+    const size_t b_items = n * sizeof(LevelArgs), b_spans = (size_t)p.nspans * sizeof(TileSpan);
+    const size_t b_fin = p.fin.size() * 4, b_cnt = p.groups.size() * 4;
+    const size_t o_spans = up16(b_items), o_fin = o_spans + up16(b_spans), o_cnt = o_fin + up16(b_fin);
+    const size_t total = o_cnt + up16(b_cnt);
     if ((e = grow(&c.blob, &c.blob_cap, total)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if (c.stage_cap < total) {
         if (c.stage) cudaFreeHost(c.stage);
@@ -213,55 +285,91 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     // the previous round's copy out of the staging buffer must be done
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload");
     c.items = reinterpret_cast<LevelArgs *>(c.blob);
-    c.tiles = reinterpret_cast<Tile *>(c.blob + o_tiles);
-    c.start = reinterpret_cast<uint32_t *>(c.blob + o_start);
-    c.list = reinterpret_cast<uint32_t *>(c.blob + o_list);
+    c.spans = reinterpret_cast<TileSpan *>(c.blob + o_spans);
+    c.fin = reinterpret_cast<uint32_t *>(c.blob + o_fin);
     c.counters = reinterpret_cast<uint32_t *>(c.blob + o_cnt);
     unsigned char *h = c.stage;
     memset(h, 0, total);
     memcpy(h, p.items.data(), b_items);
-    size_t off = o_tiles;
-    for (const auto &g : p.groups) {
-        memcpy(h + off, g.tiles.data(), g.tiles.size() * sizeof(Tile));
-        off += g.tiles.size() * sizeof(Tile);
-    }
-    memcpy(h + o_start, p.start.data(), b_start);
-    if (!p.list.empty()) memcpy(h + o_list, p.list.data(), p.list.size() * 4);
+    for (const auto &g : p.groups)
+        memcpy(h + o_spans + g.span_base * sizeof(TileSpan), g.spans.data(), g.spans.size() * sizeof(TileSpan));
+    memcpy(h + o_fin, p.fin.data(), b_fin);
     if ((e = cudaMemcpyAsync(c.blob, h, total, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(e, "upload");
     return MLMC_OK;
 }
 
+// Resident blocks per SM of a batch kernel (cached per kernel).
+int blocks_per_sm(BatchCache &c, BatchKernelFn fn) {
+    auto it = c.occupancy.find((const void *)fn);
+    if (it != c.occupancy.end()) return it->second;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 256, 0) != cudaSuccess || bps < 1) bps = 1;
+    c.occupancy[(const void *)fn] = bps;
+    return bps;
+}
+
 // Enqueues the whole batch on stream s (also used inside graph capture).
+// Groups run concurrently: the first on s, the others on side streams forked
+// from s and joined back before the finalize.  A lone group gets every
+// resident block; with several, each gets a share of the GPU proportional to
+// its work, but at least one warp for each of its tiles that is longer than
+// the whole batch's ideal time per warp (their tiles are the critical path).
 // zero_counters: reset the schedule counters on the stream (a replayed graph
 // needs it; a fresh upload has zeroed them already).
 mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStream_t s, bool copy_out,
                     bool zero_counters) {
     cudaError_t e;
-    if (zero_counters && (e = cudaMemsetAsync(c.counters, 0, p.groups.size() * sizeof(uint32_t), s)) != cudaSuccess)
+    const size_t ng = p.groups.size();
+    if (zero_counters && (e = cudaMemsetAsync(c.counters, 0, ng * sizeof(uint32_t), s)) != cudaSuccess)
         return cuda_fail(e, "memset");
-    for (size_t gi = 0; gi < p.groups.size(); ++gi) {
-        const Group &g = p.groups[gi];
-        BatchKernelFn fn = pick_batch_kernel(g.prec, g.kahan, g.icdf);
-        int bps = 0;
-        auto it = c.occupancy.find((const void *)fn);
-        if (it != c.occupancy.end()) {
-            bps = it->second;
-        } else {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 256, 0) != cudaSuccess || bps < 1) bps = 1;
-            c.occupancy[(const void *)fn] = bps;
+    std::vector<BatchKernelFn> fns(ng);
+    std::vector<int> bps(ng);
+    int bps_min = 1 << 20;
+    for (size_t gi = 0; gi < ng; ++gi) {
+        if (!(fns[gi] = pick_batch_kernel(p.groups[gi]))) return fail(MLMC_EINVAL, "no batch kernel for this variant");
+        bps[gi] = blocks_per_sm(c, fns[gi]);
+        bps_min = std::min(bps_min, bps[gi]);
+    }
+    const size_t nside = std::min<size_t>(ng - 1, BatchCache::MAX_SIDE);
+    if (nside > 0) {
+        if (!c.fork && (e = cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate");
+        for (size_t k = 0; k < nside; ++k) {
+            if (!c.side[k] && (e = cudaStreamCreateWithFlags(&c.side[k], cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamCreate");
+            if (!c.join[k] && (e = cudaEventCreateWithFlags(&c.join[k], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "cudaEventCreate");
         }
-        const uint32_t warps_needed = (uint32_t)g.tiles.size();
-        uint32_t grid = (uint32_t)bps * d.sm_count;
-        grid = std::min<uint32_t>(grid, (warps_needed + 7) / 8);
-        fn<<<grid ? grid : 1, 256, 0, s>>>(c.items, c.tiles + g.tile_base, (uint32_t)g.tiles.size(), c.counters + gi,
-                                           c.partials + g.tile_base, d.tabs);
+        if ((e = cudaEventRecord(c.fork, s)) != cudaSuccess) return cuda_fail(e, "fork");
+        for (size_t k = 0; k < nside; ++k)
+            if ((e = cudaStreamWaitEvent(c.side[k], c.fork, 0)) != cudaSuccess) return cuda_fail(e, "fork");
+    }
+    const double ideal = p.work / ((double)bps_min * d.sm_count * 8.0);
+    for (size_t gi = 0; gi < ng; ++gi) {
+        const Group &g = p.groups[gi];
+        const uint64_t full = (uint64_t)bps[gi] * d.sm_count;
+        uint64_t grid = full;
+        if (ng > 1) {
+            uint64_t long_tiles = 0;
+            for (size_t k = 0; k < g.spans.size() && g.tile_cost[k] > ideal; ++k) long_tiles += g.spans[k].count;
+            const uint64_t share = (uint64_t)ceil(g.work / p.work * (double)full);
+            grid = std::min(full, std::max(share, (long_tiles + 7) / 8));
+        }
+        grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, ((uint64_t)g.ntiles + 7) / 8));
+        cudaStream_t gs = gi == 0 ? s : c.side[(gi - 1) % BatchCache::MAX_SIDE];
+        fns[gi]<<<(unsigned)grid, 256, 0, gs>>>(c.items, c.spans + g.span_base, (uint32_t)g.spans.size(), g.ntiles,
+                                                 c.counters + gi, c.partials + g.tile_base, d.tabs);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch kernel");
+    }
+    for (size_t k = 0; k < nside; ++k) {
+        if ((e = cudaEventRecord(c.join[k], c.side[k])) != cudaSuccess) return cuda_fail(e, "join");
+        if ((e = cudaStreamWaitEvent(s, c.join[k], 0)) != cudaSuccess) return cuda_fail(e, "join");
     }
     const int n = (int)p.items.size();
     // copy_out: the finalize kernel writes the sums straight into the pinned
     // host buffer (device-accessible under unified addressing), no copy
     double2 *dst = copy_out ? c.sums_host : c.sums;
-    batch_finalize_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(c.partials, c.start, c.list, n, dst);
+    batch_finalize_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(c.partials, c.fin, n, dst);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch finalize");
     return MLMC_OK;
 }
@@ -271,24 +379,24 @@ int env_int(const char *name, int dflt) {
     return s ? atoi(s) : dflt;
 }
 
-// Times each candidate tile size once on the real batch and keeps the fastest.
-// Tile size (log2 of the path-steps per lane) for a batch's total work:
-// about four tiles per resident lane, clamped to [4, 12].
+// Tile size (log2 of the fine-step equivalents per lane and tile) for a
+// batch's total work: about four tiles per resident lane, clamped to [4, 12].
 int work_lane_log2(const DeviceState &d, const mlmc_work *w, int n) {
     double steps = 0.0;
-    for (int i = 0; i < n; ++i) steps += ldexp((double)((w[i].N + 1) / 2), w[i].l);
+    for (int i = 0; i < n; ++i) steps += (double)((w[i].N + 1) / 2) * pair_cost(w[i].l, 0);
     const double lanes = (double)d.sm_count * 24 * 32;
     const int lw = (int)floor(log2(std::max(steps / (4.0 * lanes), 1.0)));
     return std::min(12, std::max(4, lw));
 }
 
-mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed, int *best) {
+// Times each candidate tile size once on the real batch and keeps the fastest.
+mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed, cudaStream_t s,
+                     int *best) {
     // candidates around the work-based size (large batches favour longer tiles)
     const int base = work_lane_log2(d, w, n);
     const int cands[] = {base - 1, base, base + 1, base + 2};
     float best_ms = 1e30f;
     *best = base;
-    cudaStream_t s = c.capture_stream;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
@@ -329,13 +437,10 @@ mlmc_status batch_round(const DeviceState &d, BatchCache &c, const mlmc_work *w,
 
 const double2 *batch_sums_host(const BatchCache &c) { return c.sums_host; }
 
-}  // namespace mlmc
+namespace {
 
-using namespace mlmc;
-
-extern "C" mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t seed, mlmc_sums *out_host,
-                                  void *stream) {
-    if (!items || n_items <= 0 || !out_host) return fail(MLMC_EINVAL, "bad batch arguments");
+mlmc_status check_items(const mlmc_work *items, int n_items) {
+    if (!items || n_items <= 0) return fail(MLMC_EINVAL, "bad batch arguments");
     for (int i = 0; i < n_items; ++i) {
         const mlmc_work &w = items[i];
         if (w.kind != 0 && w.kind != 1) return fail(MLMC_EINVAL, "item %d: kind must be 0 or 1", i);
@@ -344,84 +449,189 @@ extern "C" mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t 
         mlmc_status st = check_level(w.kind, w.l, w.N, w.prec, w.icdf, &w.params);
         if (st) return fail(st, "item %d: %s", i, mlmc_last_error());
     }
-    DeviceState *d;
-    mlmc_status st = device_state(&d);
+    return MLMC_OK;
+}
+
+// Signature of the item list's shape: what the tiles, the kernel groups and
+// so the captured graph depend on (level, estimator, variant, SDE type and
+// scheme, N of every item).  Parameter values, payoffs, set ids, path
+// offsets and the seed only change the LevelArgs, which are re-staged.
+uint64_t shape_signature(const mlmc_work *items, int n) {
+    uint64_t h = fnv1a(&n, sizeof n);
+    for (int i = 0; i < n; ++i) {
+        const mlmc_work &w = items[i];
+        const int32_t k[8] = {w.l, w.kind, w.prec, w.kahan, w.icdf, (int32_t)w.params.sde, (int32_t)w.params.scheme, 0};
+        h = fnv1a(k, sizeof k, h);
+        h = fnv1a(&w.N, sizeof w.N, h);
+    }
+    return h;
+}
+
+std::mutex g_batch_mu;   // one enqueue at a time per process: the entries are shared
+
+// Builds a graph entry: tile size (tuned once per shape), plan, descriptor
+// upload and the captured graph (batch kernels and finalize into c.sums).
+mlmc_status build_entry(DeviceState &d, BatchGraphs &G, BatchCache &c, const mlmc_work *items, int n_items,
+                        uint64_t seed, uint64_t shape, uint64_t full, cudaStream_t s) {
+    cudaError_t e;
+    mlmc_status st;
+    if ((e = cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c.staged, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate");
+    // the capture stream must see the caller's prior work first
+    cudaEvent_t ev;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "event");
+    cudaEventRecord(ev, s);
+    cudaStreamWaitEvent(G.capture_stream, ev, 0);
+    cudaEventDestroy(ev);
+    int lw = env_int("MLMC_BATCH_LANE_WORK_LOG2", 0);
+    if (lw < 6 || lw > 20) {
+        auto it = G.tuned.find(shape);
+        if (it != G.tuned.end()) {
+            lw = it->second;
+        } else if (env_int("MLMC_AUTOTUNE", 1)) {
+            if ((st = autotune(d, c, items, n_items, seed, G.capture_stream, &lw))) return st;
+            G.tuned[shape] = lw;
+        } else {
+            lw = 12;
+        }
+    }
+    Plan p = make_plan(d, items, n_items, seed, lw);
+    if ((st = upload(c, p, G.capture_stream))) return st;
+    // the graph is launched on the caller's stream: the descriptors must have landed
+    if ((e = cudaStreamSynchronize(G.capture_stream)) != cudaSuccess) return cuda_fail(e, "upload");
+    cudaGraph_t g;
+    if ((e = cudaStreamBeginCapture(G.capture_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    st = enqueue(d, c, p, G.capture_stream, false, true);
+    e = cudaStreamEndCapture(G.capture_stream, &g);
     if (st) return st;
-    // one batch at a time per process: the cached graph and buffers are shared
-    static std::mutex batch_mu;
-    std::lock_guard<std::mutex> lock(batch_mu);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    c.shape = shape;
+    c.full = full;
+    c.items_bytes = p.items.size() * sizeof(LevelArgs);
+    c.weight = p.weight;
+    return MLMC_OK;
+}
+
+// Finds or builds the graph entry of this item list and enqueues one replay
+// on s: re-stages the descriptors if the items or the seed changed since the
+// entry's last launch (within the shape), waits (on s) for that launch, launches the
+// graph and copies the item sums to dst (device or pinned host memory; NULL:
+// the entry's pinned host buffer), then records the entry's done event.  t0/t1 (optional) bracket the graph.
+mlmc_status batch_enqueue(DeviceState &d, const mlmc_work *items, int n_items, uint64_t seed, void *dst,
+                          cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1, BatchCache **used) {
+    cudaError_t e;
+    mlmc_status st;
+    if (!d.batch) {
+        d.batch = new BatchGraphs();
+        if ((e = cudaStreamCreateWithFlags(&d.batch->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreate");
+    }
+    BatchGraphs &G = *d.batch;
+    const uint64_t shape = shape_signature(items, n_items);
+    const uint64_t full = fnv1a(items, sizeof(mlmc_work) * n_items, fnv1a(&seed, sizeof seed, shape));
+    BatchCache *c = nullptr;
+    for (BatchCache *x : G.entries)
+        if (x->shape == shape) c = x;
+    if (!c) {
+        if (G.entries.size() >= BatchGraphs::MAX_ENTRIES) {
+            auto lru = std::min_element(G.entries.begin(), G.entries.end(),
+                                        [](const BatchCache *x, const BatchCache *y) { return x->last_use < y->last_use; });
+            batch_cache_destroy(*lru);      // waits for its last launch
+            G.entries.erase(lru);
+        }
+        c = new BatchCache();
+        if ((st = build_entry(d, G, *c, items, n_items, seed, shape, full, s))) {
+            batch_cache_destroy(c);
+            return st;
+        }
+        G.entries.push_back(c);
+    }
+    c->last_use = ++G.clock;
+    // the previous launch of this entry (on any stream) must be done with
+    // the descriptors, the partials and the sums before they are reused
+    if (c->launched && (e = cudaStreamWaitEvent(s, c->done, 0)) != cudaSuccess) return cuda_fail(e, "wait");
+    if (c->full != full) {
+        // same shape, new parameters, offsets or seed: only the LevelArgs change
+        if (c->restaged && (st = wait_event(c->staged, wait_limit_s()))) return st;
+        LevelArgs *h = reinterpret_cast<LevelArgs *>(c->stage);
+        for (int i = 0; i < n_items; ++i)
+            h[i] = make_level_args(d, items[i].kind, items[i].l, items[i].N, items[i].prec, items[i].icdf,
+                                   &items[i].params, seed, items[i].path_offset, (uint32_t)items[i].set_id);
+        if ((e = cudaMemcpyAsync(c->items, h, c->items_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "descriptor upload");
+        cudaEventRecord(c->staged, s);
+        c->restaged = true;
+        c->full = full;
+    }
+    if (t0) cudaEventRecord(t0, s);
+    if ((e = cudaGraphLaunch(c->exec, s)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    if (t1) cudaEventRecord(t1, s);
+    void *out = dst ? dst : (void *)c->sums_host;
+    if ((e = cudaMemcpyAsync(out, c->sums, (size_t)n_items * sizeof(double2), cudaMemcpyDefault, s)) != cudaSuccess)
+        return cuda_fail(e, "sums copy");
+    if ((e = cudaEventRecord(c->done, s)) != cudaSuccess) return cuda_fail(e, "event");
+    c->launched = true;
+    if (used) *used = c;
+    return MLMC_OK;
+}
+
+}  // namespace
+
+}  // namespace mlmc
+
+using namespace mlmc;
+
+extern "C" mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t seed, mlmc_sums *out_host,
+                                  void *stream) {
+    mlmc_status st = check_items(items, n_items);
+    if (st) return st;
+    if (!out_host) return fail(MLMC_EINVAL, "out_host is NULL");
+    DeviceState *d;
+    if ((st = device_state(&d))) return st;
     for (int i = 0; i < n_items; ++i)
         if (items[i].icdf == MLMC_ICDF_MLP && !d->mlp_ready) return fail(MLMC_ENOTREADY, "MLP weights not set");
-    if (!d->batch) {
-        d->batch = new BatchCache();
-        cudaError_t e = cudaStreamCreateWithFlags(&d->batch->capture_stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
-    }
-    BatchCache &c = *d->batch;
+    // held to the end: the entry's pinned sums are read after the wait
+    std::lock_guard<std::mutex> lock(g_batch_mu);
     cudaStream_t s = (cudaStream_t)stream;
-    uint64_t sig = fnv1a(items, sizeof(mlmc_work) * n_items, fnv1a(&seed, sizeof seed));
-    sig = fnv1a(&n_items, sizeof n_items, sig);
-
-    if (!(c.exec && c.sig == sig)) {
-        int lw = env_int("MLMC_BATCH_LANE_WORK_LOG2", 0);
-        if (lw < 6 || lw > 20) {
-            auto it = c.tuned.find(sig);
-            if (it != c.tuned.end()) {
-                lw = it->second;
-            } else if (env_int("MLMC_AUTOTUNE", 1)) {
-                // the capture stream must see the caller's prior work first
-                cudaEvent_t ev;
-                cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-                cudaEventRecord(ev, s);
-                cudaStreamWaitEvent(c.capture_stream, ev, 0);
-                cudaEventDestroy(ev);
-                if ((st = autotune(*d, c, items, n_items, seed, &lw))) return st;
-                c.tuned[sig] = lw;
-            } else {
-                lw = 12;
-            }
-        }
-        Plan p = make_plan(*d, items, n_items, seed, lw);
-        if ((st = upload(c, p, c.capture_stream))) return st;
-        // the graph is launched on the caller's stream: the descriptors must have landed
-        cudaError_t ue = cudaStreamSynchronize(c.capture_stream);
-        if (ue != cudaSuccess) return cuda_fail(ue, "upload");
-        if (c.exec) {
-            cudaGraphExecDestroy(c.exec);
-            c.exec = nullptr;
-        }
-        cudaGraph_t g;
-        cudaError_t e = cudaStreamBeginCapture(c.capture_stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        st = enqueue(*d, c, p, c.capture_stream, true, true);
-        e = cudaStreamEndCapture(c.capture_stream, &g);
-        if (st) return st;
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&c.exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-        c.sig = sig;
-        c.weight = p.weight;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return fail(MLMC_ECUDA, "cudaEventCreate");
     }
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    cudaEventRecord(a, s);
-    cudaError_t e = cudaGraphLaunch(c.exec, s);
-    cudaEventRecord(b, s);
-    if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphLaunch");
-    if (!st) st = wait_event(b, wait_limit_s());
+    BatchCache *c = nullptr;
+    st = batch_enqueue(*d, items, n_items, seed, nullptr, s, a, b, &c);
+    if (!st) st = wait_event(c->done, wait_limit_s());
     if (!st) {
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, a, b);
         for (int i = 0; i < n_items; ++i) {
-            out_host[i].s1 = c.sums_host[i].x;
-            out_host[i].s2 = c.sums_host[i].y;
+            out_host[i].s1 = c->sums_host[i].x;
+            out_host[i].s2 = c->sums_host[i].y;
             out_host[i].n = items[i].N;
-            out_host[i].cost_ns = (double)ms * 1e6 * c.weight[i];
+            out_host[i].cost_ns = (double)ms * 1e6 * c->weight[i];
         }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     return st;
 }
+
+extern "C" mlmc_status mlmc_batch_async(const mlmc_work *items, int n_items, uint64_t seed, double *sums_dev,
+                                        void *stream) {
+    mlmc_status st = check_items(items, n_items);
+    if (st) return st;
+    if (!sums_dev) return fail(MLMC_EINVAL, "sums_dev is NULL");
+    DeviceState *d;
+    if ((st = device_state(&d))) return st;
+    for (int i = 0; i < n_items; ++i)
+        if (items[i].icdf == MLMC_ICDF_MLP && !d->mlp_ready) return fail(MLMC_ENOTREADY, "MLP weights not set");
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    return batch_enqueue(*d, items, n_items, seed, sums_dev, (cudaStream_t)stream, nullptr, nullptr, nullptr);
+}
+
+extern "C" size_t mlmc_batch_descriptor_bytes(void) { return sizeof(LevelArgs); }

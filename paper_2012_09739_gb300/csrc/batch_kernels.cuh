@@ -1,24 +1,44 @@
-// Persistent batched level kernel: many (parameter set, level, estimator)
-// items of one working-precision variant in one launch.
+// Persistent batched level kernel: many (parameter set, level) items of one
+// estimator, working-precision variant and SDE scheme in one launch.
 //
-// The host cuts every item into warp tiles (a contiguous range of sample
-// pairs; one pair per lane per round) and orders all tiles longest first.
-// Each warp of a grid of resident blocks repeatedly takes the next tile from
-// an atomic counter, simulates it with the same per-pair code as the level
-// kernels, and writes the tile's (sum D, sum D^2) to its own slot; a finalize
-// kernel then sums each item's slots in a fixed order.  No warp ever waits on
-// another warp or block.
+// Every item is cut into warp tiles (a contiguous range of sample pairs; one
+// pair per lane per round) of one size per item: a span of consecutive tile
+// indices.  The host orders the spans by tile length, longest first; it
+// never lists the tiles.  Each warp of a grid of resident blocks repeatedly
+// takes the next tile index from an atomic counter, finds its span, simulates
+// the tile with the same per-pair code as the level kernels, and writes the
+// tile's (sum D, sum D^2) to its own slot; a finalize kernel then sums each
+// item's slots in a fixed order.  No warp ever waits on another warp or
+// block.
 #pragma once
 
 #include "level_kernels.cuh"
 
 namespace mlmc {
 
-struct Tile {
-    uint32_t item;     // index into the item array
-    uint32_t npairs;   // pairs in this tile
-    uint64_t first;    // first pair index within the item
+struct TileSpan {
+    uint32_t item;       // index into the item array
+    uint32_t per_tile;   // pairs per tile (the item's last tile may be shorter)
+    uint32_t begin;      // first tile index of the item (within its launch)
+    uint32_t count;      // tiles of the item
 };
+
+// Index of the span holding tile t: the largest k with spans[k].begin <= t
+// (spans[0].begin = 0, begins strictly increasing).  Warp-cooperative: each
+// pass tests 32 evenly spaced spans and keeps the last one that starts at or
+// before t, shrinking the range 32-fold; the whole warp must call it.
+__device__ __forceinline__ uint32_t find_span(const TileSpan *spans, uint32_t n, uint32_t t, uint32_t lane) {
+    uint32_t lo = 0, hi = n;     // spans[lo].begin <= t, and t < spans[hi].begin unless hi = n
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + 31) >> 5;
+        const uint32_t k = lo + lane * step;
+        const bool ok = k < hi && spans[k].begin <= t;
+        const uint32_t m = __ballot_sync(0xffffffffu, ok);    // a prefix of the lanes; lane 0 always
+        lo += (31 - __clz(m)) * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
 
 // Warp-cooperative simulation of one pair of samples (the deep levels of a
 // batch hold items of one or two samples whose 2^l dependent steps would
@@ -97,10 +117,13 @@ __device__ void simulate_pair_seq(const LevelArgs &a, const SmemTable &tab, cons
     pair_result<MODE>(a, fine, coarse, hfine, hcoarse, d0, d1, out0, out1);
 }
 
-template <int P, bool KAHAN, int ICDF>
-__global__ void __launch_bounds__(256) batch_kernel(const LevelArgs *items, const Tile *tiles, uint32_t ntiles,
-                                                    uint32_t *counter, double2 *tile_partials,
-                                                    const DevTables *tabs) {
+// One kernel per (MODE, P, KAHAN, ICDF, SDE), like the level kernels and with
+// their register budgets, so that a batch runs at the level kernels'
+// occupancy; the host launches one per group of items that share them.
+template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
+__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 2 : (MODE == MODE_FOUR ? 3 : 4))
+batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uint32_t ntiles, uint32_t *counter,
+             double2 *tile_partials, const DevTables *tabs) {
     __shared__ SmemTable tab;
     __shared__ SeqScratch<P> seq[8];           // one per warp (warp-cooperative single pairs)
     stage_table(tab, tabs);
@@ -113,26 +136,19 @@ __global__ void __launch_bounds__(256) batch_kernel(const LevelArgs *items, cons
         if (lane == 0) t = atomicAdd(counter, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= ntiles) break;
-        const Tile tl = tiles[t];
-        const LevelArgs a = items[tl.item];
+        const TileSpan sp = spans[find_span(spans, nspans, t, lane)];
+        const LevelArgs a = items[sp.item];
+        const uint64_t first = (uint64_t)(t - sp.begin) * sp.per_tile;
+        const uint32_t npairs = a.npairs - first < sp.per_tile ? (uint32_t)(a.npairs - first) : sp.per_tile;
         KahanF32 s1, s2;
-        if (tl.npairs == 1 && a.l >= SEQ_MIN_LEVEL) {
+        if (npairs == 1 && a.l >= SEQ_MIN_LEVEL) {
             // one pair, long paths: the warp generates the normals, lane 0 steps
-            SeqScratch<P> &sc = seq[threadIdx.x >> 5];
             float d0, d1;
-            if (a.mode == MODE_TWO) {
-                if (a.sde == SDE_GBM) simulate_pair_seq<MODE_TWO, P, KAHAN, ICDF, SDE_GBM>(a, tab, mlp, tl.first, d0, d1, sc);
-                else if (a.sde == SDE_OU) simulate_pair_seq<MODE_TWO, P, KAHAN, ICDF, SDE_OU>(a, tab, mlp, tl.first, d0, d1, sc);
-                else simulate_pair_seq<MODE_TWO, P, KAHAN, ICDF, SDE_GBM_MIL>(a, tab, mlp, tl.first, d0, d1, sc);
-            } else {
-                if (a.sde == SDE_GBM) simulate_pair_seq<MODE_FOUR, P, KAHAN, ICDF, SDE_GBM>(a, tab, mlp, tl.first, d0, d1, sc);
-                else if (a.sde == SDE_OU) simulate_pair_seq<MODE_FOUR, P, KAHAN, ICDF, SDE_OU>(a, tab, mlp, tl.first, d0, d1, sc);
-                else simulate_pair_seq<MODE_FOUR, P, KAHAN, ICDF, SDE_GBM_MIL>(a, tab, mlp, tl.first, d0, d1, sc);
-            }
+            simulate_pair_seq<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, first, d0, d1, seq[threadIdx.x >> 5]);
             if (lane == 0) {
                 s1.add(d0);
                 s2.add(d0 * d0);
-                if (2 * tl.first + 1 < a.N) {
+                if (2 * first + 1 < a.N) {
                     s1.add(d1);
                     s2.add(d1 * d1);
                 }
@@ -140,21 +156,13 @@ __global__ void __launch_bounds__(256) batch_kernel(const LevelArgs *items, cons
             }
             continue;
         }
-        const uint32_t rounds = (tl.npairs + 31u) >> 5;
+        const uint32_t rounds = (npairs + 31u) >> 5;
         for (uint32_t r = 0; r < rounds; ++r) {
             const uint32_t k = (r << 5) + lane;
-            const bool active = k < tl.npairs;
-            const uint64_t g = tl.first + (active ? k : tl.npairs - 1);
+            const bool active = k < npairs;
+            const uint64_t g = first + (active ? k : npairs - 1);
             float d0, d1, o0[5], o1[5];
-            if (a.mode == MODE_TWO) {
-                if (a.sde == SDE_GBM) simulate_pair<MODE_TWO, P, KAHAN, ICDF, SDE_GBM>(a, tab, mlp, g, d0, d1, o0, o1);
-                else if (a.sde == SDE_OU) simulate_pair<MODE_TWO, P, KAHAN, ICDF, SDE_OU>(a, tab, mlp, g, d0, d1, o0, o1);
-                else simulate_pair<MODE_TWO, P, KAHAN, ICDF, SDE_GBM_MIL>(a, tab, mlp, g, d0, d1, o0, o1);
-            } else {
-                if (a.sde == SDE_GBM) simulate_pair<MODE_FOUR, P, KAHAN, ICDF, SDE_GBM>(a, tab, mlp, g, d0, d1, o0, o1);
-                else if (a.sde == SDE_OU) simulate_pair<MODE_FOUR, P, KAHAN, ICDF, SDE_OU>(a, tab, mlp, g, d0, d1, o0, o1);
-                else simulate_pair<MODE_FOUR, P, KAHAN, ICDF, SDE_GBM_MIL>(a, tab, mlp, g, d0, d1, o0, o1);
-            }
+            simulate_pair<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, d0, d1, o0, o1);
             if (!active) continue;
             s1.add(d0);
             s2.add(d0 * d0);
@@ -168,7 +176,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const LevelArgs *items, cons
     }
 }
 
-using BatchKernelFn = void (*)(const LevelArgs *, const Tile *, uint32_t, uint32_t *, double2 *,
+using BatchKernelFn = void (*)(const LevelArgs *, const TileSpan *, uint32_t, uint32_t, uint32_t *, double2 *,
                                const DevTables *);
 
 }  // namespace mlmc

@@ -23,12 +23,13 @@ def lib():
 def _declared():
     with open(os.path.join(ROOT, "include", "mlmc.h")) as f:
         text = f.read()
-    return sorted(set(re.findall(r"^(?:mlmc_status|const char \*)\s*(\w+)\(", text, re.M)))
+    return sorted(set(re.findall(r"^(?:mlmc_status|const char \*|size_t)\s*(\w+)\(", text, re.M)))
 
 
 def test_header_declares_the_boundary():
     names = _declared()
-    for n in ["mlmc_level", "mlmc_nested_level", "approx_icdf", "mlmc_run", "mlmc_batch", "mlmc_mlp_train"]:
+    for n in ["mlmc_level", "mlmc_nested_level", "approx_icdf", "mlmc_run", "mlmc_batch", "mlmc_batch_async",
+              "mlmc_mlp_train"]:
         assert n in names
 
 
@@ -62,6 +63,28 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     st = lib.mlmc_level(3, 10, 0, 0, 0, None, 1, 0, ctypes.byref(out), None)
     assert st == M.MLMC_EINVAL
     assert lib.mlmc_strerror(M.MLMC_ETIMEOUT) == b"timeout"
+
+
+def test_batch_arguments_rejected_without_gpu(lib):
+    """Both batch entry points validate every item (and the output pointer)
+    before they touch a device."""
+    p = M.sde_params()
+    good = M.mlmc_work(p, 3, 1, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 0, 1000, 0)
+    bad = [M.mlmc_work(p, 3, 2, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 0, 1000, 0),      # kind
+           M.mlmc_work(p, 19, 0, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 0, 1000, 0),     # level
+           M.mlmc_work(p, 3, 1, M.MLMC_F16, 1, M.MLMC_ICDF_EXACT, 0, 1000, 0),      # four-way exact
+           M.mlmc_work(p, 3, 0, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 70000, 1000, 0),  # set id
+           M.mlmc_work(p, 3, 0, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 0, 0, 0)]         # N = 0
+    out = (M.mlmc_sums * 2)()
+    sums = (ctypes.c_double * 4)()
+    for b in bad:
+        arr = (M.mlmc_work * 2)(good, b)
+        assert lib.mlmc_batch(arr, 2, 1, out, None) == M.MLMC_EINVAL
+        assert lib.mlmc_batch_async(arr, 2, 1, ctypes.cast(sums, ctypes.c_void_p), None) == M.MLMC_EINVAL
+    arr = (M.mlmc_work * 1)(good)
+    assert lib.mlmc_batch_async(arr, 1, 1, None, None) == M.MLMC_EINVAL
+    assert lib.mlmc_batch(arr, 0, 1, out, None) == M.MLMC_EINVAL
+    assert 128 <= M.mlmc_batch_descriptor_bytes() <= 1024 and M.mlmc_batch_descriptor_bytes() % 8 == 0
 
 
 def test_optimal_samples_match_oracle(lib):

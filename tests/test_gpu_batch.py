@@ -128,3 +128,102 @@ def test_single_pair_deep_items_with_mlp_exact():
         fn = M.mlmc_nested_level if kind else M.mlmc_level
         ref = fn(l, N, M.MLMC_F16, True, M.MLMC_ICDF_MLP, p, SEED, off)
         assert g.n == ref.n and g.s1 == ref.s1 and g.s2 == ref.s2, (kind, l, N, off)
+
+
+def _bench_items(kind, prec=M.MLMC_F16, kahan=1, icdf=M.MLMC_ICDF_TABLE, N=1 << 20, offset=0, **kw):
+    args = dict(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    args.update(kw)
+    p = M.sde_params(**args)
+    return [M.mlmc_work(p, l, kind, prec, kahan, icdf, 0, N, offset) for l in range(13)]
+
+
+def _pairs(sums):
+    return [(a.s1, a.s2) for a in sums]
+
+
+def test_batch_async_equals_sync():
+    """mlmc_batch_async replays the same graph as mlmc_batch: the device sums
+    equal the host sums bit for bit."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    items = _bench_items(1, N=1 << 14) + _bench_items(0, N=1 << 14)
+    ref = M.mlmc_batch(items, SEED)
+    out = torch.full((2 * len(items),), float("nan"), dtype=torch.float64, device="cuda")
+    M.mlmc_batch_async(items, SEED, out, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = out.view(-1, 2).cpu().tolist()
+    assert [tuple(g) for g in got] == _pairs(ref)
+
+
+def test_batch_restaged_descriptors_equal_fresh_capture():
+    """A call whose items differ from the cached shape only in parameter
+    values, payoff, path offsets or seed re-stages the descriptors and
+    replays the graph; its sums equal those of a freshly built graph of the
+    same items (the entry evicted by eight other shapes first), and agree
+    with the level kernels."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    a = _bench_items(1, N=3001) + _bench_items(0, N=3001)
+    b = _bench_items(1, N=3001, offset=777, p1=0.3) + _bench_items(0, N=3001, offset=778, p1=0.3)
+    for it in b[::3]:
+        it.params.payoff = M.MLMC_PAYOFF_X
+    ra = M.mlmc_batch(a, SEED)
+    rb = M.mlmc_batch(b, SEED + 1)                  # same shape: re-staged
+    assert _pairs(M.mlmc_batch(a, SEED)) == _pairs(ra)
+    for k in range(8):                               # evict the entry
+        M.mlmc_batch(_bench_items(0, N=100 + k)[:3], SEED)
+    assert _pairs(M.mlmc_batch(b, SEED + 1)) == _pairs(rb)     # fresh graph, same tiles
+    for it, g in zip(b, rb):
+        fn = M.mlmc_nested_level if it.kind else M.mlmc_level
+        ref = fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED + 1, it.path_offset)
+        _close(g, ref)
+
+
+def test_batch_graphs_of_two_shapes_alternate():
+    """Two item lists of different shapes keep a graph each: alternating
+    calls give the same sums every time."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    x, y = _bench_items(1, N=5000), _bench_items(0, N=7000)
+    rx, ry = M.mlmc_batch(x, SEED), M.mlmc_batch(y, SEED)
+    for _ in range(3):
+        assert _pairs(M.mlmc_batch(x, SEED)) == _pairs(rx)
+        assert _pairs(M.mlmc_batch(y, SEED)) == _pairs(ry)
+
+
+def test_batch_async_on_two_streams_is_ordered():
+    """Launches of one shape with different path offsets on two streams: the
+    library orders them on the device (each waits for the previous launch of
+    the entry), so each stream's sums are those of its own items."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    x = _bench_items(1, N=20000)
+    y = _bench_items(1, N=20000, offset=20000)
+    rx, ry = M.mlmc_batch(x, SEED), M.mlmc_batch(y, SEED)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    bx = torch.zeros(2 * len(x), dtype=torch.float64, device="cuda")
+    by = torch.zeros(2 * len(y), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        M.mlmc_batch_async(x, SEED, bx, s1.cuda_stream)
+        M.mlmc_batch_async(y, SEED, by, s2.cuda_stream)
+        torch.cuda.synchronize()
+        assert [tuple(g) for g in bx.view(-1, 2).cpu().tolist()] == _pairs(rx)
+        assert [tuple(g) for g in by.view(-1, 2).cpu().tolist()] == _pairs(ry)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_bench_step_batches_match_level_kernels(kind):
+    """The timed step of the throughput measurement: levels 0..12, N = 2^20,
+    FP16 + Kahan table, one batched launch per estimator; every level's sums
+    agree with the level kernel's (same samples, other summation grouping)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    items = _bench_items(kind)
+    out = torch.zeros(2 * len(items), dtype=torch.float64, device="cuda")
+    M.mlmc_batch_async(items, SEED, out, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = out.view(-1, 2).cpu().tolist()
+    for it, (s1, s2) in zip(items, got):
+        fn = M.mlmc_nested_level if kind else M.mlmc_level
+        ref = fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED, 0)
+        _close(M.mlmc_sums(s1, s2, it.N, 0.0), ref)
