@@ -53,8 +53,11 @@ WORKLOAD = "GBM call, levels 0..12, N=2^20 per level, two-way + four-way, FP16+K
 OPS_FOURWAY_F16K_TABLE = 50.75
 OPS_TWOWAY_F16K_TABLE = 24.25
 # DRAM bytes (read + write) of one four-way batched launch over levels 0..12
-# from an ncu capture; None until captured for the current kernel.
-TRAFFIC_FOURWAY_BYTES = None
+# at N = 2^20, from an ncu capture of that launch (dram__bytes_read.sum +
+# dram__bytes_write.sum, one pass): the descriptors and the table, 0.33 to
+# 0.67 MB over the launches captured, no writes (the tile partials stay in
+# L2).  The traffic does not grow with the path-steps.
+TRAFFIC_FOURWAY_BYTES = 669440
 
 
 def _env_rank():
@@ -273,8 +276,10 @@ def run_gpu(args):
         for i, (k, l, prec, kahan, icdf) in enumerate(lvl_items):
             M.mlmc_level_async(k, l, N_PER_LEVEL, prec, kahan, icdf, params, SEED, offset, sums[2 * i:],
                                stream.cuda_stream)
-    level_step()
-    lvl_ms = 0.0 if args.no_level_calls else timed(level_step)
+    lvl_ms = 0.0
+    if not args.no_level_calls:
+        level_step()                     # untimed warm-up of this leg
+        lvl_ms = timed(level_step)
     lvl_value = ps_step * args.steps * world / (lvl_ms / 1e3) if lvl_ms else None
 
     # --- end to end through the synchronous C-ABI call: host items in, host
@@ -348,7 +353,8 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "kernel": "batch_kernel<FOUR,F16,kahan,TABLE,GBM> (levels 0..12)",
                      "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
                      "traffic": TRAFFIC_FOURWAY_BYTES,
-                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch",
+                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch "
+                                      "(the larger of two captured); independent of the path-steps",
                      "ops_per_path_step": OPS_FOURWAY_F16K_TABLE,
                      "peak_basis": f"{sm_count} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock sampled)",
                      "launches": args.steps},

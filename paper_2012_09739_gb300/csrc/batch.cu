@@ -25,23 +25,31 @@ BatchKernelFn batch_kernel_f16_four(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_bf16_four(int kahan, int icdf, int sde);
 
 // Sums each item's tile partials (a contiguous range, fin[2i] .. + fin[2i+1])
-// in a fixed order, one warp per item, FP64.
-__global__ void batch_finalize_kernel(const double2 *tile_partials, const uint32_t *fin, int nitems, double2 *sums) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= nitems) return;
-    const uint32_t first = fin[2 * warp], count = fin[2 * warp + 1];
+// in a fixed order: one block per item, a strided FP64 sum per thread, then a
+// fixed tree over the block's threads.
+constexpr int FIN_THREADS = 256;
+
+__global__ void __launch_bounds__(FIN_THREADS) batch_finalize_kernel(const double2 *tile_partials, const uint32_t *fin,
+                                                                     double2 *sums) {
+    __shared__ double r1[FIN_THREADS], r2[FIN_THREADS];
+    const uint32_t first = fin[2 * blockIdx.x], count = fin[2 * blockIdx.x + 1];
     double s1 = 0.0, s2 = 0.0;
-    for (uint32_t i = lane; i < count; i += 32) {
+    for (uint32_t i = threadIdx.x; i < count; i += FIN_THREADS) {
         const double2 p = tile_partials[first + i];
         s1 += p.x;
         s2 += p.y;
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    r1[threadIdx.x] = s1;
+    r2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int h = FIN_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            r1[threadIdx.x] += r1[threadIdx.x + h];
+            r2[threadIdx.x] += r2[threadIdx.x + h];
+        }
+        __syncthreads();
     }
-    if (lane == 0) sums[warp] = make_double2(s1, s2);
+    if (threadIdx.x == 0) sums[blockIdx.x] = make_double2(r1[0], r2[0]);
 }
 
 namespace {
@@ -171,6 +179,15 @@ cudaError_t grow(T **p, size_t *cap, size_t n) {
 
 }  // namespace
 
+struct ShapeKey {
+    int32_t l, kind, prec, kahan, icdf, sde, scheme, zero;
+    uint64_t N;
+};
+// compared with memcmp: neither may hold padding bytes
+static_assert(sizeof(ShapeKey) == 40, "ShapeKey has no padding");
+static_assert(sizeof(mlmc_work) == sizeof(mlmc_sde_params) + 6 * 4 + 2 * 8 && sizeof(mlmc_sde_params) == 72,
+              "mlmc_work has no padding");
+
 struct BatchCache {
     // descriptors, uploaded by one copy: items, tile spans, per-item tile
     // ranges and the schedule counters (zeroed by the same copy), 16-byte
@@ -196,8 +213,9 @@ struct BatchCache {
     cudaEvent_t fork = nullptr, join[MAX_SIDE] = {};
     // mlmc_batch graph entry: the captured graph of one item-list shape
     cudaGraphExec_t exec = nullptr;
-    uint64_t shape = 0;          // signature of the items without path offsets and seed
-    uint64_t full = 0;           // signature of the items and seed the device descriptors hold
+    std::vector<ShapeKey> shape;         // the item-list shape the graph was captured for
+    std::vector<mlmc_work> staged_items; // the items the device descriptors hold
+    uint64_t staged_seed = 0;
     uint64_t last_use = 0;
     size_t items_bytes = 0;      // the LevelArgs part of the descriptors
     cudaEvent_t done = nullptr;  // after the entry's last launch and sums copy
@@ -210,7 +228,7 @@ struct BatchCache {
 struct BatchGraphs {
     std::vector<BatchCache *> entries;   // at most MAX_ENTRIES, least recently used evicted
     cudaStream_t capture_stream = nullptr;
-    std::map<uint64_t, int> tuned;       // item-list shape -> lane_work_log2
+    std::map<uint64_t, int> tuned;       // hash of the item-list shape -> lane_work_log2
     uint64_t clock = 0;
     static constexpr size_t MAX_ENTRIES = 8;
 };
@@ -369,7 +387,7 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
     // copy_out: the finalize kernel writes the sums straight into the pinned
     // host buffer (device-accessible under unified addressing), no copy
     double2 *dst = copy_out ? c.sums_host : c.sums;
-    batch_finalize_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(c.partials, c.fin, n, dst);
+    batch_finalize_kernel<<<n, FIN_THREADS, 0, s>>>(c.partials, c.fin, dst);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch finalize");
     return MLMC_OK;
 }
@@ -452,19 +470,17 @@ mlmc_status check_items(const mlmc_work *items, int n_items) {
     return MLMC_OK;
 }
 
-// Signature of the item list's shape: what the tiles, the kernel groups and
-// so the captured graph depend on (level, estimator, variant, SDE type and
-// scheme, N of every item).  Parameter values, payoffs, set ids, path
-// offsets and the seed only change the LevelArgs, which are re-staged.
-uint64_t shape_signature(const mlmc_work *items, int n) {
-    uint64_t h = fnv1a(&n, sizeof n);
+// What the tiles, the kernel groups and so the captured graph of an item
+// depend on: level, estimator, variant, SDE type and scheme, N.  Parameter
+// values, payoffs, set ids, path offsets and the seed only change the
+// LevelArgs, which are re-staged.
+std::vector<ShapeKey> shape_of(const mlmc_work *items, int n) {
+    std::vector<ShapeKey> k((size_t)n);
     for (int i = 0; i < n; ++i) {
         const mlmc_work &w = items[i];
-        const int32_t k[8] = {w.l, w.kind, w.prec, w.kahan, w.icdf, (int32_t)w.params.sde, (int32_t)w.params.scheme, 0};
-        h = fnv1a(k, sizeof k, h);
-        h = fnv1a(&w.N, sizeof w.N, h);
+        k[i] = ShapeKey{w.l, w.kind, w.prec, w.kahan, w.icdf, (int32_t)w.params.sde, (int32_t)w.params.scheme, 0, w.N};
     }
-    return h;
+    return k;
 }
 
 std::mutex g_batch_mu;   // one enqueue at a time per process: the entries are shared
@@ -472,7 +488,8 @@ std::mutex g_batch_mu;   // one enqueue at a time per process: the entries are s
 // Builds a graph entry: tile size (tuned once per shape), plan, descriptor
 // upload and the captured graph (batch kernels and finalize into c.sums).
 mlmc_status build_entry(DeviceState &d, BatchGraphs &G, BatchCache &c, const mlmc_work *items, int n_items,
-                        uint64_t seed, uint64_t shape, uint64_t full, cudaStream_t s) {
+                        uint64_t seed, std::vector<ShapeKey> &&shape, cudaStream_t s) {
+    const uint64_t shape_hash = fnv1a(shape.data(), shape.size() * sizeof(ShapeKey));
     cudaError_t e;
     mlmc_status st;
     if ((e = cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming)) != cudaSuccess ||
@@ -486,12 +503,12 @@ mlmc_status build_entry(DeviceState &d, BatchGraphs &G, BatchCache &c, const mlm
     cudaEventDestroy(ev);
     int lw = env_int("MLMC_BATCH_LANE_WORK_LOG2", 0);
     if (lw < 6 || lw > 20) {
-        auto it = G.tuned.find(shape);
+        auto it = G.tuned.find(shape_hash);
         if (it != G.tuned.end()) {
             lw = it->second;
         } else if (env_int("MLMC_AUTOTUNE", 1)) {
             if ((st = autotune(d, c, items, n_items, seed, G.capture_stream, &lw))) return st;
-            G.tuned[shape] = lw;
+            G.tuned[shape_hash] = lw;
         } else {
             lw = 12;
         }
@@ -510,8 +527,9 @@ mlmc_status build_entry(DeviceState &d, BatchGraphs &G, BatchCache &c, const mlm
     e = cudaGraphInstantiate(&c.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-    c.shape = shape;
-    c.full = full;
+    c.shape = std::move(shape);
+    c.staged_items.assign(items, items + n_items);
+    c.staged_seed = seed;
     c.items_bytes = p.items.size() * sizeof(LevelArgs);
     c.weight = p.weight;
     return MLMC_OK;
@@ -532,11 +550,12 @@ mlmc_status batch_enqueue(DeviceState &d, const mlmc_work *items, int n_items, u
             return cuda_fail(e, "cudaStreamCreate");
     }
     BatchGraphs &G = *d.batch;
-    const uint64_t shape = shape_signature(items, n_items);
-    const uint64_t full = fnv1a(items, sizeof(mlmc_work) * n_items, fnv1a(&seed, sizeof seed, shape));
+    std::vector<ShapeKey> shape = shape_of(items, n_items);
     BatchCache *c = nullptr;
     for (BatchCache *x : G.entries)
-        if (x->shape == shape) c = x;
+        if (x->shape.size() == shape.size() &&
+            memcmp(x->shape.data(), shape.data(), shape.size() * sizeof(ShapeKey)) == 0)
+            c = x;
     if (!c) {
         if (G.entries.size() >= BatchGraphs::MAX_ENTRIES) {
             auto lru = std::min_element(G.entries.begin(), G.entries.end(),
@@ -545,7 +564,7 @@ mlmc_status batch_enqueue(DeviceState &d, const mlmc_work *items, int n_items, u
             G.entries.erase(lru);
         }
         c = new BatchCache();
-        if ((st = build_entry(d, G, *c, items, n_items, seed, shape, full, s))) {
+        if ((st = build_entry(d, G, *c, items, n_items, seed, std::move(shape), s))) {
             batch_cache_destroy(c);
             return st;
         }
@@ -555,7 +574,7 @@ mlmc_status batch_enqueue(DeviceState &d, const mlmc_work *items, int n_items, u
     // the previous launch of this entry (on any stream) must be done with
     // the descriptors, the partials and the sums before they are reused
     if (c->launched && (e = cudaStreamWaitEvent(s, c->done, 0)) != cudaSuccess) return cuda_fail(e, "wait");
-    if (c->full != full) {
+    if (seed != c->staged_seed || memcmp(c->staged_items.data(), items, (size_t)n_items * sizeof(mlmc_work)) != 0) {
         // same shape, new parameters, offsets or seed: only the LevelArgs change
         if (c->restaged && (st = wait_event(c->staged, wait_limit_s()))) return st;
         LevelArgs *h = reinterpret_cast<LevelArgs *>(c->stage);
@@ -566,7 +585,8 @@ mlmc_status batch_enqueue(DeviceState &d, const mlmc_work *items, int n_items, u
             return cuda_fail(e, "descriptor upload");
         cudaEventRecord(c->staged, s);
         c->restaged = true;
-        c->full = full;
+        c->staged_items.assign(items, items + n_items);
+        c->staged_seed = seed;
     }
     if (t0) cudaEventRecord(t0, s);
     if ((e = cudaGraphLaunch(c->exec, s)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
