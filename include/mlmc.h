@@ -15,7 +15,11 @@
  *     give MLMC_EINVAL before anything is launched.  A CUDA error gives
  *     MLMC_ECUDA; mlmc_last_error() describes it.
  *   - Results are a deterministic function of (seed, path_offset, N, level,
- *     estimator kind, variant, set id) and of the launch configuration.
+ *     estimator kind, variant, set id): the sums are accumulated per chunk
+ *     group of 32-pair chunks, a split that depends on (l, N) only, and the
+ *     level and batch entry points give the same sums for the same item.
+ *     Only a level call of more than 2^22 chunk groups keeps one partial per
+ *     block instead, and then depends on the grid as well.
  *
  * Random numbers.  Philox4x32-10 (Salmon et al., SC'11; the paper names no
  * generator).  Counter (path lo32, path hi32, j, tag), key (seed lo32, seed
@@ -258,11 +262,15 @@ typedef struct {
  * shape tunes the tile size, captures and instantiates (hundreds of ms).  A
  * call with a known shape but other parameter values, payoffs, set ids, path
  * offsets or seed uploads n_items * mlmc_batch_descriptor_bytes() bytes of
- * descriptors and replays the graph.  The sums of one item are a fixed-order
- * FP64 sum of its tiles' FP32 partials: the same for every call with the
- * same items and seed.  Errors: MLMC_EINVAL for an invalid item (before any
- * launch), MLMC_ENOTREADY for MLP items without weights, MLMC_ECUDA,
- * MLMC_ETIMEOUT. */
+ * descriptors and replays the graph.  An item's sums are accumulated as the
+ * level kernels do (FP32 Kahan per lane over each chunk group of 32-pair
+ * chunks, a warp sum, FP64 partials, the same fixed-order finalize): they
+ * equal those of mlmc_level / mlmc_nested_level / mlmc_level_async for the
+ * same item, seed and offset bit for bit whenever that call keeps one
+ * partial per chunk group (at most 2^22 groups), whatever tile size the
+ * tuner picks.  Errors: MLMC_EINVAL for an invalid item or a batch beyond
+ * 2^32 - 1 tiles or partials (before any launch), MLMC_ENOTREADY for MLP
+ * items without weights, MLMC_ECUDA, MLMC_ETIMEOUT. */
 mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t seed, mlmc_sums *out_host, void *stream);
 
 /* mlmc_batch without the wait: enqueues the batch on `stream` and returns.

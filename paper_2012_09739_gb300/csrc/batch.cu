@@ -14,6 +14,7 @@
 
 #include "api_internal.h"
 #include "batch_kernels.cuh"
+#include "reduce.cuh"
 
 namespace mlmc {
 
@@ -24,32 +25,27 @@ BatchKernelFn batch_kernel_f32_four(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_f16_four(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_bf16_four(int kahan, int icdf, int sde);
 
-// Sums each item's tile partials (a contiguous range, fin[2i] .. + fin[2i+1])
-// in a fixed order: one block per item, a strided FP64 sum per thread, then a
-// fixed tree over the block's threads.
-constexpr int FIN_THREADS = 256;
-
-__global__ void __launch_bounds__(FIN_THREADS) batch_finalize_kernel(const double2 *tile_partials, const uint32_t *fin,
-                                                                     double2 *sums) {
-    __shared__ double r1[FIN_THREADS], r2[FIN_THREADS];
-    const uint32_t first = fin[2 * blockIdx.x], count = fin[2 * blockIdx.x + 1];
-    double s1 = 0.0, s2 = 0.0;
-    for (uint32_t i = threadIdx.x; i < count; i += FIN_THREADS) {
-        const double2 p = tile_partials[first + i];
-        s1 += p.x;
-        s2 += p.y;
-    }
-    r1[threadIdx.x] = s1;
-    r2[threadIdx.x] = s2;
-    __syncthreads();
-    for (int h = FIN_THREADS / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            r1[threadIdx.x] += r1[threadIdx.x + h];
-            r2[threadIdx.x] += r2[threadIdx.x + h];
+// Sums each item's group partials (fin[3i] .. + fin[3i+1]) exactly as the
+// level finalize does: one block_sum_fixed if they fit one span, else one per
+// span (into the item's scratch at fin[3i+2]) and one over the span sums.
+__global__ void __launch_bounds__(FINALIZE_THREADS) batch_finalize_kernel(double2 *partials, const uint32_t *fin,
+                                                                          double2 *sums) {
+    __shared__ double r1[FINALIZE_THREADS], r2[FINALIZE_THREADS];
+    const uint64_t first = fin[3 * blockIdx.x], count = fin[3 * blockIdx.x + 1], scratch = fin[3 * blockIdx.x + 2];
+    double2 s;
+    if (count <= FINALIZE_SPAN) {
+        s = block_sum_fixed(partials + first, 0, count, r1, r2);
+    } else {
+        const uint64_t spans = (count + FINALIZE_SPAN - 1) / FINALIZE_SPAN;
+        for (uint64_t k = 0; k < spans; ++k) {
+            const uint64_t lo = k * FINALIZE_SPAN, hi = lo + FINALIZE_SPAN < count ? lo + FINALIZE_SPAN : count;
+            const double2 t = block_sum_fixed(partials + first, lo, hi, r1, r2);
+            if (threadIdx.x == 0) partials[scratch + k] = t;
         }
         __syncthreads();
+        s = block_sum_fixed(partials + scratch, 0, spans, r1, r2);
     }
-    if (threadIdx.x == 0) sums[blockIdx.x] = make_double2(r1[0], r2[0]);
+    if (threadIdx.x == 0) sums[blockIdx.x] = s;
 }
 
 namespace {
@@ -59,7 +55,6 @@ struct Group {
     std::vector<TileSpan> spans;   // longest tiles first
     std::vector<double> tile_cost;  // per span: cost of one full tile
     uint32_t span_base = 0;        // offset of this group's spans in the device array
-    uint32_t tile_base = 0;        // offset of this group's tiles in the partials
     uint32_t ntiles = 0;
     double work = 0.0;
 };
@@ -67,11 +62,12 @@ struct Group {
 struct Plan {
     std::vector<LevelArgs> items;
     std::vector<Group> groups;
-    std::vector<uint32_t> fin;           // per item: first tile (global), tile count
+    std::vector<uint32_t> fin;           // per item: first group partial, partials, finalize scratch
     std::vector<double> weight;          // share of the launch's work per item
-    uint32_t ntiles = 0, nspans = 0;
+    uint32_t nspans = 0;
+    uint64_t npartials = 0;              // group partials and finalize scratch, all items
     double work = 0.0;
-    bool too_many_tiles = false;         // more than 2^32 - 1 tiles
+    bool too_large = false;              // tiles or partials beyond 32-bit indices
 };
 
 uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
@@ -89,13 +85,15 @@ double pair_cost(int l, int four) { return (ldexp(1.0, l) + PAIR_OVERHEAD_STEPS)
 double item_work(const mlmc_work &w) { return (double)((w.N + 1) / 2) * pair_cost(w.l, w.kind); }
 
 // Tiles: a lane takes max(1, 2^lane_work_log2 / (2^l + overhead)) pairs of an
-// item at level l, a tile is 32 such lanes.  Every item is one span of
-// consecutive tiles; each group's spans are ordered by the cost of their
-// tiles, longest first, so the host work is per item, not per tile.
+// item at level l, rounded up to whole chunk groups of the level kernel; a
+// tile is 32 such lanes.  Every item is one span of consecutive tiles; each
+// group's spans are ordered by the cost of their tiles, longest first, so the
+// host work is per item, not per tile.  Each item owns one partial per chunk
+// group and, above FINALIZE_SPAN of them, scratch for the finalize's span sums.
 Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, int lane_work_log2) {
     Plan plan;
     plan.items.resize(n);
-    plan.fin.assign(2 * (size_t)n, 0);
+    plan.fin.assign(3 * (size_t)n, 0);
     std::vector<uint32_t> group_of(n);
     for (int i = 0; i < n; ++i) plan.work += item_work(w[i]);
     for (int i = 0; i < n; ++i) {
@@ -112,17 +110,29 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
         if (gi == plan.groups.size()) plan.groups.push_back(Group{mode, w[i].prec, kahan, w[i].icdf, sde});
         Group &g = plan.groups[gi];
         group_of[i] = (uint32_t)gi;
-        const uint64_t np = (w[i].N + 1) / 2;
+        const uint64_t np = (w[i].N + 1) / 2, nchunks = (np + 31) / 32;
+        const uint32_t G = chunk_group(w[i].l, nchunks);
+        const uint64_t ngroups = (nchunks + G - 1) / G;
         const double pc = pair_cost(w[i].l, w[i].kind);
-        const uint64_t per_lane = std::max<uint64_t>(1, (uint64_t)(ldexp(1.0, lane_work_log2) / (pc / (w[i].kind ? 2.2 : 1.0))));
+        uint64_t per_lane = std::max<uint64_t>(1, (uint64_t)(ldexp(1.0, lane_work_log2) / (pc / (w[i].kind ? 2.2 : 1.0))));
+        per_lane = (per_lane + G - 1) / G * G;
         const uint64_t per_tile = 32 * per_lane;
         const uint64_t count = (np + per_tile - 1) / per_tile;
         const uint64_t rounds = (std::min(per_tile, np) + 31) / 32;
-        g.spans.push_back(TileSpan{(uint32_t)i, (uint32_t)per_tile, 0, (uint32_t)count});
+        plan.fin[3 * i] = (uint32_t)plan.npartials;
+        plan.fin[3 * i + 1] = (uint32_t)ngroups;
+        g.spans.push_back(TileSpan{(uint32_t)i, (uint32_t)per_tile, 0, (uint32_t)count, (uint32_t)plan.npartials, G});
+        plan.npartials += ngroups;
+        if (plan.npartials > 0xFFFFFFFFull || count > 0xFFFFFFFFull) plan.too_large = true;
         g.tile_cost.push_back((double)rounds * pc);
         g.work += item_work(w[i]);
     }
-    uint64_t tile_base = 0;
+    for (int i = 0; i < n; ++i) {          // finalize scratch for items above one span
+        const uint64_t cnt = plan.fin[3 * i + 1];
+        plan.fin[3 * i + 2] = (uint32_t)plan.npartials;
+        if (cnt > FINALIZE_SPAN) plan.npartials += (cnt + FINALIZE_SPAN - 1) / FINALIZE_SPAN;
+    }
+    if (plan.npartials > 0xFFFFFFFFull) plan.too_large = true;
     uint32_t span_base = 0;
     for (auto &g : plan.groups) {
         std::vector<uint32_t> order(g.spans.size());
@@ -136,21 +146,16 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
             TileSpan sp = g.spans[k];
             sp.begin = (uint32_t)begin;
             begin += sp.count;
-            plan.fin[2 * sp.item] = (uint32_t)(tile_base + sp.begin);
-            plan.fin[2 * sp.item + 1] = sp.count;
             spans.push_back(sp);
             cost.push_back(g.tile_cost[k]);
         }
         g.spans.swap(spans);
         g.tile_cost.swap(cost);
         g.ntiles = (uint32_t)begin;
-        g.tile_base = (uint32_t)tile_base;
         g.span_base = span_base;
-        tile_base += begin;
         span_base += (uint32_t)g.spans.size();
-        if (tile_base > 0xFFFFFFFFull) plan.too_many_tiles = true;
+        if (begin > 0xFFFFFFFFull) plan.too_large = true;
     }
-    plan.ntiles = (uint32_t)tile_base;
     plan.nspans = span_base;
     return plan;
 }
@@ -277,8 +282,8 @@ namespace {
 mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     cudaError_t e;
     const size_t n = p.items.size();
-    if (p.too_many_tiles) return fail(MLMC_EINVAL, "batch needs more than 2^32 - 1 tiles");
-    if ((e = grow(&c.partials, &c.partials_cap, p.ntiles)) != cudaSuccess) return cuda_fail(e, "batch buffers");
+    if (p.too_large) return fail(MLMC_EINVAL, "batch needs more than 2^32 - 1 tiles or partials");
+    if ((e = grow(&c.partials, &c.partials_cap, p.npartials)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if ((e = grow(&c.sums, &c.sums_cap, n)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if (c.sums_host_cap < n) {
         if (c.sums_host) cudaFreeHost(c.sums_host);
@@ -376,7 +381,7 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, ((uint64_t)g.ntiles + 7) / 8));
         cudaStream_t gs = gi == 0 ? s : c.side[(gi - 1) % BatchCache::MAX_SIDE];
         fns[gi]<<<(unsigned)grid, 256, 0, gs>>>(c.items, c.spans + g.span_base, (uint32_t)g.spans.size(), g.ntiles,
-                                                 c.counters + gi, c.partials + g.tile_base, d.tabs);
+                                                 c.counters + gi, c.partials, d.tabs);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch kernel");
     }
     for (size_t k = 0; k < nside; ++k) {
@@ -387,7 +392,7 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
     // copy_out: the finalize kernel writes the sums straight into the pinned
     // host buffer (device-accessible under unified addressing), no copy
     double2 *dst = copy_out ? c.sums_host : c.sums;
-    batch_finalize_kernel<<<n, FIN_THREADS, 0, s>>>(c.partials, c.fin, dst);
+    batch_finalize_kernel<<<n, FINALIZE_THREADS, 0, s>>>(c.partials, c.fin, dst);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch finalize");
     return MLMC_OK;
 }

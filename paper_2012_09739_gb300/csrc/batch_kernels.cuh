@@ -5,11 +5,16 @@
 // pair per lane per round) of one size per item: a span of consecutive tile
 // indices.  The host orders the spans by tile length, longest first; it
 // never lists the tiles.  Each warp of a grid of resident blocks repeatedly
-// takes the next tile index from an atomic counter, finds its span, simulates
-// the tile with the same per-pair code as the level kernels, and writes the
-// tile's (sum D, sum D^2) to its own slot; a finalize kernel then sums each
-// item's slots in a fixed order.  No warp ever waits on another warp or
-// block.
+// takes the next tile index from an atomic counter, finds its span and
+// simulates the tile with the same per-pair code as the level kernels.
+//
+// A tile covers whole chunk groups of the level kernel (32 pairs per chunk,
+// chunk_group(l, chunks) chunks per group) and accumulates exactly as the
+// level kernel does: per lane in FP32 with Kahan over a group's chunks, then
+// a warp sum, one FP64 (sum D, sum D^2) per group.  The finalize kernel adds
+// an item's group partials with the level finalize's fixed-order tree, so an
+// item's sums equal those of the level entry points bit for bit, whatever
+// the tile size.  No warp ever waits on another warp or block.
 #pragma once
 
 #include "level_kernels.cuh"
@@ -18,9 +23,11 @@ namespace mlmc {
 
 struct TileSpan {
     uint32_t item;       // index into the item array
-    uint32_t per_tile;   // pairs per tile (the item's last tile may be shorter)
+    uint32_t per_tile;   // pairs per tile, a multiple of 32 * group (the item's last tile may be shorter)
     uint32_t begin;      // first tile index of the item (within its launch)
     uint32_t count;      // tiles of the item
+    uint32_t part;       // the item's first group partial
+    uint32_t group;      // chunks per group partial: chunk_group(l, chunks)
 };
 
 // Index of the span holding tile t: the largest k with spans[k].begin <= t
@@ -123,7 +130,7 @@ __device__ void simulate_pair_seq(const LevelArgs &a, const SmemTable &tab, cons
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
 __global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 2 : (MODE == MODE_FOUR ? 3 : 4))
 batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uint32_t ntiles, uint32_t *counter,
-             double2 *tile_partials, const DevTables *tabs) {
+             double2 *partials, const DevTables *tabs) {
     __shared__ SmemTable tab;
     __shared__ SeqScratch<P> seq[8];           // one per warp (warp-cooperative single pairs)
     stage_table(tab, tabs);
@@ -140,6 +147,7 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
         const LevelArgs a = items[sp.item];
         const uint64_t first = (uint64_t)(t - sp.begin) * sp.per_tile;
         const uint32_t npairs = a.npairs - first < sp.per_tile ? (uint32_t)(a.npairs - first) : sp.per_tile;
+        const uint64_t chunk0 = first >> 5;        // the tile's first chunk, the start of a group
         KahanF32 s1, s2;
         if (npairs == 1 && a.l >= SEQ_MIN_LEVEL) {
             // one pair, long paths: the warp generates the normals, lane 0 steps
@@ -152,27 +160,35 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
                     s1.add(d1);
                     s2.add(d1 * d1);
                 }
-                tile_partials[t] = make_double2((double)s1.value(), (double)s2.value());
+                partials[sp.part + chunk0 / sp.group] = make_double2((double)s1.value(), (double)s2.value());
             }
             continue;
         }
         const uint32_t rounds = (npairs + 31u) >> 5;
+        uint32_t grp = sp.part + (uint32_t)(chunk0 / sp.group), in_group = 0;
         for (uint32_t r = 0; r < rounds; ++r) {
             const uint32_t k = (r << 5) + lane;
             const bool active = k < npairs;
             const uint64_t g = first + (active ? k : npairs - 1);
             float d0, d1, o0[5], o1[5];
             simulate_pair<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, d0, d1, o0, o1);
-            if (!active) continue;
-            s1.add(d0);
-            s2.add(d0 * d0);
-            if (2 * g + 1 < a.N) {
-                s1.add(d1);
-                s2.add(d1 * d1);
+            if (active) {
+                s1.add(d0);
+                s2.add(d0 * d0);
+                if (2 * g + 1 < a.N) {
+                    s1.add(d1);
+                    s2.add(d1 * d1);
+                }
+            }
+            if (++in_group == sp.group || r + 1 == rounds) {     // the end of a group (or of the item)
+                const float w1 = warp_sum(s1.value()), w2 = warp_sum(s2.value());
+                if (lane == 0) partials[grp] = make_double2((double)w1, (double)w2);
+                s1 = KahanF32();
+                s2 = KahanF32();
+                ++grp;
+                in_group = 0;
             }
         }
-        const float w1 = warp_sum(s1.value()), w2 = warp_sum(s2.value());
-        if (lane == 0) tile_partials[t] = make_double2((double)w1, (double)w2);
     }
 }
 

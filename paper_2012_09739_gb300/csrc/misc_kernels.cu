@@ -5,6 +5,7 @@
 #include "internal.h"
 #include "level_kernels.cuh"
 #include "mlp_tc.cuh"
+#include "reduce.cuh"
 
 namespace mlmc {
 
@@ -191,32 +192,17 @@ cudaError_t launch_build_table(DevTables *out, cudaStream_t s) {
 
 // ---------------------------------------------------------------- finalize
 // Deterministic FP64 sum of the partials: each block adds a fixed range of up
-// to FINALIZE_SPAN partials (fixed strided split over 1024 threads, then a
-// fixed tree).  One block when the partials fit one span; otherwise a first
-// pass writes one sum per span and a single block adds those.
-constexpr uint64_t FINALIZE_SPAN = 8192;
-
-__global__ void __launch_bounds__(1024) finalize_kernel(const double2 *partials, uint64_t count, double2 *out) {
-    __shared__ double r1[1024], r2[1024];
+// to FINALIZE_SPAN partials (block_sum_fixed).  One block when the partials
+// fit one span; otherwise a first pass writes one sum per span and a single
+// block adds those.
+__global__ void __launch_bounds__(FINALIZE_THREADS) finalize_kernel(const double2 *partials, uint64_t count,
+                                                                    double2 *out) {
+    __shared__ double r1[FINALIZE_THREADS], r2[FINALIZE_THREADS];
     const uint64_t lo = (uint64_t)blockIdx.x * FINALIZE_SPAN;
     const uint64_t hi = lo + FINALIZE_SPAN < count ? lo + FINALIZE_SPAN : count;
     const uint64_t end = gridDim.x == 1 ? count : hi;
-    double t1 = 0.0, t2 = 0.0;
-    for (uint64_t i = lo + threadIdx.x; i < end; i += 1024) {
-        t1 += partials[i].x;
-        t2 += partials[i].y;
-    }
-    r1[threadIdx.x] = t1;
-    r2[threadIdx.x] = t2;
-    __syncthreads();
-    for (int h = 512; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            r1[threadIdx.x] += r1[threadIdx.x + h];
-            r2[threadIdx.x] += r2[threadIdx.x + h];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[blockIdx.x] = make_double2(r1[0], r2[0]);
+    const double2 s = block_sum_fixed(partials, lo, end, r1, r2);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
 uint64_t finalize_scratch(uint64_t count) { return count <= FINALIZE_SPAN ? 0 : (count + FINALIZE_SPAN - 1) / FINALIZE_SPAN; }
@@ -224,10 +210,10 @@ uint64_t finalize_scratch(uint64_t count) { return count <= FINALIZE_SPAN ? 0 : 
 cudaError_t launch_finalize(const double2 *partials, uint64_t count, double *out, double2 *scratch, cudaStream_t s) {
     const uint64_t spans = finalize_scratch(count);
     if (spans == 0) {
-        finalize_kernel<<<1, 1024, 0, s>>>(partials, count, reinterpret_cast<double2 *>(out));
+        finalize_kernel<<<1, FINALIZE_THREADS, 0, s>>>(partials, count, reinterpret_cast<double2 *>(out));
     } else {
-        finalize_kernel<<<(unsigned)spans, 1024, 0, s>>>(partials, count, scratch);
-        finalize_kernel<<<1, 1024, 0, s>>>(scratch, spans, reinterpret_cast<double2 *>(out));
+        finalize_kernel<<<(unsigned)spans, FINALIZE_THREADS, 0, s>>>(partials, count, scratch);
+        finalize_kernel<<<1, FINALIZE_THREADS, 0, s>>>(scratch, spans, reinterpret_cast<double2 *>(out));
     }
     return cudaGetLastError();
 }

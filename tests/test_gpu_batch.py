@@ -1,8 +1,8 @@
 """mlmc_batch: all (set, level, estimator) items in one persistent launch give
-the same sums as item-by-item launches of the level kernels (same samples,
-different summation grouping), for GBM and OU sets, two-way and four-way,
-including items of 1 sample and ragged tiles; repeated calls replay the
-captured graph with identical results."""
+the same sums as item-by-item launches of the level kernels, bit for bit
+(same samples, same chunk-group partials, same fixed-order finalize), for GBM
+and OU sets, two-way and four-way, items of 1 sample, ragged tiles and every
+tile size; repeated calls replay the captured graph with identical results."""
 import math
 
 import numpy as np
@@ -34,11 +34,8 @@ def make_items(sets, levels, log2_n0, prec=M.MLMC_F16, kahan=1, icdf=M.MLMC_ICDF
     return items
 
 
-def _close(a, b):
-    assert a.n == b.n
-    tol1 = 2e-6 * (abs(b.s1) + math.sqrt(max(b.s2, 0.0) * b.n)) + 1e-30
-    assert abs(a.s1 - b.s1) <= tol1, (a.s1, b.s1)
-    assert abs(a.s2 - b.s2) <= 2e-6 * b.s2 + 1e-30, (a.s2, b.s2)
+def _same(a, b):
+    assert a.n == b.n and a.s1 == b.s1 and a.s2 == b.s2, (a.s1, b.s1, a.s2, b.s2)
 
 
 def test_batch_matches_level_kernels():
@@ -52,7 +49,7 @@ def test_batch_matches_level_kernels():
     for it, g in zip(items, got):
         fn = M.mlmc_nested_level if it.kind else M.mlmc_level
         ref = fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED, it.path_offset)
-        _close(g, ref)
+        _same(g, ref)
     again = M.mlmc_batch(items, SEED)           # replays the captured graph
     assert [(a.s1, a.s2) for a in again] == [(a.s1, a.s2) for a in got]
 
@@ -69,7 +66,7 @@ def test_single_item_batch_equals_level_kernel():
             g = M.mlmc_batch([it], SEED)[0]
             fn = M.mlmc_nested_level if kind else M.mlmc_level
             ref = fn(l, N, prec, True, icdf, p, SEED, 5)
-            _close(g, ref)
+            _same(g, ref)
 
 
 def test_batch_config3_full_size_statistics():
@@ -176,7 +173,7 @@ def test_batch_restaged_descriptors_equal_fresh_capture():
     for it, g in zip(b, rb):
         fn = M.mlmc_nested_level if it.kind else M.mlmc_level
         ref = fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED + 1, it.path_offset)
-        _close(g, ref)
+        _same(g, ref)
 
 
 def test_batch_graphs_of_two_shapes_alternate():
@@ -226,4 +223,25 @@ def test_bench_step_batches_match_level_kernels(kind):
     for it, (s1, s2) in zip(items, got):
         fn = M.mlmc_nested_level if kind else M.mlmc_level
         ref = fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED, 0)
-        _close(M.mlmc_sums(s1, s2, it.N, 0.0), ref)
+        _same(M.mlmc_sums(s1, s2, it.N, 0.0), ref)
+
+
+@pytest.mark.parametrize("lw", [6, 9, 12])
+def test_batch_sums_do_not_depend_on_the_tile_size(lw, monkeypatch):
+    """Tiles of any size cover whole chunk groups, so the sums are those of
+    the level entry points whatever tile size the tuner picks: here three
+    forced sizes, levels 0..7 with N giving one and several chunk groups,
+    ragged last groups and a two-stage finalize (> 8192 group partials)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    monkeypatch.setenv("MLMC_BATCH_LANE_WORK_LOG2", str(lw))
+    p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    Ns = [(1 << 22) + 37 * lw, 600001 + lw, 33 + lw, 1 << 19, 99999, 12345 + lw, 1 << 20, 777 + lw]
+    items = []
+    for l, N in enumerate(Ns):          # N differs per lw: a new shape, so a new graph at this tile size
+        items.append(M.mlmc_work(p, l, 0, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 0, N, 3))
+        items.append(M.mlmc_work(p, l, 1, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 0, N, 3))
+    got = M.mlmc_batch(items, SEED)
+    for it, g in zip(items, got):
+        fn = M.mlmc_nested_level if it.kind else M.mlmc_level
+        _same(g, fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED, it.path_offset))
