@@ -258,11 +258,12 @@ typedef struct {
  * kernel, all captured in a CUDA graph.  out_host[i] receives the sums of
  * items[i]; the call waits for them.  The library keeps the graphs of up to
  * 8 item-list shapes (the level, kind, prec, kahan, icdf, N, SDE type and
- * scheme of every item), least recently used evicted; the first call with a
+ * scheme of every item, and the seed), least recently used evicted; the first call with a
  * shape tunes the tile size, captures and instantiates (hundreds of ms).  A
- * call with a known shape but other parameter values, payoffs, set ids, path
- * offsets or seed uploads n_items * mlmc_batch_descriptor_bytes() bytes of
- * descriptors and replays the graph.  An item's sums are accumulated as the
+ * call with a known shape and seed but other parameter values, payoffs, set
+ * ids or path offsets uploads n_items * mlmc_batch_descriptor_bytes() bytes
+ * of descriptors and replays the graph; a new seed captures a new graph (the
+ * tuned tile size is kept).  An item's sums are accumulated as the
  * level kernels do (FP32 Kahan per lane over each chunk group of 32-pair
  * chunks, a warp sum, FP64 partials, the same fixed-order finalize): they
  * equal those of mlmc_level / mlmc_nested_level / mlmc_level_async for the

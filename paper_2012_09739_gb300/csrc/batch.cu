@@ -25,27 +25,32 @@ BatchKernelFn batch_kernel_f32_four(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_f16_four(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_bf16_four(int kahan, int icdf, int sde);
 
-// Sums each item's group partials (fin[3i] .. + fin[3i+1]) exactly as the
-// level finalize does: one block_sum_fixed if they fit one span, else one per
-// span (into the item's scratch at fin[3i+2]) and one over the span sums.
-__global__ void __launch_bounds__(FINALIZE_THREADS) batch_finalize_kernel(double2 *partials, const uint32_t *fin,
-                                                                          double2 *sums) {
-    __shared__ double r1[FINALIZE_THREADS], r2[FINALIZE_THREADS];
-    const uint64_t first = fin[3 * blockIdx.x], count = fin[3 * blockIdx.x + 1], scratch = fin[3 * blockIdx.x + 2];
-    double2 s;
-    if (count <= FINALIZE_SPAN) {
-        s = block_sum_fixed(partials + first, 0, count, r1, r2);
-    } else {
-        const uint64_t spans = (count + FINALIZE_SPAN - 1) / FINALIZE_SPAN;
-        for (uint64_t k = 0; k < spans; ++k) {
-            const uint64_t lo = k * FINALIZE_SPAN, hi = lo + FINALIZE_SPAN < count ? lo + FINALIZE_SPAN : count;
-            const double2 t = block_sum_fixed(partials + first, lo, hi, r1, r2);
-            if (threadIdx.x == 0) partials[scratch + k] = t;
-        }
-        __syncthreads();
-        s = block_sum_fixed(partials + scratch, 0, spans, r1, r2);
-    }
-    if (threadIdx.x == 0) sums[blockIdx.x] = s;
+// The batch finalize adds an item's group partials exactly as the level
+// finalize does (block_sum_fixed over at most FINALIZE_SPAN partials, or one
+// per span and one over the span sums): one block per item or span, all of
+// them in parallel.
+
+// First pass, items of more than FINALIZE_SPAN partials: job j = (first
+// partial, count, scratch slot) writes one span's sum.
+__global__ void __launch_bounds__(SUM_THREADS) batch_span_kernel(double2 *partials, const uint32_t *jobs) {
+    __shared__ double r1[SUM_THREADS], r2[SUM_THREADS];
+    const uint32_t j = blockIdx.x;
+    const double2 s = block_sum_fixed(partials + jobs[3 * j], jobs[3 * j + 1], r1, r2);
+    if (threadIdx.x == 0) partials[jobs[3 * j + 2]] = s;
+}
+
+// Each item's sums: over its group partials (fin[3i] .. + fin[3i+1]) when
+// they fit one span, else over its span sums (from fin[3i+2]).
+__global__ void __launch_bounds__(SUM_THREADS) batch_finalize_kernel(const double2 *partials, const uint32_t *fin,
+                                                                     double2 *sums) {
+    __shared__ double r1[SUM_THREADS], r2[SUM_THREADS];
+    const uint32_t w = blockIdx.x;
+    const uint64_t first = fin[3 * w], count = fin[3 * w + 1], scratch = fin[3 * w + 2];
+    const double2 s =
+        count <= FINALIZE_SPAN
+            ? block_sum_fixed(partials + first, count, r1, r2)
+            : block_sum_fixed(partials + scratch, (count + FINALIZE_SPAN - 1) / FINALIZE_SPAN, r1, r2);
+    if (threadIdx.x == 0) sums[w] = s;
 }
 
 namespace {
@@ -63,6 +68,7 @@ struct Plan {
     std::vector<LevelArgs> items;
     std::vector<Group> groups;
     std::vector<uint32_t> fin;           // per item: first group partial, partials, finalize scratch
+    std::vector<uint32_t> jobs;          // span jobs of the finalize's first pass: first, count, scratch slot
     std::vector<double> weight;          // share of the launch's work per item
     uint32_t nspans = 0;
     uint64_t npartials = 0;              // group partials and finalize scratch, all items
@@ -127,10 +133,15 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
         g.tile_cost.push_back((double)rounds * pc);
         g.work += item_work(w[i]);
     }
-    for (int i = 0; i < n; ++i) {          // finalize scratch for items above one span
-        const uint64_t cnt = plan.fin[3 * i + 1];
+    for (int i = 0; i < n; ++i) {          // finalize scratch and span jobs for items above one span
+        const uint64_t first = plan.fin[3 * i], cnt = plan.fin[3 * i + 1];
         plan.fin[3 * i + 2] = (uint32_t)plan.npartials;
-        if (cnt > FINALIZE_SPAN) plan.npartials += (cnt + FINALIZE_SPAN - 1) / FINALIZE_SPAN;
+        if (cnt <= FINALIZE_SPAN) continue;
+        for (uint64_t lo = 0; lo < cnt; lo += FINALIZE_SPAN) {
+            plan.jobs.push_back((uint32_t)(first + lo));
+            plan.jobs.push_back((uint32_t)std::min<uint64_t>(FINALIZE_SPAN, cnt - lo));
+            plan.jobs.push_back((uint32_t)plan.npartials++);
+        }
     }
     if (plan.npartials > 0xFFFFFFFFull) plan.too_large = true;
     uint32_t span_base = 0;
@@ -201,7 +212,8 @@ struct BatchCache {
     size_t blob_cap = 0;
     LevelArgs *items = nullptr;
     TileSpan *spans = nullptr;
-    uint32_t *fin = nullptr;             // per item: first tile, tile count
+    uint32_t *fin = nullptr;             // per item: first partial, partials, finalize scratch
+    uint32_t *jobs = nullptr;            // the finalize's span jobs
     uint32_t *counters = nullptr;
     double2 *partials = nullptr;
     size_t partials_cap = 0;
@@ -219,6 +231,7 @@ struct BatchCache {
     // mlmc_batch graph entry: the captured graph of one item-list shape
     cudaGraphExec_t exec = nullptr;
     std::vector<ShapeKey> shape;         // the item-list shape the graph was captured for
+    uint64_t graph_seed = 0;             // and the seed: the two-way kernels take its key as launch parameters
     std::vector<mlmc_work> staged_items; // the items the device descriptors hold
     uint64_t staged_seed = 0;
     uint64_t last_use = 0;
@@ -294,9 +307,9 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     }
     auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const size_t b_items = n * sizeof(LevelArgs), b_spans = (size_t)p.nspans * sizeof(TileSpan);
-    const size_t b_fin = p.fin.size() * 4, b_cnt = p.groups.size() * 4;
-    const size_t o_spans = up16(b_items), o_fin = o_spans + up16(b_spans), o_cnt = o_fin + up16(b_fin);
-    const size_t total = o_cnt + up16(b_cnt);
+    const size_t b_fin = p.fin.size() * 4, b_jobs = p.jobs.size() * 4, b_cnt = p.groups.size() * 4;
+    const size_t o_spans = up16(b_items), o_fin = o_spans + up16(b_spans), o_jobs = o_fin + up16(b_fin);
+    const size_t o_cnt = o_jobs + up16(b_jobs), total = o_cnt + up16(b_cnt);
     if ((e = grow(&c.blob, &c.blob_cap, total)) != cudaSuccess) return cuda_fail(e, "batch buffers");
     if (c.stage_cap < total) {
         if (c.stage) cudaFreeHost(c.stage);
@@ -310,6 +323,7 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     c.items = reinterpret_cast<LevelArgs *>(c.blob);
     c.spans = reinterpret_cast<TileSpan *>(c.blob + o_spans);
     c.fin = reinterpret_cast<uint32_t *>(c.blob + o_fin);
+    c.jobs = reinterpret_cast<uint32_t *>(c.blob + o_jobs);
     c.counters = reinterpret_cast<uint32_t *>(c.blob + o_cnt);
     unsigned char *h = c.stage;
     memset(h, 0, total);
@@ -317,6 +331,7 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     for (const auto &g : p.groups)
         memcpy(h + o_spans + g.span_base * sizeof(TileSpan), g.spans.data(), g.spans.size() * sizeof(TileSpan));
     memcpy(h + o_fin, p.fin.data(), b_fin);
+    if (b_jobs) memcpy(h + o_jobs, p.jobs.data(), b_jobs);
     if ((e = cudaMemcpyAsync(c.blob, h, total, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(e, "upload");
     return MLMC_OK;
 }
@@ -381,7 +396,7 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, ((uint64_t)g.ntiles + 7) / 8));
         cudaStream_t gs = gi == 0 ? s : c.side[(gi - 1) % BatchCache::MAX_SIDE];
         fns[gi]<<<(unsigned)grid, 256, 0, gs>>>(c.items, c.spans + g.span_base, (uint32_t)g.spans.size(), g.ntiles,
-                                                 c.counters + gi, c.partials, d.tabs);
+                                                 c.counters + gi, c.partials, d.tabs, p.items[0].k0, p.items[0].k1);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch kernel");
     }
     for (size_t k = 0; k < nside; ++k) {
@@ -392,7 +407,12 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
     // copy_out: the finalize kernel writes the sums straight into the pinned
     // host buffer (device-accessible under unified addressing), no copy
     double2 *dst = copy_out ? c.sums_host : c.sums;
-    batch_finalize_kernel<<<n, FINALIZE_THREADS, 0, s>>>(c.partials, c.fin, dst);
+    const uint32_t njobs = (uint32_t)(p.jobs.size() / 3);
+    if (njobs) {
+        batch_span_kernel<<<njobs, SUM_THREADS, 0, s>>>(c.partials, c.jobs);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch finalize");
+    }
+    batch_finalize_kernel<<<n, SUM_THREADS, 0, s>>>(c.partials, c.fin, dst);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch finalize");
     return MLMC_OK;
 }
@@ -533,6 +553,7 @@ mlmc_status build_entry(DeviceState &d, BatchGraphs &G, BatchCache &c, const mlm
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     c.shape = std::move(shape);
+    c.graph_seed = seed;
     c.staged_items.assign(items, items + n_items);
     c.staged_seed = seed;
     c.items_bytes = p.items.size() * sizeof(LevelArgs);
@@ -558,7 +579,7 @@ mlmc_status batch_enqueue(DeviceState &d, const mlmc_work *items, int n_items, u
     std::vector<ShapeKey> shape = shape_of(items, n_items);
     BatchCache *c = nullptr;
     for (BatchCache *x : G.entries)
-        if (x->shape.size() == shape.size() &&
+        if (x->graph_seed == seed && x->shape.size() == shape.size() &&
             memcmp(x->shape.data(), shape.data(), shape.size() * sizeof(ShapeKey)) == 0)
             c = x;
     if (!c) {
@@ -580,7 +601,7 @@ mlmc_status batch_enqueue(DeviceState &d, const mlmc_work *items, int n_items, u
     // the descriptors, the partials and the sums before they are reused
     if (c->launched && (e = cudaStreamWaitEvent(s, c->done, 0)) != cudaSuccess) return cuda_fail(e, "wait");
     if (seed != c->staged_seed || memcmp(c->staged_items.data(), items, (size_t)n_items * sizeof(mlmc_work)) != 0) {
-        // same shape, new parameters, offsets or seed: only the LevelArgs change
+        // same shape and seed, new parameters, payoffs, set ids or offsets: only the LevelArgs change
         if (c->restaged && (st = wait_event(c->staged, wait_limit_s()))) return st;
         LevelArgs *h = reinterpret_cast<LevelArgs *>(c->stage);
         for (int i = 0; i < n_items; ++i)

@@ -191,17 +191,15 @@ cudaError_t launch_build_table(DevTables *out, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- finalize
-// Deterministic FP64 sum of the partials: each block adds a fixed range of up
-// to FINALIZE_SPAN partials (block_sum_fixed).  One block when the partials
-// fit one span; otherwise a first pass writes one sum per span and a single
-// block adds those.
-__global__ void __launch_bounds__(FINALIZE_THREADS) finalize_kernel(const double2 *partials, uint64_t count,
-                                                                    double2 *out) {
-    __shared__ double r1[FINALIZE_THREADS], r2[FINALIZE_THREADS];
+// Deterministic FP64 sum of the partials (block_sum_fixed): one block when
+// the partials fit one span; otherwise a first pass, one block per span,
+// writes the span sums and one block adds those.
+__global__ void __launch_bounds__(SUM_THREADS) finalize_kernel(const double2 *partials, uint64_t count,
+                                                               uint64_t spans, double2 *out) {
+    __shared__ double r1[SUM_THREADS], r2[SUM_THREADS];
     const uint64_t lo = (uint64_t)blockIdx.x * FINALIZE_SPAN;
-    const uint64_t hi = lo + FINALIZE_SPAN < count ? lo + FINALIZE_SPAN : count;
-    const uint64_t end = gridDim.x == 1 ? count : hi;
-    const double2 s = block_sum_fixed(partials, lo, end, r1, r2);
+    const uint64_t n = spans == 0 ? count : (lo + FINALIZE_SPAN < count ? FINALIZE_SPAN : count - lo);
+    const double2 s = block_sum_fixed(partials + lo, n, r1, r2);
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
@@ -210,10 +208,10 @@ uint64_t finalize_scratch(uint64_t count) { return count <= FINALIZE_SPAN ? 0 : 
 cudaError_t launch_finalize(const double2 *partials, uint64_t count, double *out, double2 *scratch, cudaStream_t s) {
     const uint64_t spans = finalize_scratch(count);
     if (spans == 0) {
-        finalize_kernel<<<1, FINALIZE_THREADS, 0, s>>>(partials, count, reinterpret_cast<double2 *>(out));
+        finalize_kernel<<<1, SUM_THREADS, 0, s>>>(partials, count, 0, reinterpret_cast<double2 *>(out));
     } else {
-        finalize_kernel<<<(unsigned)spans, FINALIZE_THREADS, 0, s>>>(partials, count, scratch);
-        finalize_kernel<<<1, FINALIZE_THREADS, 0, s>>>(scratch, spans, reinterpret_cast<double2 *>(out));
+        finalize_kernel<<<(unsigned)spans, SUM_THREADS, 0, s>>>(partials, count, spans, scratch);
+        finalize_kernel<<<1, SUM_THREADS, 0, s>>>(scratch, spans, 0, reinterpret_cast<double2 *>(out));
     }
     return cudaGetLastError();
 }

@@ -154,10 +154,11 @@ def test_batch_async_equals_sync():
 
 def test_batch_restaged_descriptors_equal_fresh_capture():
     """A call whose items differ from the cached shape only in parameter
-    values, payoff, path offsets or seed re-stages the descriptors and
-    replays the graph; its sums equal those of a freshly built graph of the
-    same items (the entry evicted by eight other shapes first), and agree
-    with the level kernels."""
+    values, payoff or path offsets re-stages the descriptors and replays the
+    graph; its sums equal those of a freshly built graph of the same items
+    (the entry evicted by eight other shapes first) and the level kernels'.
+    A new seed gets its own graph (the two-way kernels take the key as launch
+    parameters), with the level kernels' sums for that seed."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     a = _bench_items(1, N=3001) + _bench_items(0, N=3001)
@@ -165,15 +166,16 @@ def test_batch_restaged_descriptors_equal_fresh_capture():
     for it in b[::3]:
         it.params.payoff = M.MLMC_PAYOFF_X
     ra = M.mlmc_batch(a, SEED)
-    rb = M.mlmc_batch(b, SEED + 1)                  # same shape: re-staged
+    rb = M.mlmc_batch(b, SEED)                      # same shape and seed: re-staged
     assert _pairs(M.mlmc_batch(a, SEED)) == _pairs(ra)
-    for k in range(8):                               # evict the entry
+    rc = M.mlmc_batch(b, SEED + 1)                  # a new seed
+    for k in range(8):                               # evict the entries
         M.mlmc_batch(_bench_items(0, N=100 + k)[:3], SEED)
-    assert _pairs(M.mlmc_batch(b, SEED + 1)) == _pairs(rb)     # fresh graph, same tiles
-    for it, g in zip(b, rb):
-        fn = M.mlmc_nested_level if it.kind else M.mlmc_level
-        ref = fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED + 1, it.path_offset)
-        _same(g, ref)
+    assert _pairs(M.mlmc_batch(b, SEED)) == _pairs(rb)     # fresh graph, same tiles
+    for seed, got in ((SEED, rb), (SEED + 1, rc)):
+        for it, g in zip(b, got):
+            fn = M.mlmc_nested_level if it.kind else M.mlmc_level
+            _same(g, fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, seed, it.path_offset))
 
 
 def test_batch_graphs_of_two_shapes_alternate():
