@@ -54,10 +54,10 @@ OPS_FOURWAY_F16K_TABLE = 50.75
 OPS_TWOWAY_F16K_TABLE = 24.25
 # DRAM bytes (read + write) of one four-way batched launch over levels 0..12
 # at N = 2^20, from an ncu capture of that launch (dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass): the descriptors and the table, 0.33 to
-# 0.67 MB over the launches captured, no writes (the tile partials stay in
+# dram__bytes_write.sum, one pass): the descriptors and the table, 0.20 to
+# 0.49 MB over the launches captured, no writes (the group partials stay in
 # L2).  The traffic does not grow with the path-steps.
-TRAFFIC_FOURWAY_BYTES = 669440
+TRAFFIC_FOURWAY_BYTES = 494080
 
 
 def _env_rank():
