@@ -135,17 +135,6 @@ def batch_items(M, params, kind, prec, kahan, icdf, offset):
     return [M.mlmc_work(params, l, kind, prec, int(kahan), icdf, 0, N_PER_LEVEL, offset) for l in LEVELS]
 
 
-def launches_per_level_call(l, n):
-    """Kernel launches of one mlmc_level_async call: the level kernel and a
-    one- or two-pass finalize (two passes above 8192 group partials; groups
-    of up to 64 >> l chunks of 32 sample pairs below l = 6, at least 16384
-    groups when there are enough chunks)."""
-    chunks = ((n + 1) // 2 + 31) // 32
-    g = 1 if l >= 6 else max(1, min(chunks // 16384, 64 >> l))
-    groups = (chunks + g - 1) // g
-    return 1 + (1 if groups <= 8192 else 2)
-
-
 def launches_per_batch_call(items):
     """Kernel launches of one mlmc_batch(_async) replay: one persistent batch
     kernel per group of items sharing estimator, variant and SDE scheme, and
