@@ -137,10 +137,19 @@ def batch_items(M, params, kind, prec, kahan, icdf, offset):
 
 def launches_per_batch_call(items):
     """Kernel launches of one mlmc_batch(_async) replay: one persistent batch
-    kernel per group of items sharing estimator, variant and SDE scheme, and
-    the finalize kernel."""
+    kernel per group of items sharing estimator, variant and SDE scheme, the
+    finalize's span pass when an item has more than 8192 chunk-group partials
+    (chunks of 32 sample pairs, chunk_group(l, chunks) of them per partial:
+    1 from level 6, else up to 64 >> l keeping at least 16384 groups), and the
+    finalize kernel."""
     groups = {(w.kind, w.prec, w.kahan, w.icdf, w.params.sde, w.params.scheme) for w in items}
-    return len(groups) + 1
+
+    def partials(w):
+        chunks = ((w.N + 1) // 2 + 31) // 32
+        g = 1 if w.l >= 6 else max(1, min(chunks // 16384, 64 >> w.l))
+        return (chunks + g - 1) // g
+    spans = any(partials(w) > 8192 for w in items)
+    return len(groups) + (1 if spans else 0) + 1
 
 
 def path_steps(levels, n):
