@@ -586,7 +586,9 @@ mlmc_status batch_enqueue(DeviceState &d, const mlmc_work *items, int n_items, u
         if (G.entries.size() >= BatchGraphs::MAX_ENTRIES) {
             auto lru = std::min_element(G.entries.begin(), G.entries.end(),
                                         [](const BatchCache *x, const BatchCache *y) { return x->last_use < y->last_use; });
-            batch_cache_destroy(*lru);      // waits for its last launch
+            // its last launch must be done with the buffers (bounded wait)
+            if ((*lru)->launched && (st = wait_event((*lru)->done, wait_limit_s()))) return st;
+            batch_cache_destroy(*lru);
             G.entries.erase(lru);
         }
         c = new BatchCache();
