@@ -292,7 +292,9 @@ namespace {
 // zeroed schedule counters are packed into pinned staging memory and copied
 // to the device in one asynchronous copy on s (the buffers only grow, with
 // cudaMalloc, when a larger batch arrives).
-mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
+// stage_idle: the caller knows that no copy out of the staging buffer is
+// still in flight (it waited for the previous round), so no stream sync.
+mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s, bool stage_idle = false) {
     cudaError_t e;
     const size_t n = p.items.size();
     if (p.too_large) return fail(MLMC_EINVAL, "batch needs more than 2^32 - 1 tiles or partials");
@@ -319,7 +321,7 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
         c.stage_cap = total * 2;
     }
     // the previous round's copy out of the staging buffer must be done
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload");
+    if (!stage_idle && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "upload");
     c.items = reinterpret_cast<LevelArgs *>(c.blob);
     c.spans = reinterpret_cast<TileSpan *>(c.blob + o_spans);
     c.fin = reinterpret_cast<uint32_t *>(c.blob + o_fin);
@@ -336,6 +338,10 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s) {
     return MLMC_OK;
 }
 
+// Work (pair-step cost units, pair_cost) from which a batch's groups run
+// concurrently: a few hundred microseconds of GPU time.
+constexpr double CONCURRENT_WORK = 1e8;
+
 // Resident blocks per SM of a batch kernel (cached per kernel).
 int blocks_per_sm(BatchCache &c, BatchKernelFn fn) {
     auto it = c.occupancy.find((const void *)fn);
@@ -347,8 +353,9 @@ int blocks_per_sm(BatchCache &c, BatchKernelFn fn) {
 }
 
 // Enqueues the whole batch on stream s (also used inside graph capture).
-// Groups run concurrently: the first on s, the others on side streams forked
-// from s and joined back before the finalize.  A lone group gets every
+// Groups of a large batch run concurrently: the first on s, the others on
+// side streams forked from s and joined back before the finalize (the two
+// groups of a small one run one after another on s).  A lone group gets every
 // resident block; with several, each gets a share of the GPU proportional to
 // its work, but at least one warp for each of its tiles that is longer than
 // the whole batch's ideal time per warp (their tiles are the critical path).
@@ -368,7 +375,11 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         bps[gi] = blocks_per_sm(c, fns[gi]);
         bps_min = std::min(bps_min, bps[gi]);
     }
-    const size_t nside = std::min<size_t>(ng - 1, BatchCache::MAX_SIDE);
+    // two groups of a small batch run one after another on s: forking costs
+    // more than the overlap gains when the batch takes microseconds; from
+    // three groups on, their launch latencies alone make concurrency pay
+    const bool concurrent = ng > 2 || (ng > 1 && p.work >= CONCURRENT_WORK);
+    const size_t nside = concurrent ? std::min<size_t>(ng - 1, BatchCache::MAX_SIDE) : 0;
     if (nside > 0) {
         if (!c.fork && (e = cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming)) != cudaSuccess)
             return cuda_fail(e, "cudaEventCreate");
@@ -387,14 +398,14 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         const Group &g = p.groups[gi];
         const uint64_t full = (uint64_t)bps[gi] * d.sm_count;
         uint64_t grid = full;
-        if (ng > 1) {
+        if (concurrent) {
             uint64_t long_tiles = 0;
             for (size_t k = 0; k < g.spans.size() && g.tile_cost[k] > ideal; ++k) long_tiles += g.spans[k].count;
             const uint64_t share = (uint64_t)ceil(g.work / p.work * (double)full);
             grid = std::min(full, std::max(share, (long_tiles + 7) / 8));
         }
         grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, ((uint64_t)g.ntiles + 7) / 8));
-        cudaStream_t gs = gi == 0 ? s : c.side[(gi - 1) % BatchCache::MAX_SIDE];
+        cudaStream_t gs = gi == 0 || !concurrent ? s : c.side[(gi - 1) % BatchCache::MAX_SIDE];
         fns[gi]<<<(unsigned)grid, 256, 0, gs>>>(c.items, c.spans + g.span_base, (uint32_t)g.spans.size(), g.ntiles,
                                                  c.counters + gi, c.partials, d.tabs, p.items[0].k0, p.items[0].k1);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch kernel");
@@ -473,7 +484,8 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
 mlmc_status batch_round(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed,
                         cudaStream_t s) {
     Plan p = make_plan(d, w, n, seed, work_lane_log2(d, w, n));
-    mlmc_status st = upload(c, p, s);
+    // the driver waits for every round before it plans the next one
+    mlmc_status st = upload(c, p, s, true);
     if (st) return st;
     return enqueue(d, c, p, s, true, false);
 }
