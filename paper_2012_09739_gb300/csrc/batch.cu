@@ -338,10 +338,6 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s, bool stage_idle
     return MLMC_OK;
 }
 
-// Work (pair-step cost units, pair_cost) from which a batch's groups run
-// concurrently: a few hundred microseconds of GPU time.
-constexpr double CONCURRENT_WORK = 1e8;
-
 // Resident blocks per SM of a batch kernel (cached per kernel).
 int blocks_per_sm(BatchCache &c, BatchKernelFn fn) {
     auto it = c.occupancy.find((const void *)fn);
@@ -353,9 +349,8 @@ int blocks_per_sm(BatchCache &c, BatchKernelFn fn) {
 }
 
 // Enqueues the whole batch on stream s (also used inside graph capture).
-// Groups of a large batch run concurrently: the first on s, the others on
-// side streams forked from s and joined back before the finalize (the two
-// groups of a small one run one after another on s).  A lone group gets every
+// Groups run concurrently: the first on s, the others on side streams forked
+// from s and joined back before the finalize.  A lone group gets every
 // resident block; with several, each gets a share of the GPU proportional to
 // its work, but at least one warp for each of its tiles that is longer than
 // the whole batch's ideal time per warp (their tiles are the critical path).
@@ -375,10 +370,9 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         bps[gi] = blocks_per_sm(c, fns[gi]);
         bps_min = std::min(bps_min, bps[gi]);
     }
-    // two groups of a small batch run one after another on s: forking costs
-    // more than the overlap gains when the batch takes microseconds; from
-    // three groups on, their launch latencies alone make concurrency pay
-    const bool concurrent = ng > 2 || (ng > 1 && p.work >= CONCURRENT_WORK);
+    // concurrent even for a batch of microseconds: two groups of an adaptive
+    // round at RMSE 3e-4 took 0.113 ms forked against 0.127 ms in sequence
+    const bool concurrent = ng > 1;
     const size_t nside = concurrent ? std::min<size_t>(ng - 1, BatchCache::MAX_SIDE) : 0;
     if (nside > 0) {
         if (!c.fork && (e = cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming)) != cudaSuccess)
