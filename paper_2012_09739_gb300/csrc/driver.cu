@@ -85,7 +85,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
     if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess)
         st = cuda_fail(e, "cudaEventCreate");
     // MLMC_RUN_LOG=1: one JSON line per round on stderr (items, path-steps,
-    // device and wall time)
+    // device and wall time, host time to plan and enqueue the round)
     const char *log_env = getenv("MLMC_RUN_LOG");
     const bool log = log_env && atoi(log_env) > 0;
     if (log) {
@@ -126,6 +126,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         if (log) cudaEventRecord(ev_a, s);
         mlmc_status r = batch_round(*d, *cache, items.data(), (int)items.size(), o->seed, s);
         if (r) return r;
+        const auto t_enq = std::chrono::steady_clock::now();
         if (log) cudaEventRecord(ev_b, s);
         cudaEventRecord(done, s);
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
@@ -136,8 +137,9 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
             double ps = 0.0;
             for (const auto &w : items) ps += ldexp((double)w.N, w.l);
             const double host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            const double enq_ms = std::chrono::duration<double, std::milli>(t_enq - t0).count();
             fprintf(stderr, "{\"mlmc_run_round\": %d, \"items\": %zu, \"path_steps\": %.0f, \"device_ms\": %.4f, "
-                            "\"wall_ms\": %.4f}\n", rounds, items.size(), ps, ms, host_ms);
+                            "\"wall_ms\": %.4f, \"enqueue_ms\": %.4f}\n", rounds, items.size(), ps, ms, host_ms, enq_ms);
         }
         const double2 *sums = batch_sums_host(*cache);
         for (size_t k = 0; k < which.size(); ++k) {
