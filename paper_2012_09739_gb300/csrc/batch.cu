@@ -205,9 +205,9 @@ static_assert(sizeof(mlmc_work) == sizeof(mlmc_sde_params) + 6 * 4 + 2 * 8 && si
               "mlmc_work has no padding");
 
 struct BatchCache {
-    // descriptors, uploaded by one copy: items, tile spans, per-item tile
-    // ranges and the schedule counters (zeroed by the same copy), 16-byte
-    // aligned
+    // descriptors, uploaded by one copy: items, tile spans, per-item partial
+    // ranges, the finalize's span jobs and the schedule counters (zeroed by
+    // the same copy), each 16-byte aligned
     unsigned char *blob = nullptr;
     size_t blob_cap = 0;
     LevelArgs *items = nullptr;
@@ -233,7 +233,6 @@ struct BatchCache {
     std::vector<ShapeKey> shape;         // the item-list shape the graph was captured for
     uint64_t graph_seed = 0;             // and the seed: the two-way kernels take its key as launch parameters
     std::vector<mlmc_work> staged_items; // the items the device descriptors hold
-    uint64_t staged_seed = 0;
     uint64_t last_use = 0;
     size_t items_bytes = 0;      // the LevelArgs part of the descriptors
     cudaEvent_t done = nullptr;  // after the entry's last launch and sums copy
@@ -561,17 +560,18 @@ mlmc_status build_entry(DeviceState &d, BatchGraphs &G, BatchCache &c, const mlm
     c.shape = std::move(shape);
     c.graph_seed = seed;
     c.staged_items.assign(items, items + n_items);
-    c.staged_seed = seed;
     c.items_bytes = p.items.size() * sizeof(LevelArgs);
     c.weight = p.weight;
     return MLMC_OK;
 }
 
-// Finds or builds the graph entry of this item list and enqueues one replay
-// on s: re-stages the descriptors if the items or the seed changed since the
-// entry's last launch (within the shape), waits (on s) for that launch, launches the
-// graph and copies the item sums to dst (device or pinned host memory; NULL:
-// the entry's pinned host buffer), then records the entry's done event.  t0/t1 (optional) bracket the graph.
+// Finds or builds the graph entry of this item-list shape and seed and
+// enqueues one replay on s: waits (on s) for the entry's previous launch,
+// re-stages the descriptors if the items changed since then (parameter
+// values, payoffs, set ids, path offsets), launches the graph and copies the
+// item sums to dst (device or pinned host memory; NULL: the entry's pinned
+// host buffer), then records the entry's done event.  t0/t1 (optional)
+// bracket the graph.
 mlmc_status batch_enqueue(DeviceState &d, const mlmc_work *items, int n_items, uint64_t seed, void *dst,
                           cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1, BatchCache **used) {
     cudaError_t e;
@@ -608,7 +608,7 @@ mlmc_status batch_enqueue(DeviceState &d, const mlmc_work *items, int n_items, u
     // the previous launch of this entry (on any stream) must be done with
     // the descriptors, the partials and the sums before they are reused
     if (c->launched && (e = cudaStreamWaitEvent(s, c->done, 0)) != cudaSuccess) return cuda_fail(e, "wait");
-    if (seed != c->staged_seed || memcmp(c->staged_items.data(), items, (size_t)n_items * sizeof(mlmc_work)) != 0) {
+    if (memcmp(c->staged_items.data(), items, (size_t)n_items * sizeof(mlmc_work)) != 0) {
         // same shape and seed, new parameters, payoffs, set ids or offsets: only the LevelArgs change
         if (c->restaged && (st = wait_event(c->staged, wait_limit_s()))) return st;
         LevelArgs *h = reinterpret_cast<LevelArgs *>(c->stage);
@@ -620,7 +620,6 @@ mlmc_status batch_enqueue(DeviceState &d, const mlmc_work *items, int n_items, u
         cudaEventRecord(c->staged, s);
         c->restaged = true;
         c->staged_items.assign(items, items + n_items);
-        c->staged_seed = seed;
     }
     if (t0) cudaEventRecord(t0, s);
     if ((e = cudaGraphLaunch(c->exec, s)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
