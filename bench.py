@@ -584,10 +584,11 @@ def run_reference(args):
     rates = []
     for _ in range(args.warmup):
         _cpu_sample(args.cpu_seconds / 4, threads)
-    t_total, ps_total = 0.0, 0
+    t_total, ps_total, ns = 0.0, 0, []
     for _ in range(args.steps):
         rate, n, dt = _cpu_sample(args.cpu_seconds / 2, threads)
         rates.append(rate)
+        ns.append(n)
         t_total += dt
         ps_total += 2 * path_steps(LEVELS, n)
     value = ps_total / t_total
@@ -597,9 +598,15 @@ def run_reference(args):
         "value": value, "unit": "path-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f16 (emulated in FP64)", "data": "synthetic",
-        "config": {"workload": WORKLOAD + " (bounded sample per step)"},
+        "config": {"workload": WORKLOAD, "levels": [min(LEVELS), max(LEVELS)], "N_per_level": N_PER_LEVEL,
+                   "path_steps_per_step": 2 * path_steps(LEVELS, N_PER_LEVEL),
+                   "estimators": "two-way FP16+Kahan table + four-way nested",
+                   "sample": f"each step a bounded sample of the workload: {min(ns)}-{max(ns)} samples per level "
+                             f"and estimator instead of {N_PER_LEVEL}",
+                   "parallelism": f"OpenMP over paths, {threads} host threads"},
         "cpu_baseline": {"value": value, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
-                         "sample": f"per step: levels 0..12, a few thousand samples per level, ~{args.cpu_seconds / 2:.0f} s"},
+                         "sample": f"per step: levels 0..12, {min(ns)}-{max(ns)} samples per level and estimator "
+                                   f"(two-way + four-way), ~{args.cpu_seconds / 2:.0f} s"},
         "e2e": {"value": value, "unit": "path-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
