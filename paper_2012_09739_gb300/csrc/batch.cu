@@ -100,7 +100,6 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
     Plan plan;
     plan.items.resize(n);
     plan.fin.assign(3 * (size_t)n, 0);
-    std::vector<uint32_t> group_of(n);
     for (int i = 0; i < n; ++i) plan.work += item_work(w[i]);
     for (int i = 0; i < n; ++i) {
         plan.items[i] = make_level_args(d, w[i].kind, w[i].l, w[i].N, w[i].prec, w[i].icdf, &w[i].params, seed,
@@ -115,7 +114,6 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
         }
         if (gi == plan.groups.size()) plan.groups.push_back(Group{mode, w[i].prec, kahan, w[i].icdf, sde});
         Group &g = plan.groups[gi];
-        group_of[i] = (uint32_t)gi;
         const uint64_t np = (w[i].N + 1) / 2, nchunks = (np + 31) / 32;
         const uint32_t G = chunk_group(w[i].l, nchunks);
         const uint64_t ngroups = (nchunks + G - 1) / G;
