@@ -145,8 +145,27 @@ def _stream(stream):
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _dptr(t):
+def _buf(t, name, itemsize, n, dtype=None):
+    """Device pointer of t after checking that the library may read or write n
+    elements of itemsize bytes through it: a contiguous CUDA tensor (of the
+    given dtype, if any) with at least n elements."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype} (got {t.dtype})")
+    if t.element_size() != itemsize:
+        raise ValueError(f"{name} must have {itemsize}-byte elements (got {t.dtype})")
+    if t.numel() < n:
+        raise ValueError(f"{name} needs at least {n} elements (has {t.numel()})")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _f64(name, t, n):
+    import torch
+    return _buf(t, name, 8, n, torch.float64)
 
 
 def sde_params(sde=MLMC_GBM, payoff=MLMC_PAYOFF_X, p0=0.05, p1=0.2, p2=0.0, x0=1.0, T=1.0, K=1.0,
@@ -177,39 +196,40 @@ def mlmc_nested_level(l, N, prec, kahan, icdf, params, seed, path_offset=0, stre
 def mlmc_level_async(four, l, N, prec, kahan, icdf, params, seed, path_offset, sums_dev, stream=None):
     """sums_dev: float64 CUDA tensor with >= 2 elements (receives sum D, sum D^2)."""
     _check(load().mlmc_level_async(int(four), l, N, prec, int(kahan), icdf, ctypes.byref(params), seed,
-                                   path_offset, _dptr(sums_dev), _stream(stream)))
+                                   path_offset, _f64("sums_dev", sums_dev, 2), _stream(stream)))
 
 
 def mlmc_level_noalloc(four, l, N, prec, kahan, icdf, params, seed, path_offset, sums_dev, stream=None):
     """Allocation-free variant of mlmc_level_async (fixed device scratch, N <= 2^21)."""
     _check(load().mlmc_level_noalloc(int(four), l, N, prec, int(kahan), icdf, ctypes.byref(params), seed,
-                                     path_offset, _dptr(sums_dev), _stream(stream)))
+                                     path_offset, _f64("sums_dev", sums_dev, 2), _stream(stream)))
 
 
 def mlmc_level_paths(four, l, N, prec, kahan, icdf, params, seed, path_offset, out_dev, stream=None):
     """out_dev: float32 CUDA tensor of N*3 (two-way) or N*5 (four-way) elements."""
-    need = N * (5 if four else 3)
-    if out_dev.numel() < need:
-        raise ValueError(f"out_dev needs {need} elements")
+    out = _buf(out_dev, "out_dev", 4, N * (5 if four else 3))
     _check(load().mlmc_level_paths(int(four), l, N, prec, int(kahan), icdf, ctypes.byref(params), seed,
-                                   path_offset, _dptr(out_dev), _stream(stream)))
+                                   path_offset, out, _stream(stream)))
 
 
 def approx_icdf(u_dev, z_dev, icdf, prec, stream=None):
-    """u_dev float32; z_dev float32 (F32) or float16 (F16), same length."""
-    if z_dev.numel() < u_dev.numel():
-        raise ValueError("z_dev too small")
-    _check(load().approx_icdf(_dptr(u_dev), _dptr(z_dev), u_dev.numel(), icdf, prec, _stream(stream)))
+    """u_dev float32; z_dev with 4-byte (F32) or 2-byte (F16, BF16: the format's bits) elements, as many."""
+    n = u_dev.numel()
+    u = _buf(u_dev, "u_dev", 4, n)
+    z = _buf(z_dev, "z_dev", 4 if prec == MLMC_F32 else 2, n)
+    _check(load().approx_icdf(u, z, n, icdf, prec, _stream(stream)))
 
 
 def mlmc_philox4x32_10(ctr_dev, key_dev, out_dev, stream=None):
     """ctr_dev (n, 4), key_dev (n, 2), out_dev (n, 4): int32 CUDA tensors holding uint32 bits."""
     n = ctr_dev.shape[0]
-    _check(load().mlmc_philox4x32_10(_dptr(ctr_dev), _dptr(key_dev), _dptr(out_dev), n, _stream(stream)))
+    _check(load().mlmc_philox4x32_10(_buf(ctr_dev, "ctr_dev", 4, 4 * n), _buf(key_dev, "key_dev", 4, 2 * n),
+                                     _buf(out_dev, "out_dev", 4, 4 * n), n, _stream(stream)))
 
 
 def mlmc_uniforms(w_dev, u_dev, stream=None):
-    _check(load().mlmc_uniforms(_dptr(w_dev), _dptr(u_dev), w_dev.numel(), _stream(stream)))
+    n = w_dev.numel()
+    _check(load().mlmc_uniforms(_buf(w_dev, "w_dev", 4, n), _buf(u_dev, "u_dev", 4, n), n, _stream(stream)))
 
 
 def mlmc_icdf_table():
@@ -251,15 +271,17 @@ def mlmc_mlp_get_weights():
 
 def mlmc_mlp_grad(u_dev, z_dev, grad_dev, stream=None) -> float:
     loss = ctypes.c_float(0.0)
-    _check(load().mlmc_mlp_grad(_dptr(u_dev), _dptr(z_dev), u_dev.numel(), _dptr(grad_dev), ctypes.byref(loss),
-                                _stream(stream)))
+    n = u_dev.numel()
+    _check(load().mlmc_mlp_grad(_buf(u_dev, "u_dev", 4, n), _buf(z_dev, "z_dev", 4, n), n,
+                                _buf(grad_dev, "grad_dev", 4, MLMC_MLP_PARAMS), ctypes.byref(loss), _stream(stream)))
     return float(loss.value)
 
 
 def mlmc_mlp_train(u_dev, z_dev, opts: mlmc_train_opts, stream=None) -> float:
     loss = ctypes.c_float(0.0)
-    zp = _dptr(z_dev) if z_dev is not None else ctypes.c_void_p(0)
-    _check(load().mlmc_mlp_train(_dptr(u_dev), zp, u_dev.numel(), ctypes.byref(opts), ctypes.byref(loss),
+    n = u_dev.numel()
+    zp = _buf(z_dev, "z_dev", 4, n) if z_dev is not None else ctypes.c_void_p(0)
+    _check(load().mlmc_mlp_train(_buf(u_dev, "u_dev", 4, n), zp, n, ctypes.byref(opts), ctypes.byref(loss),
                                  _stream(stream)))
     return float(loss.value)
 
@@ -274,7 +296,8 @@ def mlmc_batch(items, seed, stream=None):
 def mlmc_batch_async(items, seed, sums_dev, stream=None):
     """sums_dev: float64 CUDA tensor with >= 2 * len(items) elements."""
     arr = (mlmc_work * len(items))(*items)
-    _check(load().mlmc_batch_async(arr, len(items), seed, _dptr(sums_dev), _stream(stream)))
+    _check(load().mlmc_batch_async(arr, len(items), seed, _f64("sums_dev", sums_dev, 2 * len(items)),
+                                   _stream(stream)))
 
 
 def mlmc_batch_descriptor_bytes() -> int:

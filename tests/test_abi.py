@@ -98,3 +98,21 @@ def test_optimal_samples_match_oracle(lib):
         assert np.array_equal(M.mlmc_optimal_samples(V, C, eps).astype(np.int64), mlmc.optimal_samples(V, C, eps))
     with pytest.raises(M.MlmcError):
         M.mlmc_optimal_samples([1.0], [0.0], 1e-3)
+
+
+def test_binding_checks_device_buffers_without_gpu(lib):
+    """The binding hands the library only device pointers it may use: a host
+    tensor, a wrong dtype or too few elements is refused before any call."""
+    torch = pytest.importorskip("torch")
+    p = M.sde_params()
+    items = [M.mlmc_work(p, 3, 0, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 0, 1000, 0)] * 3
+    host = torch.zeros(6, dtype=torch.float64)
+    for call in (lambda: M.mlmc_batch_async(items, 1, host),
+                 lambda: M.mlmc_level_async(0, 3, 1000, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, p, 1, 0, host),
+                 lambda: M.mlmc_level_noalloc(0, 3, 1000, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, p, 1, 0, host),
+                 lambda: M.approx_icdf(torch.zeros(8), torch.zeros(8), M.MLMC_ICDF_TABLE, M.MLMC_F32),
+                 lambda: M.mlmc_uniforms(torch.zeros(8, dtype=torch.int32), torch.zeros(8))):
+        with pytest.raises(ValueError):
+            call()
+    with pytest.raises(ValueError):
+        M._buf(torch.zeros(4, dtype=torch.float32), "x", 8, 1)
