@@ -247,3 +247,22 @@ def test_batch_sums_do_not_depend_on_the_tile_size(lw, monkeypatch):
     for it, g in zip(items, got):
         fn = M.mlmc_nested_level if it.kind else M.mlmc_level
         _same(g, fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED, it.path_offset))
+
+
+def test_batch_graph_replay_uses_current_mlp_weights():
+    """A captured graph reads the network through the library's weight
+    buffer: after new weights are set, a replay gives the level kernels' sums
+    with the new weights."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from workloads import mlp_initial_weights
+    p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    items = [M.mlmc_work(p, l, kind, M.MLMC_F16, 1, M.MLMC_ICDF_MLP, 0, 2001, 0) for l in (2, 5) for kind in (0, 1)]
+    M.mlmc_mlp_set_weights(mlp_initial_weights(3))
+    first = M.mlmc_batch(items, SEED)
+    M.mlmc_mlp_set_weights(mlp_initial_weights(4))
+    second = M.mlmc_batch(items, SEED)             # the same graph, replayed
+    assert _pairs(first) != _pairs(second)
+    for it, g in zip(items, second):
+        fn = M.mlmc_nested_level if it.kind else M.mlmc_level
+        _same(g, fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED, it.path_offset))
