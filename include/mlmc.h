@@ -345,7 +345,11 @@ mlmc_status mlmc_peak_probe(int kind, double *ops_per_s, void *stream);
 const char *mlmc_strerror(mlmc_status s);
 const char *mlmc_last_error(void);
 const char *mlmc_version(void);
-/* Frees the library's per-device state (tables, weights, graphs). */
+/* Frees the library's per-device state (tables, weights, captured batch
+ * graphs and their buffers, the adaptive driver's round buffers), after
+ * waiting for the batch launches still in flight.  No other call may run
+ * concurrently; a later call re-creates the state (tables rebuilt, MLP
+ * weights to be set again). */
 mlmc_status mlmc_shutdown(void);
 
 #ifdef __cplusplus
