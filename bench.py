@@ -371,7 +371,17 @@ def run_gpu(args):
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        cb = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cb
+        if tte:
+            # the oracle's time to the same RMSE, from its path-steps/s on the
+            # nested workload and the path-steps each GPU run drew
+            line["time_to_eps_cpu_extrapolated"] = {
+                e: {k: r[k]["path_steps"] / cb["value"] for k in ("plain_fp32_exact", "nested_f16_kahan_table")
+                    if isinstance(r.get(k), dict)}
+                for e, r in tte.items()}
+            line["time_to_eps_cpu_extrapolated"]["note"] = ("seconds, extrapolated: path-steps of the GPU run / "
+                                                            "the oracle's path-steps/s on all host cores")
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
@@ -565,13 +575,29 @@ def _cpu_sample(target_s: float, nthreads: int):
     return ps / dt, n2, dt
 
 
+def _config1_full(nthreads: int) -> float:
+    """Seconds of the oracle on the plain-MLMC workload in full: GBM, P = X_T,
+    levels 0..6, 1e5 samples per level, two-way FP64 with exact normals."""
+    import oracle as O
+    sde = O.gbm(payoff=O.PAYOFF_X)
+    t0 = time.perf_counter()
+    for l in range(7):
+        O.level_sums(l, 100000, 0, O.variant(), sde, SEED, O.make_tag(O.KIND_STD, l), nthreads=nthreads)
+    return time.perf_counter() - t0
+
+
 def cpu_baseline(target_s: float):
     import oracle as O
     threads = os.cpu_count() or 1
     O.build()
     rate, n, dt = _cpu_sample(target_s, threads)
+    rate1, n1, dt1 = _cpu_sample(target_s / 4, 1)
     return {"value": rate, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
-            "sample": f"levels 0..12, {n} samples per level and estimator (two-way + four-way), {dt:.1f} s"}
+            "sample": f"levels 0..12, {n} samples per level and estimator (two-way + four-way), {dt:.1f} s",
+            "single_thread": {"value": rate1, "unit": "path-steps/s", "cores": 1,
+                              "sample": f"levels 0..12, {n1} samples per level and estimator, {dt1:.1f} s"},
+            "plain_mlmc_full": {"seconds": _config1_full(threads), "path_steps": 100000 * 127, "cores": threads,
+                                "workload": "GBM P=X_T, levels 0..6, N=1e5 per level, two-way FP64 exact normals"}}
 
 
 def run_reference(args):
