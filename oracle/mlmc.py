@@ -208,3 +208,207 @@ def grid_joint_moments(z, w, max_order=4):
         for b in range(max_order + 1 - a):
             table[(a, b)] = float(np.mean(z ** a * w ** b))
     return lambda a, b: table[(a, b)]
+
+
+# ---------------------------------------------------------------- adaptive driver
+# The standard adaptive MLMC algorithm that Sec. 3's T^ / T- cost comparison
+# assumes (the paper defers its steps to giles2008multilevel), with the
+# nested estimator's terms and the per-level variant choice, written as a
+# plain loop.  Samples come from a callback, so the loop can be driven by
+# exact synthetic level statistics (its pins) or replay the sums an
+# implementation drew (to compare decisions).
+#
+# Readings (stated once, used by both the oracle and the library):
+#   * terms per level l: standard estimator theta^: the FP32 exact-normal
+#     two-way difference; nested theta-: the two-way difference with
+#     approximate normals and the four-way difference;
+#   * warm-up n0 samples per new term; every draw is rounded up to a
+#     multiple of 8 samples;
+#   * V_l of a term without samples at l >= 3 is extrapolated from the two
+#     levels below it, V_{l-1} min(max(V_{l-1} / V_{l-2}, 1/4), 1); a sampled
+#     term at l >= 2 keeps V_l >= V_{l-1} / 4;
+#   * N_t = ceil(2 eps^-2 sqrt(V_t / C_t) sum_s sqrt(V_s C_s)) (Sec. 3),
+#     drawn whenever sum_t V_t / N_t > eps^2 / 2;
+#   * bias test max(|Y_L|, |Y_{L-1}| 2^-alpha, |Y_{L-2}| 2^-2alpha) /
+#     (2^alpha - 1) <= eps / sqrt(2), else L + 1 (up to max_level);
+#   * per-level choice (prec = -1): the candidates {binary16 + Kahan,
+#     binary16, binary32} nested pairs and the standard term alone, n0
+#     samples each in a round of their own; the level keeps the nested pair
+#     with the smallest sqrt(v C) + sqrt(V C), or the standard term if its
+#     sqrt(v^ c^) is smaller still; binary16 candidates stop once a level has
+#     chosen binary32 or the standard term; without trial_all, once two
+#     consecutive levels chose the same binary32 variant, finer levels take
+#     it without candidates.
+
+F32, F16 = 0, 1
+EXACT = 0
+CH_F16K, CH_F16, CH_F32, CH_STANDARD = 0, 1, 2, 3
+
+
+def moments(s1, s2, n):
+    """Sample mean and unbiased variance from the sums of n samples."""
+    m = s1 / n
+    return m, (max((s2 - s1 * m) / (n - 1), 0.0) if n > 1 else 0.0)
+
+
+def _round8(n):
+    return (n + 7) // 8 * 8
+
+
+class _Term:
+    def __init__(self, l, kind, prec, kahan, icdf, off=False):
+        self.key = (l, kind, prec, kahan, icdf)
+        self.l = l
+        self.off = off
+        self.n = 0
+        self.dn = 0
+        self.s1 = 0.0
+        self.s2 = 0.0
+
+    def V(self):
+        return moments(self.s1, self.s2, self.n)[1] if self.n else 0.0
+
+    def Y(self):
+        return moments(self.s1, self.s2, self.n)[0] if self.n else 0.0
+
+
+def adaptive_mlmc(eps, draw, cost, *, nested, prec=F16, kahan=1, icdf=1, n0=10000, min_levels=3,
+                  max_level=18, alpha=1.0, trial_all=False):
+    """Adaptive MLMC to RMSE eps.
+
+    draw(requests) -> [(s1, s2), ...]: one round; requests are
+    (key, dn, path_offset) with key = (l, kind, prec, kahan, icdf), kind 0
+    two-way, 1 four-way.  cost(key) -> C_t, the device cost per sample.
+    prec = -1 (nested only): the per-level choice.
+    Returns a dict: estimate, levels (L + 1), rounds, choice per level,
+    the terms' (key, n, mean, var)."""
+    terms = []                    # two-way and four-way slot per level (nested), one term per level (standard)
+    per = 2 if nested else 1
+    rounds = [0]
+    choice = {}
+    half_done = [False]
+
+    def run(ts):
+        req = [t for t in ts if t.dn > 0]
+        if not req:
+            return
+        sums = draw([(t.key, t.dn, t.n) for t in req])
+        for t, (s1, s2) in zip(req, sums):
+            t.s1 += s1
+            t.s2 += s2
+            t.n += t.dn
+            t.dn = 0
+        rounds[0] += 1
+
+    def vc(t):
+        return t.V() * cost(t.key)
+
+    def add_level(l):
+        if not nested:
+            t = _Term(l, 0, F32, kahan, EXACT)
+            t.dn = _round8(n0)
+            terms.append(t)
+            return
+        if prec != -1:
+            for kind in (0, 1):
+                t = _Term(l, kind, prec, kahan, icdf)
+                t.dn = _round8(n0)
+                terms.append(t)
+            return
+        carried = choice.get(l - 1) if l >= 2 and choice.get(l - 1) == choice.get(l - 2) else None
+        if not trial_all and carried in (CH_F32, CH_STANDARD):
+            choice[l] = carried
+            if carried == CH_STANDARD:
+                pair = [_Term(l, 0, F32, 1, EXACT), _Term(l, 1, F32, 0, icdf, off=True)]
+            else:
+                pair = [_Term(l, 0, F32, 0, icdf), _Term(l, 1, F32, 0, icdf)]
+            for t in pair:
+                t.dn = 0 if t.off else _round8(n0)
+            terms.extend(pair)
+            return
+        variants = [(F16, 1), (F16, 0), (F32, 0)]
+        first = 2 if half_done[0] else 0
+        cands = {c: (_Term(l, 0, *variants[c], icdf), _Term(l, 1, *variants[c], icdf)) for c in range(first, 3)}
+        standard = _Term(l, 0, F32, 1, EXACT)
+        trial = [t for c in range(first, 3) for t in cands[c]] + [standard]
+        for t in trial:
+            t.dn = _round8(n0)
+        run(trial)
+        best, best_score = first, 1e300
+        for c in range(first, 3):
+            score = math.sqrt(vc(cands[c][0])) + math.sqrt(vc(cands[c][1]))
+            if score < best_score:
+                best, best_score = c, score
+        vch = vc(standard)
+        if vch > 0.0 and math.sqrt(vch) < best_score:
+            choice[l] = CH_STANDARD
+            half_done[0] = True
+            terms.extend([standard, _Term(l, 1, F32, 0, icdf, off=True)])
+            return
+        choice[l] = best
+        if variants[best][0] == F32:
+            half_done[0] = True
+        terms.extend(cands[best])
+
+    def plan():
+        V = []
+        for i, t in enumerate(terms):
+            v = 0.0 if t.off else t.V()
+            prev_on = t.l >= 2 and not t.off and not terms[i - per].off
+            if prev_on and t.n == 0 and t.l >= 3 and not terms[i - 2 * per].off and V[i - 2 * per] > 0.0:
+                v = V[i - per] * min(max(V[i - per] / V[i - 2 * per], 0.25), 1.0)
+            elif prev_on:
+                v = max(v, 0.25 * V[i - per])
+            V.append(v)
+        C = [cost(t.key) for t in terms]
+        total = 0.0
+        var_sum = 0.0
+        for i, t in enumerate(terms):
+            total += math.sqrt(V[i] * C[i])
+            if t.n:
+                var_sum += V[i] / t.n
+        pending = any(t.dn for t in terms)
+        if var_sum <= 0.5 * eps * eps and not pending:
+            return False
+        need = pending
+        for i, t in enumerate(terms):
+            if t.off:
+                continue
+            N_t = math.ceil(2.0 / (eps * eps) * math.sqrt(V[i] / C[i]) * total)
+            short = N_t - (t.n + t.dn)
+            if short > 0:
+                t.dn = _round8(t.dn + short)
+                need = True
+        return need
+
+    L = min_levels - 1
+    for l in range(L + 1):
+        add_level(l)
+    converged = False
+    while True:
+        run(terms)
+        if plan():
+            continue
+        Y = [0.0] * (L + 1)
+        for t in terms:
+            Y[t.l] += t.Y()
+        r = 2.0 ** alpha
+        bias = abs(Y[L])
+        if L >= 1:
+            bias = max(bias, abs(Y[L - 1]) / r)
+        if L >= 2:
+            bias = max(bias, abs(Y[L - 2]) / (r * r))
+        bias /= (r - 1.0)
+        if bias <= eps / math.sqrt(2.0):
+            converged = True
+            break
+        if L >= max_level:
+            break
+        L += 1
+        add_level(L)
+        plan()
+    est = sum(t.Y() for t in terms)
+    var = sum(t.V() / t.n for t in terms if t.n)
+    return {"estimate": est, "variance": var, "levels": L + 1, "rounds": rounds[0], "converged": converged,
+            "choice": [choice.get(l) for l in range(L + 1)],
+            "terms": [(t.key, t.n, t.Y(), t.V()) for t in terms if not t.off]}

@@ -404,10 +404,12 @@ static double payoff_of(double X, const orc_sde *p, int prec)
  * four-way.  (Reading: the paper is silent on the generator.)
  * With 16-bit uniforms (RV TABLE16 on a two-way path) fine step n uses half
  * n mod 2 (low half first) of word (n / 2) mod 4 of call j = n / 8.
- * Coarsest levels (a path needs at most half a call: 2^l <= 2 words, or
- * 2^l <= 4 halves with 16-bit uniforms): paths 2k and 2k+1 share call 0 of
- * counter path field k; path p takes the words (halves) from
- * (p mod 2) 2^l on. */
+ * Coarsest levels, two-way paths: while a path needs fewer words than one
+ * call holds (2^l < 4 words, or 2^l < 8 halves with 16-bit uniforms), the
+ * S = 4 / 2^l (8 / 2^l) consecutive paths S k .. S k + S - 1 share call 0 of
+ * counter path field k, path p taking the words (halves) from
+ * (p mod S) 2^l on.  Four-way paths: at l <= 1 paths 2k and 2k+1 share
+ * call 0 of counter path field k in the same way (S = 2). */
 static void draw4w(uint64_t path, uint32_t j, uint32_t tag, uint64_t seed, uint32_t w[4])
 {
     uint32_t ctr[4] = {(uint32_t)path, (uint32_t)(path >> 32), j, tag};
@@ -437,9 +439,10 @@ static void twoway_one(int l, uint64_t path, const orc_variant *v, const orc_sde
     double zprev = 0.0, u[4];
     uint32_t w[4];
     const int u16 = v->rv == ORC_RV_TABLE16;
-    const int shared = u16 ? l <= 2 : l <= 1;
-    const uint64_t cpath = shared ? path >> 1 : path;
-    const int64_t off = shared ? (int64_t)(path & 1) << l : 0;   /* first word (half) of this path */
+    const int64_t per_call = u16 ? 8 : 4;                       /* halves or words of one call */
+    const uint64_t S = nf < per_call ? (uint64_t)(per_call / nf) : 1;   /* paths sharing a call */
+    const uint64_t cpath = path / S;
+    const int64_t off = (int64_t)(path % S) * nf;               /* first word (half) of this path */
     for (int64_t n = 0; n < nf; ++n) {
         double z;
         const int64_t q = off + n;
@@ -571,9 +574,9 @@ void orc_rounding_pairs(int l, uint64_t N, uint64_t path_offset, const int *var,
         double u[4];
         rmode exact = mode_of(ORC_F64, 0);
         const uint64_t path = path_offset + (uint64_t)i;
-        const int shared = l <= 1;
-        const uint64_t cpath = shared ? path >> 1 : path;
-        const int64_t off = shared ? (int64_t)(path & 1) << l : 0;   /* see draw4w */
+        const uint64_t S = nf < 4 ? (uint64_t)(4 / nf) : 1;          /* two-way layout, see draw4w */
+        const uint64_t cpath = path / S;
+        const int64_t off = (int64_t)(path % S) * nf;
         for (int64_t n = 0; n < nf; ++n) {
             const int64_t q = off + n;
             if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);

@@ -159,18 +159,20 @@ def test_fourway_bar_is_table_at_q16(pl_table):
 
 @pytest.mark.parametrize("l", [0, 1, 2])
 def test_twoway_table16_coarse_levels_share_a_call(l, pl_table):
-    """l <= 2: paths 2k and 2k+1 share call 0 of counter path field k; path p
-    takes the halves (p mod 2) 2^l .. (p mod 2) 2^l + 2^l - 1, low half of
-    each word first."""
+    """l <= 2: the S = 8 / 2^l paths S k .. S k + S - 1 share call 0 of
+    counter path field k; path p takes the halves (p mod S) 2^l ..
+    (p mod S) 2^l + 2^l - 1, low half of each word first."""
     sde = O.gbm(payoff=O.PAYOFF_X)
     tag = O.make_tag(O.KIND_APPROX, l)
     w = O.philox4x32_10(O.counters([10], 0, tag), O.seed_key(SEED))[0]
     halves = np.array([[x & 0xFFFF, x >> 16] for x in w.tolist()]).ravel()
     z = O.approx_icdf(O.uniforms16(halves), O.RV_TABLE, table=pl_table)
-    out = O.twoway_paths(l, [20, 21], O.variant(rv=O.RV_TABLE16), sde, SEED, tag, table=pl_table)
+    S = 8 >> l
+    out = O.twoway_paths(l, list(range(10 * S, 11 * S)), O.variant(rv=O.RV_TABLE16), sde, SEED, tag,
+                         table=pl_table)
     n = 1 << l
     d = 1.0 / n
-    for k in range(2):
+    for k in range(S):
         xf = 1.0
         for zz in z[k * n:(k + 1) * n]:
             xf = xf + (0.05 * d * xf + (0.2 * math.sqrt(d) * xf) * zz)
