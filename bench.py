@@ -145,7 +145,9 @@ def launches_per_batch_call(items):
     groups = {(w.kind, w.prec, w.kahan, w.icdf, w.params.sde, w.params.scheme) for w in items}
 
     def partials(w):
-        chunks = ((w.N + 1) // 2 + 31) // 32
+        # lane slots: pairs, or units of 4 / 8 samples at the coarsest two-way levels
+        unit = 1 if w.kind else ((4 if w.l == 0 else 2 if w.l == 1 else 1) if w.icdf == 3 else (2 if w.l == 0 else 1))
+        chunks = ((w.N + 2 * unit - 1) // (2 * unit) + 31) // 32
         g = 1 if w.l >= 6 else max(1, min(chunks // 16384, 64 >> w.l))
         return (chunks + g - 1) // g
     spans = any(partials(w) > 8192 for w in items)

@@ -27,7 +27,13 @@
  * tag = kind | level << 8 | set << 16 with kind 0 = standard two-way with
  * exact normals, 1 = two-way with approximate normals, 2 = four-way.  A word
  * w becomes the uniform u = (2 (w >> 9) + 1) 2^-24 (Sec. 3: Z_n = Phi^-1(U_n)
- * and Z~_n = Phi~^-1(U_n) share U_n).
+ * and Z~_n = Phi~^-1(U_n) share U_n).  Coarsest levels: a two-way path of
+ * level l needs 2^l words (halves with TABLE16); while that is fewer than a
+ * call holds (4 words, 8 halves), the S = 4 / 2^l (8 / 2^l) paths S k ..
+ * S k + S - 1 share call 0 of counter path field k, path p taking the words
+ * (halves) from (p mod S) 2^l on; four-way paths share a call in pairs at
+ * l <= 1 (S = 2).  A launch whose path_offset is a multiple of S computes
+ * one call per S paths, otherwise two.
  */
 #ifndef MLMC_H
 #define MLMC_H
@@ -115,12 +121,27 @@ typedef struct {
 
 /* Sums of one level estimator: s1 = sum D, s2 = sum D^2 over n samples
  * (accumulated in FP32 per thread and warp, in FP64 across warps and
- * blocks); cost_ns = device time of the level kernel in nanoseconds. */
+ * blocks); cost_ns = device time of the level kernel in nanoseconds; mean
+ * and var = the sample mean and the unbiased sample variance of D, combined
+ * from (s1, s2, n) by mlmc_moments (FP64). */
 typedef struct {
     double s1, s2;
     uint64_t n;
     double cost_ns;
+    double mean, var;
 } mlmc_sums;
+
+/* Level mean and variance from the sums of n samples (Sec. 3: the estimator
+ * of a level is the sample mean of its differences, and its variance enters
+ * the sample split through V_l / N_l):
+ *   mean = s1 / n,   var = (s2 - s1 * mean) / (n - 1)   (var = 0 for n = 1),
+ * in FP64, clamped below at 0 (s2 - s1^2 / n cancels when the mean dominates
+ * the spread; the FP64 sums keep the relative error near 1e-16 * s2 / var).
+ * sums_host = {s1, s2} as two doubles (the layout the *_async calls write).
+ * n = 0 or a NULL pointer gives MLMC_EINVAL.  Host-only; no GPU needed.  Every
+ * entry point that fills an mlmc_sums, and the adaptive driver, combine with
+ * this routine. */
+mlmc_status mlmc_moments(const double *sums_host, uint64_t n, double *mean_host, double *var_host);
 
 /* Two-way level difference D = P_l - P_{l-1} (P_{-1} = 0) over N samples,
  * paths path_offset .. path_offset + N - 1 (Sec. 3, estimator theta^ with
@@ -287,6 +308,18 @@ mlmc_status mlmc_batch_async(const mlmc_work *items, int n_items, uint64_t seed,
 size_t mlmc_batch_descriptor_bytes(void);
 
 /* ---- Adaptive MLMC to a target RMSE (Sec. 3 cost model). */
+
+/* One draw of mlmc_run: dn new samples (paths path_offset .. path_offset +
+ * dn - 1) of one estimator term, with their sums.  kind 0: two-way, 1:
+ * four-way; kept = 0 for a per-level candidate that was measured and then
+ * discarded (prec = -1), 1 for a term of the estimate; cost_ns = the cost
+ * model's device time per sample of the term (the C_t of Sec. 3). */
+typedef struct {
+    int32_t round, l, kind, prec, kahan, icdf, kept, reserved;
+    uint64_t dn, path_offset;
+    double s1, s2, cost_ns;
+} mlmc_round_record;
+
 typedef struct {
     int32_t estimator;    /* 0: standard theta^ (FP32, exact normals, plain Euler);
                              1: nested theta- (two-way approximate + four-way) */
@@ -302,6 +335,14 @@ typedef struct {
     uint64_t seed;
     double alpha;         /* weak order used in the bias test (Euler: 1) */
     double timeout_s;     /* wall-clock limit; MLMC_ETIMEOUT beyond it */
+    /* prec = -1: 0 = measure the candidates on each new level until two
+     * consecutive levels have chosen the same FP32 variant (nested FP32 or
+     * the standard term), then give finer levels that variant without
+     * candidate samples; 1 = measure every candidate on every level (the
+     * full per-level efficiency map, at the cost of the discarded samples). */
+    int32_t trial_all;
+    int32_t trace_cap;    /* capacity of trace (records); 0: no trace */
+    mlmc_round_record *trace;   /* optional caller-owned host array: every draw of the run, in order */
 } mlmc_run_opts;
 
 #define MLMC_MAX_LEVELS 19
@@ -327,6 +368,11 @@ typedef struct {
      * 0: the standard FP32 exact-normal two-way difference alone (estimator
      * 0, or prec = -1 when that is cheaper for the level). */
     int32_t nested[MLMC_MAX_LEVELS];
+    int32_t trace_len;            /* draws of the run (records written: min(trace_len, trace_cap)) */
+    int32_t reserved;
+    double model_s;               /* the cost model's device time of every sample drawn, sum of dn C_t */
+    double device_s;              /* measured device time of the rounds (CUDA events around each round) */
+    double discarded_path_steps;  /* path-steps of discarded per-level candidates */
 } mlmc_run_result;
 
 mlmc_status mlmc_run(double eps, const mlmc_sde_params *params, const mlmc_run_opts *opts, mlmc_run_result *out);

@@ -41,15 +41,9 @@ class mlmc_sde_params(ctypes.Structure):
 
 
 class mlmc_sums(ctypes.Structure):
+    """s1, s2, n, cost_ns as accumulated; mean and var filled by the library."""
     _fields_ = [("s1", ctypes.c_double), ("s2", ctypes.c_double), ("n", ctypes.c_uint64),
-                ("cost_ns", ctypes.c_double)]
-
-    def mean(self) -> float:
-        return self.s1 / self.n
-
-    def var(self) -> float:
-        n = self.n
-        return (self.s2 - self.s1 * self.s1 / n) / (n - 1) if n > 1 else 0.0
+                ("cost_ns", ctypes.c_double), ("mean", ctypes.c_double), ("var", ctypes.c_double)]
 
 
 class mlmc_train_opts(ctypes.Structure):
@@ -64,11 +58,19 @@ class mlmc_work(ctypes.Structure):
                 ("set_id", ctypes.c_int32), ("N", ctypes.c_uint64), ("path_offset", ctypes.c_uint64)]
 
 
+class mlmc_round_record(ctypes.Structure):
+    _fields_ = [("round", ctypes.c_int32), ("l", ctypes.c_int32), ("kind", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("kahan", ctypes.c_int32), ("icdf", ctypes.c_int32), ("kept", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("dn", ctypes.c_uint64), ("path_offset", ctypes.c_uint64),
+                ("s1", ctypes.c_double), ("s2", ctypes.c_double), ("cost_ns", ctypes.c_double)]
+
+
 class mlmc_run_opts(ctypes.Structure):
     _fields_ = [("estimator", ctypes.c_int32), ("prec", ctypes.c_int32), ("kahan", ctypes.c_int32),
                 ("icdf", ctypes.c_int32), ("max_level", ctypes.c_int32), ("min_levels", ctypes.c_int32),
                 ("n0", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("alpha", ctypes.c_double),
-                ("timeout_s", ctypes.c_double)]
+                ("timeout_s", ctypes.c_double), ("trial_all", ctypes.c_int32), ("trace_cap", ctypes.c_int32),
+                ("trace", ctypes.POINTER(mlmc_round_record))]
 
 
 class mlmc_run_result(ctypes.Structure):
@@ -77,7 +79,9 @@ class mlmc_run_result(ctypes.Structure):
                 ("n", (ctypes.c_uint64 * MLMC_MAX_LEVELS) * 2), ("mean", (ctypes.c_double * MLMC_MAX_LEVELS) * 2),
                 ("var", (ctypes.c_double * MLMC_MAX_LEVELS) * 2), ("cost", (ctypes.c_double * MLMC_MAX_LEVELS) * 2),
                 ("prec", ctypes.c_int32 * MLMC_MAX_LEVELS), ("kahan", ctypes.c_int32 * MLMC_MAX_LEVELS),
-                ("efficiency", ctypes.c_double * MLMC_MAX_LEVELS), ("nested", ctypes.c_int32 * MLMC_MAX_LEVELS)]
+                ("efficiency", ctypes.c_double * MLMC_MAX_LEVELS), ("nested", ctypes.c_int32 * MLMC_MAX_LEVELS),
+                ("trace_len", ctypes.c_int32), ("reserved", ctypes.c_int32), ("model_s", ctypes.c_double),
+                ("device_s", ctypes.c_double), ("discarded_path_steps", ctypes.c_double)]
 
 
 # exported symbols and their signatures
@@ -103,6 +107,7 @@ _SIGS = {
     "mlmc_batch_descriptor_bytes": [],
     "mlmc_run": [ctypes.c_double, _P(mlmc_sde_params), _P(mlmc_run_opts), _P(mlmc_run_result)],
     "mlmc_optimal_samples": [_vp, _vp, _i32, ctypes.c_double, _vp],
+    "mlmc_moments": [_vp, _u64, _vp, _vp],
     "mlmc_peak_probe": [_i32, _vp, _vp],
     "mlmc_strerror": [_i32],
     "mlmc_last_error": [],
@@ -304,10 +309,28 @@ def mlmc_batch_descriptor_bytes() -> int:
     return int(load().mlmc_batch_descriptor_bytes())
 
 
-def mlmc_run(eps, params, opts: mlmc_run_opts) -> mlmc_run_result:
+def mlmc_run(eps, params, opts: mlmc_run_opts, trace_cap: int = 0):
+    """Adaptive MLMC to RMSE eps.  With trace_cap > 0 returns (result, the
+    run's draws as a list of mlmc_round_record) instead of the result."""
     out = mlmc_run_result()
+    trace = None
+    if trace_cap > 0:
+        trace = (mlmc_round_record * trace_cap)()
+        opts = mlmc_run_opts.from_buffer_copy(opts)
+        opts.trace_cap = trace_cap
+        opts.trace = ctypes.cast(trace, ctypes.POINTER(mlmc_round_record))
     _check(load().mlmc_run(eps, ctypes.byref(params), ctypes.byref(opts), ctypes.byref(out)))
-    return out
+    if trace is None:
+        return out
+    return out, list(trace[:min(out.trace_len, trace_cap)])
+
+
+def mlmc_moments(s1, s2, n):
+    """(mean, var) of a level from its sums, combined by the library."""
+    sums = (ctypes.c_double * 2)(float(s1), float(s2))
+    mean, var = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().mlmc_moments(ctypes.cast(sums, _vp), int(n), ctypes.byref(mean), ctypes.byref(var)))
+    return mean.value, var.value
 
 
 def mlmc_optimal_samples(V, C, eps):

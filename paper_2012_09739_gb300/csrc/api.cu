@@ -130,7 +130,6 @@ static uint32_t pair_bits(double v, int prec) {
 
 LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int prec, int icdf,
                           const mlmc_sde_params *p, uint64_t seed, uint64_t path_offset, uint32_t set_id) {
-    (void)icdf;
     LevelArgs a;
     memset(&a, 0, sizeof a);
     const double delta_f = ldexp(p->T, -l);
@@ -140,7 +139,8 @@ LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int
     a.mode = four ? MODE_FOUR : MODE_TWO;
     a.sde = kernel_sde(p);
     a.N = N;
-    a.npairs = (N + 1) / 2;
+    a.unit = unit_pairs(a.mode, icdf, l);
+    a.npairs = (N + 2 * a.unit - 1) / (2 * a.unit);
     a.path_offset = path_offset;
     const uint32_t kind = four ? 2u : (icdf == MLMC_ICDF_EXACT ? 0u : 1u);
     a.tag = kind | ((uint32_t)l << 8) | (set_id << 16);
@@ -243,6 +243,14 @@ mlmc_status enqueue_level(const DeviceState &d, int four, int l, uint64_t N, int
     return MLMC_OK;
 }
 
+// Sample mean and unbiased variance of a level's differences from their
+// FP64 sums (Sec. 3); every result struct and the adaptive driver use it.
+void level_moments(double s1, double s2, uint64_t n, double *mean, double *var) {
+    const double m = s1 / (double)n;
+    *mean = m;
+    *var = n > 1 ? fmax((s2 - s1 * m) / (double)(n - 1), 0.0) : 0.0;
+}
+
 // Per-thread pinned staging for small device->host results.
 double *host_staging() {
     static thread_local double *buf = nullptr;
@@ -287,6 +295,7 @@ mlmc_status level_sync(int four, int l, uint64_t N, int prec, int kahan, int icd
         out->s2 = host[1];
         out->n = N;
         out->cost_ns = (double)ms * 1e6;
+        level_moments(out->s1, out->s2, N, &out->mean, &out->var);
     }
     return st;
 }
@@ -420,6 +429,12 @@ mlmc_status mlmc_icdf_cubic(double *d_host, float *d32_host, uint16_t *d16_host,
             if (dbf16_host) dbf16_host[4 * i + j] = (uint16_t)b16[j];
         }
     }
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_moments(const double *sums_host, uint64_t n, double *mean_host, double *var_host) {
+    if (!sums_host || !mean_host || !var_host || n == 0) return fail(MLMC_EINVAL, "bad arguments");
+    level_moments(sums_host[0], sums_host[1], n, mean_host, var_host);
     return MLMC_OK;
 }
 

@@ -38,6 +38,7 @@ mlmc_status device_state(DeviceState **out);
 mlmc_status wait_event(cudaEvent_t ev, double limit_s);
 double wait_limit_s();
 double *host_staging();
+void level_moments(double s1, double s2, uint64_t n, double *mean, double *var);
 mlmc_status check_params(const mlmc_sde_params *p);
 mlmc_status check_level(int four, int l, uint64_t N, int prec, int icdf, const mlmc_sde_params *p);
 LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int prec, int icdf, const mlmc_sde_params *p,

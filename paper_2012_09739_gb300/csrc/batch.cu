@@ -114,10 +114,11 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
         }
         if (gi == plan.groups.size()) plan.groups.push_back(Group{mode, w[i].prec, kahan, w[i].icdf, sde});
         Group &g = plan.groups[gi];
-        const uint64_t np = (w[i].N + 1) / 2, nchunks = (np + 31) / 32;
+        // lane slots: pairs, or units of pairs at the coarsest two-way levels
+        const uint64_t np = plan.items[i].npairs, nchunks = (np + 31) / 32;
         const uint32_t G = chunk_group(w[i].l, nchunks);
         const uint64_t ngroups = (nchunks + G - 1) / G;
-        const double pc = pair_cost(w[i].l, w[i].kind);
+        const double pc = pair_cost(w[i].l, w[i].kind) * plan.items[i].unit;
         uint64_t per_lane = std::max<uint64_t>(1, (uint64_t)(ldexp(1.0, lane_work_log2) / (pc / (w[i].kind ? 2.2 : 1.0))));
         per_lane = (per_lane + G - 1) / G * G;
         const uint64_t per_tile = 32 * per_lane;
@@ -335,6 +336,8 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s, bool stage_idle
     return MLMC_OK;
 }
 
+int env_int(const char *name, int dflt);
+
 // Resident blocks per SM of a batch kernel (cached per kernel).
 int blocks_per_sm(BatchCache &c, BatchKernelFn fn) {
     auto it = c.occupancy.find((const void *)fn);
@@ -367,9 +370,10 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         bps[gi] = blocks_per_sm(c, fns[gi]);
         bps_min = std::min(bps_min, bps[gi]);
     }
-    // concurrent even for a batch of microseconds: two groups of an adaptive
-    // round at RMSE 3e-4 took 0.113 ms forked against 0.127 ms in sequence
-    const bool concurrent = ng > 1;
+    // MLMC_BATCH_CONCURRENT: 1 = groups always concurrent, 0 = always one
+    // after another on s (each with the whole GPU), unset = concurrent
+    const int conc_env = env_int("MLMC_BATCH_CONCURRENT", -1);
+    const bool concurrent = ng > 1 && conc_env != 0;
     const size_t nside = concurrent ? std::min<size_t>(ng - 1, BatchCache::MAX_SIDE) : 0;
     if (nside > 0) {
         if (!c.fork && (e = cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming)) != cudaSuccess)
@@ -665,6 +669,7 @@ extern "C" mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t 
             out_host[i].s2 = c->sums_host[i].y;
             out_host[i].n = items[i].N;
             out_host[i].cost_ns = (double)ms * 1e6 * c->weight[i];
+            level_moments(out_host[i].s1, out_host[i].s2, items[i].N, &out_host[i].mean, &out_host[i].var);
         }
     }
     cudaEventDestroy(a);

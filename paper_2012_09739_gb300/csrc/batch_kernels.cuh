@@ -180,16 +180,7 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
             for (; r < r1; ++r) {
                 const uint32_t k = (r << 5) + lane;
                 const bool active = k < npairs;
-                const uint64_t g = first + (active ? k : npairs - 1);
-                float d0, d1, o0[5], o1[5];
-                simulate_pair<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, d0, d1, o0, o1);
-                if (!active) continue;
-                s1.add(d0);
-                s2.add(d0 * d0);
-                if (2 * g + 1 < a.N) {
-                    s1.add(d1);
-                    s2.add(d1 * d1);
-                }
+                run_slot<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, first + (active ? k : npairs - 1), active, s1, s2);
             }
             const float w1 = warp_sum(s1.value()), w2 = warp_sum(s2.value());
             if (lane == 0) partials[grp] = make_double2((double)w1, (double)w2);

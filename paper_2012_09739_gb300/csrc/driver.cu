@@ -38,9 +38,25 @@ struct Term {
     uint64_t dn = 0;             // samples to add this round
     double s1 = 0.0, s2 = 0.0;
     double cost = 0.0;           // ns per sample (model)
-    double var() const { return n > 1 ? fmax((s2 - s1 * s1 / n) / (n - 1), 0.0) : 0.0; }
-    double mean() const { return n ? s1 / n : 0.0; }
+    double var() const {
+        double m = 0.0, v = 0.0;
+        if (n) level_moments(s1, s2, n, &m, &v);
+        return v;
+    }
+    double mean() const {
+        double m = 0.0, v = 0.0;
+        if (n) level_moments(s1, s2, n, &m, &v);
+        return m;
+    }
 };
+
+// Per-level choice of the nested estimator with prec = -1 (Sec. 3, Fig. 4).
+enum Choice { CH_F16K = 0, CH_F16 = 1, CH_F32 = 2, CH_STANDARD = 3, CH_NONE = 4 };
+
+// Sample counts are drawn in multiples of 8, so that every term's path
+// offset is a multiple of the 4 or 8 paths that share one Philox call at the
+// coarsest two-way levels.
+uint64_t round8(uint64_t n) { return (n + 7) / 8 * 8; }
 
 // Device cost of one sample of a term: C = nu 2^l + kappa, with nu the ns
 // per fine path-step of the variant and kappa the per-sample cost (uniform
@@ -82,31 +98,35 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
     cudaStream_t s = d->run_stream;
     BatchCache *cache = d->run_cache;
     cudaEvent_t done = nullptr, ev_a = nullptr, ev_b = nullptr;
-    if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess)
+    if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreate(&ev_a)) != cudaSuccess || (e = cudaEventCreate(&ev_b)) != cudaSuccess)
         st = cuda_fail(e, "cudaEventCreate");
     // MLMC_RUN_LOG=1: one JSON line per round on stderr (items, path-steps,
-    // device and wall time, host time to plan and enqueue the round)
+    // the cost model's and the measured device time, wall time, host time to
+    // plan and enqueue the round)
     const char *log_env = getenv("MLMC_RUN_LOG");
     const bool log = log_env && atoi(log_env) > 0;
-    if (log) {
-        cudaEventCreate(&ev_a);
-        cudaEventCreate(&ev_b);
-    }
+    std::vector<mlmc_round_record> trace;
+    double model_ns = 0.0, device_ms = 0.0, discarded_steps = 0.0;
 
     std::vector<Term> terms;
     std::vector<int> lvl_prec(MLMC_MAX_LEVELS, o->prec), lvl_kahan(MLMC_MAX_LEVELS, o->kahan ? 1 : 0);
     std::vector<double> lvl_eff(MLMC_MAX_LEVELS, 0.0);
     std::vector<int> lvl_nested(MLMC_MAX_LEVELS, nested ? 1 : 0);
+    std::vector<int> lvl_choice(MLMC_MAX_LEVELS, CH_NONE);
     double path_steps = 0.0;
     const double limit = o->timeout_s > 0 ? o->timeout_s : wait_limit_s();
     int rounds = 0;
 
-    // Adds dn samples to every term with dn > 0 in one batched launch.
-    auto run_round = [&](std::vector<Term> &ts) -> mlmc_status {
+    // Adds dn samples to every term with dn > 0 in one batched launch;
+    // kept = 0 marks the draws of candidate terms (their records are fixed
+    // up once the level's choice is made).
+    auto run_round = [&](std::vector<Term> &ts, int kept) -> mlmc_status {
         std::vector<mlmc_work> items;
         std::vector<size_t> which;
         for (size_t i = 0; i < ts.size(); ++i) {
             if (ts[i].dn == 0) continue;
+            ts[i].cost = cost_of(ts[i]);
             mlmc_work w;
             memset(&w, 0, sizeof w);
             w.params = *p;
@@ -123,27 +143,47 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         }
         if (items.empty()) return MLMC_OK;
         const auto t0 = std::chrono::steady_clock::now();
-        if (log) cudaEventRecord(ev_a, s);
+        cudaEventRecord(ev_a, s);
         mlmc_status r = batch_round(*d, *cache, items.data(), (int)items.size(), o->seed, s);
         if (r) return r;
         const auto t_enq = std::chrono::steady_clock::now();
-        if (log) cudaEventRecord(ev_b, s);
+        cudaEventRecord(ev_b, s);
         cudaEventRecord(done, s);
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
         if ((r = wait_event(done, fmax(limit - el, 0.001)))) return r;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, ev_a, ev_b);
+        device_ms += ms;
+        double round_model_ns = 0.0;
+        for (size_t k = 0; k < which.size(); ++k) round_model_ns += (double)ts[which[k]].dn * ts[which[k]].cost;
+        model_ns += round_model_ns;
         if (log) {
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, ev_a, ev_b);
             double ps = 0.0;
             for (const auto &w : items) ps += ldexp((double)w.N, w.l);
             const double host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             const double enq_ms = std::chrono::duration<double, std::milli>(t_enq - t0).count();
-            fprintf(stderr, "{\"mlmc_run_round\": %d, \"items\": %zu, \"path_steps\": %.0f, \"device_ms\": %.4f, "
-                            "\"wall_ms\": %.4f, \"enqueue_ms\": %.4f}\n", rounds, items.size(), ps, ms, host_ms, enq_ms);
+            fprintf(stderr, "{\"mlmc_run_round\": %d, \"items\": %zu, \"path_steps\": %.0f, \"model_ms\": %.4f, "
+                            "\"device_ms\": %.4f, \"wall_ms\": %.4f, \"enqueue_ms\": %.4f}\n",
+                    rounds, items.size(), ps, round_model_ns * 1e-6, ms, host_ms, enq_ms);
         }
         const double2 *sums = batch_sums_host(*cache);
         for (size_t k = 0; k < which.size(); ++k) {
             Term &t = ts[which[k]];
+            mlmc_round_record rec;
+            memset(&rec, 0, sizeof rec);
+            rec.round = rounds;
+            rec.l = t.l;
+            rec.kind = t.four;
+            rec.prec = t.prec;
+            rec.kahan = t.kahan;
+            rec.icdf = t.icdf;
+            rec.kept = kept;
+            rec.dn = t.dn;
+            rec.path_offset = t.n;
+            rec.s1 = sums[k].x;
+            rec.s2 = sums[k].y;
+            rec.cost_ns = t.cost;
+            trace.push_back(rec);
             path_steps += (double)t.dn * ldexp(1.0, t.l);
             t.s1 += sums[k].x;
             t.s2 += sums[k].y;
@@ -155,21 +195,59 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
     };
     // Runs n0 samples of each candidate term at once.
     auto trial = [&](std::vector<Term> &cand) -> mlmc_status {
-        for (Term &t : cand) t.dn = o->n0;
-        return run_round(cand);
+        for (Term &t : cand) t.dn = round8(o->n0);
+        return run_round(cand, 0);
+    };
+    // The records of the candidate terms of the last trial that the level
+    // kept become kept = 1.
+    auto keep_trial_records = [&](const std::vector<Term> &kept_terms) {
+        for (auto it = trace.rbegin(); it != trace.rend() && it->kept == 0 && it->round == rounds - 1; ++it)
+            for (const Term &t : kept_terms)
+                if (!t.off && it->l == t.l && it->kind == t.four && it->prec == t.prec && it->kahan == t.kahan &&
+                    it->icdf == t.icdf)
+                    it->kept = 1;
     };
     const bool autoprec = nested && o->prec < 0;
     bool half_done = false;      // a coarser level already chose FP32 or the standard estimator
+    // The standard FP32 exact-normal two-way term alone at level l, with an
+    // empty four-way slot (both estimate E[P^_l - P^_{l-1}]).
+    auto push_standard = [&](int l, const Term &std_term) {
+        lvl_prec[l] = MLMC_F32;
+        lvl_kahan[l] = 1;
+        lvl_nested[l] = 0;
+        terms.push_back(std_term);
+        Term slot{l, 1, MLMC_F32, 0, o->icdf};
+        slot.off = true;
+        terms.push_back(slot);
+    };
     auto add_level = [&](int l) -> mlmc_status {
         if (!nested) {
             terms.push_back(Term{l, 0, MLMC_F32, o->kahan ? 1 : 0, MLMC_ICDF_EXACT});
-            terms.back().dn = o->n0;
+            terms.back().dn = round8(o->n0);
             return MLMC_OK;
         }
         if (!autoprec) {
             terms.push_back(Term{l, 0, o->prec, o->kahan ? 1 : 0, o->icdf});
             terms.push_back(Term{l, 1, o->prec, o->kahan ? 1 : 0, o->icdf});
-            terms[terms.size() - 2].dn = terms.back().dn = o->n0;
+            terms[terms.size() - 2].dn = terms.back().dn = round8(o->n0);
+            return MLMC_OK;
+        }
+        // Carried choice: once two consecutive levels have chosen the same
+        // FP32 variant, finer levels take it without candidate samples (the
+        // binary16 rounding floor only loses ground as delta shrinks, Sec. 3).
+        if (!o->trial_all && l >= 2 && lvl_choice[l - 1] == lvl_choice[l - 2] &&
+            (lvl_choice[l - 1] == CH_F32 || lvl_choice[l - 1] == CH_STANDARD)) {
+            lvl_choice[l] = lvl_choice[l - 1];
+            if (lvl_choice[l] == CH_STANDARD) {
+                push_standard(l, Term{l, 0, MLMC_F32, 1, MLMC_ICDF_EXACT});
+                terms[terms.size() - 2].dn = round8(o->n0);
+            } else {
+                lvl_prec[l] = MLMC_F32;
+                lvl_kahan[l] = 0;
+                terms.push_back(Term{l, 0, MLMC_F32, 0, o->icdf});
+                terms.push_back(Term{l, 1, MLMC_F32, 0, o->icdf});
+                terms[terms.size() - 2].dn = terms.back().dn = round8(o->n0);
+            }
             return MLMC_OK;
         }
         // candidates (two-way, four-way) x {FP16 + Kahan, FP16, FP32}, plus the
@@ -203,26 +281,25 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         }
         const double vc2 = vc(cand[2 * best]), vc4 = vc(cand[2 * best + 1]), vch = vc(cand[6]);
         if (vch > 0.0 && vc2 > 0.0) lvl_eff[l] = vc2 / vch * pow(1.0 + sqrt(vc4 / vc2), 2.0);
+        for (int c = first; c < 3; ++c) discarded_steps += (double)(cand[2 * c].n + cand[2 * c + 1].n) * ldexp(1.0, l);
+        discarded_steps += (double)cand[6].n * ldexp(1.0, l);
         if (vch > 0.0 && sqrt(vch) < best_score) {
-            // the standard estimator alone is cheaper for this level; the
-            // four-way slot stays empty (both estimate E[P^_l - P^_{l-1}])
-            lvl_prec[l] = MLMC_F32;
-            lvl_kahan[l] = 1;
-            lvl_nested[l] = 0;
+            // the standard estimator alone is cheaper for this level
+            lvl_choice[l] = CH_STANDARD;
             half_done = true;
-            terms.push_back(cand[6]);
-            Term slot = cand[1];
-            slot.off = true;
-            slot.n = 0;
-            slot.s1 = slot.s2 = 0.0;
-            terms.push_back(slot);
+            push_standard(l, cand[6]);
+            keep_trial_records({cand[6]});
+            discarded_steps -= (double)cand[6].n * ldexp(1.0, l);
             return MLMC_OK;
         }
+        lvl_choice[l] = best;
         lvl_prec[l] = cp[best];
         lvl_kahan[l] = ck[best];
         if (cp[best] == MLMC_F32) half_done = true;
         terms.push_back(cand[2 * best]);
         terms.push_back(cand[2 * best + 1]);
+        keep_trial_records({cand[2 * best], cand[2 * best + 1]});
+        discarded_steps -= (double)(cand[2 * best].n + cand[2 * best + 1].n) * ldexp(1.0, l);
         return MLMC_OK;
     };
     int L = o->min_levels - 1;
@@ -266,10 +343,11 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         if (var_sum <= 0.5 * eps * eps && !pending) return false;
         bool need = pending;
         for (size_t i = 0; i < terms.size(); ++i) {
+            if (terms[i].off) continue;
             const double Nopt = ceil(2.0 / (eps * eps) * sqrt(V[i] / C[i]) * total);
             const double dn = Nopt - (double)(terms[i].n + terms[i].dn);
             if (dn > 0.0) {
-                terms[i].dn += (uint64_t)dn;
+                terms[i].dn = round8(terms[i].dn + (uint64_t)dn);
                 need = true;
             }
         }
@@ -277,7 +355,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
     };
 
     while (!st) {
-        if ((st = run_round(terms))) break;
+        if ((st = run_round(terms, 1))) break;
         if (plan_samples()) continue;
         // ---- weak-error test on the last three level means
         std::vector<double> Y(L + 1, 0.0);
@@ -321,6 +399,12 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
             out->nested[l] = lvl_nested[l];
         }
         out->path_steps = path_steps;
+        out->trace_len = (int32_t)trace.size();
+        if (o->trace && o->trace_cap > 0)
+            memcpy(o->trace, trace.data(), std::min<size_t>(trace.size(), (size_t)o->trace_cap) * sizeof(mlmc_round_record));
+        out->model_s = model_ns * 1e-9;
+        out->device_s = device_ms * 1e-3;
+        out->discarded_path_steps = discarded_steps;
         out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
         if (!converged) st = fail(MLMC_ENOTCONV, "bias test not met at max_level %d", o->max_level);
     }

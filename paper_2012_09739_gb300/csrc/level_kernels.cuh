@@ -26,7 +26,8 @@ struct LevelArgs {
     int l;                    // level: 2^l fine steps
     int payoff;
     int mode, sde;            // MODE_*, SDE_* (read by the batched kernel)
-    uint64_t npairs;          // ceil(N / 2)
+    uint64_t npairs;          // lane slots: ceil(N / 2) pairs, or ceil(N / (2 unit)) units
+    int unit;                 // pairs per slot: 1, or 2 / 4 at the coarsest two-way levels (unit_pairs)
     uint64_t N;
     uint64_t path_offset;
     uint32_t tag, k0, k1;     // Philox counter tag and key (seed)
@@ -283,6 +284,136 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
     pair_result<MODE>(a, fine, coarse, hfine, hcoarse, d0, d1, out0, out1);
 }
 
+// Pairs per lane slot.  On two-way paths at the coarsest levels a path
+// needs fewer words than one Philox call holds (2^l < 4 words, or 2^l < 8
+// halves with 16-bit uniforms), and the S = 4 / 2^l (8 / 2^l) consecutive
+// paths S k .. S k + S - 1 share call 0 of counter path field k, path p
+// taking the words (halves) from (p mod S) 2^l on.  Where S > 2 one lane
+// simulates all S paths of a call (S / 2 pairs); elsewhere a slot is one
+// pair (at S = 2 the pair shares its call, as simulate_pair does).
+__host__ __device__ __forceinline__ int unit_pairs(int mode, int icdf, int l) {
+    if (mode != MODE_TWO) return 1;
+    if (icdf == ICDF_TABLE16) return l == 0 ? 4 : (l == 1 ? 2 : 1);
+    return l == 0 ? 2 : 1;
+}
+
+// The 2B paths of unit u, paths base .. base + 2B - 1 with base =
+// path_offset + 2B u: position q = (base mod S) + i of path i runs over the
+// S positions of call base / S, then of the next call (ALIGNED: base mod S
+// = 0, one call).  Level L = 0 (one fine step) or 1 (two fine steps, one
+// coarse; 16-bit uniforms only).  emit(i, P_f, P_c, D) receives every path
+// in order.
+template <int B, int L, bool ALIGNED, int P, bool KAHAN, int ICDF, int SDE, class Emit>
+__device__ __forceinline__ void simulate_unit(const LevelArgs &a, const SmemTable &tab, const MlpFrags &mlp,
+                                              uint64_t u, Emit &&emit) {
+    constexpr uint32_t S = 2 * B;
+    constexpr bool U16 = ICDF == ICDF_TABLE16;
+    static_assert(L == 0 || U16, "level-1 units use 16-bit uniforms");
+    const uint64_t base = a.path_offset + S * u;
+    const uint32_t m = ALIGNED ? 0u : (uint32_t)(base % S);
+    const uint64_t cp = base / S;
+    auto call_of = [&](uint64_t c) {
+        return philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), 0u, a.tag), a.k0, a.k1);
+    };
+    const uint4 r0 = call_of(cp);
+    uint4 r1 = r0;
+    if (!ALIGNED) r1 = call_of(cp + 1);
+    // the word holding position q (positions are words, or halves when
+    // U16 and L = 0)
+    auto word_at = [&](uint32_t q) -> uint32_t {
+        const uint32_t p = q % S;
+        const int wi = (int)(U16 && L == 0 ? p >> 1 : p);
+        return q < S ? word(r0, wi) : word(r1, wi);
+    };
+    auto half_at = [](uint32_t w, uint32_t hi) { return hi ? half16_bits<true>(w) : half16_bits<false>(w); };
+    PathPair<P_F32, true, SDE> unused;
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+        const uint32_t q0 = m + 2 * k, q1 = q0 + 1;
+        PathPair<P, KAHAN, SDE> fine, coarse;
+        fine.template init<false>(a, false);
+        if (L == 1) coarse.template init<false>(a, true);
+        if constexpr (U16 && L == 0) {
+            const uint32_t f0 = half_at(word_at(q0), q0 & 1), f1 = half_at(word_at(q1), q1 & 1);
+            fine.step(table_pair<P, true>(tab, f0, f1, mirrored_v16(f0), mirrored_v16(f1)));
+        } else if constexpr (U16) {
+            const uint32_t w0 = word_at(q0), w1 = word_at(q1);
+            const uint32_t a0 = half16_bits<false>(w0), a1 = half16_bits<false>(w1);
+            const uint32_t b0 = half16_bits<true>(w0), b1 = half16_bits<true>(w1);
+            const Pair<P> z1 = table_pair<P, true>(tab, a0, a1, mirrored_v16(a0), mirrored_v16(a1));
+            const Pair<P> z2 = table_pair<P, true>(tab, b0, b1, mirrored_v16(b0), mirrored_v16(b1));
+            fine.step(z1);
+            fine.step(z2);
+            coarse.step(add(z1, z2));
+        } else {
+            fine.step(icdf_pair<P, ICDF>(tab, mlp, word_at(q0), word_at(q1)));
+        }
+        float d0, d1, o0[5], o1[5];
+        pair_result<MODE_TWO>(a, fine, coarse, unused, unused, d0, d1, o0, o1);
+        emit(2 * k, o0[0], o0[1], d0);
+        emit(2 * k + 1, o1[0], o1[1], d1);
+    }
+}
+
+// One lane slot of the level described by a (slot g; inactive lanes
+// simulate the last slot and discard it): its samples' D and D^2 go to
+// k1, k2 in sample order, and with a.paths_out their outputs (3 or 5
+// floats per sample).  Shared by the level and the batched kernels, so both
+// accumulate identically.
+template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
+__device__ __forceinline__ void run_slot(const LevelArgs &a, const SmemTable &tab, const MlpFrags &mlp, uint64_t g,
+                                         bool active, KahanF32 &k1, KahanF32 &k2) {
+    if (MODE == MODE_TWO && a.unit > 1) {
+        const uint64_t first = (uint64_t)(2 * a.unit) * g;        // sample index of the unit's first path
+        auto emit = [&](int i, float pf, float pc, float d) {
+            if (!active || first + i >= a.N) return;
+            k1.add(d);
+            k2.add(d * d);
+            if (a.paths_out != nullptr) {
+                float *o = a.paths_out + (first + i) * 3;
+                o[0] = pf;
+                o[1] = pc;
+                o[2] = d;
+            }
+        };
+        const bool aligned = a.path_offset % (uint64_t)(2 * a.unit) == 0;
+        if constexpr (ICDF == ICDF_TABLE16) {
+            if (a.l == 0) {
+                if (aligned) simulate_unit<4, 0, true, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
+                else simulate_unit<4, 0, false, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
+            } else {
+                if (aligned) simulate_unit<2, 1, true, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
+                else simulate_unit<2, 1, false, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
+            }
+        } else {
+            if (aligned) simulate_unit<2, 0, true, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
+            else simulate_unit<2, 0, false, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
+        }
+        return;
+    }
+    float d0, d1, out0[5], out1[5];
+    simulate_pair<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, d0, d1, out0, out1);
+    const bool valid1 = 2 * g + 1 < a.N;
+    if (active) {
+        k1.add(d0);
+        k2.add(d0 * d0);
+        if (valid1) {
+            k1.add(d1);
+            k2.add(d1 * d1);
+        }
+    }
+    if (active && a.paths_out != nullptr) {
+        constexpr int W = MODE == MODE_TWO ? 3 : 5;
+        float *o = a.paths_out + (2 * g) * W;
+#pragma unroll
+        for (int k = 0; k < W; ++k) o[k] = out0[k];
+        if (valid1) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) o[W + k] = out1[k];
+        }
+    }
+}
+
 __device__ __forceinline__ void stage_table(SmemTable &tab, const DevTables *t) {
     static_assert(sizeof(SmemTable) % 4 == 0, "table size");
     const uint32_t *src = reinterpret_cast<const uint32_t *>(&t->e);
@@ -352,30 +483,9 @@ __global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 2 : (MODE == MODE_FOUR
         if (c0 >= nchunks) break;
         const uint64_t c1 = c0 + G < nchunks ? c0 + G : nchunks;
         for (uint64_t c = c0; c < c1; ++c) {
-            const uint64_t base = c * 32;
-            const uint64_t g = base + lane;
+            const uint64_t g = c * 32 + lane;
             const bool active = g < a.npairs;
-            float d0, d1, out0[5], out1[5];
-            simulate_pair<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, active ? g : a.npairs - 1, d0, d1, out0, out1);
-            const bool valid1 = 2 * g + 1 < a.N;
-            if (active) {
-                k1.add(d0);
-                k2.add(d0 * d0);
-                if (valid1) {
-                    k1.add(d1);
-                    k2.add(d1 * d1);
-                }
-            }
-            if (active && a.paths_out != nullptr) {
-                constexpr int W = MODE == MODE_TWO ? 3 : 5;
-                float *o = a.paths_out + (2 * g) * W;
-#pragma unroll
-                for (int k = 0; k < W; ++k) o[k] = out0[k];
-                if (valid1) {
-#pragma unroll
-                    for (int k = 0; k < W; ++k) o[W + k] = out1[k];
-                }
-            }
+            run_slot<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, active ? g : a.npairs - 1, active, k1, k2);
         }
         if (a.chunk_partials) {
             const float w1 = warp_sum(k1.value()), w2 = warp_sum(k2.value());

@@ -116,3 +116,36 @@ def test_binding_checks_device_buffers_without_gpu(lib):
             call()
     with pytest.raises(ValueError):
         M._buf(torch.zeros(4, dtype=torch.float32), "x", 8, 1)
+
+
+def test_moments_match_exact_rational_arithmetic(lib):
+    """mlmc_moments (the one routine every result struct and the adaptive
+    driver use for a level's mean and variance, Sec. 3) against the same
+    statistics in exact rational arithmetic, on samples whose FP64 sums are
+    exact (dyadic rationals of few bits): mean to 1 ulp, variance to a few ulp of
+    the cancellation-bound s2 (the sums carry no rounding of their own)."""
+    from fractions import Fraction
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        n = int(rng.integers(1, 5000))
+        shift = float(rng.choice([0.0, 0.1, 1.0, 100.0]))
+        # samples on a 2^-10 grid below 2^8: their sums and sums of squares
+        # need at most 49 significant bits, so they are exact in FP64
+        x = np.round((shift + rng.standard_normal(n)) * 2 ** 10) / 2 ** 10
+        s1 = float(np.sum(x))
+        s2 = float(np.sum(x * x))
+        fx = [Fraction(v) for v in x.tolist()]
+        assert Fraction(s1) == sum(fx) and Fraction(s2) == sum(v * v for v in fx)
+        mean, var = M.mlmc_moments(s1, s2, n)
+        em = sum(fx) / n
+        ev = (sum(v * v for v in fx) - sum(fx) * em) / (n - 1) if n > 1 else Fraction(0)
+        assert abs(Fraction(mean) - em) <= abs(em) * Fraction(2) ** -52
+        assert abs(Fraction(var) - ev) <= (Fraction(s2) / max(n - 1, 1)) * Fraction(2) ** -50 + Fraction(0)
+        assert var >= 0.0
+    # a single sample has no spread; n = 0 is refused
+    assert M.mlmc_moments(3.0, 9.0, 1) == (3.0, 0.0)
+    with pytest.raises(M.MlmcError):
+        M.mlmc_moments(1.0, 1.0, 0)
+    # the sums struct carries the same moments (filled by the library)
+    s = M.mlmc_sums()
+    assert hasattr(s, "mean") and hasattr(s, "var")

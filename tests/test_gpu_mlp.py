@@ -175,7 +175,7 @@ def test_fourway_with_mlp_paths_and_gain(trained, pl_table):
         v = {}
         for prec in (M.MLMC_F32, M.MLMC_F16):
             for icdf in (M.MLMC_ICDF_MLP, M.MLMC_ICDF_TABLE):
-                v[prec, icdf] = M.mlmc_nested_level(l, 1 << 18, prec, True, icdf, params, SEED).var()
+                v[prec, icdf] = M.mlmc_nested_level(l, 1 << 18, prec, True, icdf, params, SEED).var
         assert v[M.MLMC_F32, M.MLMC_ICDF_MLP] < 0.5 * v[M.MLMC_F32, M.MLMC_ICDF_TABLE], (l, v)
         assert v[M.MLMC_F16, M.MLMC_ICDF_MLP] < 1.05 * v[M.MLMC_F16, M.MLMC_ICDF_TABLE], (l, v)
 
@@ -192,6 +192,6 @@ def test_nested_estimator_with_mlp_is_unbiased(trained):
         a = M.mlmc_level(l, N, M.MLMC_F16, True, M.MLMC_ICDF_MLP, params, SEED)
         b = M.mlmc_nested_level(l, N, M.MLMC_F16, True, M.MLMC_ICDF_MLP, params, SEED)
         c = M.mlmc_level(l, N, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, params, SEED)
-        nested = a.mean() + b.mean()
-        se = math.sqrt(a.var() / N + b.var() / N + c.var() / N)
-        assert abs(nested - c.mean()) < 4.5 * se, (l, nested, c.mean(), se)
+        nested = a.mean + b.mean
+        se = math.sqrt(a.var / N + b.var / N + c.var / N)
+        assert abs(nested - c.mean) < 4.5 * se, (l, nested, c.mean, se)

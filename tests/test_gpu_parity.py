@@ -275,8 +275,8 @@ def test_config1_level_means_closed_form(l):
     N = 100000
     s = M.mlmc_level(l, N, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, params, SEED)
     em, ev = mlmc.euler_twoway_moments(l)
-    assert abs(s.mean() - em) < 4 * math.sqrt(ev / N)
-    assert abs(s.var() / ev - 1) < 0.05
+    assert abs(s.mean - em) < 4 * math.sqrt(ev / N)
+    assert abs(s.var / ev - 1) < 0.05
 
 
 def test_level_sums_match_oracle_sums(pl_table):
@@ -329,7 +329,7 @@ def test_edge_cases(pl_table):
                          _kind_tag(0, 1, 18), table=pl_table)
     assert np.array_equal(got, ref)
     s = M.mlmc_level(0, 1, M.MLMC_F32, False, M.MLMC_ICDF_EXACT, params, SEED)
-    assert s.n == 1 and s.var() == 0.0
+    assert s.n == 1 and s.var == 0.0
     got = gpu_paths(0, 18, 3, M.MLMC_BF16, True, M.MLMC_ICDF_TABLE, params, offset=2 ** 40 + 3)
     ref = O.twoway_paths(18, 2 ** 40 + 3 + np.arange(3), _bar_variant(M.MLMC_BF16, True), _orc_sde(params), SEED,
                          _kind_tag(0, 1, 18), table=pl_table)

@@ -40,13 +40,13 @@ def curves():
     out = {k: [] for k in ("exact", "two16", "two16k", "four32", "four32k", "four16", "four16k")}
     for l in LEVELS:
         N = 1 << 20 if l <= 12 else 1 << (32 - l)
-        out["exact"].append(M.mlmc_level(l, N, M.MLMC_F32, True, M.MLMC_ICDF_EXACT, p, 1234).var())
-        out["two16"].append(M.mlmc_level(l, N, M.MLMC_F16, False, T, p, 1234).var())
-        out["two16k"].append(M.mlmc_level(l, N, M.MLMC_F16, True, T, p, 1234).var())
-        out["four32"].append(M.mlmc_nested_level(l, N, M.MLMC_F32, False, T, p, 1234).var())
-        out["four32k"].append(M.mlmc_nested_level(l, N, M.MLMC_F32, True, T, p, 1234).var())
-        out["four16"].append(M.mlmc_nested_level(l, N, M.MLMC_F16, False, T, p, 1234).var())
-        out["four16k"].append(M.mlmc_nested_level(l, N, M.MLMC_F16, True, T, p, 1234).var())
+        out["exact"].append(M.mlmc_level(l, N, M.MLMC_F32, True, M.MLMC_ICDF_EXACT, p, 1234).var)
+        out["two16"].append(M.mlmc_level(l, N, M.MLMC_F16, False, T, p, 1234).var)
+        out["two16k"].append(M.mlmc_level(l, N, M.MLMC_F16, True, T, p, 1234).var)
+        out["four32"].append(M.mlmc_nested_level(l, N, M.MLMC_F32, False, T, p, 1234).var)
+        out["four32k"].append(M.mlmc_nested_level(l, N, M.MLMC_F32, True, T, p, 1234).var)
+        out["four16"].append(M.mlmc_nested_level(l, N, M.MLMC_F16, False, T, p, 1234).var)
+        out["four16k"].append(M.mlmc_nested_level(l, N, M.MLMC_F16, True, T, p, 1234).var)
     return {k: np.log2(np.array(v)) for k, v in out.items()}
 
 
