@@ -37,7 +37,7 @@ _lib = None
 # precision codes (oracle.c)
 F64, F32, F16, BF16, PBITS = 0, 1, 2, 3, 4
 # random-variable kinds
-RV_EXACT, RV_TABLE, RV_MLP, RV_TABLE16, RV_CUBIC = 0, 1, 2, 3, 4
+RV_EXACT, RV_TABLE, RV_MLP, RV_TABLE16, RV_CUBIC, RV_MLP16 = 0, 1, 2, 3, 4, 5
 # SDEs and payoffs
 GBM, OU = 0, 1
 PAYOFF_X, PAYOFF_CALL = 0, 1
@@ -108,6 +108,8 @@ def lib():
                                          P(SDE), ctypes.c_uint64, ctypes.c_uint32, dp, dp, ctypes.c_int, dp]
             L.orc_rounding_pairs.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ip, P(SDE),
                                              ctypes.c_uint64, ctypes.c_uint32, dp, dp, dp]
+            L.orc_mlp_feature32.argtypes = [ctypes.c_double]
+            L.orc_mlp_feature32.restype = ctypes.c_double
             L.orc_kahan_sum.argtypes = [dp, i64, ctypes.c_int, ctypes.c_int]
             L.orc_kahan_sum.restype = ctypes.c_double
             L.orc_openmp_threads.restype = ctypes.c_int
@@ -212,11 +214,17 @@ def _tables(table, cubic):
     return np.ascontiguousarray(np.concatenate([t, c]))
 
 
+def mlp_feature32(v) -> np.ndarray:
+    """The network input t = sqrt(-2 ln v) from binary32 operations (the
+    binary16 inference reading of the learned part)."""
+    return np.array([lib().orc_mlp_feature32(float(x)) for x in np.ravel(v)])
+
+
 def approx_icdf(u, rv: int, prec: int = F64, pbits: int = 53, table=None, mlp=None, cubic=None) -> np.ndarray:
     """Phi^-1 (rv=RV_EXACT), piecewise-linear table (RV_TABLE), the table at
     the 16-bit cell centre q16(u) (RV_TABLE16), piecewise cubic (RV_CUBIC,
-    coefficients `cubic`) or MLP (RV_MLP) evaluated with the rounding of
-    precision prec."""
+    coefficients `cubic`), the FP64 MLP (RV_MLP) or the MLP in binary16
+    inference arithmetic (RV_MLP16), rounded to precision prec."""
     u = _f64(u).ravel()
     z = np.empty_like(u)
     t = _tables(table, cubic)

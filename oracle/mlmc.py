@@ -407,8 +407,11 @@ def adaptive_mlmc(eps, draw, cost, *, nested, prec=F16, kahan=1, icdf=1, n0=1000
         L += 1
         add_level(L)
         plan()
-    est = sum(t.Y() for t in terms)
-    var = sum(t.V() / t.n for t in terms if t.n)
+    est = var = 0.0
+    for t in terms:                 # plain left-to-right sums (builtin sum() compensates)
+        est += t.Y()
+        if t.n:
+            var += t.V() / t.n
     return {"estimate": est, "variance": var, "levels": L + 1, "rounds": rounds[0], "converged": converged,
             "choice": [choice.get(l) for l in range(L + 1)],
             "terms": [(t.key, t.n, t.Y(), t.V()) for t in terms if not t.off]}

@@ -278,11 +278,107 @@ static double mlp_icdf(double u, const double *w)
     return upper ? y : -y;
 }
 
+/* The same network as evaluated in binary16 inference arithmetic (the
+ * reading of "FP16 MLP" used by the learned part; every step rounds where
+ * the reading says, to nearest even):
+ *   t = sqrt(-2 ln v) from binary32 operations: v = m 2^e with m in
+ *     [1/sqrt2, sqrt2] (m > R32(sqrt 2) halves m), z = R32((m - 1) / R32(m + 1)),
+ *     w = R32(z z), q = 1/9 then q = fma32(q, w, c) for c = 1/7, 1/5, 1/3, 1
+ *     (constants R32 of the fractions), ln m = R32(2 z q) -- the atanh series
+ *     ln m = 2 atanh z -- and t = R32(sqrt(fma32(-2 e, R32(ln 2), -2 ln m)));
+ *   layer 1: a_j = fma32(W1_j, t, b1_j), h1_j = R16(tanh(R16(a_j)));
+ *   layer 2: W2 rounded to binary16; c_j = R32(R32(b2_j + sum_{i<16} W2_ji h1_i)
+ *     + sum_{i>=16} W2_ji h1_i) (two 16-term steps, each sum exact, rounded
+ *     once), h2_j = R16(tanh(R16(c_j)));
+ *   layer 3: W3 rounded to binary16, y = R32(R32(b3 + sum_{j<16} W3_j h2_j)
+ *     + sum_{j>=16} W3_j h2_j).
+ * The sums are exact in binary64 while every term is a multiple of 2^-48
+ * and every partial sum stays below 2^5 in magnitude (binary16 products and
+ * biases of the trained networks' range); the function returns NaN if that
+ * does not hold.  fma32 is C's fmaf (correctly rounded). */
+static double r32(double x) { return (double)(float)x; }
+
+static double r16(double x)
+{
+    rmode m = mode_of(ORC_F16, 0);
+    return round_p(x, &m);
+}
+
+static int on_grid48(double x) { return x == 0.0 || ldexp(x, 48) == floor(ldexp(x, 48)); }
+
+double orc_mlp_feature32(double v)
+{
+    int e;
+    double m = frexp(v, &e);           /* v = m 2^e, m in [1/2, 1) */
+    m *= 2.0;
+    e -= 1;                            /* m in [1, 2) */
+    if (m > (double)(float)1.41421354f) {
+        m *= 0.5;
+        e += 1;
+    }
+    double z = r32((m - 1.0) / r32(m + 1.0));
+    double w = r32(z * z);
+    double q = (double)fmaf((float)(1.0 / 9.0), (float)w, (float)(1.0 / 7.0));
+    q = (double)fmaf((float)q, (float)w, (float)(1.0 / 5.0));
+    q = (double)fmaf((float)q, (float)w, (float)(1.0 / 3.0));
+    q = (double)fmaf((float)q, (float)w, 1.0f);
+    double lnm = r32((2.0 * z) * q);
+    double t2 = (double)fmaf((float)(-2 * e), (float)log(2.0), (float)(-2.0 * lnm));
+    return r32(sqrt(t2));
+}
+
+static double mlp_forward16(double t, const double *w)
+{
+    const double *W1 = w, *b1 = w + 32, *W2 = w + 64, *b2 = w + 64 + 1024;
+    const double *W3 = w + 64 + 1024 + 32, *b3 = w + 64 + 1024 + 64;
+    double h1[MLP_H], h2[MLP_H];
+    int ok = 1;
+    for (int j = 0; j < MLP_H; ++j) {
+        double a = (double)fmaf((float)W1[j], (float)t, (float)b1[j]);
+        h1[j] = r16(tanh(r16(a)));
+    }
+    for (int o = 0; o < MLP_H; ++o) {
+        double c = b2[o];
+        for (int k = 0; k < 2; ++k) {
+            for (int i = 16 * k; i < 16 * k + 16; ++i) {
+                double term = r16(W2[o * MLP_H + i]) * h1[i];
+                ok &= on_grid48(term);
+                c += term;
+                ok &= fabs(c) < 32.0;
+            }
+            c = r32(c);
+        }
+        h2[o] = r16(tanh(r16(c)));
+    }
+    double y = b3[0];
+    for (int k = 0; k < 2; ++k) {
+        for (int j = 16 * k; j < 16 * k + 16; ++j) {
+            double term = r16(W3[j]) * h2[j];
+            ok &= on_grid48(term);
+            y += term;
+            ok &= fabs(y) < 32.0;
+        }
+        y = r32(y);
+    }
+    ok &= on_grid48(b3[0]) || fabs(b3[0]) >= ldexp(1.0, -25);
+    for (int o = 0; o < MLP_H; ++o) ok &= on_grid48(b2[o]) || fabs(b2[o]) >= ldexp(1.0, -25);
+    return ok ? y : NAN;
+}
+
+static double mlp_icdf16(double u, const double *w)
+{
+    int upper = u > 0.5;
+    double v = upper ? 1.0 - u : u;
+    double y = mlp_forward16(orc_mlp_feature32(v), w);
+    return upper ? y : -y;
+}
+
 /* RV kinds.  TABLE16: the piecewise-linear table at the 16-bit uniform
- * q16(u) (see uniform16_of).  CUBIC: the piecewise cubic.  The `table`
- * argument of the entry points holds the linear table (32 values) followed
- * by the cubic one (64 values). */
-enum { ORC_RV_EXACT = 0, ORC_RV_TABLE = 1, ORC_RV_MLP = 2, ORC_RV_TABLE16 = 3, ORC_RV_CUBIC = 4 };
+ * q16(u) (see uniform16_of).  CUBIC: the piecewise cubic.  MLP: the FP64
+ * network; MLP16: the network in binary16 inference arithmetic (above).  The
+ * `table` argument of the entry points holds the linear table (32 values)
+ * followed by the cubic one (64 values). */
+enum { ORC_RV_EXACT = 0, ORC_RV_TABLE = 1, ORC_RV_MLP = 2, ORC_RV_TABLE16 = 3, ORC_RV_CUBIC = 4, ORC_RV_MLP16 = 5 };
 
 static double rv_of(double u, int rv, const double *table, const double *mlp, const rmode *m)
 {
@@ -291,6 +387,7 @@ static double rv_of(double u, int rv, const double *table, const double *mlp, co
     case ORC_RV_TABLE16: return table_icdf(q16(u), table, m);
     case ORC_RV_CUBIC: return cubic_icdf(u, table + 32, m);
     case ORC_RV_MLP: return round_p(mlp_icdf(u, mlp), m);
+    case ORC_RV_MLP16: return round_p(mlp_icdf16(u, mlp), m);
     default: return round_p(orc_ndtri1(u), m);
     }
 }
