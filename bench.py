@@ -307,7 +307,7 @@ def run_gpu(args):
 
     # --- time to RMSE eps through mlmc_run: nested FP16+Kahan vs plain FP32
     mlp = None if args.no_mlp else mlp_leg(M, torch, params)
-    tte = None if args.no_tte else time_to_eps(M, params, [args.eps, 3e-4, 1e-5], with_mlp=mlp is not None)
+    tte = None if args.no_tte else time_to_eps(M, params, [args.eps, 3e-4, 1e-5, 3e-6], with_mlp=mlp is not None)
 
     # --- roofline of the dominant kernel (four-way FP16+Kahan table, all levels in one launch)
     clk = clocks.summary()
@@ -438,13 +438,16 @@ def batch_leg(M, torch, stream, repeats=5):
                       "device_seconds from CUDA events around the graph launch"}
 
 
-def time_to_eps(M, params, eps_list, repeats=3, with_mlp=False):
+def time_to_eps(M, params, eps_list, repeats=5, with_mlp=False):
     """Wall time of mlmc_run to RMSE eps (Sec. 3 adaptive MLMC): the standard
     estimator (FP32, exact normals, plain Euler) against the nested estimator
     with FP16 + Kahan table normals, FP32 table normals, and the per-level
     automatic choice; the same with 16-bit uniforms for the approximate
     normals, and with the Milstein scheme.  Median of `repeats` runs with
-    different seeds, after one untimed run."""
+    different seeds, after one untimed run.  Beside the wall time: the cost
+    model's device time of the samples drawn (sum of N_t C_t, Sec. 3) and the
+    measured device time of the rounds (their difference to the wall time is
+    the host's share: planning, launches, waits)."""
     T, T16 = M.MLMC_ICDF_TABLE, M.MLMC_ICDF_TABLE16
     E, MIL = M.MLMC_EULER, M.MLMC_MILSTEIN
     variants = (("plain_fp32_exact", 0, M.MLMC_F32, 0, T, E), ("nested_f16_kahan_table", 1, M.MLMC_F16, 1, T, E),
@@ -459,7 +462,7 @@ def time_to_eps(M, params, eps_list, repeats=3, with_mlp=False):
     for eps in eps_list:
         row = {}
         for name, est, prec, kahan, icdf, scheme in variants:
-            times, res = [], None
+            times, model, device, res = [], [], [], None
             p = M.mlmc_sde_params.from_buffer_copy(params)
             p.scheme = scheme
             for rep in range(repeats + 1):
@@ -470,15 +473,22 @@ def time_to_eps(M, params, eps_list, repeats=3, with_mlp=False):
                 dt = time.perf_counter() - t0
                 if rep > 0:
                     times.append(dt)
+                    model.append(r.model_s)
+                    device.append(r.device_s)
                     res = r
-            row[name] = {"seconds": statistics.median(times), "estimate": res.estimate,
+            row[name] = {"seconds": statistics.median(times), "model_device_seconds": statistics.median(model),
+                         "device_seconds": statistics.median(device), "estimate": res.estimate,
                          "rmse_est": math.sqrt(res.variance), "levels": res.levels, "rounds": res.rounds,
-                         "path_steps": res.path_steps}
+                         "path_steps": res.path_steps, "runs": repeats}
             if est == 1 and prec == -1:
                 row[name]["prec_per_level"] = ["f16" if res.prec[l] == M.MLMC_F16 else "f32"
                                                for l in range(res.levels)]
                 row[name]["kahan_per_level"] = [int(res.kahan[l]) for l in range(res.levels)]
                 row[name]["efficiency_per_level"] = [round(res.efficiency[l], 3) for l in range(res.levels)]
+        row["speedup_auto_table16_vs_plain"] = (row["plain_fp32_exact"]["seconds"]
+                                                / row["nested_auto_table16"]["seconds"])
+        row["model_ratio_auto_table16_vs_plain"] = (row["nested_auto_table16"]["model_device_seconds"]
+                                                    / row["plain_fp32_exact"]["model_device_seconds"])
         row["speedup_f16_kahan_vs_plain"] = row["plain_fp32_exact"]["seconds"] / row["nested_f16_kahan_table"]["seconds"]
         row["speedup_f16_kahan_table16_vs_plain"] = (row["plain_fp32_exact"]["seconds"]
                                                      / row["nested_f16_kahan_table16"]["seconds"])

@@ -146,6 +146,7 @@ LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int
     a.tag = kind | ((uint32_t)l << 8) | (set_id << 16);
     a.k0 = (uint32_t)seed;
     a.k1 = (uint32_t)(seed >> 32);
+    a.rk = philox_round_keys(a.k0, a.k1);
     a.drift_f = p->p0 * delta_f;
     a.drift_c = p->p0 * (2.0 * delta_f);
     if (p->sde == MLMC_GBM) {

@@ -338,6 +338,10 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s, bool stage_idle
 
 int env_int(const char *name, int dflt);
 
+// Work (pair-cost units: fine-step equivalents of a two-way pair) below
+// which a batch is latency-sized: about 50 us on GB300.
+constexpr double SMALL_BATCH_WORK = 2e7;
+
 // Resident blocks per SM of a batch kernel (cached per kernel).
 int blocks_per_sm(BatchCache &c, BatchKernelFn fn) {
     auto it = c.occupancy.find((const void *)fn);
@@ -370,10 +374,30 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         bps[gi] = blocks_per_sm(c, fns[gi]);
         bps_min = std::min(bps_min, bps[gi]);
     }
-    // MLMC_BATCH_CONCURRENT: 1 = groups always concurrent, 0 = always one
-    // after another on s (each with the whole GPU), unset = concurrent
+    // Groups one after another on s, each with the whole GPU, unless the
+    // batch is latency-sized (below about 50 us of work: the second launch
+    // would wait for the first) or the groups' longest tiles dominate.  In
+    // per-lane step units, a group alone takes about max(ideal, tail) (its
+    // work spread over all resident lanes, or its longest tile); in sequence
+    // the groups add up, concurrently they share the GPU, at about 1.2 times
+    // the ideal sum (measured), and overlap their tails.  On GB300 adaptive
+    // rounds of 0.5-15 ms ran 10-30 % faster in sequence (RMSE 3e-6, a
+    // 15.4 ms concurrent round took 11.9 ms), the batching workload's
+    // single-pair deep items twice as fast concurrently.
+    // MLMC_BATCH_CONCURRENT = 0 / 1 forces either.
+    double seq = 0.0, ideal_sum = 0.0, tail_max = 0.0;
+    for (size_t gi = 0; gi < ng; ++gi) {
+        const Group &g = p.groups[gi];
+        const double ideal_g = g.work / ((double)bps[gi] * d.sm_count * 256.0);
+        const double tail_g = g.tile_cost.empty() ? 0.0 : g.tile_cost[0];
+        seq += std::max(ideal_g, tail_g);
+        ideal_sum += ideal_g;
+        tail_max = std::max(tail_max, tail_g);
+    }
     const int conc_env = env_int("MLMC_BATCH_CONCURRENT", -1);
-    const bool concurrent = ng > 1 && conc_env != 0;
+    const bool concurrent =
+        ng > 1 && (conc_env == 1 || (conc_env != 0 && (p.work < SMALL_BATCH_WORK ||
+                                                        1.2 * std::max(ideal_sum, tail_max) < seq)));
     const size_t nside = concurrent ? std::min<size_t>(ng - 1, BatchCache::MAX_SIDE) : 0;
     if (nside > 0) {
         if (!c.fork && (e = cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming)) != cudaSuccess)
@@ -402,7 +426,7 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, ((uint64_t)g.ntiles + 7) / 8));
         cudaStream_t gs = gi == 0 || !concurrent ? s : c.side[(gi - 1) % BatchCache::MAX_SIDE];
         fns[gi]<<<(unsigned)grid, 256, 0, gs>>>(c.items, c.spans + g.span_base, (uint32_t)g.spans.size(), g.ntiles,
-                                                 c.counters + gi, c.partials, d.tabs, p.items[0].k0, p.items[0].k1);
+                                                 c.counters + gi, c.partials, d.tabs, p.items[0].rk);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch kernel");
     }
     for (size_t k = 0; k < nside; ++k) {
@@ -474,11 +498,13 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
 // One round of a caller that owns its own cache (the adaptive driver):
 // descriptors, persistent kernels, finalize and the copy of all sums into
 // c.sums_host, enqueued on s.  The caller waits on s before reading.
-// The tile size follows the round's total work: about four tiles per
-// resident lane, each at least 16 and at most 4096 steps long per lane.
+// The tile size follows the round's total work: about sixteen tiles per
+// resident lane (every round has a new shape, so nothing is tuned), each at
+// least 16 steps long per lane; the dynamic schedule then leaves a last wave
+// of at most a sixteenth of a group's time.
 mlmc_status batch_round(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed,
                         cudaStream_t s) {
-    Plan p = make_plan(d, w, n, seed, work_lane_log2(d, w, n));
+    Plan p = make_plan(d, w, n, seed, std::max(4, work_lane_log2(d, w, n) - 2));
     // the driver waits for every round before it plans the next one
     mlmc_status st = upload(c, p, s, true);
     if (st) return st;

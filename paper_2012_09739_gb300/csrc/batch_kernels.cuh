@@ -63,8 +63,8 @@ struct SeqScratch {
 };
 
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__device__ void simulate_pair_seq(const LevelArgs &a, const SmemTable &tab, const MlpFrags &mlp, uint64_t g,
-                                  float &d0, float &d1, SeqScratch<P> &sc) {
+__device__ void simulate_pair_seq(const LevelArgs &a, const PhiloxKeys &K, const SmemTable &tab, const MlpFrags &mlp,
+                                  uint64_t g, float &d0, float &d1, SeqScratch<P> &sc) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nf = 1u << a.l;
     const uint64_t p0 = a.path_offset + 2 * g, p1 = p0 + 1;
@@ -85,7 +85,7 @@ __device__ void simulate_pair_seq(const LevelArgs &a, const SmemTable &tab, cons
         if (lane < 2 * CALLS) {
             const uint64_t path = lane < CALLS ? p0 : p1;
             const uint32_t j = blk * CALLS + (lane % CALLS);
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)path, (uint32_t)(path >> 32), j, a.tag), a.k0, a.k1);
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)path, (uint32_t)(path >> 32), j, a.tag), K);
             uint32_t *dst = &sc.w[lane < CALLS ? 0 : 1][4 * (lane % CALLS)];
             dst[0] = r.x;
             dst[1] = r.y;
@@ -130,7 +130,7 @@ __device__ void simulate_pair_seq(const LevelArgs &a, const SmemTable &tab, cons
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
 __global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 2 : (MODE == MODE_FOUR ? 3 : 4))
 batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uint32_t ntiles, uint32_t *counter,
-             double2 *partials, const DevTables *tabs, uint32_t key0, uint32_t key1) {
+             double2 *partials, const DevTables *tabs, const PhiloxKeys keys) {
     __shared__ SmemTable tab;
     __shared__ SeqScratch<P> seq[8];           // one per warp (warp-cooperative single pairs)
     stage_table(tab, tabs);
@@ -144,14 +144,9 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= ntiles) break;
         const TileSpan sp = spans[find_span(spans, nspans, t, lane)];
-        LevelArgs a = items[sp.item];
-        if constexpr (MODE == MODE_TWO) {
-            // the batch's Philox key (every item has the seed's) from the
-            // launch parameters: measured 4 % faster for the two-way kernels
-            // at their 64-register budget, 2.5 % slower for the four-way ones
-            a.k0 = key0;
-            a.k1 = key1;
-        }
+        // every item has the batch's seed: its round keys come from the
+        // launch parameters
+        const LevelArgs a = items[sp.item];
         const uint64_t first = (uint64_t)(t - sp.begin) * sp.per_tile;
         const uint32_t npairs = a.npairs - first < sp.per_tile ? (uint32_t)(a.npairs - first) : sp.per_tile;
         const uint64_t chunk0 = first >> 5;        // the tile's first chunk, the start of a group
@@ -159,7 +154,7 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
         if (npairs == 1 && a.l >= SEQ_MIN_LEVEL) {
             // one pair, long paths: the warp generates the normals, lane 0 steps
             float d0, d1;
-            simulate_pair_seq<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, first, d0, d1, seq[threadIdx.x >> 5]);
+            simulate_pair_seq<MODE, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, first, d0, d1, seq[threadIdx.x >> 5]);
             if (lane == 0) {
                 s1.add(d0);
                 s2.add(d0 * d0);
@@ -180,7 +175,7 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
             for (; r < r1; ++r) {
                 const uint32_t k = (r << 5) + lane;
                 const bool active = k < npairs;
-                run_slot<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, first + (active ? k : npairs - 1), active, s1, s2);
+                run_slot<MODE, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, first + (active ? k : npairs - 1), active, s1, s2);
             }
             const float w1 = warp_sum(s1.value()), w2 = warp_sum(s2.value());
             if (lane == 0) partials[grp] = make_double2((double)w1, (double)w2);
@@ -191,6 +186,6 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
 }
 
 using BatchKernelFn = void (*)(const LevelArgs *, const TileSpan *, uint32_t, uint32_t, uint32_t *, double2 *,
-                               const DevTables *, uint32_t, uint32_t);
+                               const DevTables *, const PhiloxKeys);
 
 }  // namespace mlmc

@@ -28,6 +28,35 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The ten round keys of one key (seed): (k0 + r W0, k1 + r W1) for r = 0..9,
+// computed once on the host.  Kernels read them from their parameter space,
+// so each round takes its key as an operand instead of advancing the
+// schedule in registers.
+struct PhiloxKeys {
+    uint32_t k[20];
+};
+
+__host__ __device__ inline PhiloxKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+    PhiloxKeys K;
+    for (int r = 0; r < 10; ++r) {
+        K.k[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        K.k[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    return K;
+}
+
+// Philox4x32-10 with the precomputed round keys (the same function as
+// philox4x32_10(c, k0, k1)).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys &K) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ K.k[2 * r], lo1, hi0 ^ c.w ^ K.k[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint32_t word(const uint4 &w, int q) {
     return q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
 }

@@ -13,7 +13,7 @@
 // Each round runs every term's new samples (fresh counter ranges:
 // path_offset = samples already taken) as the items of one persistent batched
 // launch, then copies all sums to the host once.  The allocation uses a cost
-// model C = 2^l nu (ns per path-step of each variant, measured on GB300); only
+// model of measured device time per sample of each term (kCost below); only
 // the ratios between terms matter to the split.
 #include <math.h>
 #include <stdio.h>
@@ -58,24 +58,72 @@ enum Choice { CH_F16K = 0, CH_F16 = 1, CH_F32 = 2, CH_STANDARD = 3, CH_NONE = 4 
 // coarsest two-way levels.
 uint64_t round8(uint64_t n) { return (n + 7) / 8 * 8; }
 
-// Device cost of one sample of a term: C = nu 2^l + kappa, with nu the ns
-// per fine path-step of the variant and kappa the per-sample cost (uniform
-// generation at l < 2, payoff, accumulation), measured on GB300 with the
-// level kernels at full occupancy (N = 2^24 for l <= 6, 2^(30-l) above;
-// fitted on l = 0..10).
-double nu_of(const Term &t) {
-    if (t.icdf == MLMC_ICDF_MLP) return t.four ? 9.0e-3 : 7.0e-3;
-    if (t.icdf == MLMC_ICDF_EXACT) return t.kahan ? 1.69e-3 : 1.53e-3;
-    const bool half = t.prec != MLMC_F32;   // binary16 and bfloat16 share the f16x2-style packing
-    // 16-bit uniforms: half the Philox calls per two-way fine step, one more
-    // uniform conversion per four-way step; the cubic adds a Horner evaluation
-    const bool u16 = t.icdf == MLMC_ICDF_TABLE16, cub = t.icdf == MLMC_ICDF_CUBIC;
-    if (t.four) return (u16 ? 1.06 : cub ? 1.12 : 1.0) * (half ? 2.10e-3 : 2.15e-3);
-    const double base = half ? (t.kahan ? 1.07e-3 : 0.94e-3) : (t.kahan ? 1.2e-3 : 1.065e-3);
-    return (u16 ? 0.81 : cub ? 1.3 : 1.0) * base;
+// Cost model C_t of Sec. 3: device time per sample of each estimator term,
+// measured on GB300 as single-item batched launches at full occupancy
+// (GBM call, N = max(2^27 >> (l - 1), 2^21) samples, best of three, L2
+// warm), in picoseconds per sample for levels 0..10; finer levels scale the
+// level-10 cost by 2^(l - 10).  Only the ratios between terms enter the
+// sample split and the per-level choice.
+struct CostRow {
+    int four, prec, kahan, icdf, milstein;
+    float ps[11];
+};
+const CostRow kCost[] = {
+    {0, MLMC_F32, 0, MLMC_ICDF_EXACT, 0, {2.92, 5.136, 7.495, 13.22, 25.12, 49.17, 93.64, 191.1, 358, 699.1, 1379}},
+    {0, MLMC_F32, 1, MLMC_ICDF_EXACT, 0, {3.054, 5.108, 8.007, 14.2, 26.66, 51.66, 101.4, 200.6, 387.3, 751.2, 1485}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE, 0, {2.615, 4.299, 6.114, 10.53, 19.87, 37.25, 74.39, 144.1, 272.2, 546.1, 1058}},
+    {0, MLMC_F16, 0, MLMC_ICDF_TABLE, 0, {2.603, 4.129, 5.82, 9.676, 17.65, 34.82, 67.67, 134.2, 251.5, 478.3, 972.9}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE, 0, {2.45, 4.176, 6.151, 10.47, 19.7, 37.5, 71.17, 140.4, 262.3, 507.6, 997.8}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE16, 0, {2.02, 3.38, 6.64, 8.407, 15.3, 30.21, 56.89, 117.8, 209.5, 403.9, 785.4}},
+    {0, MLMC_F16, 0, MLMC_ICDF_TABLE16, 0, {2.025, 3.244, 6.088, 8.042, 13.89, 26.03, 51.15, 102.2, 181.2, 346.4, 676.8}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE16, 0, {2.039, 3.239, 7.098, 8.886, 16.43, 30.91, 59.26, 114.8, 212.5, 409.8, 803.8}},
+    {0, MLMC_F16, 1, MLMC_ICDF_CUBIC, 0, {2.737, 4.571, 6.817, 12.18, 23.39, 45.31, 86.13, 172.2, 325.6, 635.9, 1268}},
+    {0, MLMC_F32, 0, MLMC_ICDF_CUBIC, 0, {2.741, 4.629, 7, 12.25, 22.9, 45.15, 88.56, 170.7, 333.4, 640, 1244}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE, 0, {5.148, 6.707, 9.881, 17.74, 33.85, 66.06, 130.6, 258.2, 501.1, 987.7, 1961}},
+    {1, MLMC_F16, 0, MLMC_ICDF_TABLE, 0, {5.06, 6.495, 9.593, 17.13, 33.53, 65.27, 125.8, 246.7, 478.8, 941.3, 1868}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE, 0, {5.286, 7.073, 10.16, 17.98, 33.98, 66.01, 130.2, 258.5, 499.4, 981.8, 1979}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE16, 0, {5.194, 6.908, 10.45, 18.72, 35.69, 69.73, 137.5, 273.2, 530.2, 1042, 2065}},
+    {1, MLMC_F16, 0, MLMC_ICDF_TABLE16, 0, {5.121, 6.708, 9.904, 17.98, 35.25, 68.02, 131.6, 260.4, 505, 995, 1975}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE16, 0, {5.367, 7.162, 10.57, 19.25, 37.03, 72.16, 143.9, 278.7, 540.8, 1065, 2115}},
+    {1, MLMC_F16, 1, MLMC_ICDF_CUBIC, 0, {5.212, 6.8, 10.55, 19.09, 37.15, 71.88, 144.7, 281.9, 548.6, 1082, 2151}},
+    {1, MLMC_F32, 0, MLMC_ICDF_CUBIC, 0, {5.621, 7.436, 10.69, 19.43, 38.13, 74.31, 142.3, 281.6, 548.1, 1077, 2137}},
+    {0, MLMC_F32, 0, MLMC_ICDF_EXACT, 1, {3.165, 5.362, 8.385, 14.92, 27.91, 54.05, 106.1, 209.4, 402.7, 789.3, 1563}},
+    {0, MLMC_F32, 1, MLMC_ICDF_EXACT, 1, {3.21, 5.56, 8.984, 16.14, 30.48, 59.17, 119.4, 236.6, 450.5, 870.5, 1727}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE, 1, {2.722, 4.553, 6.793, 12.43, 22.88, 44.12, 84.67, 169.3, 322, 623, 1229}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE, 1, {2.646, 4.766, 7.185, 12.6, 23, 45.75, 86.14, 176.1, 333.4, 648.8, 1261}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE16, 1, {2.087, 3.47, 6.879, 9.908, 18.89, 35.26, 71.96, 137.2, 259.2, 502.3, 988.2}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE16, 1, {2.141, 3.562, 8.801, 10.58, 19.94, 36.8, 74.39, 141.9, 268.9, 512, 1024}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE, 1, {5.179, 6.921, 11.42, 20.86, 41.59, 79.04, 158.5, 310.9, 610.8, 1217, 2381}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE, 1, {5.453, 7.437, 11.43, 21.1, 41.8, 82.21, 157.1, 313.3, 606.5, 1197, 2378}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE16, 1, {5.441, 7.366, 11.92, 21.75, 43.43, 85.63, 165.8, 332.4, 637.9, 1260, 2499}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE16, 1, {5.636, 7.763, 12.22, 22.63, 44.02, 85.87, 164.7, 328.8, 639.4, 1260, 2504}},
+};
+
+// The row of a term, or the nearest measured one: bfloat16 as binary16 (the
+// same packed arithmetic), the other Kahan setting, the Euler row for a
+// Milstein term; the network (MLP) as its table row times the measured cost
+// ratio of its inverse CDF.
+double cost_ps(int four, int prec, int kahan, int icdf, int milstein, int l) {
+    double factor = 1.0;
+    if (prec == MLMC_BF16) prec = MLMC_F16;
+    if (icdf == MLMC_ICDF_MLP) {
+        icdf = MLMC_ICDF_TABLE;
+        factor = four ? 4.3 : 6.5;
+    }
+    const CostRow *row = nullptr;
+    for (int pass = 0; pass < 4 && !row; ++pass) {
+        const int k = pass & 1 ? !kahan : kahan, m = pass & 2 ? 0 : milstein;
+        for (const CostRow &r : kCost)
+            if (r.four == four && r.prec == prec && r.kahan == k && r.icdf == icdf && r.milstein == m) row = &r;
+        if (row && m != milstein) factor *= 1.2;
+    }
+    if (!row) row = &kCost[four ? 10 : 0];
+    return factor * (l <= 10 ? (double)row->ps[l] : ldexp((double)row->ps[10], l - 10));
 }
 
-double cost_of(const Term &t) { return ldexp(1.0, t.l) * nu_of(t) + (t.four ? 5.5e-3 : 5.2e-3); }
+double cost_of(const Term &t, int milstein) {
+    return 1e-3 * cost_ps(t.four, t.prec, t.kahan, t.icdf, milstein, t.l);
+}
 
 }  // namespace
 
@@ -85,6 +133,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
     mlmc_status st = device_state(&d);
     if (st) return st;
     const bool nested = o->estimator == 1;
+    const int mil = p->scheme == MLMC_MILSTEIN && p->sde == MLMC_GBM ? 1 : 0;
     if (nested && o->icdf == MLMC_ICDF_MLP && !d->mlp_ready) return fail(MLMC_ENOTREADY, "MLP weights not set");
 
     // one run at a time per process: the stream and round buffers persist
@@ -126,7 +175,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         std::vector<size_t> which;
         for (size_t i = 0; i < ts.size(); ++i) {
             if (ts[i].dn == 0) continue;
-            ts[i].cost = cost_of(ts[i]);
+            ts[i].cost = cost_of(ts[i], mil);
             mlmc_work w;
             memset(&w, 0, sizeof w);
             w.params = *p;
@@ -269,7 +318,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         mlmc_status r = trial(tried);
         if (r) return r;
         std::copy(tried.begin(), tried.end(), cand.begin() + 2 * first);
-        auto vc = [&](const Term &t) { return t.var() * cost_of(t); };
+        auto vc = [&](const Term &t) { return t.var() * cost_of(t, mil); };
         int best = first;
         double best_score = 1e300;
         for (int c = first; c < 3; ++c) {
@@ -330,7 +379,7 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
                 // predecessor's (guards levels with few samples)
                 V[i] = fmax(V[i], 0.25 * V[i - per_level]);
             }
-            C[i] = cost_of(terms[i]);
+            C[i] = cost_of(terms[i], mil);
             terms[i].cost = C[i];
         }
         double total = 0.0, var_sum = 0.0;

@@ -31,6 +31,7 @@ struct LevelArgs {
     uint64_t N;
     uint64_t path_offset;
     uint32_t tag, k0, k1;     // Philox counter tag and key (seed)
+    PhiloxKeys rk;            // the key's ten round keys (level launches read them from here)
     // per-level coefficients in FP64, rounded once to the working precision
     // in the kernel: GBM drift = mu delta_f (fine) / mu 2 delta_f (coarse),
     // diff = sigma sqrt(delta_f), Milstein mil = sigma^2 delta_f / 2; OU
@@ -193,8 +194,9 @@ __device__ __forceinline__ void pair_result(const LevelArgs &a, const PP &fine, 
 // their differences D (d0, d1); out0/out1 receive the per-sample outputs
 // (P_f, P_c, D) or (P^_f, P^_c, P-_f, P-_c, D).
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTable &tab, const MlpFrags &mlp,
-                                              uint64_t g, float &d0, float &d1, float *out0, float *out1) {
+__device__ __forceinline__ void simulate_pair(const LevelArgs &a, const PhiloxKeys &K, const SmemTable &tab,
+                                              const MlpFrags &mlp, uint64_t g, float &d0, float &d1, float *out0,
+                                              float *out1) {
     const uint32_t nf = 1u << a.l;
     const uint32_t ncalls = (nf + 3u) >> 2;
     const uint64_t p0 = a.path_offset + 2 * g, p1 = p0 + 1;
@@ -223,7 +225,7 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
     };
 
     auto call_of = [&](uint64_t cp, uint32_t j) {
-        return philox4x32_10(make_uint4((uint32_t)cp, (uint32_t)(cp >> 32), j, a.tag), a.k0, a.k1);
+        return philox4x32_10(make_uint4((uint32_t)cp, (uint32_t)(cp >> 32), j, a.tag), K);
     };
     // Coarsest levels (a path needs at most half a call): paths 2k and 2k+1
     // share call 0 of counter path field k, path p starting at word (or
@@ -256,8 +258,8 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const SmemTabl
         }
         const uint32_t ncalls16 = nf <= 4 ? 0u : (nf + 7u) >> 3;
         for (uint32_t j = 0; j < ncalls16; ++j) {
-            const uint4 r0 = philox4x32_10(make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), j, a.tag), a.k0, a.k1);
-            const uint4 r1 = philox4x32_10(make_uint4((uint32_t)p1, (uint32_t)(p1 >> 32), j, a.tag), a.k0, a.k1);
+            const uint4 r0 = philox4x32_10(make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), j, a.tag), K);
+            const uint4 r1 = philox4x32_10(make_uint4((uint32_t)p1, (uint32_t)(p1 >> 32), j, a.tag), K);
             halves(r0.x, r1.x, 0);
             halves(r0.y, r1.y, 2);
             halves(r0.z, r1.z, 4);
@@ -304,8 +306,8 @@ __host__ __device__ __forceinline__ int unit_pairs(int mode, int icdf, int l) {
 // coarse; 16-bit uniforms only).  emit(i, P_f, P_c, D) receives every path
 // in order.
 template <int B, int L, bool ALIGNED, int P, bool KAHAN, int ICDF, int SDE, class Emit>
-__device__ __forceinline__ void simulate_unit(const LevelArgs &a, const SmemTable &tab, const MlpFrags &mlp,
-                                              uint64_t u, Emit &&emit) {
+__device__ __forceinline__ void simulate_unit(const LevelArgs &a, const PhiloxKeys &K, const SmemTable &tab,
+                                              const MlpFrags &mlp, uint64_t u, Emit &&emit) {
     constexpr uint32_t S = 2 * B;
     constexpr bool U16 = ICDF == ICDF_TABLE16;
     static_assert(L == 0 || U16, "level-1 units use 16-bit uniforms");
@@ -313,7 +315,7 @@ __device__ __forceinline__ void simulate_unit(const LevelArgs &a, const SmemTabl
     const uint32_t m = ALIGNED ? 0u : (uint32_t)(base % S);
     const uint64_t cp = base / S;
     auto call_of = [&](uint64_t c) {
-        return philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), 0u, a.tag), a.k0, a.k1);
+        return philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), 0u, a.tag), K);
     };
     const uint4 r0 = call_of(cp);
     uint4 r1 = r0;
@@ -361,8 +363,8 @@ __device__ __forceinline__ void simulate_unit(const LevelArgs &a, const SmemTabl
 // floats per sample).  Shared by the level and the batched kernels, so both
 // accumulate identically.
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__device__ __forceinline__ void run_slot(const LevelArgs &a, const SmemTable &tab, const MlpFrags &mlp, uint64_t g,
-                                         bool active, KahanF32 &k1, KahanF32 &k2) {
+__device__ __forceinline__ void run_slot(const LevelArgs &a, const PhiloxKeys &K, const SmemTable &tab,
+                                         const MlpFrags &mlp, uint64_t g, bool active, KahanF32 &k1, KahanF32 &k2) {
     if (MODE == MODE_TWO && a.unit > 1) {
         const uint64_t first = (uint64_t)(2 * a.unit) * g;        // sample index of the unit's first path
         auto emit = [&](int i, float pf, float pc, float d) {
@@ -379,20 +381,20 @@ __device__ __forceinline__ void run_slot(const LevelArgs &a, const SmemTable &ta
         const bool aligned = a.path_offset % (uint64_t)(2 * a.unit) == 0;
         if constexpr (ICDF == ICDF_TABLE16) {
             if (a.l == 0) {
-                if (aligned) simulate_unit<4, 0, true, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
-                else simulate_unit<4, 0, false, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
+                if (aligned) simulate_unit<4, 0, true, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
+                else simulate_unit<4, 0, false, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
             } else {
-                if (aligned) simulate_unit<2, 1, true, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
-                else simulate_unit<2, 1, false, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
+                if (aligned) simulate_unit<2, 1, true, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
+                else simulate_unit<2, 1, false, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
             }
         } else {
-            if (aligned) simulate_unit<2, 0, true, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
-            else simulate_unit<2, 0, false, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, emit);
+            if (aligned) simulate_unit<2, 0, true, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
+            else simulate_unit<2, 0, false, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
         }
         return;
     }
     float d0, d1, out0[5], out1[5];
-    simulate_pair<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, g, d0, d1, out0, out1);
+    simulate_pair<MODE, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, d0, d1, out0, out1);
     const bool valid1 = 2 * g + 1 < a.N;
     if (active) {
         k1.add(d0);
@@ -485,7 +487,7 @@ __global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 2 : (MODE == MODE_FOUR
         for (uint64_t c = c0; c < c1; ++c) {
             const uint64_t g = c * 32 + lane;
             const bool active = g < a.npairs;
-            run_slot<MODE, P, KAHAN, ICDF, SDE>(a, tab, mlp, active ? g : a.npairs - 1, active, k1, k2);
+            run_slot<MODE, P, KAHAN, ICDF, SDE>(a, a.rk, tab, mlp, active ? g : a.npairs - 1, active, k1, k2);
         }
         if (a.chunk_partials) {
             const float w1 = warp_sum(k1.value()), w2 = warp_sum(k2.value());

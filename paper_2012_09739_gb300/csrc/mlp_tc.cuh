@@ -48,8 +48,30 @@ __device__ __forceinline__ void mma16816(float &d0, float &d1, float &d2, float 
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(c0), "f"(c1), "f"(c2), "f"(c3));
 }
 
-// Network input from v in (0, 1/2].
-__device__ __forceinline__ float mlp_feature(float v) { return sqrtf(-2.0f * logf(v)); }
+// Network input t = sqrt(-2 ln v) from v in [2^-24, 1/2], with binary32
+// operations that each round once to nearest (so that the oracle can repeat
+// them exactly): v = m 2^e with m in [1/sqrt2, sqrt2]; ln m = 2 z (1 + z^2/3
+// + z^4/5 + z^6/7 + z^8/9) with z = (m - 1) / (m + 1), |z| <= 0.1716 (the
+// atanh series; the next term is below 7e-10); t^2 = -2 e ln2 - 2 ln m by one
+// FMA; t = sqrt(t^2) correctly rounded.
+__device__ __forceinline__ float mlp_feature(float v) {
+    const uint32_t b = __float_as_uint(v);
+    int e = (int)(b >> 23) - 127;
+    float m = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+    if (m > 1.41421354f) {
+        m = __fmul_rn(m, 0.5f);
+        e += 1;
+    }
+    const float z = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float w = __fmul_rn(z, z);
+    float q = __fmaf_rn(1.0f / 9.0f, w, 1.0f / 7.0f);
+    q = __fmaf_rn(q, w, 1.0f / 5.0f);
+    q = __fmaf_rn(q, w, 1.0f / 3.0f);
+    q = __fmaf_rn(q, w, 1.0f);
+    const float lnm = __fmul_rn(__fmul_rn(2.0f, z), q);
+    const float t2 = __fmaf_rn((float)(-2 * e), 0.693147182f, __fmul_rn(-2.0f, lnm));
+    return __fsqrt_rn(t2);
+}
 
 // Per-lane register copy of the network in fragment form.
 struct MlpFrags {

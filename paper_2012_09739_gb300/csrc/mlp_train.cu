@@ -25,6 +25,12 @@ namespace mlmc {
 constexpr int TR_WARPS = 4;
 constexpr int PART_STRIDE = 1160;          // 1153 gradients + loss, padded
 constexpr int SM_LD = 40;                  // padded row length (halves) of the staging tiles
+// Gradient scale: the backward pass works on 2^6 (y - target) (dA2 and the
+// tensor-core operands derived from it stay in binary16's normal range even
+// for residuals of 1e-5; with the 1 / B factor applied first they were
+// binary16 subnormals), and the partials are multiplied by 1 / (2^6 B)
+// when written (both factors powers of two for power-of-two batches: exact).
+constexpr float GRAD_SCALE = 64.0f;
 
 struct TrainParams {
     float lr0, lr_min, beta1, beta2, eps;
@@ -118,9 +124,10 @@ __global__ void __launch_bounds__(TR_WARPS * 32) mlp_grad_kernel(const MlpWeight
             const float r0 = (y0 - tg0) * v0, r1 = (y1 - tg1) * v1;
             if (t == 0) {
                 lossp += r0 * r0 + r1 * r1;
-                gb3 += 2.0f * (r0 + r1) * inv_batch;
+                gb3 += GRAD_SCALE * 2.0f * (r0 + r1);
             }
-            const float dy0 = 2.0f * r0 * inv_batch, dy1 = 2.0f * r1 * inv_batch;
+            // scaled residual: keeps dA2 and dH1 in binary16's normal range
+            const float dy0 = GRAD_SCALE * 2.0f * r0, dy1 = GRAD_SCALE * 2.0f * r1;
             // layer 3 and tanh of layer 2
             uint32_t da[2][4];
 #pragma unroll
@@ -231,10 +238,11 @@ __global__ void __launch_bounds__(TR_WARPS * 32) mlp_grad_kernel(const MlpWeight
         r[1153] = ls;
     }
     __syncthreads();
+    const float unscale = inv_batch / GRAD_SCALE;
     for (int i = threadIdx.x; i < PART_STRIDE; i += blockDim.x) {
         float acc = 0.0f;
         for (int w = 0; w < TR_WARPS; ++w) acc += red[w][i];
-        partials[(size_t)blockIdx.x * PART_STRIDE + i] = acc;
+        partials[(size_t)blockIdx.x * PART_STRIDE + i] = i < MLP_NPARAMS ? acc * unscale : acc;
     }
 }
 

@@ -7,9 +7,11 @@ the library's FP16 tensor-core kernels, checked against the FP64 oracle.
   minibatch indices come from the same counter-based generator);
 * training on 2^20 oracle pairs beats the piecewise-linear table in
   E|Z - Z~|^2 (the quantity of Lemma 3.1);
-* inside the four-way difference: per-path agreement with the oracle, lower
-  four-way variance than the table (what the network gains), and unbiased
-  nested level means.
+* inside the four-way difference: per-path agreement with the FP64 oracle
+  within the workload's 2e-3 at l = 2, 6, 10, 12 and with the oracle's
+  binary16 emulation of the network to one binary16 ulp (most paths bit for
+  bit), lower four-way variance than the table (what the network gains), and
+  unbiased nested level means.
 """
 import math
 
@@ -56,14 +58,16 @@ def test_gradient_matches_oracle():
     g = torch.zeros(M.MLMC_MLP_PARAMS, dtype=torch.float32, device=dev)
     loss = M.mlmc_mlp_grad(ut, zt, g)
     torch.cuda.synchronize()
-    lo, go = OM.loss_and_grad(w32, OM.features(u.astype(np.float32).astype(np.float64)),
-                              z.astype(np.float32).astype(np.float64))
+    # the kernels' input map: v = min(u, 1 - u) in binary32 (exact on the grid), t from binary32 operations
+    u32 = u.astype(np.float32).astype(np.float64)
+    lo, go = OM.loss_and_grad(w32, O.mlp_feature32(np.minimum(u32, 1.0 - u32)), z.astype(np.float32).astype(np.float64))
     gg = g.cpu().numpy().astype(np.float64)
     assert abs(loss - lo) <= 1e-2 * lo
-    assert np.linalg.norm(gg - go) <= 2e-2 * np.linalg.norm(go)
+    # binary16 operands (2^-11 relative) with FP32 accumulation against FP64 backprop: 1e-2 relative
+    assert np.linalg.norm(gg - go) <= 1e-2 * np.linalg.norm(go)
     # every block of the layout, not only the largest entries
     for a, b in [(0, 32), (32, 64), (64, 1088), (1088, 1120), (1120, 1152), (1152, 1153)]:
-        assert np.linalg.norm(gg[a:b] - go[a:b]) <= 5e-2 * np.linalg.norm(go[a:b]) + 1e-6, (a, b)
+        assert np.linalg.norm(gg[a:b] - go[a:b]) <= 1e-2 * np.linalg.norm(go[a:b]) + 1e-7, (a, b)
 
 
 def test_forward_matches_oracle():
@@ -75,10 +79,20 @@ def test_forward_matches_oracle():
     z = torch.empty(u.size, dtype=torch.float32, device=dev)
     M.approx_icdf(torch.tensor(u, dtype=torch.float32, device=dev), z, M.MLMC_ICDF_MLP, M.MLMC_F32)
     torch.cuda.synchronize()
-    ref = O.approx_icdf(u, O.RV_MLP, mlp=w32)
-    err = np.abs(z.cpu().numpy() - ref)
-    # FP16 operands and tanh.approx.f16x2 against the FP64 network
-    assert err.max() < 2e-2 and err.mean() < 3e-3
+    got = z.cpu().numpy().astype(np.float64)
+    ref16 = O.approx_icdf(u, O.RV_MLP16, mlp=w32)
+    ref64 = O.approx_icdf(u, O.RV_MLP, mlp=w32)
+    # Against the binary16 inference arithmetic the one difference left is the
+    # activation: tanh.approx.f16x2 (MUFU) against tanh rounded to nearest,
+    # at most one binary16 ulp (2^-11 relative) per activation.  An h2 change
+    # moves y by |W3_j| ulp, an h1 change by sum_j |W3_j| |W2_ji| ulp.
+    W1, b1, W2, b2, W3, b3 = OM.unpack(w32)
+    bound = 2.0 ** -11 * (np.abs(W3).sum() + np.abs(W3) @ np.abs(W2).sum(axis=1)) + 1e-6
+    d16 = np.abs(got - ref16)
+    assert d16.max() <= bound, (d16.max(), bound)
+    assert d16.mean() <= 0.1 * bound
+    # and the FP64 network within the binary16 evaluation error (pinned on the oracle side)
+    assert np.abs(got - ref64).max() < 4e-3
 
 
 def _minibatch_indices(n, batch, step, seed):
@@ -105,7 +119,7 @@ def test_one_adam_step_matches_oracle():
     w1 = M.mlmc_mlp_get_weights().astype(np.float64)
     idx = _minibatch_indices(n, batch, 0, 77)
     u32, z32 = u.astype(np.float32).astype(np.float64), z.astype(np.float32).astype(np.float64)
-    _, g = OM.loss_and_grad(w0, OM.features(u32[idx]), z32[idx])
+    _, g = OM.loss_and_grad(w0, O.mlp_feature32(np.minimum(u32[idx], 1.0 - u32[idx])), z32[idx])
     expect, _, _ = OM.adam_step(w0, g, np.zeros_like(g), np.zeros_like(g), 1, lr)
     big = np.abs(g) > 0.02 * np.abs(g).max()
     assert big.sum() > 100
@@ -153,19 +167,26 @@ def test_fourway_with_mlp_paths_and_gain(trained, pl_table):
     params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
     osde = O.SDE(params.sde, params.payoff, params.p0, params.p1, params.p2, params.x0, params.T, params.K,
                  params.disc)
-    # per path: bar pair FP16 + Kahan with the MLP against the oracle's FP64
-    # network + FP64 Euler; the tolerance covers the FP16 network evaluation
-    # (FP16 operands, tanh.approx) accumulated over 2^l steps
-    l, N = 6, 2049
-    out = torch.empty(N * 5, dtype=torch.float32, device=dev)
-    M.mlmc_level_paths(1, l, N, M.MLMC_F16, True, M.MLMC_ICDF_MLP, params, SEED, 0, out)
-    torch.cuda.synchronize()
-    got = out.cpu().numpy().astype(np.float64).reshape(N, 5)
-    ref = O.fourway_paths(l, np.arange(N), O.variant(), O.variant(rv=O.RV_MLP), osde, SEED,
-                          O.make_tag(O.KIND_FOUR, l), mlp=w32)
-    scale = np.maximum(1.0, np.abs(ref[:, 0]))
-    assert np.all(np.abs(got[:, :2] - ref[:, :2]) <= 1e-5 * scale[:, None])
-    assert np.all(np.abs(got[:, 2:4] - ref[:, 2:4]) <= 5e-3 * scale[:, None])
+    # Per path, bar pair binary16 + Kahan with the network: within the
+    # workload's 2e-3 (relative to max(1, |P_f|)) of the FP64 oracle (FP64
+    # network, FP64 Euler), and within one binary16 ulp of the oracle's
+    # binary16 emulation (binary16 network and Euler), most paths bit for bit:
+    # the only arithmetic not emulated is tanh.approx's last bit.  Hat pair
+    # (FP32 + Kahan, exact normals) within 1e-5 of FP64.
+    for l, N in ((2, 4001), (6, 2049), (10, 257), (12, 97)):
+        out = torch.empty(N * 5, dtype=torch.float32, device=dev)
+        M.mlmc_level_paths(1, l, N, M.MLMC_F16, True, M.MLMC_ICDF_MLP, params, SEED, 0, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.float64).reshape(N, 5)
+        tag = O.make_tag(O.KIND_FOUR, l)
+        ref = O.fourway_paths(l, np.arange(N), O.variant(), O.variant(rv=O.RV_MLP), osde, SEED, tag, mlp=w32)
+        emu = O.fourway_paths(l, np.arange(N), O.variant(), O.variant(prec=O.F16, kahan=True, rv=O.RV_MLP16), osde,
+                              SEED, tag, mlp=w32)
+        scale = np.maximum(1.0, np.abs(ref[:, 0]))
+        assert np.all(np.abs(got[:, :2] - ref[:, :2]) <= 1e-5 * scale[:, None]), l
+        assert np.all(np.abs(got[:, 2:4] - ref[:, 2:4]) <= 2e-3 * scale[:, None]), l
+        assert np.all(np.abs(got[:, 2:4] - emu[:, 2:4]) <= 2.0 ** -10 * scale[:, None]), l
+        assert np.mean(np.all(got[:, 2:4] == emu[:, 2:4], axis=1)) >= 0.75, l
     # What the network gains.  Lemma 3.1: the four-way variance is
     # O(delta E|Z - Z~|^2) + O(delta^-1 rho^2).  With FP32 bar paths the first
     # term dominates and the network's smaller E|Z - Z~|^2 shows directly;
