@@ -187,9 +187,11 @@ mlmc_status mlmc_level_async(int four, int l, uint64_t N, int prec, int kahan, i
  * copy of the table in the same way.
  *   - N <= 2,097,152 (the scratch holds 4096 blocks); larger N, or
  *     icdf = MLP, gives MLMC_EINVAL with a message.
- *   - The first call on a device does the set-up (looks up the arrays'
- *     device addresses, builds the private table on `stream` and waits for
- *     it); make that first call before any stream capture.
+ *   - The first call on a device does the set-up (builds the private table
+ *     on `stream` and waits for it); make that first call before any stream
+ *     capture.  Every call looks the arrays' device addresses up again and
+ *     repeats the set-up if they moved (the module was loaded anew, e.g.
+ *     after a reset of the device's primary context).
  *   - All calls share the one scratch array, which keeps the last call's
  *     contents: calls that overlap on the GPU (e.g. on different streams
  *     without ordering) race and give wrong sums.

@@ -152,11 +152,14 @@ def _stream(stream):
 
 def _buf(t, name, itemsize, n, dtype=None):
     """Device pointer of t after checking that the library may read or write n
-    elements of itemsize bytes through it: a contiguous CUDA tensor (of the
-    given dtype, if any) with at least n elements."""
+    elements of itemsize bytes through it: a contiguous CUDA tensor on the
+    current device (the one the library launches on), of the given dtype if
+    any, with at least n elements."""
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device}, the library launches on cuda:{torch.cuda.current_device()}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if dtype is not None and t.dtype != dtype:

@@ -2,8 +2,9 @@
 // tiles per item, never listed one by one); one persistent launch per group
 // of items sharing estimator, working-precision variant and SDE scheme, the
 // groups running concurrently; a finalize kernel; CUDA graphs of recent
-// item-list shapes, replayed; and an autotuner for the tile size.
+// item-list shapes, replayed; and an autotuner for the tile size and block shape.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -24,6 +25,7 @@ BatchKernelFn batch_kernel_bf16_two(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_f32_four(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_f16_four(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_bf16_four(int kahan, int icdf, int sde);
+BatchKernelFn batch_kernel_mixed(int prec, int kahan, int icdf, int sde);
 
 // The batch finalize adds an item's group partials exactly as the level
 // finalize does (block_sum_fixed over at most FINALIZE_SPAN partials, or one
@@ -55,6 +57,12 @@ __global__ void __launch_bounds__(SUM_THREADS) batch_finalize_kernel(const doubl
 
 namespace {
 
+int env_int(const char *name, int dflt);
+
+// Work (pair-cost units: fine-step equivalents of a two-way pair) below
+// which a batch is latency-sized: about 50 us on GB300.
+constexpr double SMALL_BATCH_WORK = 2e7;
+
 struct Group {
     int mode, prec, kahan, icdf, sde;
     std::vector<TileSpan> spans;   // longest tiles first
@@ -74,6 +82,7 @@ struct Plan {
     uint64_t npartials = 0;              // group partials and finalize scratch, all items
     double work = 0.0;
     bool too_large = false;              // tiles or partials beyond 32-bit indices
+    int block = 256;                     // threads per block of the batch kernels (256 or 128)
 };
 
 uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
@@ -96,16 +105,22 @@ double item_work(const mlmc_work &w) { return (double)((w.N + 1) / 2) * pair_cos
 // group's spans are ordered by the cost of their tiles, longest first, so the
 // host work is per item, not per tile.  Each item owns one partial per chunk
 // group and, above FINALIZE_SPAN of them, scratch for the finalize's span sums.
-Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, int lane_work_log2) {
+Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, int lane_work_log2,
+               int block = 256) {
     Plan plan;
+    plan.block = block;
     plan.items.resize(n);
     plan.fin.assign(3 * (size_t)n, 0);
     for (int i = 0; i < n; ++i) plan.work += item_work(w[i]);
+    // a latency-sized batch puts both estimators' items of one variant into
+    // one launch where a mixed kernel exists (MLMC_BATCH_MIXED=0 disables it)
+    const bool mixed = plan.work < SMALL_BATCH_WORK && env_int("MLMC_BATCH_MIXED", 1) != 0;
     for (int i = 0; i < n; ++i) {
         plan.items[i] = make_level_args(d, w[i].kind, w[i].l, w[i].N, w[i].prec, w[i].icdf, &w[i].params, seed,
                                         w[i].path_offset, (uint32_t)w[i].set_id);
         plan.weight.push_back(plan.work > 0 ? item_work(w[i]) / plan.work : 0.0);
-        const int mode = w[i].kind, kahan = w[i].kahan ? 1 : 0, sde = plan.items[i].sde;
+        const int kahan = w[i].kahan ? 1 : 0, sde = plan.items[i].sde;
+        const int mode = mixed && batch_kernel_mixed(w[i].prec, kahan, w[i].icdf, sde) ? (int)MODE_MIXED : w[i].kind;
         size_t gi = 0;
         while (gi < plan.groups.size()) {
             const Group &g = plan.groups[gi];
@@ -171,6 +186,7 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
 }
 
 BatchKernelFn pick_batch_kernel(const Group &g) {
+    if (g.mode == MODE_MIXED) return batch_kernel_mixed(g.prec, g.kahan, g.icdf, g.sde);
     if (g.mode == MODE_TWO)
         return g.prec == MLMC_F32   ? batch_kernel_f32_two(g.kahan, g.icdf, g.sde)
                : g.prec == MLMC_F16 ? batch_kernel_f16_two(g.kahan, g.icdf, g.sde)
@@ -222,7 +238,7 @@ struct BatchCache {
     size_t sums_host_cap = 0;
     unsigned char *stage = nullptr;      // pinned staging of the descriptors
     size_t stage_cap = 0;
-    std::map<const void *, int> occupancy;   // batch kernel -> resident blocks per SM
+    std::map<std::pair<const void *, int>, int> occupancy;   // (batch kernel, block) -> resident blocks per SM
     // streams of the concurrent groups (created on first use)
     static constexpr size_t MAX_SIDE = 7;
     cudaStream_t side[MAX_SIDE] = {};
@@ -244,7 +260,7 @@ struct BatchCache {
 struct BatchGraphs {
     std::vector<BatchCache *> entries;   // at most MAX_ENTRIES, least recently used evicted
     cudaStream_t capture_stream = nullptr;
-    std::map<uint64_t, int> tuned;       // hash of the item-list shape -> lane_work_log2
+    std::map<uint64_t, std::pair<int, int>> tuned;   // hash of the item-list shape -> (lane_work_log2, block)
     uint64_t clock = 0;
     static constexpr size_t MAX_ENTRIES = 8;
 };
@@ -336,19 +352,14 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s, bool stage_idle
     return MLMC_OK;
 }
 
-int env_int(const char *name, int dflt);
-
-// Work (pair-cost units: fine-step equivalents of a two-way pair) below
-// which a batch is latency-sized: about 50 us on GB300.
-constexpr double SMALL_BATCH_WORK = 2e7;
-
-// Resident blocks per SM of a batch kernel (cached per kernel).
-int blocks_per_sm(BatchCache &c, BatchKernelFn fn) {
-    auto it = c.occupancy.find((const void *)fn);
+// Resident blocks per SM of a batch kernel at a block size (cached).
+int blocks_per_sm(BatchCache &c, BatchKernelFn fn, int block) {
+    const auto key = std::make_pair((const void *)fn, block);
+    auto it = c.occupancy.find(key);
     if (it != c.occupancy.end()) return it->second;
     int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 256, 0) != cudaSuccess || bps < 1) bps = 1;
-    c.occupancy[(const void *)fn] = bps;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, block, 0) != cudaSuccess || bps < 1) bps = 1;
+    c.occupancy[key] = bps;
     return bps;
 }
 
@@ -371,7 +382,7 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
     int bps_min = 1 << 20;
     for (size_t gi = 0; gi < ng; ++gi) {
         if (!(fns[gi] = pick_batch_kernel(p.groups[gi]))) return fail(MLMC_EINVAL, "no batch kernel for this variant");
-        bps[gi] = blocks_per_sm(c, fns[gi]);
+        bps[gi] = blocks_per_sm(c, fns[gi], p.block);
         bps_min = std::min(bps_min, bps[gi]);
     }
     // Groups one after another on s, each with the whole GPU, unless the
@@ -388,7 +399,7 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
     double seq = 0.0, ideal_sum = 0.0, tail_max = 0.0;
     for (size_t gi = 0; gi < ng; ++gi) {
         const Group &g = p.groups[gi];
-        const double ideal_g = g.work / ((double)bps[gi] * d.sm_count * 256.0);
+        const double ideal_g = g.work / ((double)bps[gi] * d.sm_count * p.block);
         const double tail_g = g.tile_cost.empty() ? 0.0 : g.tile_cost[0];
         seq += std::max(ideal_g, tail_g);
         ideal_sum += ideal_g;
@@ -412,7 +423,8 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         for (size_t k = 0; k < nside; ++k)
             if ((e = cudaStreamWaitEvent(c.side[k], c.fork, 0)) != cudaSuccess) return cuda_fail(e, "fork");
     }
-    const double ideal = p.work / ((double)bps_min * d.sm_count * 8.0);
+    const int wpb = p.block / 32;
+    const double ideal = p.work / ((double)bps_min * d.sm_count * wpb);
     for (size_t gi = 0; gi < ng; ++gi) {
         const Group &g = p.groups[gi];
         const uint64_t full = (uint64_t)bps[gi] * d.sm_count;
@@ -421,11 +433,11 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
             uint64_t long_tiles = 0;
             for (size_t k = 0; k < g.spans.size() && g.tile_cost[k] > ideal; ++k) long_tiles += g.spans[k].count;
             const uint64_t share = (uint64_t)ceil(g.work / p.work * (double)full);
-            grid = std::min(full, std::max(share, (long_tiles + 7) / 8));
+            grid = std::min(full, std::max(share, (long_tiles + wpb - 1) / wpb));
         }
-        grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, ((uint64_t)g.ntiles + 7) / 8));
+        grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, ((uint64_t)g.ntiles + wpb - 1) / wpb));
         cudaStream_t gs = gi == 0 || !concurrent ? s : c.side[(gi - 1) % BatchCache::MAX_SIDE];
-        fns[gi]<<<(unsigned)grid, 256, 0, gs>>>(c.items, c.spans + g.span_base, (uint32_t)g.spans.size(), g.ntiles,
+        fns[gi]<<<(unsigned)grid, p.block, 0, gs>>>(c.items, c.spans + g.span_base, (uint32_t)g.spans.size(), g.ntiles,
                                                  c.counters + gi, c.partials, d.tabs, p.items[0].rk);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch kernel");
     }
@@ -462,32 +474,54 @@ int work_lane_log2(const DeviceState &d, const mlmc_work *w, int n) {
     return std::min(12, std::max(4, lw));
 }
 
-// Times each candidate tile size once on the real batch and keeps the fastest.
+// Tunes a batch shape on the real batch: tile size (log2 of the fine-step
+// equivalents per lane and tile, five candidates around the work-based size
+// of about four tiles per resident lane) x block shape (256 threads, or
+// 128 -- more, smaller blocks per SM at the same register budget).  Each
+// candidate runs three times after the plan is uploaded; the median device
+// time decides (ties to the earlier candidate).  MLMC_TUNE_LOG=1 prints
+// every candidate's times and the choice on stderr.
 mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed, cudaStream_t s,
-                     int *best) {
-    // candidates around the work-based size (large batches favour longer tiles)
+                     int *best_lw, int *best_block) {
     const int base = work_lane_log2(d, w, n);
-    const int cands[] = {base - 1, base, base + 1, base + 2};
+    const int lws[] = {base - 3, base - 2, base - 1, base, base + 1};
+    const int blocks[] = {256, 128};
+    const bool log = env_int("MLMC_TUNE_LOG", 0) > 0;
     float best_ms = 1e30f;
-    *best = base;
+    *best_lw = base;
+    *best_block = 256;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     mlmc_status st = MLMC_OK;
-    for (int lw : cands) {
-        Plan p = make_plan(d, w, n, seed, lw);
-        if ((st = upload(c, p, s))) break;
-        cudaEventRecord(a, s);
-        if ((st = enqueue(d, c, p, s, false, true))) break;
-        cudaEventRecord(b, s);
-        if ((st = wait_event(b, wait_limit_s()))) break;
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, a, b);
-        if (ms < best_ms) {
-            best_ms = ms;
-            *best = lw;
+    for (int block : blocks) {
+        for (int lw : lws) {
+            Plan p = make_plan(d, w, n, seed, lw, block);
+            if ((st = upload(c, p, s))) break;
+            float t[3];
+            for (int rep = 0; rep < 3 && !st; ++rep) {
+                cudaEventRecord(a, s);
+                if ((st = enqueue(d, c, p, s, false, true))) break;
+                cudaEventRecord(b, s);
+                if ((st = wait_event(b, wait_limit_s()))) break;
+                cudaEventElapsedTime(&t[rep], a, b);
+            }
+            if (st) break;
+            std::sort(t, t + 3);
+            if (log)
+                fprintf(stderr, "{\"mlmc_tune\": {\"items\": %d, \"lane_work_log2\": %d, \"block\": %d, "
+                                "\"ms\": [%.4f, %.4f, %.4f]}}\n", n, lw, block, t[0], t[1], t[2]);
+            if (t[1] < best_ms) {
+                best_ms = t[1];
+                *best_lw = lw;
+                *best_block = block;
+            }
         }
+        if (st) break;
     }
+    if (log && !st)
+        fprintf(stderr, "{\"mlmc_tune_choice\": {\"items\": %d, \"lane_work_log2\": %d, \"block\": %d, "
+                        "\"median_ms\": %.4f}}\n", n, *best_lw, *best_block, best_ms);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     return st;
@@ -559,19 +593,20 @@ mlmc_status build_entry(DeviceState &d, BatchGraphs &G, BatchCache &c, const mlm
     cudaEventRecord(ev, s);
     cudaStreamWaitEvent(G.capture_stream, ev, 0);
     cudaEventDestroy(ev);
-    int lw = env_int("MLMC_BATCH_LANE_WORK_LOG2", 0);
+    int lw = env_int("MLMC_BATCH_LANE_WORK_LOG2", 0), block = 256;
     if (lw < 6 || lw > 20) {
         auto it = G.tuned.find(shape_hash);
         if (it != G.tuned.end()) {
-            lw = it->second;
+            lw = it->second.first;
+            block = it->second.second;
         } else if (env_int("MLMC_AUTOTUNE", 1)) {
-            if ((st = autotune(d, c, items, n_items, seed, G.capture_stream, &lw))) return st;
-            G.tuned[shape_hash] = lw;
+            if ((st = autotune(d, c, items, n_items, seed, G.capture_stream, &lw, &block))) return st;
+            G.tuned[shape_hash] = std::make_pair(lw, block);
         } else {
             lw = 12;
         }
     }
-    Plan p = make_plan(d, items, n_items, seed, lw);
+    Plan p = make_plan(d, items, n_items, seed, lw, block);
     if ((st = upload(c, p, G.capture_stream))) return st;
     // the graph is launched on the caller's stream: the descriptors must have landed
     if ((e = cudaStreamSynchronize(G.capture_stream)) != cudaSuccess) return cuda_fail(e, "upload");

@@ -124,11 +124,60 @@ __device__ void simulate_pair_seq(const LevelArgs &a, const PhiloxKeys &K, const
     pair_result<MODE>(a, fine, coarse, hfine, hcoarse, d0, d1, out0, out1);
 }
 
+// One warp tile t of span sp: its chunk groups (the last one of the item may
+// be short), each accumulated and summed as the level kernel does, one FP64
+// partial per group; a single deep pair warp-cooperatively.
+template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
+__device__ __forceinline__ void run_tile(const LevelArgs &a, const PhiloxKeys &keys, const SmemTable &tab,
+                                         const MlpFrags &mlp, const TileSpan &sp, uint32_t t, uint32_t lane,
+                                         double2 *partials, SeqScratch<P> &seq) {
+    const uint64_t first = (uint64_t)(t - sp.begin) * sp.per_tile;
+    const uint32_t npairs = a.npairs - first < sp.per_tile ? (uint32_t)(a.npairs - first) : sp.per_tile;
+    const uint64_t chunk0 = first >> 5;        // the tile's first chunk, the start of a group
+    KahanF32 s1, s2;
+    if (npairs == 1 && a.l >= SEQ_MIN_LEVEL) {
+        // one pair, long paths: the warp generates the normals, lane 0 steps
+        float d0, d1;
+        simulate_pair_seq<MODE, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, first, d0, d1, seq);
+        if (lane == 0) {
+            s1.add(d0);
+            s2.add(d0 * d0);
+            if (2 * first + 1 < a.N) {
+                s1.add(d1);
+                s2.add(d1 * d1);
+            }
+            partials[sp.part + chunk0 / sp.group] = make_double2((double)s1.value(), (double)s2.value());
+        }
+        return;
+    }
+    const uint32_t rounds = (npairs + 31u) >> 5;
+    uint32_t grp = sp.part + (uint32_t)chunk0 / sp.group;    // chunks < 2^31 (N < 2^37)
+    for (uint32_t r = 0; r < rounds; ++grp) {
+        const uint32_t r1 = r + sp.group < rounds ? r + sp.group : rounds;
+        for (; r < r1; ++r) {
+            const uint32_t k = (r << 5) + lane;
+            const bool active = k < npairs;
+            run_slot<MODE, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, first + (active ? k : npairs - 1), active, s1, s2);
+        }
+        const float w1 = warp_sum(s1.value()), w2 = warp_sum(s2.value());
+        if (lane == 0) partials[grp] = make_double2((double)w1, (double)w2);
+        s1 = KahanF32();
+        s2 = KahanF32();
+    }
+}
+
+// MODE_MIXED: one kernel for the two-way and four-way items of one variant
+// (each tile dispatched on its item's mode), for latency-sized batches such
+// as the rounds of an adaptive run at large RMSE, where one launch instead of
+// two matters more than the four-way register budget the two-way tiles then
+// run at.  Accumulation as in the single-mode kernels, so sums are the same.
+enum { MODE_MIXED = 2 };
+
 // One kernel per (MODE, P, KAHAN, ICDF, SDE), like the level kernels and with
 // their register budgets, so that a batch runs at the level kernels'
 // occupancy; the host launches one per group of items that share them.
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 2 : (MODE == MODE_FOUR ? 3 : 4))
+__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 2 : (MODE == MODE_TWO ? 4 : 3))
 batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uint32_t ntiles, uint32_t *counter,
              double2 *partials, const DevTables *tabs, const PhiloxKeys keys) {
     __shared__ SmemTable tab;
@@ -147,40 +196,13 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
         // every item has the batch's seed: its round keys come from the
         // launch parameters
         const LevelArgs a = items[sp.item];
-        const uint64_t first = (uint64_t)(t - sp.begin) * sp.per_tile;
-        const uint32_t npairs = a.npairs - first < sp.per_tile ? (uint32_t)(a.npairs - first) : sp.per_tile;
-        const uint64_t chunk0 = first >> 5;        // the tile's first chunk, the start of a group
-        KahanF32 s1, s2;
-        if (npairs == 1 && a.l >= SEQ_MIN_LEVEL) {
-            // one pair, long paths: the warp generates the normals, lane 0 steps
-            float d0, d1;
-            simulate_pair_seq<MODE, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, first, d0, d1, seq[threadIdx.x >> 5]);
-            if (lane == 0) {
-                s1.add(d0);
-                s2.add(d0 * d0);
-                if (2 * first + 1 < a.N) {
-                    s1.add(d1);
-                    s2.add(d1 * d1);
-                }
-                partials[sp.part + chunk0 / sp.group] = make_double2((double)s1.value(), (double)s2.value());
-            }
-            continue;
-        }
-        const uint32_t rounds = (npairs + 31u) >> 5;
-        uint32_t grp = sp.part + (uint32_t)chunk0 / sp.group;    // chunks < 2^31 (N < 2^37)
-        // the tile's chunk groups (the last one of the item may be short),
-        // each accumulated and summed as the level kernel does
-        for (uint32_t r = 0; r < rounds; ++grp) {
-            const uint32_t r1 = r + sp.group < rounds ? r + sp.group : rounds;
-            for (; r < r1; ++r) {
-                const uint32_t k = (r << 5) + lane;
-                const bool active = k < npairs;
-                run_slot<MODE, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, first + (active ? k : npairs - 1), active, s1, s2);
-            }
-            const float w1 = warp_sum(s1.value()), w2 = warp_sum(s2.value());
-            if (lane == 0) partials[grp] = make_double2((double)w1, (double)w2);
-            s1 = KahanF32();
-            s2 = KahanF32();
+        if constexpr (MODE == MODE_MIXED) {
+            if (a.mode == MODE_FOUR)
+                run_tile<MODE_FOUR, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq[threadIdx.x >> 5]);
+            else
+                run_tile<MODE_TWO, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq[threadIdx.x >> 5]);
+        } else {
+            run_tile<MODE, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq[threadIdx.x >> 5]);
         }
     }
 }

@@ -38,18 +38,27 @@ struct NoallocState {
 static std::mutex g_noalloc_mu;
 static NoallocState g_noalloc[MAX_DEVICES];
 
-// First call on a device: resolve the symbol addresses, build the table into
-// the private arrays on `s`, and wait for it.  Must happen before any stream
-// capture that includes this entry point.
+// Every call looks the array addresses up again (no allocation, a table
+// lookup in the runtime): if the module was loaded anew since the last call
+// on this device -- after a reset of the device's primary context, say --
+// the arrays have moved and hold no table, so the private table is built
+// again.  A (re)build runs on `s` and waits for it, so the first call on a
+// device should come before any stream capture that includes this entry
+// point.
 static mlmc_status noalloc_setup(int dev, cudaStream_t s, NoallocState **out) {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     NoallocState &st = g_noalloc[dev];
-    if (!st.ready) {
-        cudaError_t e;
-        if ((e = cudaGetSymbolAddress((void **)&st.partials, g_noalloc_partials)) != cudaSuccess)
-            return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-        if ((e = cudaGetSymbolAddress((void **)&st.tabs, g_noalloc_tabs)) != cudaSuccess)
-            return cuda_fail(e, "cudaGetSymbolAddress(table)");
+    cudaError_t e;
+    double2 *partials = nullptr;
+    DevTables *tabs = nullptr;
+    if ((e = cudaGetSymbolAddress((void **)&partials, g_noalloc_partials)) != cudaSuccess)
+        return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    if ((e = cudaGetSymbolAddress((void **)&tabs, g_noalloc_tabs)) != cudaSuccess)
+        return cuda_fail(e, "cudaGetSymbolAddress(table)");
+    if (!st.ready || partials != st.partials || tabs != st.tabs) {
+        st.ready = false;
+        st.partials = partials;
+        st.tabs = tabs;
         if ((e = launch_build_table(st.tabs, s)) != cudaSuccess)
             return cuda_fail(e, "build_table");
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "build_table");

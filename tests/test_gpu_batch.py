@@ -266,3 +266,27 @@ def test_batch_graph_replay_uses_current_mlp_weights():
     for it, g in zip(items, second):
         fn = M.mlmc_nested_level if it.kind else M.mlmc_level
         _same(g, fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED, it.path_offset))
+
+
+@pytest.mark.parametrize("prec,kahan,icdf", [(M.MLMC_F16, 1, M.MLMC_ICDF_TABLE), (M.MLMC_F32, 0, M.MLMC_ICDF_TABLE16),
+                                             (M.MLMC_F16, 0, M.MLMC_ICDF_TABLE16)])
+def test_small_mixed_batch_matches_level_kernels(prec, kahan, icdf, monkeypatch):
+    """A latency-sized batch with both estimators' items of one variant (an
+    adaptive round at large RMSE) runs as one mixed-mode launch; its sums
+    equal the level kernels' bit for bit, and the same batch split into two
+    launches (MLMC_BATCH_MIXED=0) gives the same sums.  Ragged N, odd path
+    offsets (two Philox calls per coarse unit) and levels 0..5."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    items = []
+    for l in range(6):
+        for kind in (0, 1):
+            items.append(M.mlmc_work(p, l, kind, prec, kahan, icdf, 0, 1000 + 37 * l + 11 * kind, 3 * l + kind))
+    mixed = M.mlmc_batch(items, SEED)
+    monkeypatch.setenv("MLMC_BATCH_MIXED", "0")
+    split = M.mlmc_batch(items, SEED + 1)      # another seed: a new graph, captured without mixing
+    for it, a, b in zip(items, mixed, split):
+        fn = M.mlmc_nested_level if it.kind else M.mlmc_level
+        _same(a, fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED, it.path_offset))
+        _same(b, fn(it.l, it.N, it.prec, it.kahan, it.icdf, it.params, SEED + 1, it.path_offset))

@@ -65,3 +65,45 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         M.mlmc_level_noalloc(0, 3, (1 << 21) + 1, M.MLMC_F32, False, M.MLMC_ICDF_TABLE, params, 1, 0, out)
     assert e.value.status == M.MLMC_EINVAL
     assert "scratch" in str(e.value)
+
+
+def test_noalloc_at_the_scratch_boundary():
+    """N = 2^21 fills all 4096 block slots of the fixed scratch (one sample
+    pair per thread, 256 threads per block); 2^21 - 1 leaves the last pair
+    half full.  Both against the allocating entry point, on the same
+    samples, and a level-0 call (4 samples per lane slot) inside the bound."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda:0")
+    params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    for four, l, N, prec, kahan, icdf in ((0, 3, 1 << 21, M.MLMC_F16, True, M.MLMC_ICDF_TABLE),
+                                         (1, 2, (1 << 21) - 1, M.MLMC_F32, False, M.MLMC_ICDF_TABLE),
+                                         (0, 0, 1 << 21, M.MLMC_F32, False, M.MLMC_ICDF_EXACT)):
+        got = torch.zeros(2, dtype=torch.float64, device=dev)
+        ref = torch.zeros(2, dtype=torch.float64, device=dev)
+        M.mlmc_level_noalloc(four, l, N, prec, kahan, icdf, params, 99, 0, got)
+        M.mlmc_level_async(four, l, N, prec, kahan, icdf, params, 99, 0, ref)
+        torch.cuda.synchronize()
+        _close(got.cpu().tolist(), ref.cpu().tolist(), N)
+
+
+def test_noalloc_sums_match_the_oracle():
+    """The allocation-free call's sums against the oracle's level sums on the
+    same samples (binary16 + Kahan paths are bit-exact per sample; the sums
+    differ by the FP32 per-lane accumulation only)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    from oracle import table
+    params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+    osde = O.SDE(params.sde, params.payoff, params.p0, params.p1, params.p2, params.x0, params.T, params.K,
+                 params.disc)
+    N, l = 20000, 5
+    got = torch.zeros(2, dtype=torch.float64, device="cuda:0")
+    M.mlmc_level_noalloc(0, l, N, M.MLMC_F16, True, M.MLMC_ICDF_TABLE, params, 1234, 0, got)
+    torch.cuda.synchronize()
+    s1, s2 = got.cpu().tolist()
+    o1, o2 = O.level_sums(l, N, 0, O.variant(prec=O.F16, kahan=True, rv=O.RV_TABLE), osde, 1234,
+                          O.make_tag(O.KIND_APPROX, l), table=table.build_table(), nthreads=4)
+    assert abs(s1 - o1) <= 1e-6 * (abs(o1) + math.sqrt(o2))
+    assert abs(s2 - o2) <= 1e-6 * o2
