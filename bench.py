@@ -52,12 +52,12 @@ WORKLOAD = "GBM call, levels 0..12, N=2^20 per level, two-way + four-way, FP16+K
 #   four-way only: hat fine + coarse Euler + Kahan in FP32       12.5
 OPS_FOURWAY_F16K_TABLE = 50.75
 OPS_TWOWAY_F16K_TABLE = 24.25
-# DRAM bytes (read + write) of one four-way batched launch over levels 0..12
-# at N = 2^20, from an ncu capture of that launch (dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass): the descriptors and the table, 0.20 to
-# 0.49 MB over the launches captured, no writes (the group partials stay in
-# L2).  The traffic does not grow with the path-steps.
-TRAFFIC_FOURWAY_BYTES = 494080
+# DRAM bytes (read + write) of the timed four-way batched launch over levels
+# 0..12 at N = 2^20, from an ncu capture of the bench command
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass): the descriptors
+# and the tables, 0.16 to 0.66 MB over the launches captured, no writes (the
+# group partials stay in L2).  The traffic does not grow with the path-steps.
+TRAFFIC_FOURWAY_BYTES = 493312
 
 
 def _env_rank():
@@ -353,8 +353,8 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "kernel": "batch_kernel<FOUR,F16,kahan,TABLE,GBM> (levels 0..12)",
                      "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
                      "traffic": TRAFFIC_FOURWAY_BYTES,
-                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch "
-                                      "(the larger of two captured); independent of the path-steps",
+                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the timed full-size "
+                                      "launch of the bench command; independent of the path-steps",
                      "ops_per_path_step": OPS_FOURWAY_F16K_TABLE,
                      "peak_basis": f"{sm_count} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock sampled)",
                      "launches": args.steps},
@@ -495,6 +495,18 @@ def time_to_eps(M, params, eps_list, repeats=5, with_mlp=False):
         row["speedup_milstein_f16_kahan_table16_vs_plain_milstein"] = (
             row["plain_fp32_exact_milstein"]["seconds"] / row["nested_f16_kahan_table16_milstein"]["seconds"])
         out[f"{eps:g}"] = row
+    # the per-level efficiency map (Sec. 3, Fig. 4): every candidate measured on every level
+    if 1e-5 in eps_list:
+        o = M.mlmc_run_opts(estimator=1, prec=-1, kahan=0, icdf=T16, max_level=18, min_levels=3, n0=10000,
+                            seed=999, alpha=1.0, timeout_s=600.0, trial_all=1)
+        r = M.mlmc_run(1e-5, params, o)
+        out["efficiency_map_1e-05_table16"] = {
+            "prec_per_level": ["f16" if r.prec[l] == M.MLMC_F16 else "f32" for l in range(r.levels)],
+            "kahan_per_level": [int(r.kahan[l]) for l in range(r.levels)],
+            "nested_per_level": [int(r.nested[l]) for l in range(r.levels)],
+            "efficiency_per_level": [round(r.efficiency[l], 3) for l in range(r.levels)],
+            "note": "trial_all: all candidates measured on every level; efficiency (v c / v^ c^)(1 + sqrt(V C / v c))^2 "
+                    "against the standard FP32 exact term (< 1: the nested pair saves at that level)"}
     return out
 
 

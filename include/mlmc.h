@@ -247,6 +247,19 @@ mlmc_status mlmc_icdf_cubic(double *d_host, float *d32_host, uint16_t *d16_host,
 mlmc_status mlmc_mlp_set_weights(const float *w_host, size_t n);
 mlmc_status mlmc_mlp_get_weights(float *w_host, size_t n);
 
+/* The network tabulated on the 24-bit uniform grid (a design of this
+ * library; the network itself is not the paper's): the input v = min(u, 1-u)
+ * takes the 2^22 values v_k = (2k + 1) 2^-24, and whenever the weights are
+ * set or trained the library evaluates the network on all of them with its
+ * tensor-core inference (binary16 operands, FP32 accumulation, the
+ * input map of mlmc_mlp_grad) into a 16 MiB device table.  The level and
+ * batch kernels take Z~ = -y_k for u <= 1/2, +y_k above from that table: the
+ * same value the inference gives for the sample.  y_host receives the 2^22
+ * values y_k in k order (n must be 2^22); MLMC_ENOTREADY before weights are
+ * set.  approx_icdf with MLP evaluates the network directly (any u). */
+#define MLMC_MLP_GRID (1u << 22)
+mlmc_status mlmc_mlp_grid_table(float *y_host, size_t n);
+
 typedef struct {
     uint64_t steps;       /* Adam steps */
     uint32_t batch;       /* samples per step (multiple of 128) */

@@ -24,6 +24,7 @@ MLMC_PAYOFF_X, MLMC_PAYOFF_CALL = 0, 1
 MLMC_F32, MLMC_F16, MLMC_BF16 = 0, 1, 2
 MLMC_ICDF_EXACT, MLMC_ICDF_TABLE, MLMC_ICDF_MLP, MLMC_ICDF_TABLE16, MLMC_ICDF_CUBIC = 0, 1, 2, 3, 4
 MLMC_MLP_PARAMS = 1153
+MLMC_MLP_GRID = 1 << 22
 MLMC_MAX_LEVELS = 19
 
 
@@ -100,6 +101,7 @@ _SIGS = {
     "mlmc_icdf_cubic": [_vp, _vp, _vp, _vp],
     "mlmc_mlp_set_weights": [_vp, ctypes.c_size_t],
     "mlmc_mlp_get_weights": [_vp, ctypes.c_size_t],
+    "mlmc_mlp_grid_table": [_vp, ctypes.c_size_t],
     "mlmc_mlp_grad": [_vp, _vp, ctypes.c_size_t, _vp, _vp, _vp],
     "mlmc_mlp_train": [_vp, _vp, ctypes.c_size_t, _P(mlmc_train_opts), _vp, _vp],
     "mlmc_batch": [_P(mlmc_work), _i32, _u64, _P(mlmc_sums), _vp],
@@ -275,6 +277,14 @@ def mlmc_mlp_get_weights():
     w = np.zeros(MLMC_MLP_PARAMS, np.float32)
     _check(load().mlmc_mlp_get_weights(w.ctypes.data_as(_vp), w.size))
     return w
+
+
+def mlmc_mlp_grid_table():
+    """The network's y on the 2^22 grid points v_k = (2k + 1) 2^-24, as tabulated on the device."""
+    import numpy as np
+    y = np.zeros(1 << 22, np.float32)
+    _check(load().mlmc_mlp_grid_table(y.ctypes.data_as(_vp), y.size))
+    return y
 
 
 def mlmc_mlp_grad(u_dev, z_dev, grad_dev, stream=None) -> float:

@@ -63,7 +63,7 @@ struct SeqScratch {
 };
 
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__device__ void simulate_pair_seq(const LevelArgs &a, const PhiloxKeys &K, const SmemTable &tab, const MlpFrags &mlp,
+__device__ void simulate_pair_seq(const LevelArgs &a, const PhiloxKeys &K, const SmemTable &tab, const float *mlp,
                                   uint64_t g, float &d0, float &d1, SeqScratch<P> &sc) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nf = 1u << a.l;
@@ -129,7 +129,7 @@ __device__ void simulate_pair_seq(const LevelArgs &a, const PhiloxKeys &K, const
 // partial per group; a single deep pair warp-cooperatively.
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
 __device__ __forceinline__ void run_tile(const LevelArgs &a, const PhiloxKeys &keys, const SmemTable &tab,
-                                         const MlpFrags &mlp, const TileSpan &sp, uint32_t t, uint32_t lane,
+                                         const float *mlp, const TileSpan &sp, uint32_t t, uint32_t lane,
                                          double2 *partials, SeqScratch<P> &seq) {
     const uint64_t first = (uint64_t)(t - sp.begin) * sp.per_tile;
     const uint32_t npairs = a.npairs - first < sp.per_tile ? (uint32_t)(a.npairs - first) : sp.per_tile;
@@ -177,15 +177,14 @@ enum { MODE_MIXED = 2 };
 // their register budgets, so that a batch runs at the level kernels'
 // occupancy; the host launches one per group of items that share them.
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 2 : (MODE == MODE_TWO ? 4 : 3))
+__global__ void __launch_bounds__(256, MODE == MODE_TWO ? 4 : 3)
 batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uint32_t ntiles, uint32_t *counter,
              double2 *partials, const DevTables *tabs, const PhiloxKeys keys) {
     __shared__ SmemTable tab;
     __shared__ SeqScratch<P> seq[8];           // one per warp (warp-cooperative single pairs)
     stage_table(tab, tabs);
     __syncthreads();
-    MlpFrags mlp;
-    if (ICDF == ICDF_MLP) mlp.load(items[0].mlp);
+    const float *mlp = ICDF == ICDF_MLP ? items[0].mlp->ygrid : nullptr;
     const uint32_t lane = threadIdx.x & 31;
     for (;;) {
         uint32_t t = 0;

@@ -101,14 +101,15 @@ const CostRow kCost[] = {
 
 // The row of a term, or the nearest measured one: bfloat16 as binary16 (the
 // same packed arithmetic), the other Kahan setting, the Euler row for a
-// Milstein term; the network (MLP) as its table row times the measured cost
-// ratio of its inverse CDF.
+// Milstein term; the network (MLP, a gather from its tabulated grid values)
+// as its table row times the measured ratio (binary16 + Kahan at l = 10 and
+// 12: four-way 1.73, two-way 3.2).
 double cost_ps(int four, int prec, int kahan, int icdf, int milstein, int l) {
     double factor = 1.0;
     if (prec == MLMC_BF16) prec = MLMC_F16;
     if (icdf == MLMC_ICDF_MLP) {
         icdf = MLMC_ICDF_TABLE;
-        factor = four ? 4.3 : 6.5;
+        factor = four ? 1.73 : 3.2;
     }
     const CostRow *row = nullptr;
     for (int pass = 0; pass < 4 && !row; ++pass) {

@@ -13,7 +13,7 @@
 #pragma once
 
 #include "device.cuh"
-#include "mlp_tc.cuh"
+#include "mlp_device.cuh"
 
 namespace mlmc {
 
@@ -120,7 +120,7 @@ __device__ __forceinline__ Pair<P> table_pair(const SmemTable &s, uint32_t w0, u
 // that holds each word's 24-bit uniform, i.e. at the 16-bit uniform of the
 // word's top half (u24 = (2 (w >> 9) + 1) 2^-24 lies in cell w >> 16).
 template <int P, int ICDF>
-__device__ __forceinline__ Pair<P> icdf_pair(const SmemTable &s, const MlpFrags &mlp, uint32_t w0, uint32_t w1) {
+__device__ __forceinline__ Pair<P> icdf_pair(const SmemTable &s, const float *mlp, uint32_t w0, uint32_t w1) {
     if constexpr (ICDF == ICDF_EXACT) {
         return Pair<P>::of2(exact_z(s, w0), exact_z(s, w1));
     } else if constexpr (ICDF == ICDF_TABLE) {
@@ -138,8 +138,8 @@ __device__ __forceinline__ Pair<P> icdf_pair(const SmemTable &s, const MlpFrags 
         const uint32_t f0 = half16_bits<true>(w0), f1 = half16_bits<true>(w1);
         return table_pair<P, true>(s, f0, f1, mirrored_v16(f0), mirrored_v16(f1));
     } else {
-        const float2 z = mlp_z_warp(mlp, w0, w1);      // all 32 lanes together
-        return Pair<P>::of2(z.x, z.y);
+        // the network on the 24-bit grid, tabulated (mlp = MlpWeights::ygrid)
+        return Pair<P>::of2(mlp_grid_z(mlp, w0), mlp_grid_z(mlp, w1));
     }
 }
 
@@ -195,7 +195,7 @@ __device__ __forceinline__ void pair_result(const LevelArgs &a, const PP &fine, 
 // (P_f, P_c, D) or (P^_f, P^_c, P-_f, P-_c, D).
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
 __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const PhiloxKeys &K, const SmemTable &tab,
-                                              const MlpFrags &mlp, uint64_t g, float &d0, float &d1, float *out0,
+                                              const float *mlp, uint64_t g, float &d0, float &d1, float *out0,
                                               float *out1) {
     const uint32_t nf = 1u << a.l;
     const uint32_t ncalls = (nf + 3u) >> 2;
@@ -307,7 +307,7 @@ __host__ __device__ __forceinline__ int unit_pairs(int mode, int icdf, int l) {
 // in order.
 template <int B, int L, bool ALIGNED, int P, bool KAHAN, int ICDF, int SDE, class Emit>
 __device__ __forceinline__ void simulate_unit(const LevelArgs &a, const PhiloxKeys &K, const SmemTable &tab,
-                                              const MlpFrags &mlp, uint64_t u, Emit &&emit) {
+                                              const float *mlp, uint64_t u, Emit &&emit) {
     constexpr uint32_t S = 2 * B;
     constexpr bool U16 = ICDF == ICDF_TABLE16;
     static_assert(L == 0 || U16, "level-1 units use 16-bit uniforms");
@@ -364,7 +364,7 @@ __device__ __forceinline__ void simulate_unit(const LevelArgs &a, const PhiloxKe
 // accumulate identically.
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
 __device__ __forceinline__ void run_slot(const LevelArgs &a, const PhiloxKeys &K, const SmemTable &tab,
-                                         const MlpFrags &mlp, uint64_t g, bool active, KahanF32 &k1, KahanF32 &k2) {
+                                         const float *mlp, uint64_t g, bool active, KahanF32 &k1, KahanF32 &k2) {
     if (MODE == MODE_TWO && a.unit > 1) {
         const uint64_t first = (uint64_t)(2 * a.unit) * g;        // sample index of the unit's first path
         auto emit = [&](int i, float pf, float pc, float d) {
@@ -455,20 +455,17 @@ __host__ __device__ __forceinline__ uint32_t chunk_group(int l, uint64_t chunks)
 // Register budget: two-way kernels fit 64 registers (4 blocks of 256 per
 // SM); four-way kernels carry four paths per sample and get 80 (3 blocks),
 // which removes their spills (measured 8 % faster on GB300 than 64 registers
-// with spills); the MLP kernels hold the network's fragments and get 128 (2
-// blocks): they spill 120-170 bytes per thread to L1 but run 18 % faster than
-// with one block at 199 registers, the second block hiding the tensor-core
-// and MUFU latencies.
+// with spills).  The network's normals come from its tabulated grid values,
+// so the MLP kernels have the same budgets.
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__global__ void __launch_bounds__(256, ICDF == ICDF_MLP ? 2 : (MODE == MODE_FOUR ? 3 : 4)) level_kernel(const LevelArgs a) {
+__global__ void __launch_bounds__(256, MODE == MODE_FOUR ? 3 : 4) level_kernel(const LevelArgs a) {
     __shared__ SmemTable tab;
     __shared__ double red[2][32];
     if (ICDF != ICDF_MLP || MODE == MODE_FOUR) {
         stage_table(tab, a.tabs);
         __syncthreads();
     }
-    MlpFrags mlp;
-    if (ICDF == ICDF_MLP) mlp.load(a.mlp);
+    const float *mlp = ICDF == ICDF_MLP ? a.mlp->ygrid : nullptr;
     KahanF32 k1, k2;
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);

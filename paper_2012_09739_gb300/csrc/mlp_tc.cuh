@@ -37,11 +37,12 @@ __device__ __forceinline__ float2 unpack_h2(uint32_t x) {
     return __half22float2(*reinterpret_cast<__half2 *>(&x));
 }
 
-// D = A B + C, m16n8k16, f16 x f16 -> f32.
+// D = A B + C, m16n8k16, f16 x f16 -> f32 (not volatile: the outputs are
+// used, and the compiler may interleave independent tiles).
 __device__ __forceinline__ void mma16816(float &d0, float &d1, float &d2, float &d3, uint32_t a0, uint32_t a1,
                                          uint32_t a2, uint32_t a3, uint32_t b0, uint32_t b1, float c0, float c1,
                                          float c2, float c3) {
-    asm volatile(
+    asm(
         "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%10,%11,%12,%13};"
         : "=f"(d0), "=f"(d1), "=f"(d2), "=f"(d3)

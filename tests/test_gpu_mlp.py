@@ -95,6 +95,32 @@ def test_forward_matches_oracle():
     assert np.abs(got - ref64).max() < 4e-3
 
 
+def test_grid_table_equals_direct_evaluation():
+    """The level kernels take the network's normals from its values on the
+    2^22 grid points v_k = (2k + 1) 2^-24 of v = min(u, 1 - u), tabulated
+    when the weights change.  The table must equal the network evaluated
+    directly (approx_icdf, the same tensor-core inference) at every grid
+    point, bit for bit -- after setting weights and after one training step."""
+    dev = _dev()
+    k = np.arange(1 << 22, dtype=np.float64)
+    u = (2.0 * k + 1.0) * 2.0 ** -24
+    ut = torch.tensor(u, dtype=torch.float32, device=dev)
+    for step in range(2):
+        if step == 0:
+            M.mlmc_mlp_set_weights(_perturbed_weights(5))
+        else:
+            uu, zz = _pairs(8192, 3)
+            opts = M.mlmc_train_opts(steps=1, batch=4096, lr0=1e-3, lr_min=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                                     seed=5)
+            M.mlmc_mlp_train(torch.tensor(uu, dtype=torch.float32, device=dev),
+                             torch.tensor(zz, dtype=torch.float32, device=dev), opts)
+        z = torch.empty(u.size, dtype=torch.float32, device=dev)
+        M.approx_icdf(ut, z, M.MLMC_ICDF_MLP, M.MLMC_F32)
+        torch.cuda.synchronize()
+        y = M.mlmc_mlp_grid_table()
+        assert np.array_equal(-z.cpu().numpy(), y), step      # u_k <= 1/2: Z~ = -y
+
+
 def _minibatch_indices(n, batch, step, seed):
     ctr = np.zeros((batch, 4), dtype=np.uint32)
     ctr[:, 0] = np.arange(batch, dtype=np.uint32)
