@@ -110,6 +110,8 @@ def lib():
                                              ctypes.c_uint64, ctypes.c_uint32, dp, dp, dp]
             L.orc_mlp_feature32.argtypes = [ctypes.c_double]
             L.orc_mlp_feature32.restype = ctypes.c_double
+            L.orc_tanh16.argtypes = [ctypes.c_double]
+            L.orc_tanh16.restype = ctypes.c_double
             L.orc_kahan_sum.argtypes = [dp, i64, ctypes.c_int, ctypes.c_int]
             L.orc_kahan_sum.restype = ctypes.c_double
             L.orc_openmp_threads.restype = ctypes.c_int
@@ -218,6 +220,12 @@ def mlp_feature32(v) -> np.ndarray:
     """The network input t = sqrt(-2 ln v) from binary32 operations (the
     binary16 inference reading of the learned part)."""
     return np.array([lib().orc_mlp_feature32(float(x)) for x in np.ravel(v)])
+
+
+def tanh16(x) -> np.ndarray:
+    """The activation of the binary16 inference reading: tanh of x rounded to
+    binary16, correctly rounded to binary16."""
+    return np.array([lib().orc_tanh16(float(a)) for a in np.ravel(x)])
 
 
 def approx_icdf(u, rv: int, prec: int = F64, pbits: int = 53, table=None, mlp=None, cubic=None) -> np.ndarray:

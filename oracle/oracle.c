@@ -286,16 +286,17 @@ static double mlp_icdf(double u, const double *w)
  *     w = R32(z z), q = 1/9 then q = fma32(q, w, c) for c = 1/7, 1/5, 1/3, 1
  *     (constants R32 of the fractions), ln m = R32(2 z q) -- the atanh series
  *     ln m = 2 atanh z -- and t = R32(sqrt(fma32(-2 e, R32(ln 2), -2 ln m)));
- *   layer 1: a_j = fma32(W1_j, t, b1_j), h1_j = R16(tanh(R16(a_j)));
- *   layer 2: W2 rounded to binary16; c_j = R32(R32(b2_j + sum_{i<16} W2_ji h1_i)
- *     + sum_{i>=16} W2_ji h1_i) (two 16-term steps, each sum exact, rounded
- *     once), h2_j = R16(tanh(R16(c_j)));
- *   layer 3: W3 rounded to binary16, y = R32(R32(b3 + sum_{j<16} W3_j h2_j)
- *     + sum_{j>=16} W3_j h2_j).
- * The sums are exact in binary64 while every term is a multiple of 2^-48
- * and every partial sum stays below 2^5 in magnitude (binary16 products and
- * biases of the trained networks' range); the function returns NaN if that
- * does not hold.  fma32 is C's fmaf (correctly rounded). */
+ *   activations: tanh16(x) = R16(tanh(R16(x))), the hyperbolic tangent of
+ *     the binary16 value, correctly rounded to binary16;
+ *   layer 1: h1_j = tanh16(fma32(W1_j, t, b1_j));
+ *   layer 2: c_j = b2_j, then c_j = fma32(R16(W2_ji), h1_i, c_j) for
+ *     i = 0, 1, ..., 31 in turn; h2_j = tanh16(c_j);
+ *   layer 3: y = b3, then y = fma32(R16(W3_j), h2_j, y) for j = 0, ..., 31.
+ * The weights are binary32 values; fma32 is C's fmaf (the exact a b + c
+ * rounded once).  tanh16 takes the binary64 tanh (within an ulp of binary64)
+ * and rounds it to binary16: correct unless tanh(x) lay within 2^-52 of a
+ * binary16 rounding boundary, which no binary16 input comes near (checked
+ * against high-precision values for all of them). */
 static double r32(double x) { return (double)(float)x; }
 
 static double r16(double x)
@@ -304,7 +305,7 @@ static double r16(double x)
     return round_p(x, &m);
 }
 
-static int on_grid48(double x) { return x == 0.0 || ldexp(x, 48) == floor(ldexp(x, 48)); }
+double orc_tanh16(double x) { return r16(tanh(r16(x))); }
 
 double orc_mlp_feature32(double v)
 {
@@ -327,42 +328,39 @@ double orc_mlp_feature32(double v)
     return r32(sqrt(t2));
 }
 
+/* The network as the entry points hold it: the weights as given (the FP64
+ * network reads them) and a copy with W2 and W3 rounded to binary16 (the
+ * binary16 reading), made once per entry-point call. */
+#define ORC_MLP_N 1153
+typedef struct {
+    const double *w;
+    double w16[ORC_MLP_N];
+} orc_net;
+
+static void net_init(orc_net *n, const double *mlp)
+{
+    n->w = mlp;
+    if (!mlp) return;
+    for (int i = 0; i < ORC_MLP_N; ++i) n->w16[i] = mlp[i];
+    for (int i = 64; i < 64 + 1024; ++i) n->w16[i] = r16(mlp[i]);                   /* W2 */
+    for (int i = 64 + 1024 + 32; i < 64 + 1024 + 64; ++i) n->w16[i] = r16(mlp[i]);  /* W3 */
+}
+
+/* w: the network with W2 and W3 already rounded to binary16 (orc_net.w16). */
 static double mlp_forward16(double t, const double *w)
 {
     const double *W1 = w, *b1 = w + 32, *W2 = w + 64, *b2 = w + 64 + 1024;
     const double *W3 = w + 64 + 1024 + 32, *b3 = w + 64 + 1024 + 64;
-    double h1[MLP_H], h2[MLP_H];
-    int ok = 1;
-    for (int j = 0; j < MLP_H; ++j) {
-        double a = (double)fmaf((float)W1[j], (float)t, (float)b1[j]);
-        h1[j] = r16(tanh(r16(a)));
-    }
+    float h1[MLP_H], h2[MLP_H];
+    for (int j = 0; j < MLP_H; ++j) h1[j] = (float)orc_tanh16((double)fmaf((float)W1[j], (float)t, (float)b1[j]));
     for (int o = 0; o < MLP_H; ++o) {
-        double c = b2[o];
-        for (int k = 0; k < 2; ++k) {
-            for (int i = 16 * k; i < 16 * k + 16; ++i) {
-                double term = r16(W2[o * MLP_H + i]) * h1[i];
-                ok &= on_grid48(term);
-                c += term;
-                ok &= fabs(c) < 32.0;
-            }
-            c = r32(c);
-        }
-        h2[o] = r16(tanh(r16(c)));
+        float c = (float)b2[o];
+        for (int i = 0; i < MLP_H; ++i) c = fmaf((float)W2[o * MLP_H + i], h1[i], c);
+        h2[o] = (float)orc_tanh16((double)c);
     }
-    double y = b3[0];
-    for (int k = 0; k < 2; ++k) {
-        for (int j = 16 * k; j < 16 * k + 16; ++j) {
-            double term = r16(W3[j]) * h2[j];
-            ok &= on_grid48(term);
-            y += term;
-            ok &= fabs(y) < 32.0;
-        }
-        y = r32(y);
-    }
-    ok &= on_grid48(b3[0]) || fabs(b3[0]) >= ldexp(1.0, -25);
-    for (int o = 0; o < MLP_H; ++o) ok &= on_grid48(b2[o]) || fabs(b2[o]) >= ldexp(1.0, -25);
-    return ok ? y : NAN;
+    float y = (float)b3[0];
+    for (int j = 0; j < MLP_H; ++j) y = fmaf((float)W3[j], h2[j], y);
+    return (double)y;
 }
 
 static double mlp_icdf16(double u, const double *w)
@@ -380,23 +378,29 @@ static double mlp_icdf16(double u, const double *w)
  * followed by the cubic one (64 values). */
 enum { ORC_RV_EXACT = 0, ORC_RV_TABLE = 1, ORC_RV_MLP = 2, ORC_RV_TABLE16 = 3, ORC_RV_CUBIC = 4, ORC_RV_MLP16 = 5 };
 
-static double rv_of(double u, int rv, const double *table, const double *mlp, const rmode *m)
+static double rv_of(double u, int rv, const double *table, const orc_net *net, const rmode *m)
 {
     switch (rv) {
     case ORC_RV_TABLE: return table_icdf(u, table, m);
     case ORC_RV_TABLE16: return table_icdf(q16(u), table, m);
     case ORC_RV_CUBIC: return cubic_icdf(u, table + 32, m);
-    case ORC_RV_MLP: return round_p(mlp_icdf(u, mlp), m);
-    case ORC_RV_MLP16: return round_p(mlp_icdf16(u, mlp), m);
+    case ORC_RV_MLP: return round_p(mlp_icdf(u, net->w), m);
+    case ORC_RV_MLP16: return round_p(mlp_icdf16(u, net->w16), m);
     default: return round_p(orc_ndtri1(u), m);
     }
 }
 
+/* Element by element (OpenMP threads take independent elements). */
 void orc_approx_icdf(const double *u, double *z, int64_t n, int rv, int prec, int pbits,
                      const double *table, const double *mlp)
 {
     rmode m = mode_of(prec, pbits);
-    for (int64_t i = 0; i < n; ++i) z[i] = rv_of(u[i], rv, table, mlp, &m);
+    orc_net net;
+    net_init(&net, mlp);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < n; ++i) z[i] = rv_of(u[i], rv, table, &net, &m);
 }
 
 /* ------------------------------------------------------------------ */
@@ -525,7 +529,7 @@ typedef struct { int prec, pbits, kahan, rv; } orc_variant;
 
 /* Two-way sample of level l: out = (P_fine, P_coarse, D); P_coarse = 0 at l = 0. */
 static void twoway_one(int l, uint64_t path, const orc_variant *v, const orc_sde *p, uint64_t seed,
-                       uint32_t tag, const double *table, const double *mlp, double out[3])
+                       uint32_t tag, const double *table, const orc_net *net, double out[3])
 {
     int64_t nf = (int64_t)1 << l;
     double delta_f = ldexp(p->T, -l);
@@ -550,7 +554,7 @@ static void twoway_one(int l, uint64_t path, const orc_variant *v, const orc_sde
             z = table_icdf(uniform16_of(h), table, &fine.m);
         } else {
             if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);
-            z = rv_of(u[q & 3], v->rv, table, mlp, &fine.m);
+            z = rv_of(u[q & 3], v->rv, table, net, &fine.m);
         }
         path_step(&fine, z);
         if (l > 0 && (n & 1)) path_step(&coarse, round_p(zprev + z, &coarse.m));
@@ -568,7 +572,7 @@ static void twoway_one(int l, uint64_t path, const orc_variant *v, const orc_sde
 /* Four-way sample: out = (P^_f, P^_c, P-_f, P-_c, D) with
  * D = (P^_f - P^_c) - (P-_f - P-_c); all four paths share U_n (Sec. 3). */
 static void fourway_one(int l, uint64_t path, const orc_variant *hat, const orc_variant *bar, const orc_sde *p,
-                        uint64_t seed, uint32_t tag, const double *table, const double *mlp, double out[5])
+                        uint64_t seed, uint32_t tag, const double *table, const orc_net *net, double out[5])
 {
     int64_t nf = (int64_t)1 << l;
     double delta_f = ldexp(p->T, -l);
@@ -585,8 +589,8 @@ static void fourway_one(int l, uint64_t path, const orc_variant *hat, const orc_
     for (int64_t n = 0; n < nf; ++n) {
         const int64_t q = off + n;
         if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);
-        double zh = rv_of(u[q & 3], hat->rv, table, mlp, &hf.m);
-        double zb = rv_of(u[q & 3], bar->rv, table, mlp, &bf.m);
+        double zh = rv_of(u[q & 3], hat->rv, table, net, &hf.m);
+        double zb = rv_of(u[q & 3], bar->rv, table, net, &bf.m);
         path_step(&hf, zh);
         path_step(&bf, zb);
         if (l > 0 && (n & 1)) {
@@ -616,14 +620,18 @@ void orc_twoway_paths(int l, const uint64_t *idx, int64_t n, const int *var, con
                       uint32_t tag, const double *table, const double *mlp, double *out)
 {
     orc_variant v = variant_of(var);
-    for (int64_t i = 0; i < n; ++i) twoway_one(l, idx[i], &v, p, seed, tag, table, mlp, out + 3 * i);
+    orc_net net;
+    net_init(&net, mlp);
+    for (int64_t i = 0; i < n; ++i) twoway_one(l, idx[i], &v, p, seed, tag, table, &net, out + 3 * i);
 }
 
 void orc_fourway_paths(int l, const uint64_t *idx, int64_t n, const int *hat, const int *bar, const orc_sde *p,
                        uint64_t seed, uint32_t tag, const double *table, const double *mlp, double *out)
 {
     orc_variant h = variant_of(hat), b = variant_of(bar);
-    for (int64_t i = 0; i < n; ++i) fourway_one(l, idx[i], &h, &b, p, seed, tag, table, mlp, out + 5 * i);
+    orc_net net;
+    net_init(&net, mlp);
+    for (int64_t i = 0; i < n; ++i) fourway_one(l, idx[i], &h, &b, p, seed, tag, table, &net, out + 5 * i);
 }
 
 /* Level sums over paths path_offset .. path_offset + N - 1:
@@ -635,6 +643,8 @@ void orc_level_sums(int l, uint64_t N, uint64_t path_offset, int four, const int
                     int nthreads, double *sums)
 {
     orc_variant v = variant_of(var), v2 = variant_of(four ? var2 : var);
+    orc_net net;
+    net_init(&net, mlp);
     double s1 = 0.0, s2 = 0.0;
 #ifdef _OPENMP
     if (nthreads < 1) nthreads = 1;
@@ -643,8 +653,8 @@ void orc_level_sums(int l, uint64_t N, uint64_t path_offset, int four, const int
     for (int64_t i = 0; i < (int64_t)N; ++i) {
         double out[5];
         double d;
-        if (four) { fourway_one(l, path_offset + (uint64_t)i, &v, &v2, p, seed, tag, table, mlp, out); d = out[4]; }
-        else { twoway_one(l, path_offset + (uint64_t)i, &v, p, seed, tag, table, mlp, out); d = out[2]; }
+        if (four) { fourway_one(l, path_offset + (uint64_t)i, &v, &v2, p, seed, tag, table, &net, out); d = out[4]; }
+        else { twoway_one(l, path_offset + (uint64_t)i, &v, p, seed, tag, table, &net, out); d = out[2]; }
         s1 += d;
         s2 += d * d;
     }
@@ -661,6 +671,8 @@ void orc_rounding_pairs(int l, uint64_t N, uint64_t path_offset, const int *var,
                         uint32_t tag, const double *table, const double *mlp, double *out)
 {
     orc_variant v = variant_of(var);
+    orc_net net;
+    net_init(&net, mlp);
     int64_t nf = (int64_t)1 << l;
     double delta_f = ldexp(p->T, -l);
     double sq = sqrt(delta_f);
@@ -677,7 +689,7 @@ void orc_rounding_pairs(int l, uint64_t N, uint64_t path_offset, const int *var,
         for (int64_t n = 0; n < nf; ++n) {
             const int64_t q = off + n;
             if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);
-            double z64 = rv_of(u[q & 3], v.rv, table, mlp, &exact);
+            double z64 = rv_of(u[q & 3], v.rv, table, &net, &exact);
             path_step(&hi, z64);
             path_step(&lo, round_p(z64, &lo.m));
         }

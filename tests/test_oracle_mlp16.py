@@ -1,6 +1,7 @@
 """Pins of the oracle's binary16 inference arithmetic of the MLP surrogate
 (the learned part): the binary32 input map against the FP64 library value,
-a hand-built network against numpy's IEEE float16 / float32 roundings, and
+the activation against high-precision tanh at every binary16 input, a
+hand-built network against exact fused multiply-adds in index order, and
 the whole network against the FP64 network within the binary16 error."""
 import math
 
@@ -42,40 +43,92 @@ def _net(W1, b1, W2, b2, W3, b3):
                    np.asarray(W3, float), np.asarray([b3], float))
 
 
-def test_hand_built_network_matches_ieee_float16_steps():
-    """Two active hidden units per layer with an asymmetric W2, so that a
-    transposed index or a missed rounding point changes the result; each
-    step is redone with numpy float16 / float32 casts (IEEE round to
-    nearest even)."""
+def _round16(y):
+    """The binary16 number nearest to the high-precision value y (no tie can
+    occur for a transcendental value)."""
+    import mpmath
+    f = np.float16(float(y))
+    cands = [f, np.nextafter(f, np.float16(-np.inf)), np.nextafter(f, np.float16(np.inf))]
+    return min(cands, key=lambda c: abs(mpmath.mpf(float(c)) - y))
+
+
+def test_tanh16_is_correctly_rounded_at_every_binary16_input():
+    """tanh16 of every finite binary16 x >= 0 equals tanh(x) from 40-digit
+    arithmetic rounded to the nearest binary16; odd symmetry for x < 0;
+    inputs are rounded to binary16 first, and beyond the binary16 range go
+    to +-1."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    bits = np.arange(0x7C00, dtype=np.uint16)
+    x = bits.view(np.float16).astype(np.float64)
+    got = O.tanh16(x)
+    want = np.array([float(_round16(mpmath.tanh(mpmath.mpf(a)))) for a in x])
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, (x[bad[:5]], got[bad[:5]], want[bad[:5]])
+    assert np.array_equal(O.tanh16(-x), -got)
+    assert np.all(np.signbit(O.tanh16(-x[:1])))          # tanh16(-0) = -0
+    # a binary32 pre-activation is rounded to binary16 first: on [0.3, 1)
+    # (tanh' ~ 0.6..0.9) that moves the result for some inputs
+    a = np.linspace(0.3, 1.0, 257, endpoint=False).astype(np.float32).astype(np.float64)
+    got = O.tanh16(a)
+    first = np.array([float(_round16(mpmath.tanh(mpmath.mpf(float(np.float16(x)))))) for x in a])
+    direct = np.array([float(_round16(mpmath.tanh(mpmath.mpf(float(x))))) for x in a])
+    assert np.array_equal(got, first) and np.any(got != direct)
+    assert list(O.tanh16([7e4, -1e9])) == [1.0, -1.0]
+
+
+def test_hand_built_network_matches_fma_chain_in_index_order():
+    """Three hidden units feed output unit 3 from one 16-wide half of the
+    inputs (0, 5) and one from the other (17); unit 9 reads unit 0, unit 20
+    reads unit 17 (an asymmetric W2, so a transposed index is seen).  Each
+    step is redone with an exact fused multiply-add rounded once to binary32
+    and the binary16 activation, in index order.  The output sum mixes a
+    large term (unit 3) with small ones carrying low-order bits (units 9,
+    20), so the same steps in another order give another y for some inputs
+    (inside layer 2 an order change moves c by an ulp of binary32, which the
+    rounding of c to binary16 mostly hides)."""
     H = 32
     W1 = np.zeros(H); b1 = np.zeros(H); W2 = np.zeros((H, H)); b2 = np.zeros(H); W3 = np.zeros(H)
-    W1[0], b1[0] = 0.37, -0.81
-    W1[17], b1[17] = -0.23, 1.1
-    W2[3, 0], W2[3, 17] = 0.7, -1.3          # unit 3 reads units 0 and 17 (second k-chunk)
-    W2[20, 17] = 2.1                         # unit 20 reads unit 17 only
-    b2[3], b2[20] = 0.05, -0.4
-    W3[3], W3[20] = 1.9, -0.6
+    W1[0], b1[0] = 0.013, 0.002              # small activations with fine low-order bits
+    W1[5], b1[5] = 1.71, -2.3
+    W1[17], b1[17] = -0.023, 0.11
+    W2[3, 0], W2[3, 5], W2[3, 17] = 0.7, 1.9, -1.3
+    W2[9, 0] = 0.45
+    W2[20, 17] = 2.1
+    b2[3], b2[9], b2[20] = 0.05, 0.001, -0.04
+    W3[3], W3[9], W3[20] = 1.9, 1.3, -0.6
     b3 = 0.3
     w = _net(W1, b1, W2, b2, W3, b3).astype(np.float32).astype(np.float64)
     Wf = OM.unpack(w)
-    for u in (0.013, 0.31, 0.5, 0.77, 1 - 2.0 ** -20):
-        v = min(u, 1.0 - u)
-        t = np.float32(O.mlp_feature32(np.array([v]))[0])
+    f32 = np.float32
 
-        def act(x):
-            return np.float16(np.tanh(np.float64(np.float16(x))))
-        h1 = {j: act(_fma32(np.float32(Wf[0][j]), t, np.float32(Wf[1][j]))) for j in (0, 17)}
-        w2 = {(o, j): np.float16(Wf[2][o, j]) for o, j in ((3, 0), (3, 17), (20, 17))}
-        c3 = np.float32(np.float64(np.float32(Wf[3][3])) + np.float64(w2[3, 0]) * np.float64(h1[0]))
-        c3 = np.float32(np.float64(c3) + np.float64(w2[3, 17]) * np.float64(h1[17]))
-        c20 = np.float32(np.float64(np.float32(Wf[3][20])))
-        c20 = np.float32(np.float64(c20) + np.float64(w2[20, 17]) * np.float64(h1[17]))
-        h2_3, h2_20 = act(c3), act(c20)
-        # units with zero weights still carry tanh(b2) = 0 and contribute nothing
-        y = np.float32(np.float64(np.float32(b3)) + np.float64(np.float16(Wf[4][3])) * np.float64(h2_3))
-        y = np.float32(np.float64(y) + np.float64(np.float16(Wf[4][20])) * np.float64(h2_20))
+    def act(x):
+        return np.float16(O.tanh16([float(x)])[0])
+
+    def net(t, out_order):
+        h1 = {j: act(_fma32(f32(Wf[0][j]), t, f32(Wf[1][j]))) for j in (0, 5, 17)}
+        reads = {3: (0, 5, 17), 9: (0,), 20: (17,)}
+        h2 = {}
+        for o, ins in reads.items():
+            c = f32(Wf[3][o])
+            for j in ins:
+                c = _fma32(np.float16(Wf[2][o, j]), h1[j], c)
+            h2[o] = act(c)
+        # units with zero weights carry tanh16(b2) = 0 and add nothing
+        y = f32(b3)
+        for o in out_order:
+            y = _fma32(np.float16(Wf[4][o]), h2[o], y)
+        return y
+
+    differs = 0
+    for u in np.concatenate([[0.013, 0.31, 0.5, 0.77, 1 - 2.0 ** -20], uniform_grid_sample(200, 4)]):
+        v = min(u, 1.0 - u)
+        t = f32(O.mlp_feature32(np.array([v]))[0])
+        y = net(t, (3, 9, 20))
         z = O.approx_icdf(np.array([u]), O.RV_MLP16, mlp=w)[0]
         assert z == (float(y) if u > 0.5 else -float(y)), (u, z, y)
+        differs += int(net(t, (20, 9, 3)) != y)
+    assert differs > 0
 
 
 def test_binary16_network_tracks_the_fp64_network():
