@@ -242,7 +242,16 @@ mlmc_status mlmc_icdf_cubic(double *d_host, float *d32_host, uint16_t *d16_host,
 /* ---- MLP surrogate inverse CDF: 1 -> 32 -> 32 -> 1 tanh network on
  * t = sqrt(-2 ln v), v = min(u, 1-u); Z~ = -y for u <= 1/2, +y above.
  * 1153 parameters, layout W1[32], b1[32], W2[32][32] (row = output unit),
- * b2[32], W3[32], b3.  The library keeps one FP32 master copy per device. */
+ * b2[32], W3[32], b3.  The library keeps one FP32 master copy per device.
+ * Inference (approx_icdf with MLMC_ICDF_MLP, and the level kernels through
+ * the grid table below) is in binary16 inference arithmetic, every
+ * operation rounded once to nearest even: t from binary32 operations (the
+ * input map of mlmc_mlp_grad); each activation tanh16(x) = the tanh of x
+ * rounded to binary16, correctly rounded to binary16; h1_j =
+ * tanh16(fma(W1_j, t, b1_j)); W2 and W3 rounded to binary16; c_o = b2_o,
+ * then c_o = fma(W2_oi, h1_i, c_o) for i = 0 .. 31 in turn (binary32),
+ * h2_o = tanh16(c_o); y = b3, then y = fma(W3_o, h2_o, y) for o = 0 .. 31.
+ * The result is defined bit for bit by these steps. */
 #define MLMC_MLP_PARAMS 1153
 mlmc_status mlmc_mlp_set_weights(const float *w_host, size_t n);
 mlmc_status mlmc_mlp_get_weights(float *w_host, size_t n);
@@ -250,13 +259,12 @@ mlmc_status mlmc_mlp_get_weights(float *w_host, size_t n);
 /* The network tabulated on the 24-bit uniform grid (a design of this
  * library; the network itself is not the paper's): the input v = min(u, 1-u)
  * takes the 2^22 values v_k = (2k + 1) 2^-24, and whenever the weights are
- * set or trained the library evaluates the network on all of them with its
- * tensor-core inference (binary16 operands, FP32 accumulation, the
- * input map of mlmc_mlp_grad) into a 16 MiB device table.  The level and
- * batch kernels take Z~ = -y_k for u <= 1/2, +y_k above from that table: the
- * same value the inference gives for the sample.  y_host receives the 2^22
- * values y_k in k order (n must be 2^22); MLMC_ENOTREADY before weights are
- * set.  approx_icdf with MLP evaluates the network directly (any u). */
+ * set or trained the library evaluates the network on all of them (the
+ * inference above) into a 16 MiB device table.  The level and batch kernels
+ * take Z~ = -y_k for u <= 1/2, +y_k above from that table: the same value
+ * the inference gives for the sample.  y_host receives the 2^22 values y_k
+ * in k order (n must be 2^22); MLMC_ENOTREADY before weights are set.
+ * approx_icdf with MLP evaluates the network directly (any u). */
 #define MLMC_MLP_GRID (1u << 22)
 mlmc_status mlmc_mlp_grid_table(float *y_host, size_t n);
 

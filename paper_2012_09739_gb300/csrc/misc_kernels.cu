@@ -4,7 +4,6 @@
 
 #include "internal.h"
 #include "level_kernels.cuh"
-#include "mlp_tc.cuh"
 #include "reduce.cuh"
 
 namespace mlmc {
@@ -247,15 +246,14 @@ cudaError_t launch_uniform_bulk(const uint32_t *w, float *u, size_t n, cudaStrea
 // ---------------------------------------------------------------- bulk inverse CDF
 // Any u in (0, 1): v = min(u, 1-u) is exact in binary32 (1 - u is exact for
 // u >= 1/2), the sign comes from u > 1/2.  Each warp takes 64 consecutive
-// values per round (two per lane), so the MLP's warp-cooperative evaluation
-// sees all 32 lanes.
+// values per round (two per lane).
 template <int P, int ICDF>
 __global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const DevTables *tabs, const MlpWeights *mlpw) {
     __shared__ SmemTable tab;
+    __shared__ MlpShared mlp;
     stage_table(tab, tabs);
+    if (ICDF == ICDF_MLP) mlp_stage(mlp, mlpw);
     __syncthreads();
-    MlpFrags mlp;
-    if (ICDF == ICDF_MLP) mlp.load(mlpw);
     const size_t lane = threadIdx.x & 31;
     const size_t warps = (size_t)gridDim.x * (blockDim.x >> 5);
     for (size_t base = ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 64; base < n;
@@ -275,9 +273,10 @@ __global__ void icdf_bulk_kernel(const float *u, void *z, size_t n, const DevTab
             tt[h] = mlp_feature(v[h]);
         }
         if (ICDF == ICDF_MLP) {
-            const float2 y = mlp_eval_warp(mlp, tt[0], tt[1]);
-            r[0] = sg[0] ? y.x : -y.x;
-            r[1] = sg[1] ? y.y : -y.y;
+            for (int h = 0; h < 2; ++h) {
+                const float y = mlp_eval16(mlp, mlpw->tanh16, tt[h]);
+                r[h] = sg[h] ? y : -y;
+            }
         }
         for (int h = 0; h < 2; ++h) {
             if (idx[h] >= n) continue;

@@ -1,34 +1,42 @@
-// MLP weights on the device: the FP32 master copy, its binary16 W2, and the
-// network tabulated on the 24-bit uniform grid.
+// MLP weights on the device: the FP32 master copy, the binary16 activation
+// table, and the network tabulated on the 24-bit uniform grid.
 #include <vector>
 
 #include "api_internal.h"
-#include "mlp_tc.cuh"
+#include "mlp_device.cuh"
 
 namespace mlmc {
 
-__global__ void mlp_refresh_half_kernel(MlpWeights *m) {
-    for (int i = threadIdx.x; i < MLP_H * MLP_H; i += blockDim.x) m->w2h[i] = __float2half_rn(m->w[64 + i]);
+// The activation table (independent of the weights; rebuilt with the grid).
+__global__ void __launch_bounds__(256) mlp_tanh16_kernel(MlpWeights *m) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < MLP_TANH16; b += gridDim.x * blockDim.x) {
+        const double x = (double)__half2float(__ushort_as_half((uint16_t)b));
+        m->tanh16[b] = __half_as_ushort(__double2half(tanh(x)));
+    }
 }
 
-// y(v_k) for every grid point v_k = (2 k + 1) 2^-24, k < 2^22, by the
-// tensor-core inference: two points per lane, every lane of every warp
-// active (the grid is a multiple of 64 rows).  v_k is exact in binary32 and
-// equal to mirrored_v of any word whose uniform is u_k or 1 - u_k.
+// y(v_k) for every grid point v_k = (2 k + 1) 2^-24, k < 2^22, one point per
+// thread and round (v_k is exact in binary32 and equal to mirrored_v of any
+// word whose uniform is u_k or 1 - u_k).
 __global__ void __launch_bounds__(256) mlp_grid_kernel(MlpWeights *m) {
-    MlpFrags F;
-    F.load(m);
-    const uint32_t k0 = 2u * (blockIdx.x * blockDim.x + threadIdx.x), k1 = k0 + 1u;
-    const float v0 = __fmul_rn((float)(2u * k0 + 1u), 0x1p-24f), v1 = __fmul_rn((float)(2u * k1 + 1u), 0x1p-24f);
-    const float2 y = mlp_eval_warp(F, mlp_feature(v0), mlp_feature(v1));
-    m->ygrid[k0] = y.x;
-    m->ygrid[k1] = y.y;
+    __shared__ MlpShared s;
+    mlp_stage(s, m);
+    __syncthreads();
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < MLP_GRID; k += gridDim.x * blockDim.x) {
+        const float v = __fmul_rn((float)(2u * k + 1u), 0x1p-24f);
+        m->ygrid[k] = mlp_eval16(s, m->tanh16, mlp_feature(v));
+    }
 }
 
-// The weights' derived data: binary16 W2, then the tabulated network.
-cudaError_t mlp_refresh_half(MlpWeights *m, cudaStream_t s) {
-    mlp_refresh_half_kernel<<<1, 256, 0, s>>>(m);
-    mlp_grid_kernel<<<MLP_GRID / 512, 256, 0, s>>>(m);
+// The weights' derived data: the activation table, then the tabulated
+// network (a multiple of the SM count in blocks of 256).
+cudaError_t mlp_refresh(MlpWeights *m, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    mlp_tanh16_kernel<<<MLP_TANH16 / 256, 256, 0, s>>>(m);
+    mlp_grid_kernel<<<8 * sms, 256, 0, s>>>(m);
     return cudaGetLastError();
 }
 
@@ -46,7 +54,7 @@ mlmc_status mlmc_mlp_set_weights(const float *w_host, size_t n) {
     mlmc_status st = device_state(&d);
     if (st) return st;
     cudaError_t e = cudaMemcpy(d->mlp->w, w_host, n * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = mlp_refresh_half(d->mlp, 0);
+    if (e == cudaSuccess) e = mlp_refresh(d->mlp, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "mlmc_mlp_set_weights");
     d->mlp_ready = true;

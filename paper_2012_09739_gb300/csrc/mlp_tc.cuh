@@ -1,6 +1,7 @@
-// Warp-level FP16 tensor-core evaluation of the MLP surrogate
+// Warp-level FP16 tensor-core forward pass of the MLP surrogate
 // (1 -> 32 -> 32 -> 1, tanh) with mma.sync.m16n8k16 (FP16 operands, FP32
-// accumulation).
+// accumulation, tanh.approx activations), used by training (mlp_train.cu);
+// inference is mlp_eval16 (mlp_device.cuh).
 //
 // A warp evaluates 64 rows at a time: lane L owns rows 16 i + q + 8 h for
 // i = L % 4, q = L / 4 and h = 0, 1 (its two samples).  The rows are handled
@@ -47,31 +48,6 @@ __device__ __forceinline__ void mma16816(float &d0, float &d1, float &d2, float 
         "{%10,%11,%12,%13};"
         : "=f"(d0), "=f"(d1), "=f"(d2), "=f"(d3)
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(c0), "f"(c1), "f"(c2), "f"(c3));
-}
-
-// Network input t = sqrt(-2 ln v) from v in [2^-24, 1/2], with binary32
-// operations that each round once to nearest (so that the oracle can repeat
-// them exactly): v = m 2^e with m in [1/sqrt2, sqrt2]; ln m = 2 z (1 + z^2/3
-// + z^4/5 + z^6/7 + z^8/9) with z = (m - 1) / (m + 1), |z| <= 0.1716 (the
-// atanh series; the next term is below 7e-10); t^2 = -2 e ln2 - 2 ln m by one
-// FMA; t = sqrt(t^2) correctly rounded.
-__device__ __forceinline__ float mlp_feature(float v) {
-    const uint32_t b = __float_as_uint(v);
-    int e = (int)(b >> 23) - 127;
-    float m = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
-    if (m > 1.41421354f) {
-        m = __fmul_rn(m, 0.5f);
-        e += 1;
-    }
-    const float z = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
-    const float w = __fmul_rn(z, z);
-    float q = __fmaf_rn(1.0f / 9.0f, w, 1.0f / 7.0f);
-    q = __fmaf_rn(q, w, 1.0f / 5.0f);
-    q = __fmaf_rn(q, w, 1.0f / 3.0f);
-    q = __fmaf_rn(q, w, 1.0f);
-    const float lnm = __fmul_rn(__fmul_rn(2.0f, z), q);
-    const float t2 = __fmaf_rn((float)(-2 * e), 0.693147182f, __fmul_rn(-2.0f, lnm));
-    return __fsqrt_rn(t2);
 }
 
 // Per-lane register copy of the network in fragment form.
@@ -148,39 +124,6 @@ __device__ __forceinline__ void mlp_layer3(const MlpFrags &F, const uint32_t h[2
     mma16816(c0, c1, c2, c3, h[1][0], h[1][1], h[1][2], h[1][3], F.w3[1][0], F.w3[1][1], c0, c1, c2, c3);
     y0 = c0;
     y1 = c2;
-}
-
-// |Phi^-1| estimates y for this lane's two samples (inputs t0, t1); all 32
-// lanes must call it together.
-__device__ __forceinline__ float2 mlp_eval_warp(const MlpFrags &F, float t0, float t1) {
-    const int lane = threadIdx.x & 31, q = lane >> 2;
-    float y0 = 0.0f, y1 = 0.0f;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        // rows 16 m + q (+8) are owned by lane 4 q + m
-        const float r0 = __shfl_sync(0xffffffffu, t0, 4 * q + m);
-        const float r1 = __shfl_sync(0xffffffffu, t1, 4 * q + m);
-        uint32_t a[2][4], h[2][4];
-        mlp_layer1(F, r0, r1, a);
-        mlp_layer2(F, a, h);
-        float o0, o1;
-        mlp_layer3(F, h, o0, o1);
-        // results sit in lane 4 q; the owner is lane 4 q + m
-        const float s0 = __shfl_sync(0xffffffffu, o0, 4 * q);
-        const float s1 = __shfl_sync(0xffffffffu, o1, 4 * q);
-        if ((lane & 3) == m) {
-            y0 = s0;
-            y1 = s1;
-        }
-    }
-    return make_float2(y0, y1);
-}
-
-// Approximate normals of this lane's two words: -y for u <= 1/2, +y above.
-__device__ __forceinline__ float2 mlp_z_warp(const MlpFrags &F, uint32_t w0, uint32_t w1) {
-    const float2 y = mlp_eval_warp(F, mlp_feature(mirrored_v(w0)), mlp_feature(mirrored_v(w1)));
-    return make_float2(__uint_as_float(__float_as_uint(y.x) ^ (~w0 & 0x80000000u)),
-                       __uint_as_float(__float_as_uint(y.y) ^ (~w1 & 0x80000000u)));
 }
 
 }  // namespace mlmc

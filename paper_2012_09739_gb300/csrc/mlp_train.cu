@@ -290,7 +290,7 @@ __global__ void mlp_targets_kernel(const float *u, float *z, size_t n) {
     }
 }
 
-cudaError_t mlp_refresh_half(MlpWeights *m, cudaStream_t s);
+cudaError_t mlp_refresh(MlpWeights *m, cudaStream_t s);
 
 namespace {
 
@@ -397,7 +397,7 @@ extern "C" mlmc_status mlmc_mlp_train(const float *u_dev, const float *z_dev, si
         for (uint64_t i = 0; i < rest; ++i) enqueue_step(s);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = mlp_refresh_half(d->mlp, s);
+    if (e == cudaSuccess) e = mlp_refresh(d->mlp, s);
     float lh = 0.0f;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&lh, loss, sizeof(float), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(partials, s);
