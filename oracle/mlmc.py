@@ -230,7 +230,11 @@ def grid_joint_moments(z, w, max_order=4):
 #   * N_t = ceil(2 eps^-2 sqrt(V_t / C_t) sum_s sqrt(V_s C_s)) (Sec. 3),
 #     drawn whenever sum_t V_t / N_t > eps^2 / 2;
 #   * bias test max(|Y_L|, |Y_{L-1}| 2^-alpha, |Y_{L-2}| 2^-2alpha) /
-#     (2^alpha - 1) <= eps / sqrt(2), else L + 1 (up to max_level);
+#     (2^alpha - 1) <= eps / sqrt(2), else L + 1 (up to max_level), after
+#     every round (the loop of the MLMC review's algorithm: evaluate the
+#     extra samples, update V_l and N_l, test weak convergence, add a level
+#     if it fails), so a new level's warm-up shares a round with the top-ups;
+#     the run ends when the test holds and no term needs more samples;
 #   * per-level choice (prec = -1): the candidates {binary16 + Kahan,
 #     binary16, binary32} nested pairs and the standard term alone, n0
 #     samples each in a round of their own; the level keeps the nested pair
@@ -387,8 +391,10 @@ def adaptive_mlmc(eps, draw, cost, *, nested, prec=F16, kahan=1, icdf=1, n0=1000
     converged = False
     while True:
         run(terms)
-        if plan():
-            continue
+        need = plan()
+        # the weak-error test after every round, on the samples so far: a
+        # failed test adds level L + 1 at once, so that its warm-up shares
+        # the next round with the top-ups plan() just asked for
         Y = [0.0] * (L + 1)
         for t in terms:
             Y[t.l] += t.Y()
@@ -400,10 +406,14 @@ def adaptive_mlmc(eps, draw, cost, *, nested, prec=F16, kahan=1, icdf=1, n0=1000
             bias = max(bias, abs(Y[L - 2]) / (r * r))
         bias /= (r - 1.0)
         if bias <= eps / math.sqrt(2.0):
-            converged = True
-            break
+            if not need:
+                converged = True
+                break
+            continue
         if L >= max_level:
-            break
+            if not need:
+                break
+            continue
         L += 1
         add_level(L)
         plan()

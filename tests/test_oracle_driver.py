@@ -50,6 +50,10 @@ def test_standard_estimator_stops_at_the_closed_form_level_with_the_optimal_spli
     # <= eps / sqrt(2) first holds at L = ceil(log2(m0 sqrt(2) / eps))
     L = math.ceil(math.log2(m0 * math.sqrt(2.0) / EPS))
     assert r["converged"] and r["levels"] == L + 1
+    # the weak-error test runs after every round: the warm-up round of levels
+    # 0..2, then one round per added level (which also carries the top-ups);
+    # testing only once the top-ups are done would take one round more
+    assert r["rounds"] == r["levels"] - 2
     assert abs(r["estimate"] - sum(m0 * 2.0 ** -l for l in range(L + 1))) < 1e-12
     # the final split: N_l = round8(ceil(2 eps^-2 sqrt(V_l / C_l) sum sqrt(V C))) (Sec. 3)
     V = [v0 * 2.0 ** -l for l in range(L + 1)]
