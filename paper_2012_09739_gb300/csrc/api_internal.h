@@ -26,6 +26,7 @@ struct DeviceState {
     BatchGraphs *batch = nullptr;        // mlmc_batch: captured graphs and their buffers
     BatchCache *run_cache = nullptr;     // mlmc_run: buffers of its batched rounds
     cudaStream_t run_stream = nullptr;
+    cudaEvent_t run_events[2] = {nullptr, nullptr};   // mlmc_run: around each round's launches
 };
 
 struct LaunchCfg {

@@ -26,6 +26,8 @@ BatchKernelFn batch_kernel_f32_four(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_f16_four(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_bf16_four(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_mixed(int prec, int kahan, int icdf, int sde);
+BatchSmallFn batch_small_mixed(int prec, int kahan, int icdf, int sde);
+BatchSmallFn batch_small_two(int prec, int kahan, int icdf, int sde);
 
 // The batch finalize adds an item's group partials exactly as the level
 // finalize does (block_sum_fixed over at most FINALIZE_SPAN partials, or one
@@ -239,6 +241,7 @@ struct BatchCache {
     unsigned char *stage = nullptr;      // pinned staging of the descriptors
     size_t stage_cap = 0;
     std::map<std::pair<const void *, int>, int> occupancy;   // (batch kernel, block) -> resident blocks per SM
+    uint32_t *small_counters = nullptr;  // the fused small-round kernel's two counters (zero between rounds)
     // streams of the concurrent groups (created on first use)
     static constexpr size_t MAX_SIDE = 7;
     cudaStream_t side[MAX_SIDE] = {};
@@ -272,6 +275,7 @@ void batch_cache_destroy(BatchCache *c) {
     if (c->done) cudaEventSynchronize(c->done);
     if (c->exec) cudaGraphExecDestroy(c->exec);
     cudaFree(c->blob);
+    cudaFree(c->small_counters);
     cudaFree(c->partials);
     cudaFree(c->sums);
     if (c->sums_host) cudaFreeHost(c->sums_host);
@@ -295,6 +299,10 @@ void release_device_extras(DeviceState &d) {
     }
     batch_cache_destroy(d.run_cache);
     if (d.run_stream) cudaStreamDestroy(d.run_stream);
+    for (cudaEvent_t &ev : d.run_events) {
+        if (ev) cudaEventDestroy(ev);
+        ev = nullptr;
+    }
     d.batch = nullptr;
     d.run_cache = nullptr;
     d.run_stream = nullptr;
@@ -353,7 +361,8 @@ mlmc_status upload(BatchCache &c, const Plan &p, cudaStream_t s, bool stage_idle
 }
 
 // Resident blocks per SM of a batch kernel at a block size (cached).
-int blocks_per_sm(BatchCache &c, BatchKernelFn fn, int block) {
+template <class Fn>
+int blocks_per_sm(BatchCache &c, Fn fn, int block) {
     const auto key = std::make_pair((const void *)fn, block);
     auto it = c.occupancy.find(key);
     if (it != c.occupancy.end()) return it->second;
@@ -529,6 +538,65 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
 
 }  // namespace
 
+// A latency-sized round of one group in one launch of the fused small-round
+// kernel (descriptors as a kernel parameter, finalize by the last block,
+// sums straight into the pinned host buffer); false (nothing enqueued) where
+// the round does not qualify: several groups, more than SMALL_ITEMS items,
+// an item above one finalize span, not latency-sized, or no such kernel for
+// the variant.  MLMC_ROUND_FUSED=0 turns it off.
+bool small_round(const DeviceState &d, BatchCache &c, const Plan &p, cudaStream_t s, mlmc_status *st) {
+    if (p.groups.size() != 1 || p.items.size() > (size_t)SMALL_ITEMS || !p.jobs.empty() || p.too_large ||
+        p.block != SUM_THREADS || p.work >= SMALL_BATCH_WORK || env_int("MLMC_ROUND_FUSED", 1) == 0)
+        return false;
+    const Group &g = p.groups[0];
+    const BatchSmallFn fn = g.mode == MODE_MIXED ? batch_small_mixed(g.prec, g.kahan, g.icdf, g.sde)
+                            : g.mode == MODE_TWO ? batch_small_two(g.prec, g.kahan, g.icdf, g.sde)
+                                                 : nullptr;
+    if (!fn) return false;
+    cudaError_t e;
+    *st = MLMC_OK;
+    if (!c.small_counters) {
+        if ((e = cudaMalloc(&c.small_counters, 2 * sizeof(uint32_t))) != cudaSuccess ||
+            (e = cudaMemsetAsync(c.small_counters, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) {
+            *st = cuda_fail(e, "batch buffers");
+            return true;
+        }
+    }
+    if ((e = grow(&c.partials, &c.partials_cap, p.npartials)) != cudaSuccess) {
+        *st = cuda_fail(e, "batch buffers");
+        return true;
+    }
+    const size_t n = p.items.size();
+    if (c.sums_host_cap < n) {
+        if (c.sums_host) cudaFreeHost(c.sums_host);
+        c.sums_host = nullptr;
+        c.sums_host_cap = 0;
+        if ((e = cudaMallocHost(&c.sums_host, SMALL_ITEMS * sizeof(double2))) != cudaSuccess) {
+            *st = cuda_fail(e, "pinned");
+            return true;
+        }
+        c.sums_host_cap = SMALL_ITEMS;
+    }
+    SmallRound r;
+    memset(&r, 0, sizeof r);
+    for (size_t i = 0; i < n; ++i) {
+        r.items[i] = p.items[i];
+        r.first[i] = p.fin[3 * i];
+        r.count[i] = p.fin[3 * i + 1];
+    }
+    for (size_t k = 0; k < g.spans.size(); ++k) r.spans[k] = g.spans[k];
+    r.nitems = (uint32_t)n;
+    r.nspans = (uint32_t)g.spans.size();
+    r.ntiles = g.ntiles;
+    r.keys = p.items[0].rk;
+    const int wpb = SUM_THREADS / 32;
+    const uint64_t full = (uint64_t)blocks_per_sm(c, fn, SUM_THREADS) * d.sm_count;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(full, ((uint64_t)g.ntiles + wpb - 1) / wpb));
+    fn<<<(unsigned)grid, SUM_THREADS, 0, s>>>(r, c.small_counters, c.partials, c.sums_host, d.tabs);
+    if ((e = cudaGetLastError()) != cudaSuccess) *st = cuda_fail(e, "batch small-round kernel");
+    return true;
+}
+
 // One round of a caller that owns its own cache (the adaptive driver):
 // descriptors, persistent kernels, finalize and the copy of all sums into
 // c.sums_host, enqueued on s.  The caller waits on s before reading.
@@ -539,8 +607,10 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
 mlmc_status batch_round(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed,
                         cudaStream_t s) {
     Plan p = make_plan(d, w, n, seed, std::max(4, work_lane_log2(d, w, n) - 2));
+    mlmc_status st = MLMC_OK;
+    if (small_round(d, c, p, s, &st)) return st;
     // the driver waits for every round before it plans the next one
-    mlmc_status st = upload(c, p, s, true);
+    st = upload(c, p, s, true);
     if (st) return st;
     return enqueue(d, c, p, s, true, false);
 }

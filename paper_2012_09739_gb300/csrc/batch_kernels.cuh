@@ -18,6 +18,7 @@
 #pragma once
 
 #include "level_kernels.cuh"
+#include "reduce.cuh"
 
 namespace mlmc {
 
@@ -173,17 +174,12 @@ __device__ __forceinline__ void run_tile(const LevelArgs &a, const PhiloxKeys &k
 // run at.  Accumulation as in the single-mode kernels, so sums are the same.
 enum { MODE_MIXED = 2 };
 
-// One kernel per (MODE, P, KAHAN, ICDF, SDE), like the level kernels and with
-// their register budgets, so that a batch runs at the level kernels'
-// occupancy; the host launches one per group of items that share them.
+// The tile loop of a persistent batch kernel: each warp takes the next tile
+// index from the counter until the tiles run out.
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__global__ void __launch_bounds__(256, MODE == MODE_TWO ? 4 : 3)
-batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uint32_t ntiles, uint32_t *counter,
-             double2 *partials, const DevTables *tabs, const PhiloxKeys keys) {
-    __shared__ SmemTable tab;
-    __shared__ SeqScratch<P> seq[8];           // one per warp (warp-cooperative single pairs)
-    stage_table(tab, tabs);
-    __syncthreads();
+__device__ __forceinline__ void tile_loop(const LevelArgs *items, const TileSpan *spans, uint32_t nspans,
+                                          uint32_t ntiles, uint32_t *counter, double2 *partials,
+                                          const SmemTable &tab, const PhiloxKeys &keys, SeqScratch<P> &seq) {
     const float *mlp = ICDF == ICDF_MLP ? items[0].mlp->ygrid : nullptr;
     const uint32_t lane = threadIdx.x & 31;
     for (;;) {
@@ -197,14 +193,87 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
         const LevelArgs a = items[sp.item];
         if constexpr (MODE == MODE_MIXED) {
             if (a.mode == MODE_FOUR)
-                run_tile<MODE_FOUR, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq[threadIdx.x >> 5]);
+                run_tile<MODE_FOUR, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq);
             else
-                run_tile<MODE_TWO, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq[threadIdx.x >> 5]);
+                run_tile<MODE_TWO, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq);
         } else {
-            run_tile<MODE, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq[threadIdx.x >> 5]);
+            run_tile<MODE, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq);
         }
     }
 }
+
+// One kernel per (MODE, P, KAHAN, ICDF, SDE), like the level kernels and with
+// their register budgets, so that a batch runs at the level kernels'
+// occupancy; the host launches one per group of items that share them.
+template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
+__global__ void __launch_bounds__(256, MODE == MODE_TWO ? 4 : 3)
+batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uint32_t ntiles, uint32_t *counter,
+             double2 *partials, const DevTables *tabs, const PhiloxKeys keys) {
+    __shared__ SmemTable tab;
+    __shared__ SeqScratch<P> seq[8];           // one per warp (warp-cooperative single pairs)
+    stage_table(tab, tabs);
+    __syncthreads();
+    tile_loop<MODE, P, KAHAN, ICDF, SDE>(items, spans, nspans, ntiles, counter, partials, tab, keys,
+                                         seq[threadIdx.x >> 5]);
+}
+
+// A latency-sized round of one group (an adaptive run's round at large
+// RMSE): its descriptors travel in the kernel's parameter space, so the
+// round needs no descriptor copy, and the last block to finish adds every
+// item's partials with the finalize's fixed-order sum (so the sums equal
+// those of the two-kernel path bit for bit) and writes them to `sums`; it
+// then zeroes the two counters (tiles taken, blocks done) for the next round
+// on the stream.  Items of at most 1024 partials are summed one per warp
+// (warp_sum_fixed, the same tree), so a round's items are finalized in
+// parallel.  One launch per round instead of a copy and two launches.
+constexpr int SMALL_ITEMS = 24;
+
+struct SmallRound {
+    LevelArgs items[SMALL_ITEMS];
+    TileSpan spans[SMALL_ITEMS];
+    uint32_t first[SMALL_ITEMS];   // per item: its first group partial
+    uint32_t count[SMALL_ITEMS];   // and how many (at most FINALIZE_SPAN)
+    uint32_t nitems, nspans, ntiles;
+    PhiloxKeys keys;
+};
+
+template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
+__global__ void __launch_bounds__(256, MODE == MODE_TWO ? 4 : 3)
+batch_small_kernel(const __grid_constant__ SmallRound r, uint32_t *counters, double2 *partials, double2 *sums,
+                   const DevTables *tabs) {
+    __shared__ SmemTable tab;
+    __shared__ SeqScratch<P> seq[8];
+    __shared__ double r1[SUM_THREADS], r2[SUM_THREADS];
+    __shared__ uint32_t last;
+    stage_table(tab, tabs);
+    __syncthreads();
+    tile_loop<MODE, P, KAHAN, ICDF, SDE>(r.items, r.spans, r.nspans, r.ntiles, counters, partials, tab, r.keys,
+                                         seq[threadIdx.x >> 5]);
+    __threadfence();            // this thread's partials, before the block is counted done
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counters + 1, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();            // every block's partials are visible from here on
+    // items of at most 1024 partials one per warp, the others with the block
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (uint32_t i = warp; i < r.nitems; i += SUM_THREADS / 32) {
+        if (r.count[i] > (uint32_t)FINALIZE_THREADS) continue;
+        const double2 v = warp_sum_fixed(partials + r.first[i], r.count[i], lane);
+        if (lane == 0) sums[i] = v;
+    }
+    for (uint32_t i = 0; i < r.nitems; ++i) {
+        if (r.count[i] <= (uint32_t)FINALIZE_THREADS) continue;
+        const double2 v = block_sum_fixed(partials + r.first[i], r.count[i], r1, r2);
+        if (threadIdx.x == 0) sums[i] = v;
+    }
+    if (threadIdx.x == 0) {
+        counters[0] = 0u;
+        counters[1] = 0u;
+    }
+}
+
+using BatchSmallFn = void (*)(SmallRound, uint32_t *, double2 *, double2 *, const DevTables *);
 
 using BatchKernelFn = void (*)(const LevelArgs *, const TileSpan *, uint32_t, uint32_t, uint32_t *, double2 *,
                                const DevTables *, const PhiloxKeys);

@@ -147,10 +147,10 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
     if (!d->run_cache) d->run_cache = batch_cache_create();
     cudaStream_t s = d->run_stream;
     BatchCache *cache = d->run_cache;
-    cudaEvent_t done = nullptr, ev_a = nullptr, ev_b = nullptr;
-    if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreate(&ev_a)) != cudaSuccess || (e = cudaEventCreate(&ev_b)) != cudaSuccess)
-        st = cuda_fail(e, "cudaEventCreate");
+    // around each round's launches (created once per device); the wait is on ev_b
+    for (cudaEvent_t &ev : d->run_events)
+        if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    cudaEvent_t ev_a = d->run_events[0], ev_b = d->run_events[1];
     // MLMC_RUN_LOG=1: one JSON line per round on stderr (items, path-steps,
     // the cost model's and the measured device time, wall time, host time to
     // plan and enqueue the round)
@@ -198,9 +198,8 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         if (r) return r;
         const auto t_enq = std::chrono::steady_clock::now();
         cudaEventRecord(ev_b, s);
-        cudaEventRecord(done, s);
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-        if ((r = wait_event(done, fmax(limit - el, 0.001)))) return r;
+        if ((r = wait_event(ev_b, fmax(limit - el, 0.001)))) return r;
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, ev_a, ev_b);
         device_ms += ms;
@@ -406,8 +405,11 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
 
     while (!st) {
         if ((st = run_round(terms, 1))) break;
-        if (plan_samples()) continue;
-        // ---- weak-error test on the last three level means
+        const bool need = plan_samples();
+        // ---- weak-error test on the last three level means, after every
+        // round (the loop of the MLMC review's algorithm): a failed test adds
+        // level L + 1 at once, so that its warm-up shares the next round with
+        // the top-ups plan_samples just asked for
         std::vector<double> Y(L + 1, 0.0);
         for (const Term &t : terms) Y[t.l] += t.mean();
         const double r = pow(2.0, o->alpha);
@@ -416,10 +418,16 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         if (L >= 2) bias = fmax(bias, fabs(Y[L - 2]) / (r * r));
         bias /= (r - 1.0);
         if (bias <= eps / sqrt(2.0)) {
-            converged = true;
-            break;
+            if (!need) {
+                converged = true;
+                break;
+            }
+            continue;
         }
-        if (L >= o->max_level) break;
+        if (L >= o->max_level) {
+            if (!need) break;
+            continue;
+        }
         ++L;
         st = add_level(L);
         // the new level's warm-up and the other levels' top-ups in one round
@@ -458,9 +466,6 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
         if (!converged) st = fail(MLMC_ENOTCONV, "bias test not met at max_level %d", o->max_level);
     }
-    if (done) cudaEventDestroy(done);
-    if (ev_a) cudaEventDestroy(ev_a);
-    if (ev_b) cudaEventDestroy(ev_b);
     return st;
 }
 

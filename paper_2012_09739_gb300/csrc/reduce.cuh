@@ -65,4 +65,43 @@ __device__ __forceinline__ double2 block_sum_fixed(const double2 *p, uint64_t n,
     return make_double2(sx, sy);
 }
 
+// Strided sum J of a warp's lane (slot lane + 32 J: 0.0 plus its partial, if
+// any) after the in-lane tree levels down to stride H: the level-H step adds
+// sum J + H to sum J.  Evaluated depth first (few live values); each
+// addition has the operands of the level-by-level order.
+template <int J, int H>
+__device__ __forceinline__ double2 strided_tree(const double2 *p, uint32_t n, uint32_t lane) {
+    if constexpr (H == 32) {
+        const uint32_t i = lane + 32u * J;
+        double2 s = make_double2(0.0, 0.0);
+        if (i < n) {
+            const double2 v = p[i];
+            s.x += v.x;
+            s.y += v.y;
+        }
+        return s;
+    } else {
+        const double2 a = strided_tree<J, 2 * H>(p, n, lane);
+        const double2 b = strided_tree<J + H, 2 * H>(p, n, lane);
+        return make_double2(a.x + b.x, a.y + b.y);
+    }
+}
+
+// The same fixed-order sum of p[0 .. n) for n <= FINALIZE_THREADS, by one
+// warp: lane L holds the strided sums L + 32 j (j = 0 .. 31), each 0.0 plus
+// its one partial, so the tree levels 512 .. 32 pair sums within a lane and
+// 16 .. 1 go through the same shuffles: every addition of block_sum_fixed,
+// on the same operands.  Every lane of the warp must call it; lane 0 gets
+// the result.
+__device__ __forceinline__ double2 warp_sum_fixed(const double2 *p, uint32_t n, uint32_t lane) {
+    const double2 s = strided_tree<0, 1>(p, n, lane);
+    double sx = s.x, sy = s.y;
+#pragma unroll
+    for (int h = 16; h > 0; h >>= 1) {
+        sx += __shfl_down_sync(0xffffffffu, sx, h);
+        sy += __shfl_down_sync(0xffffffffu, sy, h);
+    }
+    return make_double2(sx, sy);
+}
+
 }  // namespace mlmc

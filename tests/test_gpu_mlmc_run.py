@@ -167,3 +167,32 @@ def test_mlmc_run_decisions_replayed_by_the_oracle_driver(eps, est, prec, kahan,
     assert abs(kept + r.discarded_path_steps - r.path_steps) <= 1e-9 * r.path_steps
     # the accounting: the cost model's time of the samples drawn, and the measured device time
     assert r.model_s > 0 and r.device_s > 0 and r.wall_s >= r.device_s
+
+
+@pytest.mark.parametrize("est,prec,kahan,icdf,scheme", [
+    (0, M.MLMC_F32, 0, M.MLMC_ICDF_EXACT, M.MLMC_EULER),
+    (0, M.MLMC_F32, 1, M.MLMC_ICDF_EXACT, M.MLMC_MILSTEIN),
+    (1, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE16, M.MLMC_EULER),
+    (1, M.MLMC_F32, 0, M.MLMC_ICDF_TABLE, M.MLMC_EULER),
+])
+def test_fused_small_rounds_give_the_same_runs(monkeypatch, est, prec, kahan, icdf, scheme):
+    """Latency-sized rounds of one kernel group run as one fused launch
+    (descriptors as kernel parameters, finalize by the last block); the same
+    runs with the two-kernel path (MLMC_ROUND_FUSED=0) must take the same
+    draws and get the same sums, bit for bit, at an RMSE where every round
+    is small (1e-3) and where the later ones are not (1e-4)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0, scheme=scheme)
+    for eps in (1e-3, 1e-4):
+        runs = []
+        for fused in ("1", "0"):
+            monkeypatch.setenv("MLMC_ROUND_FUSED", fused)
+            runs.append(M.mlmc_run(eps, params, _opts(est, prec=prec, kahan=kahan, icdf=icdf, seed=91),
+                                   trace_cap=4096))
+        (a, ta), (b, tb) = runs
+        assert a.estimate == b.estimate and a.variance == b.variance and a.rounds == b.rounds, eps
+        assert len(ta) == len(tb)
+        for x, y in zip(ta, tb):
+            assert (x.round, x.l, x.kind, x.dn, x.path_offset, x.s1, x.s2) == \
+                (y.round, y.l, y.kind, y.dn, y.path_offset, y.s1, y.s2), eps
