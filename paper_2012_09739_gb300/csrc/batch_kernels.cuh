@@ -175,18 +175,17 @@ __device__ __forceinline__ void run_tile(const LevelArgs &a, const PhiloxKeys &k
 enum { MODE_MIXED = 2 };
 
 // The tile loop of a persistent batch kernel: each warp takes the next tile
-// index from the counter until the tiles run out.
-template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
+// index from the counter until the tiles run out; or (STATIC) warp w of W
+// first takes tile w and then W + the counter's next value, so that a
+// launch of at most one tile per warp needs no atomic at all.  A tile's
+// partials do not depend on which warp runs it.
+template <bool STATIC, int MODE, int P, bool KAHAN, int ICDF, int SDE>
 __device__ __forceinline__ void tile_loop(const LevelArgs *items, const TileSpan *spans, uint32_t nspans,
                                           uint32_t ntiles, uint32_t *counter, double2 *partials,
                                           const SmemTable &tab, const PhiloxKeys &keys, SeqScratch<P> &seq) {
     const float *mlp = ICDF == ICDF_MLP ? items[0].mlp->ygrid : nullptr;
     const uint32_t lane = threadIdx.x & 31;
-    for (;;) {
-        uint32_t t = 0;
-        if (lane == 0) t = atomicAdd(counter, 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= ntiles) break;
+    auto tile = [&](uint32_t t) {
         const TileSpan sp = spans[find_span(spans, nspans, t, lane)];
         // every item has the batch's seed: its round keys come from the
         // launch parameters
@@ -198,6 +197,25 @@ __device__ __forceinline__ void tile_loop(const LevelArgs *items, const TileSpan
                 run_tile<MODE_TWO, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq);
         } else {
             run_tile<MODE, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq);
+        }
+    };
+    if constexpr (STATIC) {
+        uint32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        while (t < ntiles) {
+            tile(t);
+            const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+            if (warps >= ntiles) break;
+            uint32_t k = 0;
+            if (lane == 0) k = atomicAdd(counter, 1u);
+            t = warps + __shfl_sync(0xffffffffu, k, 0);
+        }
+    } else {
+        for (;;) {
+            uint32_t t = 0;
+            if (lane == 0) t = atomicAdd(counter, 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= ntiles) break;
+            tile(t);
         }
     }
 }
@@ -213,7 +231,7 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
     __shared__ SeqScratch<P> seq[8];           // one per warp (warp-cooperative single pairs)
     stage_table(tab, tabs);
     __syncthreads();
-    tile_loop<MODE, P, KAHAN, ICDF, SDE>(items, spans, nspans, ntiles, counter, partials, tab, keys,
+    tile_loop<false, MODE, P, KAHAN, ICDF, SDE>(items, spans, nspans, ntiles, counter, partials, tab, keys,
                                          seq[threadIdx.x >> 5]);
 }
 
@@ -223,7 +241,8 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
 // item's partials with the finalize's fixed-order sum (so the sums equal
 // those of the two-kernel path bit for bit) and writes them to `sums`; it
 // then zeroes the two counters (tiles taken, blocks done) for the next round
-// on the stream.  Items of at most 1024 partials are summed one per warp
+// on the stream.  A warp's first tile is its own index (no atomic).
+// Items of at most 1024 partials are summed one per warp
 // (warp_sum_fixed, the same tree), so a round's items are finalized in
 // parallel.  One launch per round instead of a copy and two launches.
 constexpr int SMALL_ITEMS = 24;
@@ -237,8 +256,11 @@ struct SmallRound {
     PhiloxKeys keys;
 };
 
+// A latency-sized round fills a fraction of one wave, so the kernel takes a
+// register budget of two blocks per SM instead of the occupancy the bulk
+// kernels need.
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
-__global__ void __launch_bounds__(256, MODE == MODE_TWO ? 4 : 3)
+__global__ void __launch_bounds__(256, 2)
 batch_small_kernel(const __grid_constant__ SmallRound r, uint32_t *counters, double2 *partials, double2 *sums,
                    const DevTables *tabs) {
     __shared__ SmemTable tab;
@@ -247,7 +269,7 @@ batch_small_kernel(const __grid_constant__ SmallRound r, uint32_t *counters, dou
     __shared__ uint32_t last;
     stage_table(tab, tabs);
     __syncthreads();
-    tile_loop<MODE, P, KAHAN, ICDF, SDE>(r.items, r.spans, r.nspans, r.ntiles, counters, partials, tab, r.keys,
+    tile_loop<true, MODE, P, KAHAN, ICDF, SDE>(r.items, r.spans, r.nspans, r.ntiles, counters, partials, tab, r.keys,
                                          seq[threadIdx.x >> 5]);
     __threadfence();            // this thread's partials, before the block is counted done
     __syncthreads();
