@@ -499,8 +499,13 @@ static double payoff_of(double X, const orc_sde *p, int prec)
 }
 
 /* Random-number counter layout.  ctr = (path lo32, path hi32, j, tag),
- * key = (seed lo32, seed hi32); fine step n of a path uses word n mod 4 of
- * call j = n / 4.  tag = kind | level << 8 | set << 16 with kind 0: standard
+ * key = (seed lo32, seed hi32).  A uniform takes the top 23 bits of a word
+ * (uniform_of), so one call (x, y, z, w) carries five: its four words and
+ * a fifth word assembled from the low bytes of x, y and z as bits 8..15,
+ * 16..23, 24..31 (spare_word: the uniform reads bits 9..31, disjoint from
+ * the bits the four words' uniforms read).  Fine step n of a path of
+ * 2^l >= 4 steps uses uniform n mod 5 of call j = n / 5 (0..3: the words,
+ * 4: the spare).  tag = kind | level << 8 | set << 16 with kind 0: standard
  * two-way with exact normals, 1: two-way with approximate normals, 2:
  * four-way.  (Reading: the paper is silent on the generator.)
  * With 16-bit uniforms (RV TABLE16 on a two-way path) fine step n uses half
@@ -525,6 +530,28 @@ static void draw4(uint64_t path, uint32_t j, uint32_t tag, uint64_t seed, double
     for (int i = 0; i < 4; ++i) u[i] = uniform_of(w[i]);
 }
 
+static uint32_t spare_word(const uint32_t w[4])
+{
+    return ((w[0] & 0xFFu) << 8) | ((w[1] & 0xFFu) << 16) | ((w[2] & 0xFFu) << 24);
+}
+
+/* The five uniforms of a call: its four words, then the spare word. */
+static void draw5(uint64_t path, uint32_t j, uint32_t tag, uint64_t seed, double u[5])
+{
+    uint32_t w[4];
+    draw4w(path, j, tag, seed, w);
+    for (int i = 0; i < 4; ++i) u[i] = uniform_of(w[i]);
+    u[4] = uniform_of(spare_word(w));
+}
+
+/* The uniform of fine step n of a path of at least 4 steps (calls of its
+ * own counter path field, five uniforms each); u holds the current call's. */
+static double uniform_at(uint64_t path, int64_t n, uint32_t tag, uint64_t seed, double u[5])
+{
+    if (n % 5 == 0) draw5(path, (uint32_t)(n / 5), tag, seed, u);
+    return u[n % 5];
+}
+
 typedef struct { int prec, pbits, kahan, rv; } orc_variant;
 
 /* Two-way sample of level l: out = (P_fine, P_coarse, D); P_coarse = 0 at l = 0. */
@@ -537,7 +564,7 @@ static void twoway_one(int l, uint64_t path, const orc_variant *v, const orc_sde
     path_state fine, coarse;
     path_init(&fine, p, v->prec, v->pbits, v->kahan, delta_f, sq, 0);
     path_init(&coarse, p, v->prec, v->pbits, v->kahan, 2.0 * delta_f, sq, 1);
-    double zprev = 0.0, u[4];
+    double zprev = 0.0, u[5];
     uint32_t w[4];
     const int u16 = v->rv == ORC_RV_TABLE16;
     const int64_t per_call = u16 ? 8 : 4;                       /* halves or words of one call */
@@ -552,9 +579,11 @@ static void twoway_one(int l, uint64_t path, const orc_variant *v, const orc_sde
             uint32_t word = w[(q >> 1) & 3];
             uint32_t h = (q & 1) ? word >> 16 : word & 0xFFFFu;
             z = table_icdf(uniform16_of(h), table, &fine.m);
-        } else {
+        } else if (S > 1) {
             if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);
             z = rv_of(u[q & 3], v->rv, table, net, &fine.m);
+        } else {
+            z = rv_of(uniform_at(path, n, tag, seed, u), v->rv, table, net, &fine.m);
         }
         path_step(&fine, z);
         if (l > 0 && (n & 1)) path_step(&coarse, round_p(zprev + z, &coarse.m));
@@ -582,15 +611,21 @@ static void fourway_one(int l, uint64_t path, const orc_variant *hat, const orc_
     path_init(&hc, p, hat->prec, hat->pbits, hat->kahan, 2.0 * delta_f, sq, 1);
     path_init(&bf, p, bar->prec, bar->pbits, bar->kahan, delta_f, sq, 0);
     path_init(&bc, p, bar->prec, bar->pbits, bar->kahan, 2.0 * delta_f, sq, 1);
-    double zh_prev = 0.0, zb_prev = 0.0, u[4];
+    double zh_prev = 0.0, zb_prev = 0.0, u[5];
     const int shared = l <= 1;
     const uint64_t cpath = shared ? path >> 1 : path;
     const int64_t off = shared ? (int64_t)(path & 1) << l : 0;   /* see draw4w */
     for (int64_t n = 0; n < nf; ++n) {
         const int64_t q = off + n;
-        if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);
-        double zh = rv_of(u[q & 3], hat->rv, table, net, &hf.m);
-        double zb = rv_of(u[q & 3], bar->rv, table, net, &bf.m);
+        double un;
+        if (shared) {
+            if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);
+            un = u[q & 3];
+        } else {
+            un = uniform_at(path, n, tag, seed, u);
+        }
+        double zh = rv_of(un, hat->rv, table, net, &hf.m);
+        double zb = rv_of(un, bar->rv, table, net, &bf.m);
         path_step(&hf, zh);
         path_step(&bf, zb);
         if (l > 0 && (n & 1)) {
@@ -680,7 +715,7 @@ void orc_rounding_pairs(int l, uint64_t N, uint64_t path_offset, const int *var,
         path_state hi, lo;
         path_init(&hi, p, ORC_F64, 53, 0, delta_f, sq, 0);
         path_init(&lo, p, v.prec, v.pbits, v.kahan, delta_f, sq, 0);
-        double u[4];
+        double u[5];
         rmode exact = mode_of(ORC_F64, 0);
         const uint64_t path = path_offset + (uint64_t)i;
         const uint64_t S = nf < 4 ? (uint64_t)(4 / nf) : 1;          /* two-way layout, see draw4w */
@@ -688,8 +723,14 @@ void orc_rounding_pairs(int l, uint64_t N, uint64_t path_offset, const int *var,
         const int64_t off = (int64_t)(path % S) * nf;
         for (int64_t n = 0; n < nf; ++n) {
             const int64_t q = off + n;
-            if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);
-            double z64 = rv_of(u[q & 3], v.rv, table, &net, &exact);
+            double un;
+            if (S > 1) {
+                if (n == 0 || (q & 3) == 0) draw4(cpath, (uint32_t)(q >> 2), tag, seed, u);
+                un = u[q & 3];
+            } else {
+                un = uniform_at(path, n, tag, seed, u);
+            }
+            double z64 = rv_of(un, v.rv, table, &net, &exact);
             path_step(&hi, z64);
             path_step(&lo, round_p(z64, &lo.m));
         }

@@ -132,6 +132,34 @@ def test_level2_coarse_uses_pairwise_sums():
     assert abs(out[0] - xf) < 1e-14 and abs(out[1] - xc) < 1e-14
 
 
+def test_level3_five_uniforms_per_call_by_hand():
+    # l = 3: 8 fine steps from the path's own calls, five uniforms each: the
+    # four words, then the spare word (the low bytes of x, y, z as bits
+    # 8..15, 16..23, 24..31); steps 0..4 from call 0, steps 5..7 from the
+    # words 0..2 of call 1
+    mu, sigma = 0.07, 0.3
+    sde = O.gbm(mu=mu, sigma=sigma, payoff=O.PAYOFF_X)
+    tag = O.make_tag(O.KIND_STD, 3)
+    path = 5
+    c0 = O.philox4x32_10(O.counters([path], 0, tag), O.seed_key(SEED))[0].astype(np.uint64)
+    c1 = O.philox4x32_10(O.counters([path], 1, tag), O.seed_key(SEED))[0]
+    spare = ((c0[0] & 0xFF) << 8) | ((c0[1] & 0xFF) << 16) | ((c0[2] & 0xFF) << 24)
+    words = [int(x) for x in c0] + [int(spare)] + [int(x) for x in c1[:3]]
+    z = O.ndtri(O.uniforms(np.array(words, dtype=np.uint32)))
+    d = 0.125
+    xf = 1.0
+    for k in range(8):
+        xf = xf + (mu * d * xf + sigma * math.sqrt(d) * xf * z[k])
+    xc = 1.0
+    for k in range(4):
+        xc = xc + (mu * 2 * d * xc + sigma * math.sqrt(d) * xc * (z[2 * k] + z[2 * k + 1]))
+    out = O.twoway_paths(3, [path], O.variant(), sde, SEED, tag)[0]
+    assert abs(out[0] - xf) < 1e-14 and abs(out[1] - xc) < 1e-14
+    # the four-way paths use the same uniforms (hat: exact normals)
+    four = O.fourway_paths(3, [path], O.variant(), O.variant(rv=O.RV_TABLE), sde, SEED, tag)[0]
+    assert four[0] == out[0] and four[1] == out[1]
+
+
 def test_ou_mean_reversion_closed_form():
     # Euler OU: E X_{n+1} = m + (1 - theta delta)(E X_n - m); Var via (1 - theta delta)^2 V + s^2 delta
     theta, m, s, l = 2.0, 0.5, 0.4, 4
