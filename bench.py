@@ -42,7 +42,9 @@ WORKLOAD = "GBM call, levels 0..12, N=2^20 per level, two-way + four-way, FP16+K
 # estimator), counted from the method's operations in their minimal form on
 # this ISA (a wide 32x32 multiply and a three-input XOR count one each;
 # binary16 work per f16x2 operation, i.e. half per sample):
-#   Philox (1/4 call x 10 rounds x (2 multiplies + 2 XOR))      10
+#   Philox (1/5 call x (10 rounds x (2 multiplies + 2 XOR) + 2 byte
+#     permutes for the call's fifth uniform); the levels 0..2 of the
+#     workload, 0.1 % of its path-steps, take 1/4 call)            8.4
 #   uniform and mirror (funnel shift, three adds)                 4
 #   table normal (exponent, lookup, v -> f16, mul, add, sign)     4
 #   fine Euler + Kahan (8 f16x2 ops per pair)                     4
@@ -50,8 +52,8 @@ WORKLOAD = "GBM call, levels 0..12, N=2^20 per level, two-way + four-way, FP16+K
 #   four-way only: exact normal in FP32 (binade lookup, local
 #     variable, 7 FMA Horner, centring, sign)                    14
 #   four-way only: hat fine + coarse Euler + Kahan in FP32       12.5
-OPS_FOURWAY_F16K_TABLE = 50.75
-OPS_TWOWAY_F16K_TABLE = 24.25
+OPS_FOURWAY_F16K_TABLE = 49.15
+OPS_TWOWAY_F16K_TABLE = 22.65
 # DRAM bytes (read + write) of the timed four-way batched launch over levels
 # 0..12 at N = 2^20, from an ncu capture of the bench command
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass): the descriptors

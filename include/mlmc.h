@@ -23,11 +23,14 @@
  *
  * Random numbers.  Philox4x32-10 (Salmon et al., SC'11; the paper names no
  * generator).  Counter (path lo32, path hi32, j, tag), key (seed lo32, seed
- * hi32); fine step n of a path uses word n mod 4 of call j = n / 4;
- * tag = kind | level << 8 | set << 16 with kind 0 = standard two-way with
- * exact normals, 1 = two-way with approximate normals, 2 = four-way.  A word
- * w becomes the uniform u = (2 (w >> 9) + 1) 2^-24 (Sec. 3: Z_n = Phi^-1(U_n)
- * and Z~_n = Phi~^-1(U_n) share U_n).  Coarsest levels: a two-way path of
+ * hi32); tag = kind | level << 8 | set << 16 with kind 0 = standard two-way
+ * with exact normals, 1 = two-way with approximate normals, 2 = four-way.  A
+ * word w becomes the uniform u = (2 (w >> 9) + 1) 2^-24 (Sec. 3: Z_n =
+ * Phi^-1(U_n) and Z~_n = Phi~^-1(U_n) share U_n).  As a uniform reads only a
+ * word's top 23 bits, a call (x, y, z, w) gives five: its four words, then
+ * the spare word whose bits 8..15, 16..23, 24..31 are the low bytes of x, y
+ * and z.  Fine step n of a path of 2^l >= 4 steps uses uniform n mod 5 of
+ * call j = n / 5 (0..3 the words, 4 the spare).  Coarsest levels: a two-way path of
  * level l needs 2^l words (halves with TABLE16); while that is fewer than a
  * call holds (4 words, 8 halves), the S = 4 / 2^l (8 / 2^l) paths S k ..
  * S k + S - 1 share call 0 of counter path field k, path p taking the words
@@ -66,8 +69,8 @@ typedef enum { MLMC_PAYOFF_X = 0, MLMC_PAYOFF_CALL = 1 } mlmc_payoff;
 typedef enum { MLMC_F32 = 0, MLMC_F16 = 1, MLMC_BF16 = 2 } mlmc_prec;
 /* How the normals of the approximate paths are formed from the Philox words
  * (counter (path lo32, path hi32, j, tag), key = seed; 24-bit uniform
- * u = (2 (w >> 9) + 1) 2^-24 from a word w; fine step n uses word n mod 4 of
- * call j = n / 4):
+ * u = (2 (w >> 9) + 1) 2^-24 from a word w; five uniforms per call, as
+ * above):
  *   EXACT    Phi^-1(u) in FP32 (no approximation beyond binary32: on each
  *            binade of v = min(u, 1-u) a degree-7 polynomial of the
  *            binade's local variable times (v - 1/2), built on the device

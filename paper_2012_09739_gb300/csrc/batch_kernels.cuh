@@ -58,7 +58,7 @@ constexpr int SEQ_MIN_LEVEL = 10;
 
 template <int P>
 struct SeqScratch {
-    uint32_t w[2][32];         // the block's Philox words of paths p0, p1
+    uint32_t w[2][40];         // the block's uniforms' words of paths p0, p1 (five per call, or halves)
     Pair<P> zb[32];            // approximate normals of the 32 steps (both paths)
     Pair<P_F32> zh[32];        // exact normals (four-way)
 };
@@ -69,7 +69,10 @@ __device__ void simulate_pair_seq(const LevelArgs &a, const PhiloxKeys &K, const
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nf = 1u << a.l;
     const uint64_t p0 = a.path_offset + 2 * g, p1 = p0 + 1;
-    // 16-bit uniforms on a two-way path: two steps per word, 4 calls per block
+    // 16-bit uniforms on a two-way path: two steps per word, 4 calls per
+    // block; otherwise five uniforms per call, calls c0 .. c0 + 7 with
+    // c0 = 32 blk / 5 cover the block's steps (its first step is uniform
+    // 32 blk - 5 c0 of call c0)
     constexpr bool U16 = ICDF == ICDF_TABLE16 && MODE == MODE_TWO;
     constexpr uint32_t CALLS = U16 ? 4u : 8u;
     PathPair<P, KAHAN, SDE> fine, coarse;
@@ -83,15 +86,17 @@ __device__ void simulate_pair_seq(const LevelArgs &a, const PhiloxKeys &K, const
     Pair<P> zprev;
     Pair<P_F32> zhprev;
     for (uint32_t blk = 0; blk < (nf >> 5); ++blk) {
+        const uint32_t c0 = U16 ? blk * CALLS : (32u * blk) / 5u;
         if (lane < 2 * CALLS) {
             const uint64_t path = lane < CALLS ? p0 : p1;
-            const uint32_t j = blk * CALLS + (lane % CALLS);
+            const uint32_t j = c0 + (lane % CALLS);
             const uint4 r = philox4x32_10(make_uint4((uint32_t)path, (uint32_t)(path >> 32), j, a.tag), K);
-            uint32_t *dst = &sc.w[lane < CALLS ? 0 : 1][4 * (lane % CALLS)];
+            uint32_t *dst = &sc.w[lane < CALLS ? 0 : 1][(U16 ? 4u : 5u) * (lane % CALLS)];
             dst[0] = r.x;
             dst[1] = r.y;
             dst[2] = r.z;
             dst[3] = r.w;
+            if (!U16) dst[4] = spare_word(r);
         }
         __syncwarp();
         if constexpr (U16) {
@@ -100,7 +105,8 @@ __device__ void simulate_pair_seq(const LevelArgs &a, const PhiloxKeys &K, const
             const uint32_t f1 = (lane & 1) ? half16_bits<true>(w1) : half16_bits<false>(w1);
             sc.zb[lane] = table_pair<P, true>(tab, f0, f1, mirrored_v16(f0), mirrored_v16(f1));
         } else {
-            const uint32_t w0 = sc.w[0][lane], w1 = sc.w[1][lane];
+            const uint32_t k = 32u * blk + lane - 5u * c0;
+            const uint32_t w0 = sc.w[0][k], w1 = sc.w[1][k];
             sc.zb[lane] = icdf_pair<P, ICDF>(tab, mlp, w0, w1);
             if (MODE == MODE_FOUR) sc.zh[lane] = Pair<P_F32>::of2(exact_z(tab, w0), exact_z(tab, w1));
         }

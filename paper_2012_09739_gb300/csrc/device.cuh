@@ -61,6 +61,14 @@ __device__ __forceinline__ uint32_t word(const uint4 &w, int q) {
     return q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
 }
 
+// The fifth uniform of a Philox call (x, y, z, w): a uniform reads a word's
+// top 23 bits, so the low bytes of x, y and z, placed as bits 8..15, 16..23
+// and 24..31 of a spare word (two byte permutes; its bits 0..7 are not
+// read), give one more from bits no other uniform of the call reads.
+__device__ __forceinline__ uint32_t spare_word(const uint4 &r) {
+    return __byte_perm(__byte_perm(r.x, r.y, 0x0400u), r.z, 0x4210u);
+}
+
 // u = (2 (w >> 9) + 1) 2^-24, exact in binary32.
 __device__ __forceinline__ float uniform_of(uint32_t w) {
     return __fsub_rn(__uint_as_float((w >> 9) | 0x3F800000u), 0x1.fffffep-1f);

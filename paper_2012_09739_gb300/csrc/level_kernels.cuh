@@ -198,7 +198,6 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const PhiloxKe
                                               const float *mlp, uint64_t g, float &d0, float &d1, float *out0,
                                               float *out1) {
     const uint32_t nf = 1u << a.l;
-    const uint32_t ncalls = (nf + 3u) >> 2;
     const uint64_t p0 = a.path_offset + 2 * g, p1 = p0 + 1;
     PathPair<P, KAHAN, SDE> fine, coarse;
     fine.template init<false>(a, false);
@@ -265,21 +264,47 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const PhiloxKe
             halves(r0.z, r1.z, 4);
             halves(r0.w, r1.w, 6);
         }
+    } else if (nf <= 2) {
+        const uint4 ra = call_of(c0, 0);
+        const uint4 rb = c1 == c0 ? ra : call_of(c1, 0);
+        body(word(ra, (int)o0), word(rb, (int)o1), 0);
+        if (nf == 2) body(word(ra, (int)o0 + 1), word(rb, (int)o1 + 1), 1);
     } else {
-        if (nf <= 2) {
-            const uint4 ra = call_of(c0, 0);
-            const uint4 rb = c1 == c0 ? ra : call_of(c1, 0);
-            body(word(ra, (int)o0), word(rb, (int)o1), 0);
-            if (nf == 2) body(word(ra, (int)o0 + 1), word(rb, (int)o1 + 1), 1);
+        // five uniforms per call (the four words, then the spare word): full
+        // blocks of 10 fine steps from two calls, then the remaining 2, 4, 6
+        // or 8 steps (2^l mod 10) from one or two more
+        const uint32_t blocks = nf / 10u, rest = nf - 10u * blocks;
+        for (uint32_t m = 0; m < blocks; ++m) {
+            const uint4 a0 = call_of(p0, 2 * m), a1 = call_of(p1, 2 * m);
+            body(a0.x, a1.x, 0);
+            body(a0.y, a1.y, 1);
+            body(a0.z, a1.z, 2);
+            body(a0.w, a1.w, 3);
+            body(spare_word(a0), spare_word(a1), 4);
+            const uint4 b0 = call_of(p0, 2 * m + 1), b1 = call_of(p1, 2 * m + 1);
+            body(b0.x, b1.x, 5);
+            body(b0.y, b1.y, 6);
+            body(b0.z, b1.z, 7);
+            body(b0.w, b1.w, 8);
+            body(spare_word(b0), spare_word(b1), 9);
         }
-        const uint32_t ncalls_full = nf <= 2 ? 0u : ncalls;
-        for (uint32_t j = 0; j < ncalls_full; ++j) {
-            const uint4 r0 = call_of(p0, j);
-            const uint4 r1 = call_of(p1, j);
-            body(r0.x, r1.x, 0);
-            body(r0.y, r1.y, 1);
-            body(r0.z, r1.z, 2);
-            body(r0.w, r1.w, 3);
+        if (rest) {
+            const uint4 a0 = call_of(p0, 2 * blocks), a1 = call_of(p1, 2 * blocks);
+            body(a0.x, a1.x, 0);
+            body(a0.y, a1.y, 1);
+            if (rest >= 4) {
+                body(a0.z, a1.z, 2);
+                body(a0.w, a1.w, 3);
+            }
+            if (rest >= 6) {
+                body(spare_word(a0), spare_word(a1), 4);
+                const uint4 b0 = call_of(p0, 2 * blocks + 1), b1 = call_of(p1, 2 * blocks + 1);
+                body(b0.x, b1.x, 5);
+                if (rest == 8) {
+                    body(b0.y, b1.y, 6);
+                    body(b0.z, b1.z, 7);
+                }
+            }
         }
     }
 
