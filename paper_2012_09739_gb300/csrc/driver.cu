@@ -69,47 +69,47 @@ struct CostRow {
     float ps[11];
 };
 const CostRow kCost[] = {
-    {0, MLMC_F32, 0, MLMC_ICDF_EXACT, 0, {2.92, 5.136, 7.495, 13.22, 25.12, 49.17, 93.64, 191.1, 358, 699.1, 1379}},
-    {0, MLMC_F32, 1, MLMC_ICDF_EXACT, 0, {3.054, 5.108, 8.007, 14.2, 26.66, 51.66, 101.4, 200.6, 387.3, 751.2, 1485}},
-    {0, MLMC_F16, 1, MLMC_ICDF_TABLE, 0, {2.615, 4.299, 6.114, 10.53, 19.87, 37.25, 74.39, 144.1, 272.2, 546.1, 1058}},
-    {0, MLMC_F16, 0, MLMC_ICDF_TABLE, 0, {2.603, 4.129, 5.82, 9.676, 17.65, 34.82, 67.67, 134.2, 251.5, 478.3, 972.9}},
-    {0, MLMC_F32, 0, MLMC_ICDF_TABLE, 0, {2.45, 4.176, 6.151, 10.47, 19.7, 37.5, 71.17, 140.4, 262.3, 507.6, 997.8}},
-    {0, MLMC_F16, 1, MLMC_ICDF_TABLE16, 0, {2.02, 3.38, 6.64, 8.407, 15.3, 30.21, 56.89, 117.8, 209.5, 403.9, 785.4}},
-    {0, MLMC_F16, 0, MLMC_ICDF_TABLE16, 0, {2.025, 3.244, 6.088, 8.042, 13.89, 26.03, 51.15, 102.2, 181.2, 346.4, 676.8}},
-    {0, MLMC_F32, 0, MLMC_ICDF_TABLE16, 0, {2.039, 3.239, 7.098, 8.886, 16.43, 30.91, 59.26, 114.8, 212.5, 409.8, 803.8}},
-    {0, MLMC_F16, 1, MLMC_ICDF_CUBIC, 0, {2.737, 4.571, 6.817, 12.18, 23.39, 45.31, 86.13, 172.2, 325.6, 635.9, 1268}},
-    {0, MLMC_F32, 0, MLMC_ICDF_CUBIC, 0, {2.741, 4.629, 7, 12.25, 22.9, 45.15, 88.56, 170.7, 333.4, 640, 1244}},
-    {1, MLMC_F16, 1, MLMC_ICDF_TABLE, 0, {5.148, 6.707, 9.881, 17.74, 33.85, 66.06, 130.6, 258.2, 501.1, 987.7, 1961}},
-    {1, MLMC_F16, 0, MLMC_ICDF_TABLE, 0, {5.06, 6.495, 9.593, 17.13, 33.53, 65.27, 125.8, 246.7, 478.8, 941.3, 1868}},
-    {1, MLMC_F32, 0, MLMC_ICDF_TABLE, 0, {5.286, 7.073, 10.16, 17.98, 33.98, 66.01, 130.2, 258.5, 499.4, 981.8, 1979}},
-    {1, MLMC_F16, 1, MLMC_ICDF_TABLE16, 0, {5.194, 6.908, 10.45, 18.72, 35.69, 69.73, 137.5, 273.2, 530.2, 1042, 2065}},
-    {1, MLMC_F16, 0, MLMC_ICDF_TABLE16, 0, {5.121, 6.708, 9.904, 17.98, 35.25, 68.02, 131.6, 260.4, 505, 995, 1975}},
-    {1, MLMC_F32, 0, MLMC_ICDF_TABLE16, 0, {5.367, 7.162, 10.57, 19.25, 37.03, 72.16, 143.9, 278.7, 540.8, 1065, 2115}},
-    {1, MLMC_F16, 1, MLMC_ICDF_CUBIC, 0, {5.212, 6.8, 10.55, 19.09, 37.15, 71.88, 144.7, 281.9, 548.6, 1082, 2151}},
-    {1, MLMC_F32, 0, MLMC_ICDF_CUBIC, 0, {5.621, 7.436, 10.69, 19.43, 38.13, 74.31, 142.3, 281.6, 548.1, 1077, 2137}},
-    {0, MLMC_F32, 0, MLMC_ICDF_EXACT, 1, {3.165, 5.362, 8.385, 14.92, 27.91, 54.05, 106.1, 209.4, 402.7, 789.3, 1563}},
-    {0, MLMC_F32, 1, MLMC_ICDF_EXACT, 1, {3.21, 5.56, 8.984, 16.14, 30.48, 59.17, 119.4, 236.6, 450.5, 870.5, 1727}},
-    {0, MLMC_F16, 1, MLMC_ICDF_TABLE, 1, {2.722, 4.553, 6.793, 12.43, 22.88, 44.12, 84.67, 169.3, 322, 623, 1229}},
-    {0, MLMC_F32, 0, MLMC_ICDF_TABLE, 1, {2.646, 4.766, 7.185, 12.6, 23, 45.75, 86.14, 176.1, 333.4, 648.8, 1261}},
-    {0, MLMC_F16, 1, MLMC_ICDF_TABLE16, 1, {2.087, 3.47, 6.879, 9.908, 18.89, 35.26, 71.96, 137.2, 259.2, 502.3, 988.2}},
-    {0, MLMC_F32, 0, MLMC_ICDF_TABLE16, 1, {2.141, 3.562, 8.801, 10.58, 19.94, 36.8, 74.39, 141.9, 268.9, 512, 1024}},
-    {1, MLMC_F16, 1, MLMC_ICDF_TABLE, 1, {5.179, 6.921, 11.42, 20.86, 41.59, 79.04, 158.5, 310.9, 610.8, 1217, 2381}},
-    {1, MLMC_F32, 0, MLMC_ICDF_TABLE, 1, {5.453, 7.437, 11.43, 21.1, 41.8, 82.21, 157.1, 313.3, 606.5, 1197, 2378}},
-    {1, MLMC_F16, 1, MLMC_ICDF_TABLE16, 1, {5.441, 7.366, 11.92, 21.75, 43.43, 85.63, 165.8, 332.4, 637.9, 1260, 2499}},
-    {1, MLMC_F32, 0, MLMC_ICDF_TABLE16, 1, {5.636, 7.763, 12.22, 22.63, 44.02, 85.87, 164.7, 328.8, 639.4, 1260, 2504}},
+    {0, MLMC_F32, 0, MLMC_ICDF_EXACT, 0, {2.905, 4.894, 7.35, 13.36, 25.73, 47.68, 91.59, 176.4, 332.5, 643.8, 1265}},
+    {0, MLMC_F32, 1, MLMC_ICDF_EXACT, 0, {2.898, 5.071, 7.853, 14.25, 27.72, 51.59, 97.01, 192.7, 366.1, 711.2, 1402}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE, 0, {2.537, 4.038, 5.875, 10.53, 20.23, 36.8, 68.75, 134, 251.3, 479.1, 936.9}},
+    {0, MLMC_F16, 0, MLMC_ICDF_TABLE, 0, {2.521, 4.089, 5.62, 9.763, 18.62, 33.14, 62.98, 125.1, 226.2, 432.6, 839}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE, 0, {2.55, 4.346, 6.126, 10.68, 20.07, 36.35, 70, 134.4, 249.3, 477.1, 929.4}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE16, 0, {1.876, 3.101, 6.295, 8.559, 15.61, 29.74, 57.92, 116, 210.4, 400.3, 779.1}},
+    {0, MLMC_F16, 0, MLMC_ICDF_TABLE16, 0, {1.855, 3.002, 6.073, 7.893, 14.1, 26.97, 51.48, 100.5, 182.2, 345.1, 672.7}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE16, 0, {1.87, 3.114, 7.174, 8.713, 15.81, 30.05, 59.32, 114, 209.2, 401.3, 783.7}},
+    {0, MLMC_F16, 1, MLMC_ICDF_CUBIC, 0, {2.7, 4.4, 6.693, 12.12, 23.08, 42.68, 80.73, 159.2, 298.2, 577.3, 1133}},
+    {0, MLMC_F32, 0, MLMC_ICDF_CUBIC, 0, {2.695, 4.574, 6.756, 12.18, 23.39, 42.8, 79.94, 157, 293.4, 565.4, 1111}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE, 0, {4.264, 5.699, 9.583, 17.32, 37.09, 63.96, 125.7, 249, 475.2, 927.4, 1831}},
+    {1, MLMC_F16, 0, MLMC_ICDF_TABLE, 0, {4.305, 5.749, 9.116, 16.53, 34.18, 59.98, 118, 233.2, 441.8, 863.2, 1706}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE, 0, {4.356, 5.99, 9.739, 17.28, 36.09, 62.15, 123.4, 235.7, 451.4, 878.3, 1734}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE16, 0, {4.308, 5.961, 10.11, 18.41, 38.85, 67.89, 135, 265.5, 503.3, 994.2, 1950}},
+    {1, MLMC_F16, 0, MLMC_ICDF_TABLE16, 0, {4.37, 5.921, 9.582, 17.51, 37.21, 65.64, 125.5, 251, 475.2, 927.4, 1833}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE16, 0, {4.445, 6.172, 10.25, 18.52, 38.84, 67.52, 133.2, 260.2, 495.3, 967.7, 1911}},
+    {1, MLMC_F16, 1, MLMC_ICDF_CUBIC, 0, {4.273, 5.864, 10.32, 18.7, 39.64, 69.59, 136.3, 271.9, 521.2, 1029, 2018}},
+    {1, MLMC_F32, 0, MLMC_ICDF_CUBIC, 0, {4.397, 6.243, 10.29, 18.78, 39.37, 68.19, 135.1, 263.7, 508.2, 983.8, 1943}},
+    {0, MLMC_F32, 0, MLMC_ICDF_EXACT, 1, {3.018, 5.277, 7.961, 14.8, 29.18, 53.69, 104.6, 202.7, 383.5, 760.1, 1474}},
+    {0, MLMC_F32, 1, MLMC_ICDF_EXACT, 1, {2.998, 5.413, 8.666, 15.76, 30.76, 56.24, 108.4, 216, 411.8, 801.3, 1580}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE, 1, {2.584, 4.189, 6.611, 11.9, 23.21, 42.53, 80.71, 159.1, 301.2, 581.1, 1141}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE, 1, {2.698, 4.564, 6.774, 12.12, 23.4, 42.44, 80.83, 154.2, 291.9, 564.3, 1106}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE16, 1, {1.896, 3.291, 6.741, 9.915, 18.74, 35.74, 70.4, 138.4, 262.1, 497.7, 978.2}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE16, 1, {2, 3.582, 8.853, 10.27, 19, 36.51, 72.17, 139.1, 259, 498.5, 977.2}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE, 1, {4.473, 6.307, 10.88, 20.1, 44.37, 79.25, 154.8, 307.8, 585.1, 1142, 2268}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE, 1, {4.468, 6.591, 11.01, 20.31, 45.1, 78.09, 151.3, 305.4, 574.4, 1092, 2149}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE16, 1, {4.446, 6.435, 11.42, 21.1, 46.29, 83.48, 162.1, 325.6, 613.4, 1195, 2369}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE16, 1, {4.707, 6.978, 11.63, 21.5, 47.1, 82.82, 167.1, 337.4, 619.2, 1169, 2317}},
 };
 
 // The row of a term, or the nearest measured one: bfloat16 as binary16 (the
 // same packed arithmetic), the other Kahan setting, the Euler row for a
 // Milstein term; the network (MLP, a gather from its tabulated grid values)
 // as its table row times the measured ratio (binary16 + Kahan at l = 10 and
-// 12: four-way 1.73, two-way 3.2).
+// 12: four-way 1.81, two-way 3.55).
 double cost_ps(int four, int prec, int kahan, int icdf, int milstein, int l) {
     double factor = 1.0;
     if (prec == MLMC_BF16) prec = MLMC_F16;
     if (icdf == MLMC_ICDF_MLP) {
         icdf = MLMC_ICDF_TABLE;
-        factor = four ? 1.73 : 3.2;
+        factor = four ? 1.81 : 3.55;
     }
     const CostRow *row = nullptr;
     for (int pass = 0; pass < 4 && !row; ++pass) {
