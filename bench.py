@@ -57,10 +57,10 @@ OPS_TWOWAY_F16K_TABLE = 22.65
 # DRAM bytes (read + write) of the timed four-way batched launch over levels
 # 0..12 at N = 2^20, from an ncu capture of the bench command
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass): the descriptors
-# and the tables, 0.05 to 0.89 MB over the 33 launches captured (the tuner's
+# and the tables, 0.17 to 0.67 MB over the 33 launches captured (the tuner's
 # candidates, the replays), no writes (the group partials stay in L2).  The
 # traffic does not grow with the path-steps.
-TRAFFIC_FOURWAY_BYTES = 674816
+TRAFFIC_FOURWAY_BYTES = 167680
 
 
 def _env_rank():
