@@ -237,7 +237,9 @@ def grid_joint_moments(z, w, max_order=4):
 #     the run ends when the test holds and no term needs more samples;
 #   * per-level choice (prec = -1): the candidates {binary16 + Kahan,
 #     binary16, binary32} nested pairs and the standard term alone, n0
-#     samples each in a round of their own; the level keeps the nested pair
+#     samples each in a round of their own (the initial levels' candidates
+#     all in one round, each level then chosen in order of l, the rules
+#     below applied at the choice); the level keeps the nested pair
 #     with the smallest sqrt(v C) + sqrt(V C), or the standard term if its
 #     sqrt(v^ c^) is smaller still; binary16 candidates stop once a level has
 #     chosen binary32 or the standard term; without trial_all, once two
@@ -307,6 +309,8 @@ def adaptive_mlmc(eps, draw, cost, *, nested, prec=F16, kahan=1, icdf=1, n0=1000
     def vc(t):
         return t.V() * cost(t.key)
 
+    variants = [(F16, 1), (F16, 0), (F32, 0)]     # the nested pairs' candidates CH_F16K, CH_F16, CH_F32
+
     def add_level(l):
         if not nested:
             t = _Term(l, 0, F32, kahan, EXACT)
@@ -330,14 +334,37 @@ def adaptive_mlmc(eps, draw, cost, *, nested, prec=F16, kahan=1, icdf=1, n0=1000
                 t.dn = 0 if t.off else _round8(n0)
             terms.extend(pair)
             return
-        variants = [(F16, 1), (F16, 0), (F32, 0)]
-        first = 2 if half_done[0] else 0
+        cands, standard = trial_terms(l, 2 if half_done[0] else 0)
+        run([t for c in sorted(cands) for t in cands[c]] + [standard])
+        choose(l, cands, standard)
+
+    def trial_terms(l, first):
+        """The candidates of level l (the nested pairs from variant `first`
+        on, and the standard term), n0 samples each."""
         cands = {c: (_Term(l, 0, *variants[c], icdf), _Term(l, 1, *variants[c], icdf)) for c in range(first, 3)}
         standard = _Term(l, 0, F32, 1, EXACT)
-        trial = [t for c in range(first, 3) for t in cands[c]] + [standard]
-        for t in trial:
-            t.dn = _round8(n0)
-        run(trial)
+        for c in cands:
+            for t in cands[c]:
+                t.dn = _round8(n0)
+        standard.dn = _round8(n0)
+        return cands, standard
+
+    def choose(l, cands, standard):
+        """The level's variant from its sampled candidates (levels coarser
+        than l already chosen): the carried binary32 choice where two
+        coarser levels agree on it (its candidate's samples are its
+        warm-up), else the smallest score among the variants still allowed
+        (binary32 only once a coarser level chose binary32 or the standard
+        term), or the standard term if cheaper still."""
+        carried = choice.get(l - 1) if l >= 2 and choice.get(l - 1) == choice.get(l - 2) else None
+        if not trial_all and carried in (CH_F32, CH_STANDARD):
+            choice[l] = carried
+            if carried == CH_STANDARD:
+                terms.extend([standard, _Term(l, 1, F32, 0, icdf, off=True)])
+            else:
+                terms.extend(cands[CH_F32])
+            return
+        first = 2 if half_done[0] else min(cands)
         best, best_score = first, 1e300
         for c in range(first, 3):
             score = math.sqrt(vc(cands[c][0])) + math.sqrt(vc(cands[c][1]))
@@ -386,8 +413,16 @@ def adaptive_mlmc(eps, draw, cost, *, nested, prec=F16, kahan=1, icdf=1, n0=1000
         return need
 
     L = min_levels - 1
-    for l in range(L + 1):
-        add_level(l)
+    if nested and prec == -1:
+        # the initial levels' candidates in one round, then each level's
+        # choice in order of l
+        batch = [(l, *trial_terms(l, 0)) for l in range(L + 1)]
+        run([t for _, cands, standard in batch for t in [x for c in sorted(cands) for x in cands[c]] + [standard]])
+        for l, cands, standard in batch:
+            choose(l, cands, standard)
+    else:
+        for l in range(L + 1):
+            add_level(l)
     converged = False
     while True:
         run(terms)

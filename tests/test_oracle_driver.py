@@ -98,7 +98,7 @@ def test_per_level_choice_follows_the_scores_and_stops_trying_once_settled():
     small four-way variance: 0.148 and 0.153 against binary32's 0.158) and
     binary32 from level 2 on (the growing binary16 floor: 0.164 against
     0.158); after two binary32 levels finer levels take binary32 without
-    candidates."""
+    candidates.  The initial levels' candidates are drawn in one round."""
     m0, v0 = 0.3, 0.04
 
     def stats(k):
@@ -123,10 +123,19 @@ def test_per_level_choice_follows_the_scores_and_stops_trying_once_settled():
     assert all(c == mlmc.CH_F32 for c in ch[2:])
     # candidates (more than one variant of a level in one round) only while unsettled
     def tried(rounds):
-        # a candidate round: all draws at one level, more than one variant
-        return {rnd[0][0][0] for rnd in rounds
-                if len({q[0][0] for q in rnd}) == 1 and len({q[0][2:] for q in rnd}) > 1}
+        out = set()
+        for rnd in rounds:
+            by_level = {}
+            for q in rnd:
+                by_level.setdefault(q[0][0], set()).add(q[0][2:])
+            out |= {l for l, v in by_level.items() if len(v) > 1}
+        return out
     assert r["levels"] > 5 and tried(syn.rounds) == {0, 1, 2, 3}
+    # the initial levels' candidates share the first round: every variant of
+    # levels 0..2 and their standard terms
+    first = syn.rounds[0]
+    assert {q[0][0] for q in first} == {0, 1, 2} and len(first) == 3 * 7
+    assert tried(syn.rounds[1:]) == {3}
     # with trial_all every level is tried
     syn2 = Synthetic(stats)
     r2 = mlmc.adaptive_mlmc(EPS, syn2, cost, nested=True, prec=-1, icdf=1, n0=64, trial_all=True)
