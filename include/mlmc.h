@@ -365,7 +365,8 @@ typedef struct {
      * consecutive levels have chosen the same FP32 variant (nested FP32 or
      * the standard term), then give finer levels that variant without
      * candidate samples; 1 = measure every candidate on every level (the
-     * full per-level efficiency map, at the cost of the discarded samples). */
+     * full per-level efficiency map, at the cost of the discarded samples).
+     * The candidates of the min_levels initial levels share one round. */
     int32_t trial_all;
     int32_t trace_cap;    /* capacity of trace (records); 0: no trace */
     mlmc_round_record *trace;   /* optional caller-owned host array: every draw of the run, in order */

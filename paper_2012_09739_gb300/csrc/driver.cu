@@ -242,11 +242,6 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         ++rounds;
         return MLMC_OK;
     };
-    // Runs n0 samples of each candidate term at once.
-    auto trial = [&](std::vector<Term> &cand) -> mlmc_status {
-        for (Term &t : cand) t.dn = round8(o->n0);
-        return run_round(cand, 0);
-    };
     // The records of the candidate terms of the last trial that the level
     // kept become kept = 1.
     auto keep_trial_records = [&](const std::vector<Term> &kept_terms) {
@@ -268,6 +263,85 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
         Term slot{l, 1, MLMC_F32, 0, o->icdf};
         slot.off = true;
         terms.push_back(slot);
+    };
+    // Candidates of level l (two-way, four-way) x {FP16 + Kahan, FP16, FP32},
+    // plus the standard FP32 exact-normal two-way term (with Kahan, the
+    // four-way hat paths' arithmetic): the efficiency reference and a
+    // candidate.  Seven terms in that order; those from variant `first` on
+    // and the standard term draw n0 samples.  Once a level has chosen FP32
+    // (or the standard estimator) the binary16 candidates are not tried
+    // again: their rounding variance does not decay with delta while the
+    // level variance does (Sec. 3), so they only lose further on finer
+    // levels.
+    const int cp[3] = {MLMC_F16, MLMC_F16, MLMC_F32}, ck[3] = {1, 0, 0};
+    auto candidates = [&](int l, int first) {
+        std::vector<Term> cand;
+        for (int c = 0; c < 3; ++c) {
+            cand.push_back(Term{l, 0, cp[c], ck[c], o->icdf});
+            cand.push_back(Term{l, 1, cp[c], ck[c], o->icdf});
+        }
+        cand.push_back(Term{l, 0, MLMC_F32, 1, MLMC_ICDF_EXACT});
+        for (size_t i = 0; i < cand.size(); ++i)
+            if (i >= (size_t)(2 * first)) cand[i].dn = round8(o->n0);
+        return cand;
+    };
+    // The level's choice from its sampled candidates (coarser levels already
+    // chosen): the carried FP32 choice where two coarser levels agree on it
+    // (its candidate's samples are its warm-up), else the smallest score
+    // sqrt(v c) + sqrt(V C) among the variants still allowed, or the
+    // standard term if cheaper still.
+    auto choose_level = [&](int l, std::vector<Term> cand) {
+        auto vc = [&](const Term &t) { return t.var() * cost_of(t, mil); };
+        auto steps = [&](const Term &t) { return (double)t.n * ldexp(1.0, l); };
+        for (const Term &t : cand) discarded_steps += steps(t);
+        if (!o->trial_all && l >= 2 && lvl_choice[l - 1] == lvl_choice[l - 2] &&
+            (lvl_choice[l - 1] == CH_F32 || lvl_choice[l - 1] == CH_STANDARD)) {
+            lvl_choice[l] = lvl_choice[l - 1];
+            if (lvl_choice[l] == CH_STANDARD) {
+                push_standard(l, cand[6]);
+                keep_trial_records({cand[6]});
+                discarded_steps -= steps(cand[6]);
+            } else {
+                lvl_prec[l] = MLMC_F32;
+                lvl_kahan[l] = 0;
+                terms.push_back(cand[4]);
+                terms.push_back(cand[5]);
+                keep_trial_records({cand[4], cand[5]});
+                discarded_steps -= steps(cand[4]) + steps(cand[5]);
+            }
+            return;
+        }
+        int first = 0;
+        while (first < 2 && cand[2 * first].n == 0) ++first;
+        if (half_done) first = 2;
+        int best = first;
+        double best_score = 1e300;
+        for (int c = first; c < 3; ++c) {
+            const double score = sqrt(vc(cand[2 * c])) + sqrt(vc(cand[2 * c + 1]));
+            if (score < best_score) {
+                best_score = score;
+                best = c;
+            }
+        }
+        const double vc2 = vc(cand[2 * best]), vc4 = vc(cand[2 * best + 1]), vch = vc(cand[6]);
+        if (vch > 0.0 && vc2 > 0.0) lvl_eff[l] = vc2 / vch * pow(1.0 + sqrt(vc4 / vc2), 2.0);
+        if (vch > 0.0 && sqrt(vch) < best_score) {
+            // the standard estimator alone is cheaper for this level
+            lvl_choice[l] = CH_STANDARD;
+            half_done = true;
+            push_standard(l, cand[6]);
+            keep_trial_records({cand[6]});
+            discarded_steps -= steps(cand[6]);
+            return;
+        }
+        lvl_choice[l] = best;
+        lvl_prec[l] = cp[best];
+        lvl_kahan[l] = ck[best];
+        if (cp[best] == MLMC_F32) half_done = true;
+        terms.push_back(cand[2 * best]);
+        terms.push_back(cand[2 * best + 1]);
+        keep_trial_records({cand[2 * best], cand[2 * best + 1]});
+        discarded_steps -= steps(cand[2 * best]) + steps(cand[2 * best + 1]);
     };
     auto add_level = [&](int l) -> mlmc_status {
         if (!nested) {
@@ -299,60 +373,33 @@ static mlmc_status run_impl(double eps, const mlmc_sde_params *p, const mlmc_run
             }
             return MLMC_OK;
         }
-        // candidates (two-way, four-way) x {FP16 + Kahan, FP16, FP32}, plus the
-        // standard FP32 exact-normal two-way term (with Kahan, the four-way
-        // hat paths' arithmetic): the efficiency reference and a candidate.
-        // Once a level has chosen FP32 (or the standard estimator) the
-        // binary16 candidates are not tried again: their rounding variance
-        // does not decay with delta while the level variance does (Sec. 3),
-        // so they only lose further on finer levels.
-        const int cp[3] = {MLMC_F16, MLMC_F16, MLMC_F32}, ck[3] = {1, 0, 0};
-        const int first = half_done ? 2 : 0;
-        std::vector<Term> cand;
-        for (int c = 0; c < 3; ++c) {
-            cand.push_back(Term{l, 0, cp[c], ck[c], o->icdf});
-            cand.push_back(Term{l, 1, cp[c], ck[c], o->icdf});
-        }
-        cand.push_back(Term{l, 0, MLMC_F32, 1, MLMC_ICDF_EXACT});
-        std::vector<Term> tried(cand.begin() + 2 * first, cand.end());
-        mlmc_status r = trial(tried);
+        std::vector<Term> cand = candidates(l, half_done ? 2 : 0);
+        std::vector<Term> tried;
+        for (const Term &t : cand)
+            if (t.dn) tried.push_back(t);
+        mlmc_status r = run_round(tried, 0);
         if (r) return r;
-        std::copy(tried.begin(), tried.end(), cand.begin() + 2 * first);
-        auto vc = [&](const Term &t) { return t.var() * cost_of(t, mil); };
-        int best = first;
-        double best_score = 1e300;
-        for (int c = first; c < 3; ++c) {
-            const double score = sqrt(vc(cand[2 * c])) + sqrt(vc(cand[2 * c + 1]));
-            if (score < best_score) {
-                best_score = score;
-                best = c;
-            }
-        }
-        const double vc2 = vc(cand[2 * best]), vc4 = vc(cand[2 * best + 1]), vch = vc(cand[6]);
-        if (vch > 0.0 && vc2 > 0.0) lvl_eff[l] = vc2 / vch * pow(1.0 + sqrt(vc4 / vc2), 2.0);
-        for (int c = first; c < 3; ++c) discarded_steps += (double)(cand[2 * c].n + cand[2 * c + 1].n) * ldexp(1.0, l);
-        discarded_steps += (double)cand[6].n * ldexp(1.0, l);
-        if (vch > 0.0 && sqrt(vch) < best_score) {
-            // the standard estimator alone is cheaper for this level
-            lvl_choice[l] = CH_STANDARD;
-            half_done = true;
-            push_standard(l, cand[6]);
-            keep_trial_records({cand[6]});
-            discarded_steps -= (double)cand[6].n * ldexp(1.0, l);
-            return MLMC_OK;
-        }
-        lvl_choice[l] = best;
-        lvl_prec[l] = cp[best];
-        lvl_kahan[l] = ck[best];
-        if (cp[best] == MLMC_F32) half_done = true;
-        terms.push_back(cand[2 * best]);
-        terms.push_back(cand[2 * best + 1]);
-        keep_trial_records({cand[2 * best], cand[2 * best + 1]});
-        discarded_steps -= (double)(cand[2 * best].n + cand[2 * best + 1].n) * ldexp(1.0, l);
+        for (Term &t : cand)
+            for (const Term &u : tried)
+                if (t.l == u.l && t.four == u.four && t.prec == u.prec && t.kahan == u.kahan && t.icdf == u.icdf) t = u;
+        choose_level(l, cand);
         return MLMC_OK;
     };
     int L = o->min_levels - 1;
-    for (int l = 0; l <= L && !st; ++l) st = add_level(l);
+    if (autoprec) {
+        // the initial levels' candidates in one round, then each level's
+        // choice in order of l
+        std::vector<Term> all;
+        for (int l = 0; l <= L; ++l) {
+            std::vector<Term> c = candidates(l, 0);
+            all.insert(all.end(), c.begin(), c.end());
+        }
+        st = run_round(all, 0);
+        for (int l = 0; l <= L && !st; ++l)
+            choose_level(l, std::vector<Term>(all.begin() + 7 * l, all.begin() + 7 * (l + 1)));
+    } else {
+        for (int l = 0; l <= L && !st; ++l) st = add_level(l);
+    }
     const int per_level = nested ? 2 : 1;
     bool converged = false;
 
