@@ -514,8 +514,9 @@ static double payoff_of(double X, const orc_sde *p, int prec)
  * call holds (2^l < 4 words, or 2^l < 8 halves with 16-bit uniforms), the
  * S = 4 / 2^l (8 / 2^l) consecutive paths S k .. S k + S - 1 share call 0 of
  * counter path field k, path p taking the words (halves) from
- * (p mod S) 2^l on.  Four-way paths: at l <= 1 paths 2k and 2k+1 share
- * call 0 of counter path field k in the same way (S = 2). */
+ * (p mod S) 2^l on.  Four-way paths share call 0 of counter path field k
+ * in the same way at l = 0 (S = 4: paths 4k .. 4k+3, word p mod 4) and at
+ * l = 1 (S = 2: paths 2k, 2k+1, words 2 (p mod 2) and the next). */
 static void draw4w(uint64_t path, uint32_t j, uint32_t tag, uint64_t seed, uint32_t w[4])
 {
     uint32_t ctr[4] = {(uint32_t)path, (uint32_t)(path >> 32), j, tag};
@@ -613,8 +614,9 @@ static void fourway_one(int l, uint64_t path, const orc_variant *hat, const orc_
     path_init(&bc, p, bar->prec, bar->pbits, bar->kahan, 2.0 * delta_f, sq, 1);
     double zh_prev = 0.0, zb_prev = 0.0, u[5];
     const int shared = l <= 1;
-    const uint64_t cpath = shared ? path >> 1 : path;
-    const int64_t off = shared ? (int64_t)(path & 1) << l : 0;   /* see draw4w */
+    const uint64_t S4 = l == 0 ? 4 : 2;                           /* paths sharing a call, see draw4w */
+    const uint64_t cpath = shared ? path / S4 : path;
+    const int64_t off = shared ? (int64_t)(path % S4) << l : 0;
     for (int64_t n = 0; n < nf; ++n) {
         const int64_t q = off + n;
         double un;

@@ -74,7 +74,8 @@ def test_per_path_components_consistent(pl_table):
 def test_level0_single_step_by_hand():
     # l = 0: one step X1 = x0 + mu x0 T + sigma x0 sqrt(T) Z; the two-way
     # paths 12 .. 15 share call 0 of counter path field 3, path 12 + k taking
-    # word k; the four-way paths 6 and 7 share call 0 of field 3 (words 0, 1)
+    # word k; so do the four-way paths 12 .. 15 (both the exact-normal and the
+    # approximate path of a sample take the same word)
     sde = O.gbm(mu=0.05, sigma=0.2, payoff=O.PAYOFF_X)
     tag = O.make_tag(O.KIND_STD, 0)
     w = O.philox4x32_10(O.counters([3], 0, tag), O.seed_key(SEED))[0]
@@ -87,9 +88,12 @@ def test_level0_single_step_by_hand():
     w2 = O.philox4x32_10(O.counters([2], 0, tag), O.seed_key(SEED))[0]
     out = O.twoway_paths(0, [11], O.variant(), sde, SEED, tag)
     assert abs(out[0, 0] - (1 + 0.05 + 0.2 * O.ndtri(O.uniforms(w2[3:]))[0])) < 1e-15
-    four = O.fourway_paths(0, [6, 7], O.variant(), O.variant(rv=O.RV_TABLE), sde, SEED, tag)
-    for k in range(2):
+    four = O.fourway_paths(0, [12, 13, 14, 15], O.variant(), O.variant(rv=O.RV_TABLE), sde, SEED, tag)
+    for k in range(4):
         assert abs(four[k, 0] - (1 + 0.05 + 0.2 * z[k])) < 1e-15
+    # four-way path 11: word 3 of field 2, as the two-way path 11
+    four = O.fourway_paths(0, [11], O.variant(), O.variant(rv=O.RV_TABLE), sde, SEED, tag)
+    assert abs(four[0, 0] - (1 + 0.05 + 0.2 * O.ndtri(O.uniforms(w2[3:]))[0])) < 1e-15
 
 
 def test_level1_paths_share_a_call_by_hand():
