@@ -69,34 +69,34 @@ struct CostRow {
     float ps[11];
 };
 const CostRow kCost[] = {
-    {0, MLMC_F32, 0, MLMC_ICDF_EXACT, 0, {2.905, 4.894, 7.35, 13.36, 25.73, 47.68, 91.59, 176.4, 332.5, 643.8, 1265}},
-    {0, MLMC_F32, 1, MLMC_ICDF_EXACT, 0, {2.898, 5.071, 7.853, 14.25, 27.72, 51.59, 97.01, 192.7, 366.1, 711.2, 1402}},
-    {0, MLMC_F16, 1, MLMC_ICDF_TABLE, 0, {2.537, 4.038, 5.875, 10.53, 20.23, 36.8, 68.75, 134, 251.3, 479.1, 936.9}},
-    {0, MLMC_F16, 0, MLMC_ICDF_TABLE, 0, {2.521, 4.089, 5.62, 9.763, 18.62, 33.14, 62.98, 125.1, 226.2, 432.6, 839}},
-    {0, MLMC_F32, 0, MLMC_ICDF_TABLE, 0, {2.55, 4.346, 6.126, 10.68, 20.07, 36.35, 70, 134.4, 249.3, 477.1, 929.4}},
-    {0, MLMC_F16, 1, MLMC_ICDF_TABLE16, 0, {1.876, 3.101, 6.295, 8.559, 15.61, 29.74, 57.92, 116, 210.4, 400.3, 779.1}},
-    {0, MLMC_F16, 0, MLMC_ICDF_TABLE16, 0, {1.855, 3.002, 6.073, 7.893, 14.1, 26.97, 51.48, 100.5, 182.2, 345.1, 672.7}},
-    {0, MLMC_F32, 0, MLMC_ICDF_TABLE16, 0, {1.87, 3.114, 7.174, 8.713, 15.81, 30.05, 59.32, 114, 209.2, 401.3, 783.7}},
-    {0, MLMC_F16, 1, MLMC_ICDF_CUBIC, 0, {2.7, 4.4, 6.693, 12.12, 23.08, 42.68, 80.73, 159.2, 298.2, 577.3, 1133}},
-    {0, MLMC_F32, 0, MLMC_ICDF_CUBIC, 0, {2.695, 4.574, 6.756, 12.18, 23.39, 42.8, 79.94, 157, 293.4, 565.4, 1111}},
-    {1, MLMC_F16, 1, MLMC_ICDF_TABLE, 0, {4.264, 5.699, 9.583, 17.32, 37.09, 63.96, 125.7, 249, 475.2, 927.4, 1831}},
-    {1, MLMC_F16, 0, MLMC_ICDF_TABLE, 0, {4.305, 5.749, 9.116, 16.53, 34.18, 59.98, 118, 233.2, 441.8, 863.2, 1706}},
-    {1, MLMC_F32, 0, MLMC_ICDF_TABLE, 0, {4.356, 5.99, 9.739, 17.28, 36.09, 62.15, 123.4, 235.7, 451.4, 878.3, 1734}},
-    {1, MLMC_F16, 1, MLMC_ICDF_TABLE16, 0, {4.308, 5.961, 10.11, 18.41, 38.85, 67.89, 135, 265.5, 503.3, 994.2, 1950}},
-    {1, MLMC_F16, 0, MLMC_ICDF_TABLE16, 0, {4.37, 5.921, 9.582, 17.51, 37.21, 65.64, 125.5, 251, 475.2, 927.4, 1833}},
-    {1, MLMC_F32, 0, MLMC_ICDF_TABLE16, 0, {4.445, 6.172, 10.25, 18.52, 38.84, 67.52, 133.2, 260.2, 495.3, 967.7, 1911}},
-    {1, MLMC_F16, 1, MLMC_ICDF_CUBIC, 0, {4.273, 5.864, 10.32, 18.7, 39.64, 69.59, 136.3, 271.9, 521.2, 1029, 2018}},
-    {1, MLMC_F32, 0, MLMC_ICDF_CUBIC, 0, {4.397, 6.243, 10.29, 18.78, 39.37, 68.19, 135.1, 263.7, 508.2, 983.8, 1943}},
-    {0, MLMC_F32, 0, MLMC_ICDF_EXACT, 1, {3.018, 5.277, 7.961, 14.8, 29.18, 53.69, 104.6, 202.7, 383.5, 760.1, 1474}},
-    {0, MLMC_F32, 1, MLMC_ICDF_EXACT, 1, {2.998, 5.413, 8.666, 15.76, 30.76, 56.24, 108.4, 216, 411.8, 801.3, 1580}},
-    {0, MLMC_F16, 1, MLMC_ICDF_TABLE, 1, {2.584, 4.189, 6.611, 11.9, 23.21, 42.53, 80.71, 159.1, 301.2, 581.1, 1141}},
-    {0, MLMC_F32, 0, MLMC_ICDF_TABLE, 1, {2.698, 4.564, 6.774, 12.12, 23.4, 42.44, 80.83, 154.2, 291.9, 564.3, 1106}},
-    {0, MLMC_F16, 1, MLMC_ICDF_TABLE16, 1, {1.896, 3.291, 6.741, 9.915, 18.74, 35.74, 70.4, 138.4, 262.1, 497.7, 978.2}},
-    {0, MLMC_F32, 0, MLMC_ICDF_TABLE16, 1, {2, 3.582, 8.853, 10.27, 19, 36.51, 72.17, 139.1, 259, 498.5, 977.2}},
-    {1, MLMC_F16, 1, MLMC_ICDF_TABLE, 1, {4.473, 6.307, 10.88, 20.1, 44.37, 79.25, 154.8, 307.8, 585.1, 1142, 2268}},
-    {1, MLMC_F32, 0, MLMC_ICDF_TABLE, 1, {4.468, 6.591, 11.01, 20.31, 45.1, 78.09, 151.3, 305.4, 574.4, 1092, 2149}},
-    {1, MLMC_F16, 1, MLMC_ICDF_TABLE16, 1, {4.446, 6.435, 11.42, 21.1, 46.29, 83.48, 162.1, 325.6, 613.4, 1195, 2369}},
-    {1, MLMC_F32, 0, MLMC_ICDF_TABLE16, 1, {4.707, 6.978, 11.63, 21.5, 47.1, 82.82, 167.1, 337.4, 619.2, 1169, 2317}},
+    {0, MLMC_F32, 0, MLMC_ICDF_EXACT, 0, {2.9, 4.893, 7.367, 13.34, 25.47, 47.57, 91.66, 176.8, 332.8, 642.6, 1264}},
+    {0, MLMC_F32, 1, MLMC_ICDF_EXACT, 0, {2.867, 5.058, 7.856, 14.16, 27.76, 51.63, 97.19, 192.7, 365.7, 709.4, 1401}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE, 0, {2.522, 4.044, 5.871, 10.6, 20.31, 36.63, 68.36, 134.2, 250.9, 479.5, 935.8}},
+    {0, MLMC_F16, 0, MLMC_ICDF_TABLE, 0, {2.475, 4.071, 5.61, 9.742, 18.39, 32.73, 62.36, 124.1, 227.1, 432, 836.9}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE, 0, {2.539, 4.349, 6.062, 10.65, 20.18, 36, 68.91, 132.8, 249.4, 476.5, 930.2}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE16, 0, {1.867, 3.099, 6.302, 8.54, 15.53, 29.52, 57.62, 116.8, 209.5, 398.6, 776.9}},
+    {0, MLMC_F16, 0, MLMC_ICDF_TABLE16, 0, {1.863, 2.99, 6.059, 7.798, 14.03, 26.69, 50.99, 99.76, 182.3, 344.7, 670.2}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE16, 0, {1.863, 3.106, 7.181, 8.778, 15.97, 29.75, 60.51, 113.1, 208.8, 401, 781}},
+    {0, MLMC_F16, 1, MLMC_ICDF_CUBIC, 0, {2.695, 4.385, 6.697, 12.09, 22.94, 42.71, 80.51, 158.3, 298.3, 575.5, 1131}},
+    {0, MLMC_F32, 0, MLMC_ICDF_CUBIC, 0, {2.672, 4.57, 6.747, 12.03, 23.28, 42.47, 79.8, 156.6, 293.5, 565.1, 1109}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE, 0, {3.459, 5.811, 9.566, 17.46, 37.08, 64.19, 125.3, 248.3, 472.8, 926.7, 1830}},
+    {1, MLMC_F16, 0, MLMC_ICDF_TABLE, 0, {3.417, 5.731, 9.109, 16.66, 34.97, 61.45, 117.8, 231.3, 442.8, 860.1, 1699}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE, 0, {3.409, 6.081, 9.894, 17.69, 36.7, 62.91, 121.6, 240.1, 458.7, 891.4, 1761}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE16, 0, {3.626, 6.069, 9.991, 18.25, 38.92, 67.65, 132.1, 265.1, 506.3, 981.5, 1943}},
+    {1, MLMC_F16, 0, MLMC_ICDF_TABLE16, 0, {3.553, 6.01, 9.688, 17.69, 37.69, 65.53, 125.6, 248, 470.3, 914.6, 1808}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE16, 0, {3.537, 6.444, 10.39, 18.67, 38.28, 67.02, 130.7, 258.9, 496.6, 967.3, 1914}},
+    {1, MLMC_F16, 1, MLMC_ICDF_CUBIC, 0, {3.554, 6.036, 10.27, 18.72, 39.86, 69.48, 139.7, 273, 519, 1024, 2020}},
+    {1, MLMC_F32, 0, MLMC_ICDF_CUBIC, 0, {3.592, 6.483, 10.56, 19.1, 38.85, 68.38, 133.6, 264.9, 506.2, 983.2, 1942}},
+    {0, MLMC_F32, 0, MLMC_ICDF_EXACT, 1, {3, 5.264, 7.974, 14.72, 29.1, 53.41, 104, 202.5, 383.3, 748.9, 1472}},
+    {0, MLMC_F32, 1, MLMC_ICDF_EXACT, 1, {2.982, 5.391, 8.641, 15.73, 30.92, 56.03, 108.7, 215.7, 410.4, 799.7, 1577}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE, 1, {2.548, 4.168, 6.65, 11.89, 23.16, 42.43, 80.51, 158.9, 301.6, 580.3, 1140}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE, 1, {2.657, 4.562, 6.741, 12.08, 23.32, 42.36, 80.96, 154.3, 292, 563.6, 1104}},
+    {0, MLMC_F16, 1, MLMC_ICDF_TABLE16, 1, {1.896, 3.284, 6.702, 9.871, 18.65, 35.68, 70.92, 137.6, 259.7, 497.3, 976.3}},
+    {0, MLMC_F32, 0, MLMC_ICDF_TABLE16, 1, {1.983, 3.578, 8.87, 10.24, 19.02, 36.67, 71.91, 138.2, 258.4, 497.5, 975.6}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE, 1, {3.396, 6.303, 10.89, 20.17, 45.3, 79.15, 153.9, 300.2, 579.6, 1130, 2239}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE, 1, {3.608, 6.691, 11.16, 20.3, 46, 82.57, 155.5, 304.6, 578.9, 1087, 2151}},
+    {1, MLMC_F16, 1, MLMC_ICDF_TABLE16, 1, {3.491, 6.613, 11.48, 21.38, 46.18, 83.45, 161.9, 318.5, 615, 1200, 2376}},
+    {1, MLMC_F32, 0, MLMC_ICDF_TABLE16, 1, {3.748, 7.041, 11.93, 21.6, 48.4, 85.3, 170.1, 342.5, 608.3, 1170, 2320}},
 };
 
 // The row of a term, or the nearest measured one: bfloat16 as binary16 (the

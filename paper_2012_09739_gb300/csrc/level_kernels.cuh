@@ -27,7 +27,7 @@ struct LevelArgs {
     int payoff;
     int mode, sde;            // MODE_*, SDE_* (read by the batched kernel)
     uint64_t npairs;          // lane slots: ceil(N / 2) pairs, or ceil(N / (2 unit)) units
-    int unit;                 // pairs per slot: 1, or 2 / 4 at the coarsest two-way levels (unit_pairs)
+    int unit;                 // pairs per slot: 1, or 2 / 4 at the coarsest levels (unit_pairs)
     uint64_t N;
     uint64_t path_offset;
     uint32_t tag, k0, k1;     // Philox counter tag and key (seed)
@@ -315,11 +315,13 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const PhiloxKe
 // needs fewer words than one Philox call holds (2^l < 4 words, or 2^l < 8
 // halves with 16-bit uniforms), and the S = 4 / 2^l (8 / 2^l) consecutive
 // paths S k .. S k + S - 1 share call 0 of counter path field k, path p
-// taking the words (halves) from (p mod S) 2^l on.  Where S > 2 one lane
-// simulates all S paths of a call (S / 2 pairs); elsewhere a slot is one
-// pair (at S = 2 the pair shares its call, as simulate_pair does).
+// taking the words (halves) from (p mod S) 2^l on; four-way paths at level
+// 0 share a call in fours too (S = 4, both paths of a sample reading its
+// word).  Where S > 2 one lane simulates all S paths of a call (S / 2
+// pairs); elsewhere a slot is one pair (at S = 2 the pair shares its call,
+// as simulate_pair does).
 __host__ __device__ __forceinline__ int unit_pairs(int mode, int icdf, int l) {
-    if (mode != MODE_TWO) return 1;
+    if (mode != MODE_TWO) return l == 0 ? 2 : 1;
     if (icdf == ICDF_TABLE16) return l == 0 ? 4 : (l == 1 ? 2 : 1);
     return l == 0 ? 2 : 1;
 }
@@ -330,11 +332,11 @@ __host__ __device__ __forceinline__ int unit_pairs(int mode, int icdf, int l) {
 // = 0, one call).  Level L = 0 (one fine step) or 1 (two fine steps, one
 // coarse; 16-bit uniforms only).  emit(i, P_f, P_c, D) receives every path
 // in order.
-template <int B, int L, bool ALIGNED, int P, bool KAHAN, int ICDF, int SDE, class Emit>
+template <int MODE, int B, int L, bool ALIGNED, int P, bool KAHAN, int ICDF, int SDE, class Emit>
 __device__ __forceinline__ void simulate_unit(const LevelArgs &a, const PhiloxKeys &K, const SmemTable &tab,
                                               const float *mlp, uint64_t u, Emit &&emit) {
     constexpr uint32_t S = 2 * B;
-    constexpr bool U16 = ICDF == ICDF_TABLE16;
+    constexpr bool U16 = ICDF == ICDF_TABLE16 && MODE == MODE_TWO;     // four-way paths read 24-bit words
     static_assert(L == 0 || U16, "level-1 units use 16-bit uniforms");
     const uint64_t base = a.path_offset + S * u;
     const uint32_t m = ALIGNED ? 0u : (uint32_t)(base % S);
@@ -353,11 +355,11 @@ __device__ __forceinline__ void simulate_unit(const LevelArgs &a, const PhiloxKe
         return q < S ? word(r0, wi) : word(r1, wi);
     };
     auto half_at = [](uint32_t w, uint32_t hi) { return hi ? half16_bits<true>(w) : half16_bits<false>(w); };
-    PathPair<P_F32, true, SDE> unused;
 #pragma unroll
     for (int k = 0; k < B; ++k) {
         const uint32_t q0 = m + 2 * k, q1 = q0 + 1;
         PathPair<P, KAHAN, SDE> fine, coarse;
+        PathPair<P_F32, true, SDE> hfine, hcoarse;     // exact-normal pair (four-way, level 0)
         fine.template init<false>(a, false);
         if (L == 1) coarse.template init<false>(a, true);
         if constexpr (U16 && L == 0) {
@@ -373,12 +375,17 @@ __device__ __forceinline__ void simulate_unit(const LevelArgs &a, const PhiloxKe
             fine.step(z2);
             coarse.step(add(z1, z2));
         } else {
-            fine.step(icdf_pair<P, ICDF>(tab, mlp, word_at(q0), word_at(q1)));
+            const uint32_t w0 = word_at(q0), w1 = word_at(q1);
+            fine.step(icdf_pair<P, ICDF>(tab, mlp, w0, w1));
+            if constexpr (MODE == MODE_FOUR) {
+                hfine.template init<true>(a, false);
+                hfine.step(Pair<P_F32>::of2(exact_z(tab, w0), exact_z(tab, w1)));
+            }
         }
         float d0, d1, o0[5], o1[5];
-        pair_result<MODE_TWO>(a, fine, coarse, unused, unused, d0, d1, o0, o1);
-        emit(2 * k, o0[0], o0[1], d0);
-        emit(2 * k + 1, o1[0], o1[1], d1);
+        pair_result<MODE>(a, fine, coarse, hfine, hcoarse, d0, d1, o0, o1);
+        emit(2 * k, o0, d0);
+        emit(2 * k + 1, o1, d1);
     }
 }
 
@@ -390,31 +397,31 @@ __device__ __forceinline__ void simulate_unit(const LevelArgs &a, const PhiloxKe
 template <int MODE, int P, bool KAHAN, int ICDF, int SDE>
 __device__ __forceinline__ void run_slot(const LevelArgs &a, const PhiloxKeys &K, const SmemTable &tab,
                                          const float *mlp, uint64_t g, bool active, KahanF32 &k1, KahanF32 &k2) {
-    if (MODE == MODE_TWO && a.unit > 1) {
+    if (a.unit > 1) {
         const uint64_t first = (uint64_t)(2 * a.unit) * g;        // sample index of the unit's first path
-        auto emit = [&](int i, float pf, float pc, float d) {
+        auto emit = [&](int i, const float *out, float d) {
             if (!active || first + i >= a.N) return;
             k1.add(d);
             k2.add(d * d);
             if (a.paths_out != nullptr) {
-                float *o = a.paths_out + (first + i) * 3;
-                o[0] = pf;
-                o[1] = pc;
-                o[2] = d;
+                constexpr int W = MODE == MODE_TWO ? 3 : 5;
+                float *o = a.paths_out + (first + i) * W;
+#pragma unroll
+                for (int k = 0; k < W; ++k) o[k] = out[k];
             }
         };
         const bool aligned = a.path_offset % (uint64_t)(2 * a.unit) == 0;
-        if constexpr (ICDF == ICDF_TABLE16) {
+        if constexpr (ICDF == ICDF_TABLE16 && MODE == MODE_TWO) {
             if (a.l == 0) {
-                if (aligned) simulate_unit<4, 0, true, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
-                else simulate_unit<4, 0, false, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
+                if (aligned) simulate_unit<MODE, 4, 0, true, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
+                else simulate_unit<MODE, 4, 0, false, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
             } else {
-                if (aligned) simulate_unit<2, 1, true, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
-                else simulate_unit<2, 1, false, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
+                if (aligned) simulate_unit<MODE, 2, 1, true, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
+                else simulate_unit<MODE, 2, 1, false, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
             }
         } else {
-            if (aligned) simulate_unit<2, 0, true, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
-            else simulate_unit<2, 0, false, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
+            if (aligned) simulate_unit<MODE, 2, 0, true, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
+            else simulate_unit<MODE, 2, 0, false, P, KAHAN, ICDF, SDE>(a, K, tab, mlp, g, emit);
         }
         return;
     }
