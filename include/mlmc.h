@@ -34,8 +34,9 @@
  * level l needs 2^l words (halves with TABLE16); while that is fewer than a
  * call holds (4 words, 8 halves), the S = 4 / 2^l (8 / 2^l) paths S k ..
  * S k + S - 1 share call 0 of counter path field k, path p taking the words
- * (halves) from (p mod S) 2^l on; four-way paths share a call in pairs at
- * l <= 1 (S = 2).  A launch whose path_offset is a multiple of S computes
+ * (halves) from (p mod S) 2^l on; four-way paths share a call in fours at
+ * l = 0 (S = 4) and in pairs at l = 1 (S = 2), both paths of a sample
+ * reading its words.  A launch whose path_offset is a multiple of S computes
  * one call per S paths, otherwise two.
  */
 #ifndef MLMC_H
