@@ -207,6 +207,21 @@ def test_fourway_table_paths(prec, kahan, l, pl_table):
     assert np.all(np.abs(got[:, 4] - ref[:, 4]) <= 2 * TOL32 * scale)
 
 
+@pytest.mark.parametrize("icdf,rv", [(M.MLMC_ICDF_TABLE, O.RV_TABLE), (M.MLMC_ICDF_TABLE16, O.RV_TABLE16)])
+@pytest.mark.parametrize("offset", [6, 2 ** 33 + 3])
+def test_fourway_level0_shared_calls_at_unaligned_offsets(icdf, rv, offset, pl_table):
+    """At level 0 four four-way paths share one Philox call; a launch whose
+    path offset is not a multiple of 4 has slots that span two calls."""
+    params = M.sde_params(**GBM_CALL)
+    N = 37
+    got = gpu_paths(1, 0, N, M.MLMC_F16, True, icdf, params, offset=offset)
+    ref = O.fourway_paths(0, offset + np.arange(N), O.variant(), _bar_variant(M.MLMC_F16, True, rv), _orc_sde(params),
+                          SEED, _kind_tag(1, icdf, 0), table=pl_table)
+    assert np.array_equal(got[:, 2:4], ref[:, 2:4])
+    scale = np.maximum(1.0, np.abs(ref[:, 0]))
+    assert np.all(np.abs(got[:, 0:2] - ref[:, 0:2]) <= TOL32 * scale[:, None])
+
+
 @pytest.mark.parametrize("l", [0, 1, 2, 4, 6])
 @pytest.mark.parametrize("kahan", [False, True])
 def test_twoway_exact_fp32_within_1e5(l, kahan):
