@@ -226,10 +226,12 @@ __device__ __forceinline__ void simulate_pair(const LevelArgs &a, const PhiloxKe
     auto call_of = [&](uint64_t cp, uint32_t j) {
         return philox4x32_10(make_uint4((uint32_t)cp, (uint32_t)(cp >> 32), j, a.tag), K);
     };
-    // Coarsest levels (a path needs at most half a call): paths 2k and 2k+1
-    // share call 0 of counter path field k, path p starting at word (or
-    // half) (p mod 2) 2^l.  p0 = path_offset + 2g has the launch's parity,
-    // so whether the pair's two paths share one call is uniform.
+    // Coarsest levels (a path needs at most half a call; level 1, and level
+    // 2 with 16-bit uniforms -- level 0 runs in lane slots of several pairs,
+    // run_slot): paths 2k and 2k+1 share call 0 of counter path field k,
+    // path p starting at word (or half) (p mod 2) 2^l.  p0 = path_offset + 2g
+    // has the launch's parity, so whether the pair's two paths share one call
+    // is uniform.
     const uint64_t c0 = p0 >> 1, c1 = p1 >> 1;
     const uint32_t o0 = (uint32_t)(p0 & 1) << a.l, o1 = (uint32_t)(p1 & 1) << a.l;
 
