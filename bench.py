@@ -61,6 +61,12 @@ OPS_TWOWAY_F16K_TABLE = 22.65
 # candidates, the replays), no writes (the group partials stay in L2).  The
 # traffic does not grow with the path-steps.
 TRAFFIC_FOURWAY_BYTES = 167680
+# Pipe utilisation of the same kernel from the committed ncu capture (the
+# small case of the batch-kernel profile: levels 0..12, N = 2^18, full
+# section set), of peak over active cycles; the non-tensor pipes bound it.
+PIPES_FOURWAY_NCU = {"issue_active": 0.779, "fma_pipe_cycles_active": 0.651, "fmaheavy_cycles_active": 0.608,
+                     "alu_pipe_cycles_active": 0.425, "thread_instructions_per_path_step": 55.7,
+                     "source": "profiles/batch_kernels_gbm_call_l0-12_N2e20.md"}
 
 
 def _env_rank():
@@ -360,7 +366,8 @@ def run_gpu(args):
                                       "launch of the bench command; independent of the path-steps",
                      "ops_per_path_step": OPS_FOURWAY_F16K_TABLE,
                      "peak_basis": f"{sm_count} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock sampled)",
-                     "launches": args.steps},
+                     "launches": args.steps,
+                     "pipes_ncu": PIPES_FOURWAY_NCU},
         "e2e": {"value": e2e_value, "unit": "path-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 2 * len(LEVELS) * 16,
                 "note": "synchronous mlmc_batch over the 26 items; new path offsets each step"},
