@@ -241,7 +241,7 @@ struct BatchCache {
     unsigned char *stage = nullptr;      // pinned staging of the descriptors
     size_t stage_cap = 0;
     std::map<std::pair<const void *, int>, int> occupancy;   // (batch kernel, block) -> resident blocks per SM
-    uint32_t *small_counters = nullptr;  // the fused small-round kernel's two counters (zero between rounds)
+    uint32_t *small_counters = nullptr;  // the fused small-round kernel's counters (zero between rounds)
     // streams of the concurrent groups (created on first use)
     static constexpr size_t MAX_SIDE = 7;
     cudaStream_t side[MAX_SIDE] = {};
@@ -539,11 +539,11 @@ mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, in
 }  // namespace
 
 // A latency-sized round of one group in one launch of the fused small-round
-// kernel (descriptors as a kernel parameter, finalize by the last block,
-// sums straight into the pinned host buffer); false (nothing enqueued) where
-// the round does not qualify: several groups, more than SMALL_ITEMS items,
-// an item above one finalize span, not latency-sized, or no such kernel for
-// the variant.  MLMC_ROUND_FUSED=0 turns it off.
+// kernel (descriptors as a kernel parameter, finalized in the launch, sums
+// straight into the pinned host buffer); false (nothing enqueued) where the
+// round does not qualify: several groups, more than SMALL_ITEMS items, an
+// item above one finalize span, not latency-sized, or no such kernel for the
+// variant.  MLMC_ROUND_FUSED=0 turns it off.
 bool small_round(const DeviceState &d, BatchCache &c, const Plan &p, cudaStream_t s, mlmc_status *st) {
     if (p.groups.size() != 1 || p.items.size() > (size_t)SMALL_ITEMS || !p.jobs.empty() || p.too_large ||
         p.block != SUM_THREADS || p.work >= SMALL_BATCH_WORK || env_int("MLMC_ROUND_FUSED", 1) == 0)
@@ -556,8 +556,8 @@ bool small_round(const DeviceState &d, BatchCache &c, const Plan &p, cudaStream_
     cudaError_t e;
     *st = MLMC_OK;
     if (!c.small_counters) {
-        if ((e = cudaMalloc(&c.small_counters, 2 * sizeof(uint32_t))) != cudaSuccess ||
-            (e = cudaMemsetAsync(c.small_counters, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) {
+        if ((e = cudaMalloc(&c.small_counters, SMALL_COUNTERS * sizeof(uint32_t))) != cudaSuccess ||
+            (e = cudaMemsetAsync(c.small_counters, 0, SMALL_COUNTERS * sizeof(uint32_t), s)) != cudaSuccess) {
             *st = cuda_fail(e, "batch buffers");
             return true;
         }

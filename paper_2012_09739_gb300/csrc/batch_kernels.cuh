@@ -184,11 +184,13 @@ enum { MODE_MIXED = 2 };
 // index from the counter until the tiles run out; or (STATIC) warp w of W
 // first takes tile w and then W + the counter's next value, so that a
 // launch of at most one tile per warp needs no atomic at all.  A tile's
-// partials do not depend on which warp runs it.
-template <bool STATIC, int MODE, int P, bool KAHAN, int ICDF, int SDE>
+// partials do not depend on which warp runs it.  The whole warp calls
+// after(span) once each tile's partials are written.
+template <bool STATIC, int MODE, int P, bool KAHAN, int ICDF, int SDE, class After>
 __device__ __forceinline__ void tile_loop(const LevelArgs *items, const TileSpan *spans, uint32_t nspans,
                                           uint32_t ntiles, uint32_t *counter, double2 *partials,
-                                          const SmemTable &tab, const PhiloxKeys &keys, SeqScratch<P> &seq) {
+                                          const SmemTable &tab, const PhiloxKeys &keys, SeqScratch<P> &seq,
+                                          After after) {
     const float *mlp = ICDF == ICDF_MLP ? items[0].mlp->ygrid : nullptr;
     const uint32_t lane = threadIdx.x & 31;
     auto tile = [&](uint32_t t) {
@@ -204,6 +206,7 @@ __device__ __forceinline__ void tile_loop(const LevelArgs *items, const TileSpan
         } else {
             run_tile<MODE, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq);
         }
+        after(sp);
     };
     if constexpr (STATIC) {
         uint32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -238,20 +241,25 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
     stage_table(tab, tabs);
     __syncthreads();
     tile_loop<false, MODE, P, KAHAN, ICDF, SDE>(items, spans, nspans, ntiles, counter, partials, tab, keys,
-                                         seq[threadIdx.x >> 5]);
+                                         seq[threadIdx.x >> 5], [](const TileSpan &) {});
 }
 
 // A latency-sized round of one group (an adaptive run's round at large
 // RMSE): its descriptors travel in the kernel's parameter space, so the
-// round needs no descriptor copy, and the last block to finish adds every
-// item's partials with the finalize's fixed-order sum (so the sums equal
-// those of the two-kernel path bit for bit) and writes them to `sums`; it
-// then zeroes the two counters (tiles taken, blocks done) for the next round
-// on the stream.  A warp's first tile is its own index (no atomic).
-// Items of at most 1024 partials are summed one per warp
-// (warp_sum_fixed, the same tree), so a round's items are finalized in
-// parallel.  One launch per round instead of a copy and two launches.
+// round needs no descriptor copy, and its sums are finalized inside the
+// launch with the finalize's fixed-order sums (so they equal those of the
+// two-kernel path bit for bit), written to `sums`.  A warp's first tile is
+// its own index (no atomic).  Each item counts its finished tiles: the warp
+// that finishes an item's last tile adds the item's partials (at most 1024:
+// warp_sum_fixed, the same tree) while other warps still simulate, and
+// zeroes the item's count; the last block to finish adds the partials of
+// larger items with the whole block and zeroes the tile and block counts
+// for the next round on the stream.  One launch per round instead of a
+// copy and two launches.
+//
+// counters: [0] tiles taken, [1] blocks done, [2 + i] tiles done of item i.
 constexpr int SMALL_ITEMS = 24;
+constexpr int SMALL_COUNTERS = 2 + SMALL_ITEMS;
 
 struct SmallRound {
     LevelArgs items[SMALL_ITEMS];
@@ -275,21 +283,28 @@ batch_small_kernel(const __grid_constant__ SmallRound r, uint32_t *counters, dou
     __shared__ uint32_t last;
     stage_table(tab, tabs);
     __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    // lane 0 wrote the tile's partials: fenced before they are counted, so
+    // the warp that counts an item's last tile sees all of the item's
+    auto item_done = [&](const TileSpan &sp) {
+        uint32_t done = 0;
+        if (lane == 0) {
+            __threadfence();
+            done = atomicAdd(counters + 2 + sp.item, 1u) == sp.count - 1;
+            if (done) counters[2 + sp.item] = 0u;
+        }
+        if (!__shfl_sync(0xffffffffu, done, 0) || r.count[sp.item] > (uint32_t)FINALIZE_THREADS) return;
+        __threadfence();
+        const double2 v = warp_sum_fixed(partials + r.first[sp.item], r.count[sp.item], lane);
+        if (lane == 0) sums[sp.item] = v;
+    };
     tile_loop<true, MODE, P, KAHAN, ICDF, SDE>(r.items, r.spans, r.nspans, r.ntiles, counters, partials, tab, r.keys,
-                                         seq[threadIdx.x >> 5]);
-    __threadfence();            // this thread's partials, before the block is counted done
-    __syncthreads();
+                                         seq[threadIdx.x >> 5], item_done);
+    __syncthreads();            // every warp's partials are fenced (item_done)
     if (threadIdx.x == 0) last = atomicAdd(counters + 1, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();            // every block's partials are visible from here on
-    // items of at most 1024 partials one per warp, the others with the block
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (uint32_t i = warp; i < r.nitems; i += SUM_THREADS / 32) {
-        if (r.count[i] > (uint32_t)FINALIZE_THREADS) continue;
-        const double2 v = warp_sum_fixed(partials + r.first[i], r.count[i], lane);
-        if (lane == 0) sums[i] = v;
-    }
     for (uint32_t i = 0; i < r.nitems; ++i) {
         if (r.count[i] <= (uint32_t)FINALIZE_THREADS) continue;
         const double2 v = block_sum_fixed(partials + r.first[i], r.count[i], r1, r2);

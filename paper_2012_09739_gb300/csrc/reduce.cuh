@@ -75,7 +75,7 @@ __device__ __forceinline__ double2 strided_tree(const double2 *p, uint32_t n, ui
         const uint32_t i = lane + 32u * J;
         double2 s = make_double2(0.0, 0.0);
         if (i < n) {
-            const double2 v = p[i];
+            const double2 v = __ldcg(p + i);      // written by other SMs in the same launch
             s.x += v.x;
             s.y += v.y;
         }

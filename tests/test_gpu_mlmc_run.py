@@ -177,7 +177,8 @@ def test_mlmc_run_decisions_replayed_by_the_oracle_driver(eps, est, prec, kahan,
 ])
 def test_fused_small_rounds_give_the_same_runs(monkeypatch, est, prec, kahan, icdf, scheme):
     """Latency-sized rounds of one kernel group run as one fused launch
-    (descriptors as kernel parameters, finalize by the last block); the same
+    (descriptors as kernel parameters, each item's sum by the warp that
+    finishes its last tile, larger items' by the last block); the same
     runs with the two-kernel path (MLMC_ROUND_FUSED=0) must take the same
     draws and get the same sums, bit for bit, at an RMSE where every round
     is small (1e-3) and where the later ones are not (1e-4)."""
