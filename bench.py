@@ -9,8 +9,8 @@ table).  One step = 2 x 2^20 x (2^13 - 1) = 1.718e10 fine Euler path-steps.
 Beside it, the plain FP32 exact-normal two-way MLMC over the same levels.
 
 A step is two batched launches (mlmc_batch_async): the 13 two-way items and
-the 13 four-way items, each one persistent kernel over all levels, longest
-tiles first, replayed from a captured graph.  value: fine path-steps per
+the 13 four-way items, each one persistent kernel over all levels in the
+tuned tile order, replayed from a captured graph.  value: fine path-steps per
 second of that step, timed on the device with CUDA events; e2e: the same
 through the synchronous mlmc_batch call with host items and host sums, new
 path offsets every step (the descriptors are re-staged).  The same step
@@ -422,13 +422,14 @@ def batch_leg(M, torch, stream, repeats=5):
     M.mlmc_batch(items, SEED)            # tunes, captures the graph
     first_s = time.perf_counter() - t0
     M.mlmc_batch(items, SEED)
-    times = []
+    times, devs = [], []
     for _ in range(repeats):
         t0 = time.perf_counter()
-        M.mlmc_batch(items, SEED)
+        r = M.mlmc_batch(items, SEED)
         times.append(time.perf_counter() - t0)
+        devs.append(sum(x.cost_ns for x in r) * 1e-9)
     t_batch = statistics.median(times)
-    dev_s = sum(x.cost_ns for x in M.mlmc_batch(items, SEED)) * 1e-9
+    dev_s = statistics.median(devs)
     sums = torch.zeros(2 * len(items), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     seq = []
@@ -445,7 +446,7 @@ def batch_leg(M, torch, stream, repeats=5):
             "device_seconds": dev_s,
             "one_launch_per_item_seconds": t_seq, "speedup_vs_one_launch_per_item": t_seq / t_batch,
             "timing": "wall clock around the synchronous mlmc_batch call (graph replay), median of 5; "
-                      "device_seconds from CUDA events around the graph launch"}
+                      "device_seconds from CUDA events around the graph launch of the same 5 calls, median"}
 
 
 def time_to_eps(M, params, eps_list, repeats=5, with_mlp=False):

@@ -300,26 +300,27 @@ typedef struct {
     uint64_t N, path_offset;
 } mlmc_work;
 
-/* Runs all items, longest first: one persistent kernel per group of items
+/* Runs all items, tiles by length (longest first or interleaved long and
+ * short, tuned with the tile size): one persistent kernel per group of items
  * that share estimator, working precision, Kahan flag, inverse CDF and SDE
  * scheme (the same per-sample code as the level kernels), then one finalize
  * kernel, all captured in a CUDA graph.  out_host[i] receives the sums of
- * items[i]; the call waits for them.  The library keeps the graphs of up to
- * 8 item-list shapes (the level, kind, prec, kahan, icdf, N, SDE type and
- * scheme of every item, and the seed), least recently used evicted; the first call with a
- * shape tunes the tile size, captures and instantiates (hundreds of ms).  A
- * call with a known shape and seed but other parameter values, payoffs, set
- * ids or path offsets uploads n_items * mlmc_batch_descriptor_bytes() bytes
- * of descriptors and replays the graph; a new seed captures a new graph (the
- * tuned tile size is kept).  An item's sums are accumulated as the
- * level kernels do (FP32 Kahan per lane over each chunk group of 32-pair
- * chunks, a warp sum, FP64 partials, the same fixed-order finalize): they
- * equal those of mlmc_level / mlmc_nested_level / mlmc_level_async for the
- * same item, seed and offset bit for bit whenever that call keeps one
- * partial per chunk group (at most 2^22 groups), whatever tile size the
- * tuner picks.  Errors: MLMC_EINVAL for an invalid item or a batch beyond
- * 2^32 - 1 tiles or partials (before any launch), MLMC_ENOTREADY for MLP
- * items without weights, MLMC_ECUDA, MLMC_ETIMEOUT. */
+ * items[i]; the call waits for them.  The library keeps the graphs of up to 8
+ * item-list shapes (the level, kind, prec, kahan, icdf, N, SDE type and
+ * scheme of every item, and the seed), least recently used evicted; the first
+ * call with a shape tunes the tile size, block shape and tile order, captures
+ * and instantiates (hundreds of ms).  A call with a known shape and seed but
+ * other parameter values, payoffs, set ids or path offsets uploads n_items *
+ * mlmc_batch_descriptor_bytes() bytes of descriptors and replays the graph; a
+ * new seed captures a new graph (the tuned choice is kept).  An item's sums
+ * are accumulated as the level kernels do (FP32 Kahan per lane over each
+ * chunk group of 32-pair chunks, a warp sum, FP64 partials, the same
+ * fixed-order finalize): they equal those of mlmc_level / mlmc_nested_level /
+ * mlmc_level_async for the same item, seed and offset bit for bit whenever
+ * that call keeps one partial per chunk group (at most 2^22 groups), whatever
+ * tile size and order the tuner picks.  Errors: MLMC_EINVAL for an invalid
+ * item or a batch beyond 2^32 - 1 tiles or partials (before any launch),
+ * MLMC_ENOTREADY for MLP items without weights, MLMC_ECUDA, MLMC_ETIMEOUT. */
 mlmc_status mlmc_batch(const mlmc_work *items, int n_items, uint64_t seed, mlmc_sums *out_host, void *stream);
 
 /* mlmc_batch without the wait: enqueues the batch on `stream` and returns.

@@ -1,8 +1,9 @@
-// Host side of mlmc_batch: warp tiles in longest-first order (one span of
-// tiles per item, never listed one by one); one persistent launch per group
-// of items sharing estimator, working-precision variant and SDE scheme, the
-// groups running concurrently; a finalize kernel; CUDA graphs of recent
-// item-list shapes, replayed; and an autotuner for the tile size and block shape.
+// Host side of mlmc_batch: warp tiles in longest-first (or interleaved)
+// order (one span of tiles per item, never listed one by one); one
+// persistent launch per group of items sharing estimator, working-precision
+// variant and SDE scheme, the groups running concurrently; a finalize
+// kernel; CUDA graphs of recent item-list shapes, replayed; and an autotuner
+// for the tile size, block shape and span order.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -67,7 +68,7 @@ constexpr double SMALL_BATCH_WORK = 2e7;
 
 struct Group {
     int mode, prec, kahan, icdf, sde;
-    std::vector<TileSpan> spans;   // longest tiles first
+    std::vector<TileSpan> spans;   // in the plan's span order (ORDER_*)
     std::vector<double> tile_cost;  // per span: cost of one full tile
     uint32_t span_base = 0;        // offset of this group's spans in the device array
     uint32_t ntiles = 0;
@@ -101,14 +102,19 @@ double pair_cost(int l, int four) { return (ldexp(1.0, l) + PAIR_OVERHEAD_STEPS)
 
 double item_work(const mlmc_work &w) { return (double)((w.N + 1) / 2) * pair_cost(w.l, w.kind); }
 
+// Span orders: by the cost of their tiles, longest first; or interleaved
+// from both ends of that order (longest, shortest, second longest, ...), so
+// that warps taking consecutive tiles mix long and short ones.
+enum { ORDER_LONGEST_FIRST = 0, ORDER_INTERLEAVED = 1 };
+
 // Tiles: a lane takes max(1, 2^lane_work_log2 / (2^l + overhead)) pairs of an
 // item at level l, rounded up to whole chunk groups of the level kernel; a
 // tile is 32 such lanes.  Every item is one span of consecutive tiles; each
-// group's spans are ordered by the cost of their tiles, longest first, so the
+// group's spans are ordered by the cost of their tiles (ORDER_*), so the
 // host work is per item, not per tile.  Each item owns one partial per chunk
 // group and, above FINALIZE_SPAN of them, scratch for the finalize's span sums.
 Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, int lane_work_log2,
-               int block = 256) {
+               int block = 256, int span_order = ORDER_LONGEST_FIRST) {
     Plan plan;
     plan.block = block;
     plan.items.resize(n);
@@ -166,6 +172,14 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
         for (uint32_t k = 0; k < order.size(); ++k) order[k] = k;
         std::stable_sort(order.begin(), order.end(),
                          [&](uint32_t a, uint32_t b) { return g.tile_cost[a] > g.tile_cost[b]; });
+        if (span_order == ORDER_INTERLEAVED) {
+            std::vector<uint32_t> mixed;
+            for (size_t lo = 0, hi = order.size(); lo < hi;) {
+                mixed.push_back(order[lo++]);
+                if (lo < hi) mixed.push_back(order[--hi]);
+            }
+            order.swap(mixed);
+        }
         std::vector<TileSpan> spans;
         std::vector<double> cost;
         uint64_t begin = 0;
@@ -259,11 +273,17 @@ struct BatchCache {
     std::vector<double> weight;
 };
 
+// A plan's shape: tile size (log2 of the fine-step equivalents per lane and
+// tile), block threads and span order (ORDER_*).
+struct Tuning {
+    int lw, block, order;
+};
+
 // The graph entries of mlmc_batch / mlmc_batch_async on one device.
 struct BatchGraphs {
     std::vector<BatchCache *> entries;   // at most MAX_ENTRIES, least recently used evicted
     cudaStream_t capture_stream = nullptr;
-    std::map<uint64_t, std::pair<int, int>> tuned;   // hash of the item-list shape -> (lane_work_log2, block)
+    std::map<uint64_t, Tuning> tuned;   // hash of the item-list shape -> its tuned plan shape
     uint64_t clock = 0;
     static constexpr size_t MAX_ENTRIES = 8;
 };
@@ -409,7 +429,7 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
     for (size_t gi = 0; gi < ng; ++gi) {
         const Group &g = p.groups[gi];
         const double ideal_g = g.work / ((double)bps[gi] * d.sm_count * p.block);
-        const double tail_g = g.tile_cost.empty() ? 0.0 : g.tile_cost[0];
+        const double tail_g = g.tile_cost.empty() ? 0.0 : *std::max_element(g.tile_cost.begin(), g.tile_cost.end());
         seq += std::max(ideal_g, tail_g);
         ideal_sum += ideal_g;
         tail_max = std::max(tail_max, tail_g);
@@ -440,7 +460,8 @@ mlmc_status enqueue(const DeviceState &d, BatchCache &c, const Plan &p, cudaStre
         uint64_t grid = full;
         if (concurrent) {
             uint64_t long_tiles = 0;
-            for (size_t k = 0; k < g.spans.size() && g.tile_cost[k] > ideal; ++k) long_tiles += g.spans[k].count;
+            for (size_t k = 0; k < g.spans.size(); ++k)
+                if (g.tile_cost[k] > ideal) long_tiles += g.spans[k].count;
             const uint64_t share = (uint64_t)ceil(g.work / p.work * (double)full);
             grid = std::min(full, std::max(share, (long_tiles + wpb - 1) / wpb));
         }
@@ -486,51 +507,53 @@ int work_lane_log2(const DeviceState &d, const mlmc_work *w, int n) {
 // Tunes a batch shape on the real batch: tile size (log2 of the fine-step
 // equivalents per lane and tile, five candidates around the work-based size
 // of about four tiles per resident lane) x block shape (256 threads, or
-// 128 -- more, smaller blocks per SM at the same register budget).  Each
-// candidate runs three times after the plan is uploaded; the median device
-// time decides (ties to the earlier candidate).  MLMC_TUNE_LOG=1 prints
-// every candidate's times and the choice on stderr.
+// 128 -- more, smaller blocks per SM at the same register budget) with the
+// spans longest first, then the best of those with the spans interleaved.
+// Each candidate runs three times after the plan is uploaded; the median
+// device time decides (ties to the earlier candidate).  MLMC_TUNE_LOG=1
+// prints every candidate's times and the choice on stderr.
 mlmc_status autotune(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed, cudaStream_t s,
-                     int *best_lw, int *best_block) {
+                     Tuning *best) {
     const int base = work_lane_log2(d, w, n);
     const int lws[] = {base - 3, base - 2, base - 1, base, base + 1};
     const int blocks[] = {256, 128};
     const bool log = env_int("MLMC_TUNE_LOG", 0) > 0;
     float best_ms = 1e30f;
-    *best_lw = base;
-    *best_block = 256;
+    *best = Tuning{base, 256, ORDER_LONGEST_FIRST};
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    mlmc_status st = MLMC_OK;
-    for (int block : blocks) {
-        for (int lw : lws) {
-            Plan p = make_plan(d, w, n, seed, lw, block);
-            if ((st = upload(c, p, s))) break;
-            float t[3];
-            for (int rep = 0; rep < 3 && !st; ++rep) {
-                cudaEventRecord(a, s);
-                if ((st = enqueue(d, c, p, s, false, true))) break;
-                cudaEventRecord(b, s);
-                if ((st = wait_event(b, wait_limit_s()))) break;
-                cudaEventElapsedTime(&t[rep], a, b);
-            }
-            if (st) break;
-            std::sort(t, t + 3);
-            if (log)
-                fprintf(stderr, "{\"mlmc_tune\": {\"items\": %d, \"lane_work_log2\": %d, \"block\": %d, "
-                                "\"ms\": [%.4f, %.4f, %.4f]}}\n", n, lw, block, t[0], t[1], t[2]);
-            if (t[1] < best_ms) {
-                best_ms = t[1];
-                *best_lw = lw;
-                *best_block = block;
-            }
+    auto trial = [&](const Tuning &tu) -> mlmc_status {
+        Plan p = make_plan(d, w, n, seed, tu.lw, tu.block, tu.order);
+        mlmc_status st = upload(c, p, s);
+        if (st) return st;
+        float t[3];
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(a, s);
+            if ((st = enqueue(d, c, p, s, false, true))) return st;
+            cudaEventRecord(b, s);
+            if ((st = wait_event(b, wait_limit_s()))) return st;
+            cudaEventElapsedTime(&t[rep], a, b);
         }
-        if (st) break;
-    }
+        std::sort(t, t + 3);
+        if (log)
+            fprintf(stderr, "{\"mlmc_tune\": {\"items\": %d, \"lane_work_log2\": %d, \"block\": %d, "
+                            "\"order\": %d, \"ms\": [%.4f, %.4f, %.4f]}}\n", n, tu.lw, tu.block, tu.order, t[0], t[1],
+                    t[2]);
+        if (t[1] < best_ms) {
+            best_ms = t[1];
+            *best = tu;
+        }
+        return MLMC_OK;
+    };
+    mlmc_status st = MLMC_OK;
+    for (int block : blocks)
+        for (int lw : lws)
+            if (!st) st = trial(Tuning{lw, block, ORDER_LONGEST_FIRST});
+    if (!st) st = trial(Tuning{best->lw, best->block, ORDER_INTERLEAVED});
     if (log && !st)
         fprintf(stderr, "{\"mlmc_tune_choice\": {\"items\": %d, \"lane_work_log2\": %d, \"block\": %d, "
-                        "\"median_ms\": %.4f}}\n", n, *best_lw, *best_block, best_ms);
+                        "\"order\": %d, \"median_ms\": %.4f}}\n", n, best->lw, best->block, best->order, best_ms);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     return st;
@@ -663,20 +686,22 @@ mlmc_status build_entry(DeviceState &d, BatchGraphs &G, BatchCache &c, const mlm
     cudaEventRecord(ev, s);
     cudaStreamWaitEvent(G.capture_stream, ev, 0);
     cudaEventDestroy(ev);
-    int lw = env_int("MLMC_BATCH_LANE_WORK_LOG2", 0), block = 256;
-    if (lw < 6 || lw > 20) {
+    // MLMC_BATCH_LANE_WORK_LOG2 (6..20) forces the tile size, with 256-thread
+    // blocks and MLMC_BATCH_ORDER's span order (default longest first)
+    Tuning tu{env_int("MLMC_BATCH_LANE_WORK_LOG2", 0), 256,
+              env_int("MLMC_BATCH_ORDER", 0) == ORDER_INTERLEAVED ? ORDER_INTERLEAVED : ORDER_LONGEST_FIRST};
+    if (tu.lw < 6 || tu.lw > 20) {
         auto it = G.tuned.find(shape_hash);
         if (it != G.tuned.end()) {
-            lw = it->second.first;
-            block = it->second.second;
+            tu = it->second;
         } else if (env_int("MLMC_AUTOTUNE", 1)) {
-            if ((st = autotune(d, c, items, n_items, seed, G.capture_stream, &lw, &block))) return st;
-            G.tuned[shape_hash] = std::make_pair(lw, block);
+            if ((st = autotune(d, c, items, n_items, seed, G.capture_stream, &tu))) return st;
+            G.tuned[shape_hash] = tu;
         } else {
-            lw = 12;
+            tu = Tuning{12, 256, ORDER_LONGEST_FIRST};
         }
     }
-    Plan p = make_plan(d, items, n_items, seed, lw, block);
+    Plan p = make_plan(d, items, n_items, seed, tu.lw, tu.block, tu.order);
     if ((st = upload(c, p, G.capture_stream))) return st;
     // the graph is launched on the caller's stream: the descriptors must have landed
     if ((e = cudaStreamSynchronize(G.capture_stream)) != cudaSuccess) return cuda_fail(e, "upload");

@@ -228,19 +228,23 @@ def test_bench_step_batches_match_level_kernels(kind):
         _same(M.mlmc_sums(s1, s2, it.N, 0.0), ref)
 
 
-@pytest.mark.parametrize("lw", [6, 9, 12])
-def test_batch_sums_do_not_depend_on_the_tile_size(lw, monkeypatch):
-    """Tiles of any size cover whole chunk groups, so the sums are those of
-    the level entry points whatever tile size the tuner picks: here three
-    forced sizes, levels 0..7 with N giving one and several chunk groups,
-    ragged last groups and a two-stage finalize (> 8192 group partials)."""
+@pytest.mark.parametrize("lw,order", [(6, 0), (9, 1), (12, 0), (12, 1)])
+def test_batch_sums_do_not_depend_on_the_tile_size(lw, order, monkeypatch):
+    """Tiles of any size cover whole chunk groups, and an item's partials do
+    not depend on which warp takes its tiles when, so the sums are those of
+    the level entry points whatever tile size and span order (longest first,
+    or interleaved) the tuner picks: here three forced sizes and both
+    orders, levels 0..7 with N giving one and several chunk groups, ragged
+    last groups and a two-stage finalize (> 8192 group partials)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     monkeypatch.setenv("MLMC_BATCH_LANE_WORK_LOG2", str(lw))
+    monkeypatch.setenv("MLMC_BATCH_ORDER", str(order))
     p = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
-    Ns = [(1 << 22) + 37 * lw, 600001 + lw, 33 + lw, 1 << 19, 99999, 12345 + lw, 1 << 20, 777 + lw]
+    v = lw + 100 * order
+    Ns = [(1 << 22) + 37 * v, 600001 + v, 33 + v, 1 << 19, 99999, 12345 + v, 1 << 20, 777 + v]
     items = []
-    for l, N in enumerate(Ns):          # N differs per lw: a new shape, so a new graph at this tile size
+    for l, N in enumerate(Ns):          # N differs per case: a new shape, so a new graph at this tile size
         items.append(M.mlmc_work(p, l, 0, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 0, N, 3))
         items.append(M.mlmc_work(p, l, 1, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE, 0, N, 3))
     got = M.mlmc_batch(items, SEED)
