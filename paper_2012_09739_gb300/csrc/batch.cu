@@ -615,6 +615,8 @@ bool small_round(const DeviceState &d, BatchCache &c, const Plan &p, cudaStream_
     const int wpb = SUM_THREADS / 32;
     const uint64_t full = (uint64_t)blocks_per_sm(c, fn, SUM_THREADS) * d.sm_count;
     const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(full, ((uint64_t)g.ntiles + wpb - 1) / wpb));
+    r.tail = grid * wpb < (uint64_t)g.ntiles;
+    for (size_t i = 0; i < n; ++i) r.tail |= r.count[i] > (uint32_t)FINALIZE_THREADS;
     fn<<<(unsigned)grid, SUM_THREADS, 0, s>>>(r, c.small_counters, c.partials, c.sums_host, d.tabs);
     if ((e = cudaGetLastError()) != cudaSuccess) *st = cuda_fail(e, "batch small-round kernel");
     return true;

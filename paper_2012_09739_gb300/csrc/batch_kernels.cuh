@@ -252,8 +252,9 @@ batch_kernel(const LevelArgs *items, const TileSpan *spans, uint32_t nspans, uin
 // its own index (no atomic).  Each item counts its finished tiles: the warp
 // that finishes an item's last tile adds the item's partials (at most 1024:
 // warp_sum_fixed, the same tree) while other warps still simulate, and
-// zeroes the item's count; the last block to finish adds the partials of
-// larger items with the whole block and zeroes the tile and block counts
+// zeroes the item's count; if an item has more partials, or the grid has
+// fewer warps than tiles (tail), the last block to finish adds the partials
+// of larger items with the whole block and zeroes the tile and block counts
 // for the next round on the stream.  One launch per round instead of a
 // copy and two launches.
 //
@@ -267,8 +268,21 @@ struct SmallRound {
     uint32_t first[SMALL_ITEMS];   // per item: its first group partial
     uint32_t count[SMALL_ITEMS];   // and how many (at most FINALIZE_SPAN)
     uint32_t nitems, nspans, ntiles;
+    uint32_t tail;                 // 1: an item above 1024 partials, or more tiles than warps
     PhiloxKeys keys;
 };
+
+// atomicAdd with acquire-release semantics at GPU scope: the calling
+// thread's earlier writes are visible to whoever acquires this location
+// later, and whatever the earlier writers to it released is visible to the
+// caller.  In place of __threadfence() (a sequentially consistent fence)
+// and a relaxed atomicAdd: the release covers only the caller's own writes,
+// which is all a count of one warp's tile needs.
+__device__ __forceinline__ uint32_t atomic_add_acq_rel(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 
 // A latency-sized round fills a fraction of one wave, so the kernel takes a
 // register budget of two blocks per SM instead of the occupancy the bulk
@@ -284,27 +298,32 @@ batch_small_kernel(const __grid_constant__ SmallRound r, uint32_t *counters, dou
     stage_table(tab, tabs);
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31;
-    // lane 0 wrote the tile's partials: fenced before they are counted, so
-    // the warp that counts an item's last tile sees all of the item's
+    // lane 0 wrote the tile's partials and counts the tile with release
+    // semantics; the count that completes the item also acquires the other
+    // tiles' partials, and __syncwarp passes them on to the whole warp,
+    // which reads them from L2 (warp_sum_fixed)
     auto item_done = [&](const TileSpan &sp) {
         uint32_t done = 0;
         if (lane == 0) {
-            __threadfence();
-            done = atomicAdd(counters + 2 + sp.item, 1u) == sp.count - 1;
+            done = atomic_add_acq_rel(counters + 2 + sp.item, 1u) == sp.count - 1;
             if (done) counters[2 + sp.item] = 0u;
         }
         if (!__shfl_sync(0xffffffffu, done, 0) || r.count[sp.item] > (uint32_t)FINALIZE_THREADS) return;
-        __threadfence();
+        __syncwarp();
         const double2 v = warp_sum_fixed(partials + r.first[sp.item], r.count[sp.item], lane);
         if (lane == 0) sums[sp.item] = v;
     };
     tile_loop<true, MODE, P, KAHAN, ICDF, SDE>(r.items, r.spans, r.nspans, r.ntiles, counters, partials, tab, r.keys,
                                          seq[threadIdx.x >> 5], item_done);
-    __syncthreads();            // every warp's partials are fenced (item_done)
-    if (threadIdx.x == 0) last = atomicAdd(counters + 1, 1u) == gridDim.x - 1;
+    // without larger items or a shared tile counter to reset, the items'
+    // warps have finished the round
+    if (!r.tail) return;
+    // the block's partials were released by its warps (item_done) before
+    // this barrier; thread 0's count releases them again for the last block
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomic_add_acq_rel(counters + 1, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return;
-    __threadfence();            // every block's partials are visible from here on
     for (uint32_t i = 0; i < r.nitems; ++i) {
         if (r.count[i] <= (uint32_t)FINALIZE_THREADS) continue;
         const double2 v = block_sum_fixed(partials + r.first[i], r.count[i], r1, r2);

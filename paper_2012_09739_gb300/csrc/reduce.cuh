@@ -29,7 +29,7 @@ __device__ __forceinline__ double2 block_sum_fixed(const double2 *p, uint64_t n,
         for (int k = 0; k < 4; ++k) {
             const uint64_t i = base + t + SUM_THREADS * k;
             if (i < n) {
-                const double2 v = p[i];
+                const double2 v = __ldcg(p + i);      // from L2: other SMs wrote them
                 x[k] += v.x;
                 y[k] += v.y;
             }
@@ -81,7 +81,11 @@ __device__ __forceinline__ double2 strided_tree(const double2 *p, uint32_t n, ui
         }
         return s;
     } else {
+        // a subtree of empty slots sums to +0.0 exactly, and no sum here is
+        // -0.0 (each slot is 0.0 plus its partial), so adding it changes
+        // nothing: skipped (binary64 additions are slow on this GPU)
         const double2 a = strided_tree<J, 2 * H>(p, n, lane);
+        if (lane + 32u * (J + H) >= n) return a;
         const double2 b = strided_tree<J + H, 2 * H>(p, n, lane);
         return make_double2(a.x + b.x, a.y + b.y);
     }
