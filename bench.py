@@ -689,6 +689,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batching leg")
     ap.add_argument("--no-mlp", action="store_true", help="skip the MLP leg")
     ap.add_argument("--mlp-only", action="store_true", help="run only the MLP leg (profiling)")
+    ap.add_argument("--tte-only", action="store_true", help="run only the time-to-eps leg at --eps (profiling)")
     ap.add_argument("--mlp-steps", type=int, default=20000)
     ap.add_argument("--eps", type=float, default=1e-3)
     ap.add_argument("--levels", type=str, default=None, help="comma-separated levels (profiling runs)")
@@ -708,6 +709,11 @@ def main():
         params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
         print(json.dumps(mlp_leg(M, torch, params, steps=args.mlp_steps, level=LEVELS[-1], n=N_PER_LEVEL,
                                  workload=args.n is None)))
+    elif args.tte_only:
+        # profiling mode: the adaptive runs of the time-to-eps leg at one RMSE
+        import paper_2012_09739_gb300 as M
+        params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0)
+        print(json.dumps(time_to_eps(M, params, [args.eps])))
     else:
         run_gpu(args)
 

@@ -627,11 +627,13 @@ bool small_round(const DeviceState &d, BatchCache &c, const Plan &p, cudaStream_
 // c.sums_host, enqueued on s.  The caller waits on s before reading.
 // The tile size follows the round's total work: about sixteen tiles per
 // resident lane (every round has a new shape, so nothing is tuned), each at
-// least 16 steps long per lane; the dynamic schedule then leaves a last wave
-// of at most a sixteenth of a group's time.
+// least 4 steps long per lane; the dynamic schedule then leaves a last wave
+// of at most a sixteenth of a group's time.  A latency-sized round, which
+// fills a fraction of the GPU, gets the shortest tiles (a pair or two per
+// lane): its time is its longest tile's.
 mlmc_status batch_round(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed,
                         cudaStream_t s) {
-    Plan p = make_plan(d, w, n, seed, std::max(4, work_lane_log2(d, w, n) - 2));
+    Plan p = make_plan(d, w, n, seed, std::max(2, work_lane_log2(d, w, n) - 2));
     mlmc_status st = MLMC_OK;
     if (small_round(d, c, p, s, &st)) return st;
     // the driver waits for every round before it plans the next one
