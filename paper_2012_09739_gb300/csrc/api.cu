@@ -138,6 +138,8 @@ LevelArgs make_level_args(const DeviceState &d, int four, int l, uint64_t N, int
     a.payoff = p->payoff;
     a.mode = four ? MODE_FOUR : MODE_TWO;
     a.sde = kernel_sde(p);
+    a.prec = prec;
+    a.icdf = icdf;
     a.N = N;
     a.unit = unit_pairs(a.mode, icdf, l);
     a.npairs = (N + 2 * a.unit - 1) / (2 * a.unit);

@@ -29,6 +29,7 @@ BatchKernelFn batch_kernel_bf16_four(int kahan, int icdf, int sde);
 BatchKernelFn batch_kernel_mixed(int prec, int kahan, int icdf, int sde);
 BatchSmallFn batch_small_mixed(int prec, int kahan, int icdf, int sde);
 BatchSmallFn batch_small_two(int prec, int kahan, int icdf, int sde);
+BatchSmallFn batch_small_choice(int icdf, int sde);
 
 // The batch finalize adds an item's group partials exactly as the level
 // finalize does (block_sum_fixed over at most FINALIZE_SPAN partials, or one
@@ -114,28 +115,62 @@ enum { ORDER_LONGEST_FIRST = 0, ORDER_INTERLEAVED = 1 };
 // host work is per item, not per tile.  Each item owns one partial per chunk
 // group and, above FINALIZE_SPAN of them, scratch for the finalize's span sums.
 Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, int lane_work_log2,
-               int block = 256, int span_order = ORDER_LONGEST_FIRST) {
+               int block = 256, int span_order = ORDER_LONGEST_FIRST, bool choice = false) {
     Plan plan;
     plan.block = block;
     plan.items.resize(n);
     plan.fin.assign(3 * (size_t)n, 0);
     for (int i = 0; i < n; ++i) plan.work += item_work(w[i]);
-    // a latency-sized batch puts both estimators' items of one variant into
-    // one launch where a mixed kernel exists (MLMC_BATCH_MIXED=0 disables it)
-    const bool mixed = plan.work < SMALL_BATCH_WORK && env_int("MLMC_BATCH_MIXED", 1) != 0;
     for (int i = 0; i < n; ++i) {
         plan.items[i] = make_level_args(d, w[i].kind, w[i].l, w[i].N, w[i].prec, w[i].icdf, &w[i].params, seed,
                                         w[i].path_offset, (uint32_t)w[i].set_id);
+        plan.items[i].kahan = w[i].kahan ? 1 : 0;
+    }
+    // a latency-sized batch puts both estimators' items of one variant into
+    // one launch where a mixed kernel exists (MLMC_BATCH_MIXED=0 disables it)
+    const bool mixed = plan.work < SMALL_BATCH_WORK && env_int("MLMC_BATCH_MIXED", 1) != 0;
+    // and (choice: an adaptive round) the items of several variants, or of
+    // one without a mixed kernel, where all are candidates of the per-level
+    // choice (binary16 with or without Kahan, or binary32, with one table
+    // inverse CDF; or the standard binary32 exact-normal two-way term), into
+    // one launch of the fused choice kernel
+    int choice_icdf = -1;
+    bool use_choice = choice && mixed && n <= SMALL_ITEMS && env_int("MLMC_ROUND_FUSED", 1) != 0;
+    bool several = false;
+    const int choice_sde = n > 0 ? plan.items[0].sde : SDE_GBM;
+    for (int i = 0; i < n && use_choice; ++i) {
+        const mlmc_work &x = w[i];
+        if (plan.items[i].sde != choice_sde) {
+            use_choice = false;
+        } else if (x.icdf == MLMC_ICDF_EXACT) {
+            use_choice = x.kind == 0 && x.prec == MLMC_F32 && x.kahan;
+        } else if (choice_icdf >= 0 && x.icdf != choice_icdf) {
+            use_choice = false;
+        } else {
+            choice_icdf = x.icdf;
+            use_choice = x.prec == MLMC_F16 || (x.prec == MLMC_F32 && !x.kahan);
+        }
+        several |= x.prec != w[0].prec || (x.kahan != 0) != (w[0].kahan != 0) || x.icdf != w[0].icdf;
+    }
+    // (one variant: where no mixed kernel takes both estimators' items)
+    if (use_choice && !several) use_choice = !batch_kernel_mixed(w[0].prec, w[0].kahan ? 1 : 0, w[0].icdf, choice_sde);
+    use_choice = use_choice && choice_icdf >= 0 && batch_small_choice(choice_icdf, choice_sde) != nullptr;
+    for (int i = 0; i < n; ++i) {
         plan.weight.push_back(plan.work > 0 ? item_work(w[i]) / plan.work : 0.0);
-        const int kahan = w[i].kahan ? 1 : 0, sde = plan.items[i].sde;
-        const int mode = mixed && batch_kernel_mixed(w[i].prec, kahan, w[i].icdf, sde) ? (int)MODE_MIXED : w[i].kind;
+        int kahan = w[i].kahan ? 1 : 0, sde = plan.items[i].sde, prec = w[i].prec, icdf = w[i].icdf;
+        int mode = mixed && batch_kernel_mixed(prec, kahan, icdf, sde) ? (int)MODE_MIXED : w[i].kind;
+        if (use_choice) {
+            mode = MODE_CHOICE;
+            prec = kahan = -1;
+            icdf = choice_icdf;
+        }
         size_t gi = 0;
         while (gi < plan.groups.size()) {
             const Group &g = plan.groups[gi];
-            if (g.mode == mode && g.prec == w[i].prec && g.kahan == kahan && g.icdf == w[i].icdf && g.sde == sde) break;
+            if (g.mode == mode && g.prec == prec && g.kahan == kahan && g.icdf == icdf && g.sde == sde) break;
             ++gi;
         }
-        if (gi == plan.groups.size()) plan.groups.push_back(Group{mode, w[i].prec, kahan, w[i].icdf, sde});
+        if (gi == plan.groups.size()) plan.groups.push_back(Group{mode, prec, kahan, icdf, sde});
         Group &g = plan.groups[gi];
         // lane slots: pairs, or units of pairs at the coarsest two-way levels
         const uint64_t np = plan.items[i].npairs, nchunks = (np + 31) / 32;
@@ -198,10 +233,14 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
         if (begin > 0xFFFFFFFFull) plan.too_large = true;
     }
     plan.nspans = span_base;
+    // the choice kernel runs only as one fused launch (small_round)
+    if (use_choice && (!plan.jobs.empty() || plan.too_large || block != SUM_THREADS))
+        return make_plan(d, w, n, seed, lane_work_log2, block, span_order, false);
     return plan;
 }
 
 BatchKernelFn pick_batch_kernel(const Group &g) {
+    if (g.mode == MODE_CHOICE) return nullptr;      // fused launches only
     if (g.mode == MODE_MIXED) return batch_kernel_mixed(g.prec, g.kahan, g.icdf, g.sde);
     if (g.mode == MODE_TWO)
         return g.prec == MLMC_F32   ? batch_kernel_f32_two(g.kahan, g.icdf, g.sde)
@@ -572,7 +611,8 @@ bool small_round(const DeviceState &d, BatchCache &c, const Plan &p, cudaStream_
         p.block != SUM_THREADS || p.work >= SMALL_BATCH_WORK || env_int("MLMC_ROUND_FUSED", 1) == 0)
         return false;
     const Group &g = p.groups[0];
-    const BatchSmallFn fn = g.mode == MODE_MIXED ? batch_small_mixed(g.prec, g.kahan, g.icdf, g.sde)
+    const BatchSmallFn fn = g.mode == MODE_CHOICE ? batch_small_choice(g.icdf, g.sde)
+                            : g.mode == MODE_MIXED ? batch_small_mixed(g.prec, g.kahan, g.icdf, g.sde)
                             : g.mode == MODE_TWO ? batch_small_two(g.prec, g.kahan, g.icdf, g.sde)
                                                  : nullptr;
     if (!fn) return false;
@@ -633,7 +673,8 @@ bool small_round(const DeviceState &d, BatchCache &c, const Plan &p, cudaStream_
 // lane): its time is its longest tile's.
 mlmc_status batch_round(const DeviceState &d, BatchCache &c, const mlmc_work *w, int n, uint64_t seed,
                         cudaStream_t s) {
-    Plan p = make_plan(d, w, n, seed, std::max(2, work_lane_log2(d, w, n) - 2));
+    Plan p = make_plan(d, w, n, seed, std::max(2, work_lane_log2(d, w, n) - 2), SUM_THREADS, ORDER_LONGEST_FIRST,
+                       true);
     mlmc_status st = MLMC_OK;
     if (small_round(d, c, p, s, &st)) return st;
     // the driver waits for every round before it plans the next one

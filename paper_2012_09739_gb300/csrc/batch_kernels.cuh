@@ -17,6 +17,8 @@
 // the tile size.  No warp ever waits on another warp or block.
 #pragma once
 
+#include <type_traits>
+
 #include "level_kernels.cuh"
 #include "reduce.cuh"
 
@@ -180,6 +182,23 @@ __device__ __forceinline__ void run_tile(const LevelArgs &a, const PhiloxKeys &k
 // run at.  Accumulation as in the single-mode kernels, so sums are the same.
 enum { MODE_MIXED = 2 };
 
+// MODE_CHOICE: a candidate round of the adaptive driver's per-level choice of
+// working precision -- the two-way and four-way items of binary16 with and
+// without Kahan and binary32 with one table inverse CDF, and the standard
+// binary32 exact-normal two-way term -- in one launch, each tile dispatched
+// on its item's variant (LevelArgs prec, kahan, icdf).  Accumulation as in
+// the single-variant kernels, so the sums are the same.
+enum { MODE_CHOICE = 3 };
+
+// Scratch of the warp-cooperative single pairs for either working precision.
+union ChoiceScratch {
+    SeqScratch<P_F32> f32;
+    SeqScratch<P_F16> f16;
+};
+
+template <int MODE, int P>
+using TileScratch = std::conditional_t<MODE == MODE_CHOICE, ChoiceScratch, SeqScratch<P>>;
+
 // The tile loop of a persistent batch kernel: each warp takes the next tile
 // index from the counter until the tiles run out; or (STATIC) warp w of W
 // first takes tile w and then W + the counter's next value, so that a
@@ -189,7 +208,7 @@ enum { MODE_MIXED = 2 };
 template <bool STATIC, int MODE, int P, bool KAHAN, int ICDF, int SDE, class After>
 __device__ __forceinline__ void tile_loop(const LevelArgs *items, const TileSpan *spans, uint32_t nspans,
                                           uint32_t ntiles, uint32_t *counter, double2 *partials,
-                                          const SmemTable &tab, const PhiloxKeys &keys, SeqScratch<P> &seq,
+                                          const SmemTable &tab, const PhiloxKeys &keys, TileScratch<MODE, P> &seq,
                                           After after) {
     const float *mlp = ICDF == ICDF_MLP ? items[0].mlp->ygrid : nullptr;
     const uint32_t lane = threadIdx.x & 31;
@@ -198,7 +217,24 @@ __device__ __forceinline__ void tile_loop(const LevelArgs *items, const TileSpan
         // every item has the batch's seed: its round keys come from the
         // launch parameters
         const LevelArgs a = items[sp.item];
-        if constexpr (MODE == MODE_MIXED) {
+        if constexpr (MODE == MODE_CHOICE) {
+            auto either = [&](auto p, auto kahan, auto &sc) {
+                constexpr int PP = decltype(p)::value;
+                constexpr bool KK = decltype(kahan)::value;
+                if (a.mode == MODE_FOUR)
+                    run_tile<MODE_FOUR, PP, KK, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, sc);
+                else
+                    run_tile<MODE_TWO, PP, KK, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, sc);
+            };
+            if (a.icdf == ICDF_EXACT)
+                run_tile<MODE_TWO, P_F32, true, ICDF_EXACT, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq.f32);
+            else if (a.prec == P_F32)
+                either(std::integral_constant<int, P_F32>(), std::false_type(), seq.f32);
+            else if (a.kahan)
+                either(std::integral_constant<int, P_F16>(), std::true_type(), seq.f16);
+            else
+                either(std::integral_constant<int, P_F16>(), std::false_type(), seq.f16);
+        } else if constexpr (MODE == MODE_MIXED) {
             if (a.mode == MODE_FOUR)
                 run_tile<MODE_FOUR, P, KAHAN, ICDF, SDE>(a, keys, tab, mlp, sp, t, lane, partials, seq);
             else
@@ -292,7 +328,7 @@ __global__ void __launch_bounds__(256, 2)
 batch_small_kernel(const __grid_constant__ SmallRound r, uint32_t *counters, double2 *partials, double2 *sums,
                    const DevTables *tabs) {
     __shared__ SmemTable tab;
-    __shared__ SeqScratch<P> seq[8];
+    __shared__ TileScratch<MODE, P> seq[8];
     __shared__ double r1[SUM_THREADS], r2[SUM_THREADS];
     __shared__ uint32_t last;
     stage_table(tab, tabs);

@@ -26,6 +26,7 @@ struct LevelArgs {
     int l;                    // level: 2^l fine steps
     int payoff;
     int mode, sde;            // MODE_*, SDE_* (read by the batched kernel)
+    int prec, kahan, icdf;    // working precision (P_*), Kahan flag, ICDF_* (read by the choice kernel)
     uint64_t npairs;          // lane slots: ceil(N / 2) pairs, or ceil(N / (2 unit)) units
     int unit;                 // pairs per slot: 1, or 2 / 4 at the coarsest levels (unit_pairs)
     uint64_t N;

@@ -174,11 +174,18 @@ def test_mlmc_run_decisions_replayed_by_the_oracle_driver(eps, est, prec, kahan,
     (0, M.MLMC_F32, 1, M.MLMC_ICDF_EXACT, M.MLMC_MILSTEIN),
     (1, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE16, M.MLMC_EULER),
     (1, M.MLMC_F32, 0, M.MLMC_ICDF_TABLE, M.MLMC_EULER),
+    (1, -1, 0, M.MLMC_ICDF_TABLE16, M.MLMC_EULER),
+    (1, -1, 0, M.MLMC_ICDF_TABLE, M.MLMC_EULER),
+    (1, -1, 0, M.MLMC_ICDF_TABLE16, M.MLMC_MILSTEIN),
+    (1, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE16, M.MLMC_MILSTEIN),
 ])
 def test_fused_small_rounds_give_the_same_runs(monkeypatch, est, prec, kahan, icdf, scheme):
     """Latency-sized rounds of one kernel group run as one fused launch
     (descriptors as kernel parameters, each item's sum by the warp that
-    finishes its last tile, larger items' by the last block); the same
+    finishes its last tile, larger items' by the last block), and so do the
+    per-level choice's rounds of several variants (prec -1: the choice
+    kernel, each tile dispatched on its item's variant) and the rounds of
+    one variant without a mixed kernel (Milstein); the same
     runs with the two-kernel path (MLMC_ROUND_FUSED=0) must take the same
     draws and get the same sums, bit for bit, at an RMSE where every round
     is small (1e-3) and where the later ones are not (1e-4)."""
