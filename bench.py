@@ -57,10 +57,11 @@ OPS_TWOWAY_F16K_TABLE = 22.65
 # DRAM bytes (read + write) of the timed four-way batched launch over levels
 # 0..12 at N = 2^20, from an ncu capture of the bench command
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass): the descriptors
-# and the tables, 0.17 to 0.67 MB over the 33 launches captured (the tuner's
-# candidates, the replays), no writes (the group partials stay in L2).  The
-# traffic does not grow with the path-steps.
-TRAFFIC_FOURWAY_BYTES = 167680
+# and the tables, 0.07 to 0.74 MB read over the 36 launches captured (the
+# tuner's candidates, the replays; ncu starts each from cold caches), 2 KB
+# written (the group partials stay in L2).  The traffic does not grow with
+# the path-steps.
+TRAFFIC_FOURWAY_BYTES = 614656
 # Pipe utilisation of the same kernel from the committed ncu capture (the
 # small case of the batch-kernel profile: levels 0..12, N = 2^18, full
 # section set), of peak over active cycles; the non-tensor pipes bound it.
