@@ -208,12 +208,12 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
         std::stable_sort(order.begin(), order.end(),
                          [&](uint32_t a, uint32_t b) { return g.tile_cost[a] > g.tile_cost[b]; });
         if (span_order == ORDER_INTERLEAVED) {
-            std::vector<uint32_t> mixed;
+            std::vector<uint32_t> both_ends;
             for (size_t lo = 0, hi = order.size(); lo < hi;) {
-                mixed.push_back(order[lo++]);
-                if (lo < hi) mixed.push_back(order[--hi]);
+                both_ends.push_back(order[lo++]);
+                if (lo < hi) both_ends.push_back(order[--hi]);
             }
-            order.swap(mixed);
+            order.swap(both_ends);
         }
         std::vector<TileSpan> spans;
         std::vector<double> cost;

@@ -4,9 +4,10 @@
 // Every item is cut into warp tiles (a contiguous range of sample pairs; one
 // pair per lane per round) of one size per item: a span of consecutive tile
 // indices.  The host orders the spans by tile length (longest first, or
-// interleaved long and short); it never lists the tiles.  Each warp of a grid of resident blocks repeatedly
-// takes the next tile index from an atomic counter, finds its span and
-// simulates the tile with the same per-pair code as the level kernels.
+// interleaved long and short); it never lists the tiles.  Each warp of a
+// grid of resident blocks repeatedly takes the next tile index from an
+// atomic counter, finds its span and simulates the tile with the same
+// per-pair code as the level kernels.
 //
 // A tile covers whole chunk groups of the level kernel (32 pairs per chunk,
 // chunk_group(l, chunks) chunks per group) and accumulates exactly as the
