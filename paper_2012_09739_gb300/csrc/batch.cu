@@ -131,9 +131,9 @@ Plan make_plan(const DeviceState &d, const mlmc_work *w, int n, uint64_t seed, i
     const bool mixed = plan.work < SMALL_BATCH_WORK && env_int("MLMC_BATCH_MIXED", 1) != 0;
     // and (choice: an adaptive round) the items of several variants, or of
     // one without a mixed kernel, where all are candidates of the per-level
-    // choice (binary16 with or without Kahan, or binary32, with one table
-    // inverse CDF; or the standard binary32 exact-normal two-way term), into
-    // one launch of the fused choice kernel
+    // choice (binary16 with or without Kahan, or binary32, with one
+    // approximate inverse CDF; or the standard binary32 exact-normal two-way
+    // term), into one launch of the fused choice kernel
     int choice_icdf = -1;
     bool use_choice = choice && mixed && n <= SMALL_ITEMS && env_int("MLMC_ROUND_FUSED", 1) != 0;
     bool several = false;

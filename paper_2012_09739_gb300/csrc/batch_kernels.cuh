@@ -185,7 +185,7 @@ enum { MODE_MIXED = 2 };
 
 // MODE_CHOICE: a candidate round of the adaptive driver's per-level choice of
 // working precision -- the two-way and four-way items of binary16 with and
-// without Kahan and binary32 with one table inverse CDF, and the standard
+// without Kahan and binary32 with one approximate inverse CDF, and the standard
 // binary32 exact-normal two-way term -- in one launch, each tile dispatched
 // on its item's variant (LevelArgs prec, kahan, icdf).  Accumulation as in
 // the single-variant kernels, so the sums are the same.

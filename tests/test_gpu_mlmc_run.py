@@ -178,6 +178,7 @@ def test_mlmc_run_decisions_replayed_by_the_oracle_driver(eps, est, prec, kahan,
     (1, -1, 0, M.MLMC_ICDF_TABLE, M.MLMC_EULER),
     (1, -1, 0, M.MLMC_ICDF_TABLE16, M.MLMC_MILSTEIN),
     (1, M.MLMC_F16, 1, M.MLMC_ICDF_TABLE16, M.MLMC_MILSTEIN),
+    (1, M.MLMC_F16, 1, M.MLMC_ICDF_MLP, M.MLMC_EULER),
 ])
 def test_fused_small_rounds_give_the_same_runs(monkeypatch, est, prec, kahan, icdf, scheme):
     """Latency-sized rounds of one kernel group run as one fused launch
@@ -185,12 +186,15 @@ def test_fused_small_rounds_give_the_same_runs(monkeypatch, est, prec, kahan, ic
     finishes its last tile, larger items' by the last block), and so do the
     per-level choice's rounds of several variants (prec -1: the choice
     kernel, each tile dispatched on its item's variant) and the rounds of
-    one variant without a mixed kernel (Milstein); the same
+    one variant without a mixed kernel (Milstein, the network); the same
     runs with the two-kernel path (MLMC_ROUND_FUSED=0) must take the same
     draws and get the same sums, bit for bit, at an RMSE where every round
     is small (1e-3) and where the later ones are not (1e-4)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    if icdf == M.MLMC_ICDF_MLP:
+        from workloads import mlp_initial_weights
+        M.mlmc_mlp_set_weights(mlp_initial_weights(5))
     params = M.sde_params(sde=M.MLMC_GBM, payoff=M.MLMC_PAYOFF_CALL, p0=0.05, p1=0.2, K=1.0, scheme=scheme)
     for eps in (1e-3, 1e-4):
         runs = []
