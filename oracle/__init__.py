@@ -3,8 +3,8 @@ approximate random variables (Giles & Sheridan-Methven, arXiv 2012.09739).
 
 TEST INFRASTRUCTURE ONLY.  This package is a plain, slow FP64 CPU
 restatement of the method used to check the CUDA library.  Only the tests,
-``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
-import it.  It imports nothing from the CUDA package and the CUDA package
+``__graft_entry__.smoke()`` and the CPU-baseline and reference legs of
+``bench.py`` may import it.  It imports nothing from the CUDA package and the CUDA package
 imports nothing from it.
 
 Modules:
